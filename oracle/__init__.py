@@ -1,0 +1,250 @@
+"""CPU oracle for raycast-RMP evaluation -- TEST INFRASTRUCTURE.
+
+A ctypes wrapper around ``rmp_oracle.c``, the plain single-threaded C statement of the
+method (Sec. III of arXiv 2301.08068).  Only the test suite, ``__graft_entry__.smoke()``
+and the benchmark's CPU-baseline / reference legs may import this package; the library
+in ``paper_2301_08068_gb300`` never does, and the two share no code.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rmp_oracle.c")
+_SO = os.path.join(_HERE, "librmp_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+HIT, MISS_RANGE, MISS_EXIT = 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/librmp_oracle.so (gcc, -O2, no FP contraction)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "rmp_oracle.h"))):
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class Params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("eta_rep", "nu_rep", "eta_damp", "nu_damp", "r", "c",
+                                          "eps", "max_range", "min_range")] + \
+               [("halton_offset", C.c_uint32), ("w_mode", C.c_uint32)]
+
+
+class Hit(C.Structure):
+    _fields_ = [("voxel", C.c_int32 * 3), ("steps", C.c_uint32), ("d", C.c_float),
+                ("status", C.c_uint8), ("pad", C.c_uint8 * 3)]
+
+
+class Result(C.Structure):
+    _fields_ = [("sumA", C.c_double * 6), ("sumAf", C.c_double * 3), ("f", C.c_double * 3),
+                ("eig", C.c_double * 3), ("n_rays", C.c_uint32), ("n_hits", C.c_uint32),
+                ("n_active", C.c_uint32), ("rank", C.c_uint32)]
+
+
+class MapT(C.Structure):
+    _fields_ = [("kind", C.c_int), ("voxel_size", C.c_double), ("origin", C.c_double * 3),
+                ("dims", C.c_int32 * 3), ("occ", C.c_void_p), ("n_blocks", C.c_uint32),
+                ("keys", C.c_void_p), ("tsdf", C.c_void_p), ("sorted", C.c_void_p)]
+
+
+HIT_DTYPE = np.dtype([("voxel", "<i4", (3,)), ("steps", "<u4"), ("d", "<f4"),
+                      ("status", "u1"), ("pad", "u1", (3,))])
+assert HIT_DTYPE.itemsize == C.sizeof(Hit) == 24
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_SO)
+            P = C.c_void_p
+            sig = {
+                "orc_halton2": (C.c_float, [C.c_uint32]),
+                "orc_halton3": (C.c_float, [C.c_uint32]),
+                "orc_halton3_numerator": (C.c_uint32, [C.c_uint32]),
+                "orc_halton_batch": (None, [C.c_uint32, C.c_uint32, P, P, P]),
+                "orc_sincos_batch": (None, [C.c_uint32, P, P, P]),
+                "orc_ray_dirs": (None, [C.c_uint32, C.c_uint32, P]),
+                "orc_quantize_dirs": (None, [C.c_uint32, P, P]),
+                "orc_quantize_pos": (C.c_int64, [C.c_double, C.c_double, C.c_double]),
+                "orc_range_fx": (C.c_int64, [C.c_double, C.c_double]),
+                "orc_map_prepare": (C.c_int, [P]),
+                "orc_map_free": (None, [P]),
+                "orc_dda_batch": (C.c_int, [P, C.c_uint32, P, P, C.c_int64, P]),
+                "orc_ray_policy": (None, [P, P, C.c_double, P, C.c_int, C.c_int, P, P]),
+                "orc_active32": (C.c_int, [P, P]),
+                "orc_pinv3": (None, [P, P, P, P]),
+                "orc_raycast_eval": (C.c_int, [P, P, P, C.c_uint32, P, P, P, P]),
+                "orc_scan_eval": (C.c_int, [P, C.c_uint32, P, P, P, P, P]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def make_params(d: dict, max_range: float) -> Params:
+    p = Params()
+    for k in ("eta_rep", "nu_rep", "eta_damp", "nu_damp", "r", "c", "eps", "min_range"):
+        setattr(p, k, float(d[k]))
+    p.max_range = float(max_range)
+    p.halton_offset = int(d.get("halton_offset", 1))
+    p.w_mode = int(d.get("w_mode", 0))
+    return p
+
+
+class OracleMap:
+    """Oracle view of a workloads.DenseMap or workloads.HashedMap (keeps arrays alive)."""
+
+    def __init__(self, m):
+        self.m = MapT()
+        self._keep = []
+        self.m.voxel_size = float(m.voxel_size)
+        if hasattr(m, "occ"):
+            occ = np.ascontiguousarray(m.occ, np.uint8)
+            self._keep.append(occ)
+            self.m.kind = 0
+            for a in range(3):
+                self.m.origin[a] = float(m.origin[a])
+                self.m.dims[a] = int(m.dims[a])
+            self.m.occ = occ.ctypes.data
+        else:
+            keys = np.ascontiguousarray(m.keys, np.int32)
+            tsdf = np.ascontiguousarray(m.tsdf, np.float32)
+            self._keep += [keys, tsdf]
+            self.m.kind = 1
+            self.m.n_blocks = keys.shape[0]
+            self.m.keys = keys.ctypes.data if keys.size else None
+            self.m.tsdf = tsdf.ctypes.data if tsdf.size else None
+        rc = lib().orc_map_prepare(C.byref(self.m))
+        if rc != 0:
+            raise ValueError("oracle map rejected (duplicate block keys?)")
+
+    @property
+    def ref(self):
+        return C.byref(self.m)
+
+    def __del__(self):
+        try:
+            lib().orc_map_free(C.byref(self.m))
+        except Exception:
+            pass
+
+
+def halton(n: int, offset: int = 1):
+    u = np.empty(n, np.float32)
+    v = np.empty(n, np.float32)
+    num = np.empty(n, np.uint32)
+    lib().orc_halton_batch(n, offset, _ptr(u), _ptr(v), _ptr(num))
+    return u, v, num
+
+
+def sincos_turns(v: np.ndarray):
+    v = np.ascontiguousarray(v, np.float32)
+    c = np.empty_like(v)
+    s = np.empty_like(v)
+    lib().orc_sincos_batch(v.size, _ptr(v), _ptr(c), _ptr(s))
+    return c, s
+
+
+def ray_dirs(n: int, offset: int = 1) -> np.ndarray:
+    out = np.empty((n, 3), np.float32)
+    lib().orc_ray_dirs(n, offset, _ptr(out))
+    return out
+
+
+def quantize_dirs(dirs: np.ndarray) -> np.ndarray:
+    dirs = np.ascontiguousarray(dirs, np.float32)
+    D = np.empty(dirs.shape, np.int32)
+    lib().orc_quantize_dirs(dirs.shape[0], _ptr(dirs), _ptr(D))
+    return D
+
+
+def quantize_pos(x, origin, vs) -> np.ndarray:
+    return np.array([lib().orc_quantize_pos(float(x[a]), float(origin[a]), float(vs))
+                     for a in range(3)], np.int64)
+
+
+def range_fx(max_range: float, vs: float) -> int:
+    return int(lib().orc_range_fx(float(max_range), float(vs)))
+
+
+def dda(omap: OracleMap, P: np.ndarray, D: np.ndarray, R_fx: int) -> np.ndarray:
+    """March rays (P (n,3) int64 fixed point, D (n,3) int32) -> hit records."""
+    P = np.ascontiguousarray(np.broadcast_to(P, D.shape), np.int64)
+    D = np.ascontiguousarray(D, np.int32)
+    out = np.zeros(D.shape[0], HIT_DTYPE)
+    lib().orc_dda_batch(omap.ref, D.shape[0], _ptr(P), _ptr(D), int(R_fx), _ptr(out))
+    return out
+
+
+def ray_policy(params: Params, r, d: float, xdot, active: bool, in_radius: bool):
+    r = np.ascontiguousarray(r, np.float64)
+    xd = np.ascontiguousarray(xdot, np.float64)
+    f = np.zeros(3)
+    A = np.zeros(6)
+    lib().orc_ray_policy(C.byref(params), _ptr(r), float(d), _ptr(xd), int(active),
+                         int(in_radius), _ptr(f), _ptr(A))
+    return f, A
+
+
+def active32(xdot, u) -> bool:
+    xd = np.ascontiguousarray(xdot, np.float64)
+    uu = np.ascontiguousarray(u, np.float32)
+    return bool(lib().orc_active32(_ptr(xd), _ptr(uu)))
+
+
+def pinv3(S6):
+    S = np.ascontiguousarray(S6, np.float64)
+    P = np.zeros(6)
+    eig = np.zeros(3)
+    rank = C.c_uint32(0)
+    lib().orc_pinv3(_ptr(S), _ptr(P), _ptr(eig), C.byref(rank))
+    return P, eig, int(rank.value)
+
+
+def _result(res: Result) -> dict:
+    return dict(sumA=np.array(res.sumA[:]), sumAf=np.array(res.sumAf[:]), f=np.array(res.f[:]),
+                eig=np.array(res.eig[:]), n_rays=res.n_rays, n_hits=res.n_hits,
+                n_active=res.n_active, rank=res.rank)
+
+
+def raycast_eval(omap: OracleMap, x, xdot, n_rays: int, params: Params,
+                 want_hits: bool = True, want_per_ray: bool = True):
+    x = np.ascontiguousarray(x, np.float64)
+    xd = np.ascontiguousarray(xdot, np.float64)
+    res = Result()
+    hits = np.zeros(n_rays, HIT_DTYPE) if want_hits else None
+    per = np.zeros((n_rays, 9)) if want_per_ray else None
+    lib().orc_raycast_eval(omap.ref, _ptr(x), _ptr(xd), int(n_rays), C.byref(params),
+                           C.byref(res), _ptr(hits) if want_hits else None,
+                           _ptr(per) if want_per_ray else None)
+    return _result(res), hits, per
+
+
+def scan_eval(points: np.ndarray, x, xdot, params: Params, want_per_ray: bool = True):
+    pts = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+    x = np.ascontiguousarray(x, np.float64)
+    xd = np.ascontiguousarray(xdot, np.float64)
+    res = Result()
+    per = np.zeros((pts.shape[0], 9)) if want_per_ray else None
+    lib().orc_scan_eval(_ptr(pts), pts.shape[0], _ptr(x), _ptr(xd), C.byref(params),
+                        C.byref(res), _ptr(per) if want_per_ray else None)
+    return _result(res), per
