@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark: raycast-RMP evaluation throughput on one GB300 (or N replicas).
+
+Workload: hashed TSDF map (8^3 blocks, 0.1 m voxels over 40 x 40 x 10 m, 200 seeded boxes and
+spheres, truncation 0.3 m), 65536 Halton rays per evaluation, max range 10 m, one robot
+state per call (states cycle over 64 seeded free positions with N(0,1) velocities).  A step
+is one full evaluation: Halton directions, exact DDA march, per-ray obstacle policy,
+reduction and FP64 resolve (one fused kernel).
+
+Printed JSON line (rank 0):
+  value     whole-job rays/s (Grays/s): rays of all ranks / max over ranks of the mean
+            per-step device time (CUDA events around each evaluation, inputs resident in HBM,
+            L2 flushed by a 256 MiB write between timed steps, outside the events);
+  e2e       the same metric through the public synchronous call rmp_raycast_eval with host
+            x/xdot and a host result (H2D of the state and D2H of the result inside the
+            timed region), wall clock per call;
+  roofline  algorithmic bytes per launch / mean kernel time against the measured HBM copy
+            bandwidth; traffic from the committed ncu capture when it matches this kernel;
+  cpu_baseline  the C oracle, single-threaded on this host, on a bounded sample.
+--impl reference times the oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Grays/s and RMP evals/s at 65536 rays; served p50/p99 latency vs plain kernel"
+UNIT = "Grays/s"
+WORKLOAD = ("hashed TSDF 40x40x10 m at 0.1 m (8^3 blocks, 200 boxes/spheres, trunc 0.3 m), "
+            "65536 Halton rays, max range 10 m, one state per call")
+N_RAYS = 65536
+N_STATES = 64
+FLUSH_BYTES = 256 << 20
+PAPER_RATE = 65536 * 3000 / 1e9   # 65536 rays at up to 3 kHz (abstract), other hardware
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def workload(rank: int):
+    from paper_2301_08068_gb300 import workloads as W
+    # every rank gets its own seeded states (independent work; the map is replicated)
+    return W.hashed_workload(n_states=N_STATES, state_seed_index=1 + 1000 * rank)
+
+
+def cpu_cores_used() -> int:
+    return 1
+
+
+def time_oracle(wl, seconds: float, max_evals: int):
+    """Single-threaded oracle evaluations of the workload's states until `seconds` pass."""
+    import oracle as O
+    om = O.OracleMap(wl.map)
+    p = O.make_params(wl.params, wl.max_range)
+    t0 = time.perf_counter()
+    n = 0
+    times = []
+    while n < max_evals and (time.perf_counter() - t0 < seconds or n == 0):
+        s = wl.states[n % len(wl.states)]
+        t1 = time.perf_counter()
+        O.raycast_eval(om, s.x, s.xdot, N_RAYS, p, want_hits=False, want_per_ray=False)
+        times.append(time.perf_counter() - t1)
+        n += 1
+    return n, sum(times), times
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9], float(parts[3])))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v == "Active"})
+        loaded = [r[0] for r in rows if r[3] > 0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("rmp_kernels.cu", "rmp_internal.h", "rmp_api.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2301_08068_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(src_hash: str):
+    """Per-launch DRAM bytes of the raycast kernel from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "raycast_hashed_65536_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("kernel_source_sha256_16") != src_hash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def measured_peak_hbm():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_reference(args):
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return
+    wl = workload(0)
+    import oracle as O
+    om = O.OracleMap(wl.map)
+    p = O.make_params(wl.params, wl.max_range)
+    for i in range(args.warmup):
+        s = wl.states[i % N_STATES]
+        O.raycast_eval(om, s.x, s.xdot, N_RAYS, p, want_hits=False, want_per_ray=False)
+    times = []
+    for i in range(args.steps):
+        s = wl.states[i % N_STATES]
+        t = time.perf_counter()
+        O.raycast_eval(om, s.x, s.xdot, N_RAYS, p, want_hits=False, want_per_ray=False)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    value = N_RAYS / (ms / 1e3) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_rays": N_RAYS, "states": N_STATES},
+        "evals_per_s": 1e3 / ms,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "each step: one full evaluation (65536 rays) of the workload, "
+                                   "single-threaded C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2301_08068_gb300 import rmp as R
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    wl = workload(rank)
+    ctx = R.Context(local_rank)
+    mid = ctx.upload(wl.map)
+    params = R.make_params(wl.params, wl.max_range)
+    states = torch.tensor(np.stack([np.concatenate([s.x, s.xdot]) for s in wl.states]),
+                          dtype=torch.float64, device=dev)
+    ws = torch.empty(R.rmp_workspace_bytes(), dtype=torch.uint8, device=dev)
+    R.rmp_workspace_init(ws)
+    outs = torch.empty((N_STATES, R.RESULT_BYTES), dtype=torch.uint8, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # algorithmic bytes per launch from the exact per-ray step and block counts
+    hits = torch.empty(N_RAYS * 24, dtype=torch.uint8, device=dev)
+    alg = []
+    for i in range(N_STATES):
+        R.rmp_raycast_eval_async(ctx.handle, mid, states[i], N_RAYS, params, ws, outs[i], hits=hits)
+        h = hits.cpu().numpy().view(R.HIT_DTYPE)
+        alg.append(float(((h["steps"].astype(np.int64) + 1) * 4).sum() +
+                         16 * h["blocks"].astype(np.int64).sum()))
+    grid = min((N_RAYS + 127) // 128, 4096)
+    alg_bytes = float(np.mean(alg)) + grid * 80 + 48 + 144
+
+    def step(i):
+        R.rmp_raycast_eval_async(ctx.handle, mid, states[i % N_STATES], N_RAYS, params, ws,
+                                 outs[i % N_STATES])
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)                 # evict L2 between timed evaluations
+        ev[i][0].record()
+        step(i)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    per = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(per))
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+
+    # check the results are real (finite, status ok) -- outside the timed region
+    res = [R.result_from_bytes(outs[i].cpu().numpy().tobytes()) for i in range(N_STATES)]
+    assert all(r["status"] == 0 and np.all(np.isfinite(r["f"])) for r in res)
+
+    # end to end through the public synchronous call with host buffers
+    n_e2e = max(1, min(args.steps, 2000))
+    e2e_t = []
+    for i in range(n_e2e):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        s = wl.states[i % N_STATES]
+        t = time.perf_counter()
+        R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, N_RAYS, params)
+        e2e_t.append(time.perf_counter() - t)
+    e2e_ms = 1e3 * float(np.mean(e2e_t))
+    e2e_t_max = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(e2e_t_max, op=torch.distributed.ReduceOp.MAX)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, secs, _ = time_oracle(wl, args.cpu_seconds, 200)
+        cpu = {"value": n * N_RAYS / secs / 1e9, "unit": UNIT, "cores": cpu_cores_used(),
+               "kind": "oracle",
+               "sample": "%d full evaluations (65536 rays each) of the workload's states, "
+                         "single-threaded C oracle, %.1f s" % (n, secs)}
+
+    src = kernel_source_hash()
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    traffic = committed_traffic(src)
+    if rank == 0:
+        value = world * N_RAYS / (ms_max / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_rays": N_RAYS, "states": N_STATES,
+                       "map_blocks": wl.map.n_blocks, "parallelism": "replicas x%d" % world,
+                       "l2": "flushed between timed steps (256 MiB write outside the events)",
+                       "launch": {"block": 128, "grid": grid}},
+            "evals_per_s": world * 1e3 / ms_max,
+            "ms_per_step_p50": float(np.percentile(per, 50)),
+            "ms_per_step_p99": float(np.percentile(per, 99)),
+            "timed_wall_s": wall,
+            "e2e": {"value": world * N_RAYS / (float(e2e_t_max.item()) / 1e3) / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": 48, "d2h_bytes_per_step": R.RESULT_BYTES,
+                    "ms_per_call": e2e_ms, "calls": n_e2e},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel": "raycast_rmp_kernel<HASHED_TSDF, KAHAN32>",
+                         "kernel_source_sha256_16": src},
+            "cpu_baseline": cpu,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "paper_context": {"value": PAPER_RATE, "unit": UNIT,
+                              "note": "65536 rays at up to 3 kHz (abstract), unnamed GPU of "
+                                      "Jetson NX / MX150 / Titan Xp, different map"},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

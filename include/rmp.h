@@ -1,0 +1,221 @@
+/* rmp.h -- C ABI of librmp.so: raycast Riemannian Motion Policy evaluation on one GPU.
+ *
+ * Method: Pantic, Meijer et al., "Obstacle avoidance using raycasting and Riemannian
+ * Motion Policies at kHz rates for MAVs" (arXiv 2301.08068).  From one robot state
+ * (x, xdot), N rays with Halton directions (Sec. III-E, Eq. halton) are marched through a
+ * voxel map (Sec. III-F), each ray yields an obstacle policy (f_i, A_i) (Sec. III-C), the
+ * policies are summed and resolved by Eq. (1): f = (sum A_i)^+ sum A_i f_i (Sec. III-A,
+ * Eq. raytracing_policy).  The LiDAR variant (Sec. III-G) takes a scan's points as the
+ * rays' end points.
+ *
+ * Conventions for every call:
+ *  - Every call returns an int status (RMP_OK = 0, else an RMP_ERR_* code); no C++
+ *    exception crosses this boundary.  Out-parameters are written only on RMP_OK.
+ *  - Pointers named *_dev are device pointers on the context's device; all others are
+ *    host pointers.  The caller keeps ownership of every buffer it passes in; the
+ *    context owns what it allocates (maps, internal scratch, pinned staging).
+ *  - Streams are cudaStream_t values passed as void* (NULL = legacy default stream).
+ *    Synchronous calls return after their stream has finished their work; _async calls
+ *    only enqueue work and never synchronise.
+ *  - A context may be used from several host threads; synchronous calls on one context
+ *    serialise on an internal lock.
+ *  - Arithmetic: FP32 march, direction and per-ray policy; the cross-ray reduction is a
+ *    compensated FP32 sum (default) or FP64; the 3x3 pseudo-inverse resolve is FP64.
+ */
+#ifndef RMP_H
+#define RMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RMP_ABI_VERSION 1
+
+/* ------------------------------------------------------------------ status codes */
+#define RMP_OK 0
+#define RMP_ERR_INVALID_ARG 1   /* a pointer, size, parameter or map is invalid        */
+#define RMP_ERR_NO_MEMORY 2     /* device or pinned host allocation failed             */
+#define RMP_ERR_CUDA 3          /* a CUDA runtime call or kernel launch failed         */
+#define RMP_ERR_TIMEOUT 4       /* a bounded wait expired (serving)                    */
+#define RMP_ERR_BUSY 5          /* no free slot / over the memory budget (serving)     */
+#define RMP_ERR_UNKNOWN_MAP 6   /* map id not registered in this context               */
+#define RMP_ERR_NOT_READY 7     /* polled work has not completed yet (serving)         */
+
+/* Per-ray march outcome (rmp_ray_hit_t.status). */
+#define RMP_RAY_HIT 1           /* entered an occupied voxel                           */
+#define RMP_RAY_MISS_RANGE 2    /* next voxel's entry distance exceeds max_range       */
+#define RMP_RAY_MISS_EXIT 3     /* left the dense grid (dense maps only)               */
+
+typedef struct rmp_ctx rmp_ctx;
+typedef void* rmp_stream_t;
+
+/* ------------------------------------------------------------------ parameters
+ * Obstacle-policy tuning of Sec. III-C / Table I plus this library's settings.
+ *  eta_rep, nu_rep     repulsive gain and length scale:  f_rep = eta_rep exp(-d/nu_rep) r
+ *  eta_damp, nu_damp   damping gain and length scale:
+ *                      f_damp = eta_damp / (d/nu_damp + eps) * max(0, -xdot.r)^2 r
+ *  r                   policy radius of w_r (metres)
+ *  c                   soft-normalisation parameter of s(v) (Eq. softmax)
+ *  eps                 the paper's 0 < eps << 1 (no value given; preset 1e-3)
+ *  max_range           rays: march limit in metres (<= 16384 voxels); scans: points
+ *                      farther than this are ignored
+ *  min_range           scans only: points nearer than this are ignored (vehicle body)
+ *  halton_offset       ray j uses Halton index j + halton_offset (preset 1; 0 adds the
+ *                      degenerate pole ray H(0) = 0 of the paper's i = 0)
+ *  w_mode              0: w_r(d) = d^2/r^2 - 2d/r + 1 as printed; 1: the cubic spline
+ *                      1 - 3(d/r)^2 + 2(d/r)^3 the text describes; both 0 for d >= r
+ *  reduce_mode         RMP_REDUCE_KAHAN32 (compensated FP32) or RMP_REDUCE_FP64
+ *  flags               must be 0 */
+typedef struct {
+  double eta_rep, nu_rep, eta_damp, nu_damp, r, c, eps;
+  double max_range, min_range;
+  uint32_t halton_offset, w_mode, reduce_mode, flags;
+} rmp_params_t;
+
+#define RMP_PRESET_STATIC_MAP 0 /* Table I "Static Map" column, max_range 10 m        */
+#define RMP_PRESET_LIDAR 1      /* Table I "LiDAR" column, max_range 30 m, min 0.2 m   */
+#define RMP_REDUCE_KAHAN32 0
+#define RMP_REDUCE_FP64 1
+
+/* ------------------------------------------------------------------ results
+ * Result of one evaluation (Eq. 1 / Eq. raytracing_policy).  A and Af hold sum_i A_i
+ * (6 unique entries xx xy xz yy yz zz) and sum_i A_i f_i; f = A^+ Af; eig are A's
+ * eigenvalues in ascending order; rank counts eigenvalues above 1e-12 * the largest.
+ * n_rays: rays (or points) evaluated; n_hits: rays that hit (points that were valid);
+ * n_active: hits with a nonzero metric (moving towards the obstacle, d < r).
+ * status: RMP_OK, or RMP_ERR_INVALID_ARG when the device-side state was unusable
+ * (non-finite or out of the map's coordinate range) -- then all sums are zero. */
+typedef struct {
+  double f[3];
+  double A[6];
+  double Af[3];
+  double eig[3];
+  uint32_t n_rays, n_hits, n_active, rank;
+  int32_t status;
+  uint32_t reserved;
+} rmp_result_t; /* 144 bytes */
+
+/* Per-ray march record: the last voxel the ray entered (global voxel index), the
+ * number of voxel steps to it (= its L1 distance from the start voxel), its entry
+ * distance d in metres along the ray (0 for the start voxel), the outcome, and the
+ * number of distinct 8^3-aligned blocks whose occupancy the march looked up. */
+typedef struct {
+  int32_t voxel[3];
+  uint32_t steps;
+  float d;
+  uint8_t status;
+  uint8_t pad;
+  uint16_t blocks;
+} rmp_ray_hit_t; /* 24 bytes */
+
+/* ------------------------------------------------------------------ maps
+ * RMP_MAP_DENSE_U8: dims[0] x dims[1] x dims[2] uint8 voxels, x fastest; nonzero =
+ *   occupied.  Voxel (i,j,k) covers origin + [i,i+1) x [j,j+1) x [k,k+1) voxel sizes.
+ *   Rays that leave the grid end with RMP_RAY_MISS_EXIT.
+ * RMP_MAP_HASHED_TSDF: n_blocks blocks of 8^3 float TSDF values, voxblox-style and
+ *   world-anchored (voxel k covers [k, k+1) voxel sizes; origin is ignored).
+ *   block_keys: n_blocks x 3 int32 block coordinates (|key| < 2^20, no duplicates);
+ *   tsdf: n_blocks x 512 floats, voxel lx + 8 ly + 64 lz of each block.  A voxel is
+ *   occupied iff its block exists and its TSDF value is <= 0; missing blocks are free.
+ * data_on_device: 0 = occ/block_keys/tsdf are host pointers, 1 = device pointers.
+ * The library copies what it needs; the caller's buffers may be freed after upload. */
+#define RMP_MAP_DENSE_U8 0
+#define RMP_MAP_HASHED_TSDF 1
+
+typedef struct {
+  int32_t kind;
+  int32_t data_on_device;
+  double voxel_size;
+  double origin[3];
+  int32_t dims[3];
+  uint32_t n_blocks;
+  const uint8_t* occ;
+  const int32_t* block_keys;
+  const float* tsdf;
+} rmp_map_desc_t;
+
+typedef struct {
+  int32_t kind;
+  uint32_t n_bricks;        /* 8^3 occupancy bricks held on the device */
+  uint32_t hash_capacity;   /* hashed maps: table entries (power of two) */
+  uint32_t reserved;
+  uint64_t device_bytes;    /* device memory held by the map */
+} rmp_map_info_t;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+int rmp_ctx_create(rmp_ctx** out, int device);
+
+/* Destroy a context and free every map and buffer it owns.  No work of this context
+ * may still be running. */
+int rmp_ctx_destroy(rmp_ctx* ctx);
+
+/* Static description of a status code (never NULL). */
+const char* rmp_status_string(int status);
+
+/* Fill *out with a parameter preset (Table I). */
+int rmp_params_preset(int preset, rmp_params_t* out);
+
+/* Upload a map (Sec. III-F: the map lives in GPU memory, shared by all evaluations).
+ * Work is enqueued on `stream` and completed before return.  *map_id receives a
+ * context-local id.  INVALID_ARG on bad dims, keys out of range or duplicate keys. */
+int rmp_map_upload(rmp_ctx* ctx, const rmp_map_desc_t* desc, rmp_stream_t stream,
+                   uint32_t* map_id);
+
+/* Free a map.  No evaluation using it may still be running. */
+int rmp_map_release(rmp_ctx* ctx, uint32_t map_id);
+
+int rmp_map_info(rmp_ctx* ctx, uint32_t map_id, rmp_map_info_t* out);
+
+/* ------------------------------------------------------------------ evaluation
+ * Raycast RMP evaluation of one state (Sec. III-E, Eq. raytracing_policy, resolved by
+ * Eq. 1), synchronous: copies x and xdot (3 doubles each, host) to the device, runs
+ * one fused kernel on `stream` (Halton direction, exact DDA march, per-ray policy,
+ * reduction, FP64 resolve) and copies the result back into *out (host).
+ * n_rays in [1, 2^24 - halton_offset].  hits_dev (nullable) receives n_rays records;
+ * per_ray_dev (nullable) receives n_rays x 9 floats: f_i (3) then A_i (6), zero for
+ * rays that did not hit. */
+int rmp_raycast_eval(rmp_ctx* ctx, uint32_t map_id, const double x[3], const double xdot[3],
+                     uint32_t n_rays, const rmp_params_t* params, rmp_stream_t stream,
+                     rmp_result_t* out, rmp_ray_hit_t* hits_dev, float* per_ray_dev);
+
+/* Bytes of device scratch one in-flight _async evaluation needs (independent of the
+ * ray count). */
+size_t rmp_workspace_bytes(void);
+
+/* Zero a workspace before its first use (enqueued on `stream`).  Each evaluation
+ * leaves its workspace ready for the next one, so this is needed once. */
+int rmp_workspace_init(void* workspace_dev, size_t bytes, rmp_stream_t stream);
+
+/* Asynchronous form of rmp_raycast_eval for device-resident inputs and outputs:
+ * state_dev holds x[3] then xdot[3] (doubles), the result is written to *out_dev.
+ * Only enqueues one kernel; no host synchronisation, no allocation, so it may be
+ * captured in a CUDA graph.  workspace_dev (>= rmp_workspace_bytes(), zeroed once by
+ * rmp_workspace_init) must not be shared by evaluations that may run concurrently. */
+int rmp_raycast_eval_async(rmp_ctx* ctx, uint32_t map_id, const double* state_dev,
+                           uint32_t n_rays, const rmp_params_t* params, void* workspace_dev,
+                           size_t workspace_bytes, rmp_stream_t stream, rmp_result_t* out_dev,
+                           rmp_ray_hit_t* hits_dev, float* per_ray_dev);
+
+/* LiDAR scan policy (Sec. III-G), synchronous.  points_dev: n x 3 floats (device,
+ * caller-owned), each a beam's end point in the same frame as x; NaN/inf rows and
+ * points whose range |p - x| is 0, below min_range or above max_range are skipped.
+ * Each valid point gives d = |p - x|, r = -(p - x)/d and the obstacle policy. */
+int rmp_scan_eval(rmp_ctx* ctx, const float* points_dev, uint32_t n, const double x[3],
+                  const double xdot[3], const rmp_params_t* params, rmp_stream_t stream,
+                  rmp_result_t* out, float* per_ray_dev);
+
+/* Asynchronous form of rmp_scan_eval; state_dev as for rmp_raycast_eval_async. */
+int rmp_scan_eval_async(rmp_ctx* ctx, const float* points_dev, uint32_t n,
+                        const double* state_dev, const rmp_params_t* params,
+                        void* workspace_dev, size_t workspace_bytes, rmp_stream_t stream,
+                        rmp_result_t* out_dev, float* per_ray_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RMP_H */

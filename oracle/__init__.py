@@ -42,7 +42,7 @@ class Params(C.Structure):
 
 class Hit(C.Structure):
     _fields_ = [("voxel", C.c_int32 * 3), ("steps", C.c_uint32), ("d", C.c_float),
-                ("status", C.c_uint8), ("pad", C.c_uint8 * 3)]
+                ("status", C.c_uint8), ("pad", C.c_uint8), ("blocks", C.c_uint16)]
 
 
 class Result(C.Structure):
@@ -58,7 +58,7 @@ class MapT(C.Structure):
 
 
 HIT_DTYPE = np.dtype([("voxel", "<i4", (3,)), ("steps", "<u4"), ("d", "<f4"),
-                      ("status", "u1"), ("pad", "u1", (3,))])
+                      ("status", "u1"), ("pad", "u1"), ("blocks", "<u2")])
 assert HIT_DTYPE.itemsize == C.sizeof(Hit) == 24
 
 

@@ -258,11 +258,16 @@ static float entry_distance(uint64_t N, uint64_t absD, double vs) {
   return t256 * (float)vs;
 }
 
+/* Block (8^3-aligned) of voxel k, for counting the distinct blocks a ray tests. */
+static void block_of(const int64_t k[3], int64_t b[3]) {
+  for (int a = 0; a < 3; ++a) b[a] = floor_div(k[a], 8);
+}
+
 int orc_dda(const orc_map_t* m, const int64_t P[3], const int32_t D[3], int64_t R_fx,
             orc_hit_t* out) {
-  int64_t k[3], B[3];
+  int64_t k[3], B[3], blk[3], nb[3];
   int sgn[3];
-  uint32_t steps = 0;
+  uint32_t steps = 0, blocks = 0;
   float d = 0.0f;
   for (int a = 0; a < 3; ++a) {
     k[a] = floor_div(P[a], FX_POS);
@@ -270,9 +275,10 @@ int orc_dda(const orc_map_t* m, const int64_t P[3], const int32_t D[3], int64_t 
     B[a] = D[a] > 0 ? (k[a] + 1) * FX_POS : k[a] * FX_POS;
   }
   int status;
+  block_of(k, blk);
   if (m->kind == 0 && !inside_dense(m, k)) {
     status = ORC_RAY_MISS_EXIT;
-  } else if (occupied(m, k)) {
+  } else if ((blocks = 1, occupied(m, k))) {
     status = ORC_RAY_HIT;
   } else {
     for (;;) {
@@ -293,6 +299,11 @@ int orc_dda(const orc_map_t* m, const int64_t P[3], const int32_t D[3], int64_t 
       steps += 1;
       d = entry_distance(bn, bd, m->voxel_size);
       if (m->kind == 0 && !inside_dense(m, k)) { status = ORC_RAY_MISS_EXIT; break; }
+      block_of(k, nb);
+      if (nb[0] != blk[0] || nb[1] != blk[1] || nb[2] != blk[2]) {
+        blocks += 1;
+        for (int a = 0; a < 3; ++a) blk[a] = nb[a];
+      }
       if (occupied(m, k)) { status = ORC_RAY_HIT; break; }
     }
   }
@@ -301,6 +312,7 @@ int orc_dda(const orc_map_t* m, const int64_t P[3], const int32_t D[3], int64_t 
   out->steps = steps;
   out->d = d;
   out->status = (uint8_t)status;
+  out->blocks = (uint16_t)blocks;
   return 0;
 }
 

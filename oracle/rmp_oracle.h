@@ -30,7 +30,8 @@ typedef struct {
   uint32_t steps;
   float d;
   uint8_t status;
-  uint8_t pad[3];
+  uint8_t pad;
+  uint16_t blocks;  /* distinct 8^3 blocks whose occupancy was tested */
 } orc_hit_t;
 
 typedef struct {

@@ -1,0 +1,464 @@
+// rmp_api.cu -- host implementation of the C ABI declared in include/rmp.h: contexts,
+// map upload (Sec. III-F: the map is kept in GPU memory and shared by all evaluations),
+// parameter validation and the evaluation entry points.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+
+#include "rmp_internal.h"
+
+using namespace rmp;
+
+namespace {
+
+struct MapRec {
+  DevMap dm;
+  void* bricks = nullptr;
+  void* table = nullptr;
+  uint32_t n_bricks = 0;
+  uint32_t cap = 0;
+  uint64_t bytes = 0;
+};
+
+}  // namespace
+
+struct rmp_ctx {
+  int device = 0;
+  int sm_count = 0;
+  std::mutex mu;
+  std::map<uint32_t, MapRec> maps;
+  uint32_t next_id = 1;
+  // scratch of the synchronous calls (serialised by mu)
+  void* ws = nullptr;
+  double* state_dev = nullptr;
+  rmp_result_t* result_dev = nullptr;
+  double* state_host = nullptr;        // pinned
+  rmp_result_t* result_host = nullptr; // pinned
+};
+
+namespace {
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    ok_ = cudaGetDevice(&prev_) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (ok_) cudaSetDevice(prev_);
+  }
+  bool ok() const { return ok_; }
+
+ private:
+  int prev_ = 0;
+  bool ok_ = false;
+};
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return RMP_OK;
+  if (e == cudaErrorMemoryAllocation) return RMP_ERR_NO_MEMORY;
+  cudaGetLastError();  // clear a sticky launch error so later calls can proceed
+  return RMP_ERR_CUDA;
+}
+
+#define RMP_CUDA(expr)                       \
+  do {                                       \
+    cudaError_t e_ = (expr);                 \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Smallest float >= v (v finite, in float range).
+float round_up_f32(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+// Largest float <= v.
+float round_down_f32(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+
+// Derive the per-evaluation constants; validates every parameter.
+int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalConsts* k) {
+  if (!p) return RMP_ERR_INVALID_ARG;
+  if (!(std::isfinite(p->eta_rep) && p->eta_rep >= 0.0) || !finite_pos(p->nu_rep) ||
+      !(std::isfinite(p->eta_damp) && p->eta_damp >= 0.0) || !finite_pos(p->nu_damp) ||
+      !finite_pos(p->r) || !finite_pos(p->c) || !finite_pos(p->eps) ||
+      !finite_pos(p->max_range) || !(std::isfinite(p->min_range) && p->min_range >= 0.0) ||
+      p->r > 1e30 || p->max_range > 1e30 || p->w_mode > 1 || p->reduce_mode > 1 ||
+      p->flags != 0)
+    return RMP_ERR_INVALID_ARG;
+  if (n == 0) return RMP_ERR_INVALID_ARG;
+  std::memset(k, 0, sizeof(*k));
+  k->eta_rep = (float)p->eta_rep;
+  k->inv_nu_rep = (float)(1.0 / p->nu_rep);
+  k->eta_damp = (float)p->eta_damp;
+  k->inv_nu_damp = (float)(1.0 / p->nu_damp);
+  k->eps = (float)p->eps;
+  k->c = (float)p->c;
+  k->r_up = round_up_f32(p->r);
+  k->inv_r = (float)(1.0 / p->r);
+  k->r_hi = (float)p->r;
+  k->r_lo = (float)(p->r - (double)k->r_hi);
+  k->min_up = round_up_f32(p->min_range);
+  k->max_dn = round_down_f32(p->max_range);
+  k->n_rays = n;
+  k->halton_offset = p->halton_offset;
+  k->w_mode = (int)p->w_mode;
+  k->reduce_mode = (int)p->reduce_mode;
+  if (!scan) {
+    if ((uint64_t)n + p->halton_offset > (1ull << 24)) return RMP_ERR_INVALID_ARG;
+    const double vox = p->max_range / vs;
+    if (!(vox <= (double)kMaxRangeVoxels)) return RMP_ERR_INVALID_ARG;
+    k->R_fx = std::llrint(vox * 65536.0);
+  }
+  return RMP_OK;
+}
+
+void launch_shape(const rmp_ctx* ctx, uint32_t n, int* block, int* grid) {
+  (void)ctx;
+  const int b = 128;
+  uint64_t g = ((uint64_t)n + b - 1) / b;
+  if (g > (uint64_t)kMaxGrid) g = kMaxGrid;
+  if (g < 1) g = 1;
+  *block = b;
+  *grid = (int)g;
+}
+
+void free_map(MapRec& r) {
+  if (r.bricks) cudaFree(r.bricks);
+  if (r.table) cudaFree(r.table);
+  r.bricks = r.table = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rmp_status_string(int status) {
+  switch (status) {
+    case RMP_OK: return "ok";
+    case RMP_ERR_INVALID_ARG: return "invalid argument";
+    case RMP_ERR_NO_MEMORY: return "out of memory";
+    case RMP_ERR_CUDA: return "CUDA error";
+    case RMP_ERR_TIMEOUT: return "timed out";
+    case RMP_ERR_BUSY: return "busy";
+    case RMP_ERR_UNKNOWN_MAP: return "unknown map id";
+    case RMP_ERR_NOT_READY: return "not ready";
+    default: return "unknown status";
+  }
+}
+
+int rmp_params_preset(int preset, rmp_params_t* out) {
+  if (!out) return RMP_ERR_INVALID_ARG;
+  rmp_params_t p;
+  std::memset(&p, 0, sizeof(p));
+  if (preset == RMP_PRESET_STATIC_MAP) {         // Table I, "Static Map"
+    p.eta_rep = 88.0; p.nu_rep = 1.4; p.eta_damp = 140.0; p.nu_damp = 1.2;
+    p.r = 2.4; p.c = 0.2; p.max_range = 10.0; p.min_range = 0.0;
+  } else if (preset == RMP_PRESET_LIDAR) {       // Table I, "LiDAR"
+    p.eta_rep = 1.2; p.nu_rep = 1.5; p.eta_damp = 3.0; p.nu_damp = 1.0;
+    p.r = 1.3; p.c = 1.0; p.max_range = 30.0; p.min_range = 0.2;
+  } else {
+    return RMP_ERR_INVALID_ARG;
+  }
+  p.eps = 1e-3;
+  p.halton_offset = 1;
+  p.w_mode = 0;
+  p.reduce_mode = RMP_REDUCE_KAHAN32;
+  *out = p;
+  return RMP_OK;
+}
+
+int rmp_ctx_create(rmp_ctx** out, int device) {
+  if (!out) return RMP_ERR_INVALID_ARG;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) { cudaGetLastError(); return RMP_ERR_CUDA; }
+  if (device < 0 || device >= n) return RMP_ERR_INVALID_ARG;
+  DeviceGuard g(device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  rmp_ctx* c = new (std::nothrow) rmp_ctx();
+  if (!c) return RMP_ERR_NO_MEMORY;
+  c->device = device;
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  cudaError_t e = cudaMalloc(&c->ws, workspace_bytes());
+  if (e == cudaSuccess) e = cudaMemset(c->ws, 0, workspace_bytes());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->state_dev, 6 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->result_dev, sizeof(rmp_result_t));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->state_host, 6 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->result_host, sizeof(rmp_result_t));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    rmp_ctx_destroy(c);
+    return cuda_status(e);
+  }
+  *out = c;
+  return RMP_OK;
+}
+
+int rmp_ctx_destroy(rmp_ctx* c) {
+  if (!c) return RMP_ERR_INVALID_ARG;
+  {
+    DeviceGuard g(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (auto& kv : c->maps) free_map(kv.second);
+    c->maps.clear();
+    if (c->ws) cudaFree(c->ws);
+    if (c->state_dev) cudaFree(c->state_dev);
+    if (c->result_dev) cudaFree(c->result_dev);
+    if (c->state_host) cudaFreeHost(c->state_host);
+    if (c->result_host) cudaFreeHost(c->result_host);
+  }
+  delete c;
+  return RMP_OK;
+}
+
+int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uint32_t* map_id) {
+  if (!c || !d || !map_id) return RMP_ERR_INVALID_ARG;
+  if (!finite_pos(d->voxel_size) || d->voxel_size > 1e6) return RMP_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  MapRec r;
+  std::memset(&r.dm, 0, sizeof(r.dm));
+  r.dm.kind = d->kind;
+  r.dm.vs = d->voxel_size;
+  r.dm.vs_f = (float)d->voxel_size;
+  void* tmp_a = nullptr;
+  void* tmp_b = nullptr;
+  unsigned int* err_dev = nullptr;
+  auto fail = [&](int st) {
+    if (tmp_a) cudaFree(tmp_a);
+    if (tmp_b) cudaFree(tmp_b);
+    if (err_dev) cudaFree(err_dev);
+    free_map(r);
+    return st;
+  };
+  if (d->kind == RMP_MAP_DENSE_U8) {
+    for (int a = 0; a < 3; ++a) {
+      if (d->dims[a] <= 0 || d->dims[a] > (1 << 20) || !std::isfinite(d->origin[a]))
+        return RMP_ERR_INVALID_ARG;
+      r.dm.dims[a] = d->dims[a];
+      r.dm.nb[a] = (d->dims[a] + 7) / 8;
+      r.dm.origin[a] = d->origin[a];
+    }
+    if (!d->occ) return RMP_ERR_INVALID_ARG;
+    const uint64_t nvox = (uint64_t)d->dims[0] * d->dims[1] * d->dims[2];
+    const uint64_t nbr = (uint64_t)r.dm.nb[0] * r.dm.nb[1] * r.dm.nb[2];
+    if (nbr > (1ull << 31)) return RMP_ERR_INVALID_ARG;
+    const uint8_t* occ = d->occ;
+    if (!d->data_on_device) {
+      cudaError_t e = cudaMalloc(&tmp_a, nvox);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(tmp_a, d->occ, nvox, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return fail(cuda_status(e));
+      occ = (const uint8_t*)tmp_a;
+    }
+    r.n_bricks = (uint32_t)nbr;
+    cudaError_t e = cudaMalloc(&r.bricks, nbr * 64);
+    if (e == cudaSuccess) e = launch_dense_bricks(occ, r.dm.dims, r.dm.nb, (uint32_t*)r.bricks, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    r.bytes = nbr * 64;
+  } else if (d->kind == RMP_MAP_HASHED_TSDF) {
+    const uint32_t n = d->n_blocks;
+    if (n > (1u << 26)) return RMP_ERR_INVALID_ARG;
+    if (n > 0 && (!d->block_keys || !d->tsdf)) return RMP_ERR_INVALID_ARG;
+    uint32_t cap = 16;
+    while (cap < 4ull * n) cap <<= 1;
+    int log2cap = 0;
+    while ((1u << log2cap) < cap) ++log2cap;
+    r.cap = cap;
+    r.dm.cap_mask = cap - 1;
+    r.dm.hash_shift = 64 - log2cap;
+    r.n_bricks = n;
+    cudaError_t e = cudaMalloc(&r.table, (size_t)cap * sizeof(HashEntry));
+    if (e == cudaSuccess) e = cudaMemsetAsync(r.table, 0xFF, (size_t)cap * sizeof(HashEntry), s);
+    if (e == cudaSuccess && n > 0) e = cudaMalloc(&r.bricks, (size_t)n * 64);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&err_dev, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err_dev, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    if (n > 0) {
+      const int32_t* keys = d->block_keys;
+      const float* tsdf = d->tsdf;
+      if (!d->data_on_device) {
+        e = cudaMalloc(&tmp_a, (size_t)n * 3 * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&tmp_b, (size_t)n * 512 * sizeof(float));
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(tmp_a, d->block_keys, (size_t)n * 3 * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(tmp_b, d->tsdf, (size_t)n * 512 * sizeof(float),
+                              cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return fail(cuda_status(e));
+        keys = (const int32_t*)tmp_a;
+        tsdf = (const float*)tmp_b;
+      }
+      e = launch_tsdf_bricks(tsdf, n, (uint32_t*)r.bricks, s);
+      if (e == cudaSuccess)
+        e = launch_hash_build(keys, n, (HashEntry*)r.table, r.dm.cap_mask, r.dm.hash_shift,
+                              err_dev, s);
+      if (e != cudaSuccess) return fail(cuda_status(e));
+    }
+    unsigned int err_host = 0;
+    e = cudaMemcpyAsync(&err_host, err_dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    if (err_host != 0) return fail(RMP_ERR_INVALID_ARG);
+    r.bytes = (uint64_t)cap * sizeof(HashEntry) + (uint64_t)n * 64;
+  } else {
+    return RMP_ERR_INVALID_ARG;
+  }
+  if (tmp_a) cudaFree(tmp_a);
+  if (tmp_b) cudaFree(tmp_b);
+  if (err_dev) cudaFree(err_dev);
+  tmp_a = tmp_b = nullptr;
+  err_dev = nullptr;
+  r.dm.bricks = (const uint4*)r.bricks;
+  r.dm.table = (const HashEntry*)r.table;
+  std::lock_guard<std::mutex> lk(c->mu);
+  const uint32_t id = c->next_id++;
+  c->maps[id] = r;
+  *map_id = id;
+  return RMP_OK;
+}
+
+int rmp_map_release(rmp_ctx* c, uint32_t map_id) {
+  if (!c) return RMP_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->maps.find(map_id);
+  if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
+  free_map(it->second);
+  c->maps.erase(it);
+  return RMP_OK;
+}
+
+int rmp_map_info(rmp_ctx* c, uint32_t map_id, rmp_map_info_t* out) {
+  if (!c || !out) return RMP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->maps.find(map_id);
+  if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
+  std::memset(out, 0, sizeof(*out));
+  out->kind = it->second.dm.kind;
+  out->n_bricks = it->second.n_bricks;
+  out->hash_capacity = it->second.cap;
+  out->device_bytes = it->second.bytes;
+  return RMP_OK;
+}
+
+size_t rmp_workspace_bytes(void) { return workspace_bytes(); }
+
+int rmp_workspace_init(void* ws, size_t bytes, rmp_stream_t stream) {
+  if (!ws || bytes < workspace_bytes()) return RMP_ERR_INVALID_ARG;
+  RMP_CUDA(cudaMemsetAsync(ws, 0, workspace_bytes(), (cudaStream_t)stream));
+  return RMP_OK;
+}
+
+int rmp_raycast_eval_async(rmp_ctx* c, uint32_t map_id, const double* state_dev, uint32_t n_rays,
+                           const rmp_params_t* params, void* ws, size_t ws_bytes,
+                           rmp_stream_t stream, rmp_result_t* out_dev, rmp_ray_hit_t* hits_dev,
+                           float* per_ray_dev) {
+  if (!c || !state_dev || !ws || !out_dev || ws_bytes < workspace_bytes())
+    return RMP_ERR_INVALID_ARG;
+  DevMap dm;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->maps.find(map_id);
+    if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
+    dm = it->second.dm;
+  }
+  EvalConsts k;
+  int st = make_consts(params, dm.vs, n_rays, false, &k);
+  if (st != RMP_OK) return st;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  int block, grid;
+  launch_shape(c, n_rays, &block, &grid);
+  RMP_CUDA(launch_raycast(dm, k, state_dev, ws, out_dev, hits_dev, per_ray_dev, block, grid,
+                          (cudaStream_t)stream));
+  return RMP_OK;
+}
+
+int rmp_raycast_eval(rmp_ctx* c, uint32_t map_id, const double x[3], const double xdot[3],
+                     uint32_t n_rays, const rmp_params_t* params, rmp_stream_t stream,
+                     rmp_result_t* out, rmp_ray_hit_t* hits_dev, float* per_ray_dev) {
+  if (!c || !x || !xdot || !out) return RMP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);      // held until the result is back
+  auto it = c->maps.find(map_id);
+  if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
+  const DevMap dm = it->second.dm;
+  EvalConsts k;
+  int st = make_consts(params, dm.vs, n_rays, false, &k);
+  if (st != RMP_OK) return st;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int a = 0; a < 3; ++a) {
+    c->state_host[a] = x[a];
+    c->state_host[3 + a] = xdot[a];
+  }
+  int block, grid;
+  launch_shape(c, n_rays, &block, &grid);
+  RMP_CUDA(cudaMemcpyAsync(c->state_dev, c->state_host, 6 * sizeof(double),
+                           cudaMemcpyHostToDevice, s));
+  RMP_CUDA(launch_raycast(dm, k, c->state_dev, c->ws, c->result_dev, hits_dev, per_ray_dev,
+                          block, grid, s));
+  RMP_CUDA(cudaMemcpyAsync(c->result_host, c->result_dev, sizeof(rmp_result_t),
+                           cudaMemcpyDeviceToHost, s));
+  RMP_CUDA(cudaStreamSynchronize(s));
+  *out = *c->result_host;
+  return RMP_OK;
+}
+
+int rmp_scan_eval_async(rmp_ctx* c, const float* points_dev, uint32_t n, const double* state_dev,
+                        const rmp_params_t* params, void* ws, size_t ws_bytes,
+                        rmp_stream_t stream, rmp_result_t* out_dev, float* per_ray_dev) {
+  if (!c || !points_dev || !state_dev || !ws || !out_dev || ws_bytes < workspace_bytes())
+    return RMP_ERR_INVALID_ARG;
+  EvalConsts k;
+  int st = make_consts(params, 1.0, n, true, &k);
+  if (st != RMP_OK) return st;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  int block, grid;
+  launch_shape(c, n, &block, &grid);
+  RMP_CUDA(launch_scan(points_dev, k, state_dev, ws, out_dev, per_ray_dev, block, grid,
+                       (cudaStream_t)stream));
+  return RMP_OK;
+}
+
+int rmp_scan_eval(rmp_ctx* c, const float* points_dev, uint32_t n, const double x[3],
+                  const double xdot[3], const rmp_params_t* params, rmp_stream_t stream,
+                  rmp_result_t* out, float* per_ray_dev) {
+  if (!c || !points_dev || !x || !xdot || !out) return RMP_ERR_INVALID_ARG;
+  EvalConsts k;
+  int st = make_consts(params, 1.0, n, true, &k);
+  if (st != RMP_OK) return st;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int a = 0; a < 3; ++a) {
+    c->state_host[a] = x[a];
+    c->state_host[3 + a] = xdot[a];
+  }
+  int block, grid;
+  launch_shape(c, n, &block, &grid);
+  RMP_CUDA(cudaMemcpyAsync(c->state_dev, c->state_host, 6 * sizeof(double),
+                           cudaMemcpyHostToDevice, s));
+  RMP_CUDA(launch_scan(points_dev, k, c->state_dev, c->ws, c->result_dev, per_ray_dev, block,
+                       grid, s));
+  RMP_CUDA(cudaMemcpyAsync(c->result_host, c->result_dev, sizeof(rmp_result_t),
+                           cudaMemcpyDeviceToHost, s));
+  RMP_CUDA(cudaStreamSynchronize(s));
+  *out = *c->result_host;
+  return RMP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// rmp_internal.h -- types shared by the library's host code and kernels (not part of the
+// public ABI).  Layouts in HBM:
+//   * occupancy bricks: one 8^3 voxel brick = 512 bits = 64 bytes = 16 uint32 words;
+//     bit b = lx + 8 ly + 64 lz lives in word b >> 5, bit b & 31.  Dense maps store
+//     ceil(dims/8) bricks in x-fastest order; hashed maps store one brick per TSDF block
+//     (a voxel is occupied iff its TSDF value <= 0), addressed through the hash table.
+//   * hash table: power-of-two array of 16-byte entries {key, slot}; key packs the block
+//     coordinates (21 bits each, offset by 2^20); empty entries hold ~0; linear probing
+//     from a Fibonacci (multiply-shift) hash, load factor <= 1/4.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rmp.h"
+
+namespace rmp {
+
+constexpr int kBrickWords = 16;
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr int kKeyBias = 1 << 20;
+constexpr int kMaxGrid = 4096;          // CTAs of one evaluation (grid-stride beyond)
+constexpr int kWsHeaderBytes = 256;
+constexpr int kMaxRangeVoxels = 16384;  // keeps every DDA crossing numerator below 2^31
+
+struct HashEntry {
+  unsigned long long key;
+  uint32_t slot;
+  uint32_t pad;
+};
+
+struct DevMap {
+  int kind;                 // RMP_MAP_DENSE_U8 / RMP_MAP_HASHED_TSDF
+  int hash_shift;           // 64 - log2(capacity)
+  float vs_f;               // RN32(voxel size)
+  uint32_t cap_mask;
+  double vs;
+  double origin[3];         // dense only (hashed maps are world-anchored)
+  int dims[3];              // dense voxels per axis
+  int nb[3];                // dense bricks per axis
+  const uint4* bricks;      // n_bricks x 4 uint4
+  const HashEntry* table;   // hashed only
+};
+
+// Constants of one evaluation derived on the host from rmp_params_t.
+struct EvalConsts {
+  float eta_rep, inv_nu_rep, eta_damp, inv_nu_damp, eps, c, r_up, inv_r;
+  float r_hi, r_lo;         // r = r_hi + r_lo (FP32 pair)
+  float min_up, max_dn;     // scans: d >= min_range <=> d >= min_up; d <= max <=> d <= max_dn
+  long long R_fx;           // llrint(max_range / vs * 2^16)
+  uint32_t n_rays, halton_offset;
+  int w_mode, reduce_mode;
+};
+
+struct WsHeader {
+  unsigned int ticket;      // CTAs finished; the last one resets it to 0
+  unsigned int pad[kWsHeaderBytes / 4 - 1];
+};
+
+struct CtaPartial {         // 80 bytes per CTA
+  double v[9];              // sum A (6), sum A f (3)
+  unsigned int n_hits, n_active;
+};
+
+inline size_t workspace_bytes() {
+  return kWsHeaderBytes + sizeof(CtaPartial) * (size_t)kMaxGrid;
+}
+
+inline unsigned long long pack_key(int bx, int by, int bz) {
+  return (unsigned long long)(uint32_t)(bx + kKeyBias) |
+         ((unsigned long long)(uint32_t)(by + kKeyBias) << 21) |
+         ((unsigned long long)(uint32_t)(bz + kKeyBias) << 42);
+}
+
+// Launchers (rmp_kernels.cu).  All enqueue on `stream` and return cudaGetLastError().
+cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,
+                           void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
+                           float* per_ray, int block, int grid, cudaStream_t stream);
+cudaError_t launch_scan(const float* pts, const EvalConsts& k, const double* state_dev,
+                        void* ws, rmp_result_t* out_dev, float* per_ray, int block, int grid,
+                        cudaStream_t stream);
+cudaError_t launch_dense_bricks(const uint8_t* occ, const int dims[3], const int nb[3],
+                                uint32_t* bricks, cudaStream_t stream);
+cudaError_t launch_tsdf_bricks(const float* tsdf, uint32_t n_blocks, uint32_t* bricks,
+                               cudaStream_t stream);
+cudaError_t launch_hash_build(const int32_t* keys, uint32_t n_blocks, HashEntry* table,
+                              uint32_t cap_mask, int hash_shift, unsigned int* err,
+                              cudaStream_t stream);
+
+}  // namespace rmp

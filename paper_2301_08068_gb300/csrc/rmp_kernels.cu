@@ -1,0 +1,851 @@
+// rmp_kernels.cu -- sm_103a kernels of librmp: the fused raycast-RMP evaluation, the
+// LiDAR scan policy and the map-build kernels.
+//
+// One evaluation is ONE launch: each thread generates its ray's Halton direction in
+// registers (Sec. III-E, Eq. halton), marches it with an exact fixed-point DDA through
+// the occupancy bricks (Sec. III-F; the current 8^3 brick of each ray is staged in shared
+// memory, so steps inside a brick touch no global memory), evaluates the obstacle policy
+// (Sec. III-C), and the block reduces the 9 unique terms of sum A_i and sum A_i f_i
+// (Fig. 3's block reduce) with a compensated FP32 tree (or FP64).  The last CTA to
+// finish sums the per-CTA partials in a fixed order in FP64 and resolves Eq. (1) with an
+// FP64 Jacobi pseudo-inverse, so the result is deterministic.
+//
+// Bit-exact steps (Halton direction, DDA, hit distance, the FP32 decisions that gate a
+// ray) use explicitly rounded intrinsics (__fmul_rn, __fmaf_rn, ...) so that no
+// contraction or fast-math rewrite can change them.
+#include "rmp_internal.h"
+
+namespace rmp {
+namespace {
+
+// ------------------------------------------------------------------ Halton directions
+// Radical inverse base 2 of i, rounded to FP32 (exact for i < 2^24).
+__device__ __forceinline__ float halton2(uint32_t i) {
+  return __fmul_rn(__uint2float_rn(__brev(i)), 2.3283064365386963e-10f);  // * 2^-32
+}
+
+// The 20 base-3 digits of i (< 3^20) reversed: H(i,3) * 3^20.
+__device__ __forceinline__ uint32_t halton3_numerator(uint32_t i) {
+  uint32_t num = 0;
+#pragma unroll
+  for (int k = 0; k < 20; ++k) {
+    uint32_t q = i / 3u;
+    num = num * 3u + (i - 3u * q);
+    i = q;
+  }
+  return num;
+}
+
+// num / 3^20 correctly rounded to FP32 with integer arithmetic only (FP64 division is
+// slow on this GPU): scale num by 2^s so the quotient has exactly 24 significant bits,
+// divide, and round to nearest on the remainder (no ties: 3^20 is odd).
+__device__ __forceinline__ float halton3_f32(uint32_t num) {
+  if (num == 0) return 0.0f;
+  constexpr unsigned long long M = 3486784401ull;
+  int s = 55 - (32 - __clz(num));
+  unsigned long long X = (unsigned long long)num << s;
+  if (X < (M << 23)) {
+    X <<= 1;
+    ++s;
+  }
+  unsigned long long q = X / M;
+  unsigned long long rem = X - q * M;
+  if (2ull * rem > M) ++q;
+  return __fmul_rn(__ull2float_rn(q), __int_as_float((127 - s) << 23));
+}
+
+// cos and sin of 2*pi*v by a fixed FP32 recipe: octant q = floor(8v), fraction t,
+// reduced angle a = x * RN(pi/4) (x = t, or 1 - t in odd octants), Taylor series of
+// sin (through a^11) and cos (through a^12) with RN(1/n!) coefficients by Horner's rule
+// with fused multiply-adds, then the octant's symmetry.
+__device__ __forceinline__ void sincos_turns(float v, float& c_out, float& s_out) {
+  constexpr float kPi4 = 0.78539816339744830962f;
+  constexpr float f2 = 1.0f / 2.0f, f3 = 1.0f / 6.0f, f4 = 1.0f / 24.0f, f5 = 1.0f / 120.0f,
+                  f6 = 1.0f / 720.0f, f7 = 1.0f / 5040.0f, f8 = 1.0f / 40320.0f,
+                  f9 = 1.0f / 362880.0f, f10 = 1.0f / 3628800.0f, f11 = 1.0f / 39916800.0f,
+                  f12 = 1.0f / 479001600.0f;
+  const float w = __fmul_rn(v, 8.0f);
+  const int q = __float2int_rz(w);
+  const float t = __fsub_rn(w, __int2float_rn(q));
+  const float x = (q & 1) ? __fsub_rn(1.0f, t) : t;
+  const float a = __fmul_rn(x, kPi4);
+  const float a2 = __fmul_rn(a, a);
+  float ps = -f11;
+  ps = __fmaf_rn(ps, a2, f9);
+  ps = __fmaf_rn(ps, a2, -f7);
+  ps = __fmaf_rn(ps, a2, f5);
+  ps = __fmaf_rn(ps, a2, -f3);
+  const float sa = __fmaf_rn(__fmul_rn(a2, a), ps, a);
+  float pc = f12;
+  pc = __fmaf_rn(pc, a2, -f10);
+  pc = __fmaf_rn(pc, a2, f8);
+  pc = __fmaf_rn(pc, a2, -f6);
+  pc = __fmaf_rn(pc, a2, f4);
+  pc = __fmaf_rn(pc, a2, -f2);
+  const float ca = __fmaf_rn(a2, pc, 1.0f);
+  const int o = q & 7;
+  // octant o: angle = o*pi/4 + (t pi/4); odd octants measure a from the next multiple
+  const bool swap = ((o + 1) & 2) != 0;          // octants 1,2,5,6: cos <-> sin
+  float c = swap ? sa : ca;
+  float s = swap ? ca : sa;
+  if (o >= 2 && o <= 5) c = -c;                  // cos < 0 in octants 2..5
+  if (o >= 4) s = -s;                            // sin < 0 in octants 4..7
+  c_out = c;
+  s_out = s;
+}
+
+struct Ray {
+  float dir[3];
+  int D[3];
+};
+
+__device__ __forceinline__ Ray make_ray(uint32_t i) {
+  const float u = halton2(i);
+  const float v = halton3_f32(halton3_numerator(i));
+  const float z = __fsub_rn(1.0f, __fmul_rn(2.0f, u));
+  const float st = __fmul_rn(2.0f, __fsqrt_rn(__fmul_rn(u, __fsub_rn(1.0f, u))));
+  float c, s;
+  sincos_turns(v, c, s);
+  Ray r;
+  r.dir[0] = __fmul_rn(st, c);
+  r.dir[1] = __fmul_rn(st, s);
+  r.dir[2] = z;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) r.D[a] = __float2int_rn(__fmul_rn(r.dir[a], 16777216.0f));
+  return r;
+}
+
+// ------------------------------------------------------------------ map access
+__device__ __forceinline__ int hash_lookup(const DevMap& m, int bx, int by, int bz) {
+  const unsigned long long key = (unsigned long long)(uint32_t)(bx + kKeyBias) |
+                                 ((unsigned long long)(uint32_t)(by + kKeyBias) << 21) |
+                                 ((unsigned long long)(uint32_t)(bz + kKeyBias) << 42);
+  uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> m.hash_shift);
+  for (uint32_t probe = 0; probe <= m.cap_mask; ++probe) {   // bounded: table has empties
+    const unsigned long long k = __ldg(&m.table[h].key);
+    if (k == key) return (int)__ldg(&m.table[h].slot);
+    if (k == kEmptyKey) return -1;
+    h = (h + 1) & m.cap_mask;
+  }
+  return -1;
+}
+
+// Stage brick (bx,by,bz) of this thread in shared memory (word w at cache[w*stride]).
+// Returns false for a missing or all-free brick (nothing is staged then).
+template <int KIND>
+__device__ __forceinline__ bool stage_brick(const DevMap& m, int bx, int by, int bz,
+                                            uint32_t* cache, int stride) {
+  int slot;
+  if (KIND == RMP_MAP_DENSE_U8) {
+    slot = bx + m.nb[0] * (by + m.nb[1] * bz);
+  } else {
+    slot = hash_lookup(m, bx, by, bz);
+    if (slot < 0) return false;
+  }
+  const uint4* src = m.bricks + 4 * (size_t)slot;
+  const uint4 w0 = __ldg(src), w1 = __ldg(src + 1), w2 = __ldg(src + 2), w3 = __ldg(src + 3);
+  const uint32_t any = w0.x | w0.y | w0.z | w0.w | w1.x | w1.y | w1.z | w1.w | w2.x | w2.y |
+                       w2.z | w2.w | w3.x | w3.y | w3.z | w3.w;
+  if (any == 0) return false;
+  cache[0 * stride] = w0.x;  cache[1 * stride] = w0.y;
+  cache[2 * stride] = w0.z;  cache[3 * stride] = w0.w;
+  cache[4 * stride] = w1.x;  cache[5 * stride] = w1.y;
+  cache[6 * stride] = w1.z;  cache[7 * stride] = w1.w;
+  cache[8 * stride] = w2.x;  cache[9 * stride] = w2.y;
+  cache[10 * stride] = w2.z; cache[11 * stride] = w2.w;
+  cache[12 * stride] = w3.x; cache[13 * stride] = w3.y;
+  cache[14 * stride] = w3.z; cache[15 * stride] = w3.w;
+  return true;
+}
+
+__device__ __forceinline__ bool cached_bit(const uint32_t* cache, int stride, int kx, int ky,
+                                           int kz) {
+  const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
+  const uint32_t w = cache[((ly >> 2) + 2 * lz) * stride];
+  return (w >> (lx + 8 * (ly & 3))) & 1u;
+}
+
+// ------------------------------------------------------------------ exact DDA (raycast R)
+// Fixed point: P in 2^-16 voxel units, D in 2^-24 units.  N_a = distance (in P units)
+// to the next boundary of axis a; the ray reaches it at t_a = N_a / |D_a|.  Each
+// iteration steps the axis with the smallest t_a (cross-multiplied exactly in 64 bits;
+// ties go to the lowest axis); an axis with D_a = 0 has |D_a| = 0, N_a = 1 and so never
+// wins.  A voxel is entered only if N_a 2^24 <= R_fx |D_a|, i.e. N_a <= L_a.
+struct MarchOut {
+  int k[3];
+  uint32_t steps;
+  uint32_t blocks;          // distinct blocks whose occupancy was looked up
+  uint32_t n_last, a_last;  // entry numerator / |D| of the last voxel (0/1 at the start)
+  int status;
+};
+
+template <int KIND>
+__device__ __forceinline__ MarchOut march(const DevMap& m, const long long P[3], const int D[3],
+                                          long long R_fx, uint32_t* cache, int stride) {
+  int k[3], s[3];
+  uint32_t N[3], A[3], L[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    k[a] = (int)(P[a] >> 16);
+    s[a] = D[a] > 0 ? 1 : -1;
+    A[a] = (uint32_t)abs(D[a]);
+    const long long lo = (long long)k[a] << 16;
+    N[a] = D[a] > 0 ? (uint32_t)(lo + 65536 - P[a]) : (D[a] < 0 ? (uint32_t)(P[a] - lo) : 1u);
+    L[a] = (uint32_t)(((unsigned long long)R_fx * A[a]) >> 24);
+  }
+  MarchOut o;
+  o.steps = 0;
+  o.blocks = 0;
+  o.n_last = 0;
+  o.a_last = 1;
+  if (KIND == RMP_MAP_DENSE_U8 &&
+      ((unsigned)k[0] >= (unsigned)m.dims[0] || (unsigned)k[1] >= (unsigned)m.dims[1] ||
+       (unsigned)k[2] >= (unsigned)m.dims[2])) {
+    o.status = RMP_RAY_MISS_EXIT;
+  } else {
+    bool staged = stage_brick<KIND>(m, k[0] >> 3, k[1] >> 3, k[2] >> 3, cache, stride);
+    o.blocks = 1;
+    if (staged && cached_bit(cache, stride, k[0], k[1], k[2])) {
+      o.status = RMP_RAY_HIT;
+    } else {
+      o.status = RMP_RAY_MISS_RANGE;
+      for (uint32_t guard = 0; guard < 3u * (kMaxRangeVoxels + 2); ++guard) {
+        const bool ylx = (unsigned long long)N[1] * A[0] < (unsigned long long)N[0] * A[1];
+        const uint32_t nw = ylx ? N[1] : N[0];
+        const uint32_t aw = ylx ? A[1] : A[0];
+        const bool zlw = (unsigned long long)N[2] * aw < (unsigned long long)nw * A[2];
+        const int ax = zlw ? 2 : (ylx ? 1 : 0);
+        const uint32_t na = zlw ? N[2] : nw;
+        const uint32_t aa = zlw ? A[2] : aw;
+        const uint32_t la = ax == 0 ? L[0] : (ax == 1 ? L[1] : L[2]);
+        if (na > la) break;                                   // next voxel beyond range
+        o.n_last = na;
+        o.a_last = aa;
+        o.steps += 1;
+        bool crossed = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (ax == a) {
+            const int kn = k[a] + s[a];
+            crossed = ((kn ^ k[a]) & ~7) != 0;
+            k[a] = kn;
+            N[a] += 65536u;
+          }
+        }
+        if (KIND == RMP_MAP_DENSE_U8 &&
+            ((unsigned)k[0] >= (unsigned)m.dims[0] || (unsigned)k[1] >= (unsigned)m.dims[1] ||
+             (unsigned)k[2] >= (unsigned)m.dims[2])) {
+          o.status = RMP_RAY_MISS_EXIT;
+          break;
+        }
+        if (crossed) {
+          staged = stage_brick<KIND>(m, k[0] >> 3, k[1] >> 3, k[2] >> 3, cache, stride);
+          o.blocks += 1;
+        }
+        if (staged && cached_bit(cache, stride, k[0], k[1], k[2])) {
+          o.status = RMP_RAY_HIT;
+          break;
+        }
+      }
+    }
+  }
+  o.k[0] = k[0];
+  o.k[1] = k[1];
+  o.k[2] = k[2];
+  return o;
+}
+
+__device__ __forceinline__ float entry_distance(uint32_t n, uint32_t a, float vs_f) {
+  const float t = __fdiv_rn(__uint2float_rn(n), __uint2float_rn(a));
+  return __fmul_rn(__fmul_rn(t, 256.0f), vs_f);
+}
+
+// ------------------------------------------------------------------ obstacle policy (Sec. III-C)
+// u: unit direction towards the obstacle (r = -u points away), d: distance; the velocity
+// is carried as an unevaluated FP32 pair vh + vl (= xdot to ~2^-48 relative).  Writes
+// f_i (3), A_i (6 unique) and A_i f_i (3).  `active` and `in_radius` are the FP32
+// decisions specified in the header; the values are FP32 except that xdot.r is a
+// compensated dot product (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005)
+// because f_damp amplifies its rounding error by eta_damp / eps at small d, and w_r uses
+// (r - d) formed exactly instead of 1 - d/r, which cancels near the radius.
+__device__ __forceinline__ float dot2(const float vh[3], const float vl[3], const float r[3]) {
+  float p = __fmul_rn(vh[0], r[0]);
+  float e = __fmaf_rn(vh[0], r[0], -p);
+#pragma unroll
+  for (int a = 1; a < 3; ++a) {
+    const float h = __fmul_rn(vh[a], r[a]);
+    const float eh = __fmaf_rn(vh[a], r[a], -h);
+    const float t = __fadd_rn(p, h);
+    const float bp = __fsub_rn(t, p);
+    const float es = __fadd_rn(__fsub_rn(p, __fsub_rn(t, bp)), __fsub_rn(h, bp));
+    p = t;
+    e = __fadd_rn(e, __fadd_rn(eh, es));
+  }
+  const float lo = vl[0] * r[0] + vl[1] * r[1] + vl[2] * r[2];
+  return __fadd_rn(p, __fadd_rn(e, lo));
+}
+
+__device__ __forceinline__ void obstacle_policy(const EvalConsts& k, const float u[3], float d,
+                                                const float vh[3], const float vl[3],
+                                                bool active, bool in_radius, float f[3],
+                                                float A[6], float af[3]) {
+  const float r[3] = {-u[0], -u[1], -u[2]};
+  const float frep = k.eta_rep * expf(-d * k.inv_nu_rep);
+  const float xr = dot2(vh, vl, r);
+  const float mm = active ? xr * xr : 0.0f;
+  const float kd = k.eta_damp / (d * k.inv_nu_damp + k.eps);
+  const float z = kd * mm;                       // |f_damp| (|r| = 1)
+  const float fr = frep + z;                     // f = (f_rep + |f_damp|) r
+  f[0] = fr * r[0];
+  f[1] = fr * r[1];
+  f[2] = fr * r[2];
+  float w = 0.0f;
+  if (in_radius) {
+    const float y = (__fsub_rn(k.r_hi, d) + k.r_lo) * k.inv_r;   // 1 - d/r
+    const float x = d * k.inv_r;
+    w = k.w_mode == 0 ? y * y : y * y * (1.0f + 2.0f * x);      // (1-x)^2 ; 1-3x^2+2x^3
+  }
+  const float h = z + k.c * log1pf(expf(-2.0f * k.c * z));
+  const float sc = z / h;                        // s(f_damp) = sc * r
+  const float alpha = w * sc * sc;               // A = alpha r r^T
+  A[0] = alpha * r[0] * r[0];
+  A[1] = alpha * r[0] * r[1];
+  A[2] = alpha * r[0] * r[2];
+  A[3] = alpha * r[1] * r[1];
+  A[4] = alpha * r[1] * r[2];
+  A[5] = alpha * r[2] * r[2];
+  const float rf = r[0] * f[0] + r[1] * f[1] + r[2] * f[2];
+  const float g = alpha * rf;                    // A f = alpha (r.f) r
+  af[0] = g * r[0];
+  af[1] = g * r[1];
+  af[2] = g * r[2];
+}
+
+__device__ __forceinline__ bool active32(const float v[3], const float u[3]) {
+  const float dot = __fmaf_rn(v[2], u[2], __fmaf_rn(v[1], u[1], __fmul_rn(v[0], u[0])));
+  return dot > 0.0f;
+}
+
+// ------------------------------------------------------------------ reduction
+// Compensated FP32 accumulator: (s, c) with s + c the running sum; additions use the
+// error-free TwoSum so the tree keeps about twice FP32's precision.
+struct Acc32 {
+  float s[9], c[9];
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+__device__ __forceinline__ void acc_add(Acc32& acc, const float v[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    float s, e;
+    two_sum(acc.s[q], v[q], s, e);
+    acc.s[q] = s;
+    acc.c[q] = __fadd_rn(acc.c[q], e);
+  }
+}
+
+__device__ __forceinline__ void acc_merge(Acc32& acc, float s2, float c2, int q) {
+  float s, e;
+  two_sum(acc.s[q], s2, s, e);
+  acc.s[q] = s;
+  acc.c[q] = __fadd_rn(__fadd_rn(acc.c[q], c2), e);
+}
+
+struct Acc64 {
+  double s[9];
+};
+
+// Block-level reduction of the per-thread accumulators into 9 doubles (thread 0).
+template <int RED>
+struct BlockReduce;
+
+template <>
+struct BlockReduce<RMP_REDUCE_KAHAN32> {
+  using Acc = Acc32;
+  __device__ static void init(Acc& a) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) a.s[q] = a.c[q] = 0.0f;
+  }
+  __device__ static void add(Acc& a, const float v[9]) { acc_add(a, v); }
+  __device__ static void reduce(Acc& a, double out[9]) {
+    __shared__ float sh[32][18];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const float s2 = __shfl_down_sync(0xffffffffu, a.s[q], off);
+        const float c2 = __shfl_down_sync(0xffffffffu, a.c[q], off);
+        acc_merge(a, s2, c2, q);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        sh[warp][q] = a.s[q];
+        sh[warp][9 + q] = a.c[q];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < nw; ++w)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc_merge(a, sh[w][q], sh[w][9 + q], q);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) out[q] = (double)a.s[q] + (double)a.c[q];
+    }
+  }
+};
+
+template <>
+struct BlockReduce<RMP_REDUCE_FP64> {
+  using Acc = Acc64;
+  __device__ static void init(Acc& a) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) a.s[q] = 0.0;
+  }
+  __device__ static void add(Acc& a, const float v[9]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) a.s[q] += (double)v[q];
+  }
+  __device__ static void reduce(Acc& a, double out[9]) {
+    __shared__ double sh[32][9];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < 9; ++q) a.s[q] += __shfl_down_sync(0xffffffffu, a.s[q], off);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < 9; ++q) sh[warp][q] = a.s[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < nw; ++w)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) a.s[q] += sh[w][q];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) out[q] = a.s[q];
+    }
+  }
+};
+
+__device__ __forceinline__ unsigned block_sum_u32(unsigned v) {
+  __shared__ unsigned shu[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = __reduce_add_sync(0xffffffffu, v);
+  if (lane == 0) shu[warp] = v;
+  __syncthreads();
+  unsigned t = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) t += shu[w];
+  __syncthreads();
+  return t;
+}
+
+// ------------------------------------------------------------------ FP64 resolve (Eq. 1)
+// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations, then
+// f = sum over eigenvalues > 1e-12 lambda_max of (q^T b / lambda) q.
+__device__ void resolve_pinv(const double S[6], const double b[3], rmp_result_t& r) {
+  double a00 = S[0], a01 = S[1], a02 = S[2], a11 = S[3], a12 = S[4], a22 = S[5];
+  double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int sweep = 0; sweep < 32; ++sweep) {
+    const double off = fabs(a01) + fabs(a02) + fabs(a12);
+    const double dia = fabs(a00) + fabs(a11) + fabs(a22);
+    if (off == 0.0 || off <= 1e-18 * dia) break;
+    for (int pq = 0; pq < 3; ++pq) {
+      // rotation in plane (p,q) in {(0,1), (0,2), (1,2)}; o is the remaining index
+      double app, aqq, apq, apo, aqo;
+      if (pq == 0) { app = a00; aqq = a11; apq = a01; apo = a02; aqo = a12; }
+      else if (pq == 1) { app = a00; aqq = a22; apq = a02; apo = a01; aqo = a12; }
+      else { app = a11; aqq = a22; apq = a12; apo = a01; aqo = a02; }
+      if (apq == 0.0) continue;
+      const double tau = (aqq - app) / (2.0 * apq);
+      const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      const double c = rsqrt(1.0 + t * t), s = t * c;
+      const double npp = app - t * apq, nqq = aqq + t * apq;
+      const double npo = c * apo - s * aqo, nqo = s * apo + c * aqo;
+      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      if (pq == 0) { a00 = npp; a11 = nqq; a01 = 0.0; a02 = npo; a12 = nqo; }
+      else if (pq == 1) { a00 = npp; a22 = nqq; a02 = 0.0; a01 = npo; a12 = nqo; }
+      else { a11 = npp; a22 = nqq; a12 = 0.0; a01 = npo; a02 = nqo; }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double vp = V[i][p], vq = V[i][q];
+        V[i][p] = c * vp - s * vq;
+        V[i][q] = s * vp + c * vq;
+      }
+    }
+  }
+  double lam[3] = {a00, a11, a22};
+  int idx[3] = {0, 1, 2};
+  if (lam[idx[1]] < lam[idx[0]]) { int t = idx[0]; idx[0] = idx[1]; idx[1] = t; }
+  if (lam[idx[2]] < lam[idx[1]]) { int t = idx[1]; idx[1] = idx[2]; idx[2] = t; }
+  if (lam[idx[1]] < lam[idx[0]]) { int t = idx[0]; idx[0] = idx[1]; idx[1] = t; }
+  const double lmax = lam[idx[2]];
+  double f[3] = {0.0, 0.0, 0.0};
+  uint32_t rank = 0;
+  for (int i = 0; i < 3; ++i) {
+    const int e = idx[i];
+    r.eig[i] = lam[e];
+    if (!(lmax > 1e-300) || lam[e] <= 1e-12 * lmax) continue;
+    ++rank;
+    const double proj = (V[0][e] * b[0] + V[1][e] * b[1] + V[2][e] * b[2]) / lam[e];
+    f[0] += proj * V[0][e];
+    f[1] += proj * V[1][e];
+    f[2] += proj * V[2][e];
+  }
+  r.f[0] = f[0];
+  r.f[1] = f[1];
+  r.f[2] = f[2];
+  r.rank = rank;
+}
+
+// Grid completion: every CTA stores its partial; the last one (ticket) sums all partials
+// in index order in FP64 and resolves.  Called by all threads of every CTA.
+__device__ void grid_finish(const double part[9], unsigned hits, unsigned act, WsHeader* ws,
+                            CtaPartial* parts, rmp_result_t* out, uint32_t n_rays, int status) {
+  __shared__ bool last;
+  __shared__ double tot[9];
+  __shared__ unsigned tot_h, tot_a;
+  if (threadIdx.x == 0) {
+    CtaPartial p;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) p.v[q] = part[q];
+    p.n_hits = hits;
+    p.n_active = act;
+    parts[blockIdx.x] = p;
+    __threadfence();
+    const unsigned t = atomicAdd(&ws->ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = gridDim.x;
+  for (int q = warp; q < 11; q += nw) {
+    if (q < 9) {
+      double s = 0.0;
+      for (int g = lane; g < G; g += 32) s += __ldcg(&parts[g].v[q]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (lane == 0) tot[q] = s;
+    } else {
+      unsigned s = 0;
+      for (int g = lane; g < G; g += 32)
+        s += __ldcg(q == 9 ? &parts[g].n_hits : &parts[g].n_active);
+      s = __reduce_add_sync(0xffffffffu, s);
+      if (lane == 0) (q == 9 ? tot_h : tot_a) = s;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    rmp_result_t r;
+    for (int q = 0; q < 6; ++q) r.A[q] = tot[q];
+    for (int q = 0; q < 3; ++q) r.Af[q] = tot[6 + q];
+    r.n_rays = n_rays;
+    r.n_hits = tot_h;
+    r.n_active = tot_a;
+    r.status = status;
+    r.reserved = 0;
+    resolve_pinv(r.A, r.Af, r);
+    *out = r;
+    ws->ticket = 0;                   // ready for the next evaluation
+  }
+}
+
+// Per-CTA state: quantised position (FP64, once per CTA) and FP32 velocity.
+struct CtaState {
+  long long P[3];
+  float v[3];     // RN32(xdot)
+  float vl[3];    // RN32(xdot - v)
+  float xf[3];
+  int bad;
+};
+
+__device__ __forceinline__ void split_velocity(const double* state, CtaState& cs) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double x = state[3 + a];
+    cs.v[a] = __double2float_rn(x);
+    cs.vl[a] = __double2float_rn(__dsub_rn(x, (double)cs.v[a]));
+  }
+}
+
+// ------------------------------------------------------------------ fused raycast kernel
+template <int KIND, int RED>
+__global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k,
+                                                          const double* __restrict__ state,
+                                                          WsHeader* ws, CtaPartial* parts,
+                                                          rmp_result_t* out, rmp_ray_hit_t* hits,
+                                                          float* per_ray) {
+  extern __shared__ uint32_t brick_cache[];
+  __shared__ CtaState cs;
+  if (threadIdx.x == 0) {
+    int bad = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double o = KIND == RMP_MAP_DENSE_U8 ? m.origin[a] : 0.0;
+      const double q = __dmul_rn(__ddiv_rn(__dsub_rn(state[a], o), m.vs), 65536.0);
+      // |voxel| < 2^22 keeps block keys and fixed-point products in range; NaN fails too
+      if (!(fabs(q) < 274877906944.0)) bad = 1;
+      cs.P[a] = bad ? 0 : __double2ll_rn(q);
+    }
+    split_velocity(state, cs);
+    cs.bad = bad;
+  }
+  __syncthreads();
+  typename BlockReduce<RED>::Acc acc;
+  BlockReduce<RED>::init(acc);
+  unsigned n_hit = 0, n_act = 0;
+  uint32_t* cache = brick_cache + threadIdx.x;
+  const int stride = blockDim.x;
+  if (!cs.bad) {
+    const long long P[3] = {cs.P[0], cs.P[1], cs.P[2]};
+    const float v[3] = {cs.v[0], cs.v[1], cs.v[2]};
+    const float vl[3] = {cs.vl[0], cs.vl[1], cs.vl[2]};
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < k.n_rays;
+         j += gridDim.x * blockDim.x) {
+      const Ray ray = make_ray(j + k.halton_offset);
+      const MarchOut mo = march<KIND>(m, P, ray.D, k.R_fx, cache, stride);
+      const float d = mo.n_last == 0 ? 0.0f : entry_distance(mo.n_last, mo.a_last, m.vs_f);
+      float f[3] = {0.f, 0.f, 0.f}, A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, af[3];
+      if (mo.status == RMP_RAY_HIT) {
+        const bool act = active32(v, ray.dir);
+        const bool inr = d < k.r_up;
+        n_hit += 1;
+        n_act += (act && inr) ? 1u : 0u;
+        obstacle_policy(k, ray.dir, d, v, vl, act, inr, f, A, af);
+        const float vals[9] = {A[0], A[1], A[2], A[3], A[4], A[5], af[0], af[1], af[2]};
+        BlockReduce<RED>::add(acc, vals);
+      }
+      if (hits) {
+        rmp_ray_hit_t h;
+        h.voxel[0] = mo.k[0];
+        h.voxel[1] = mo.k[1];
+        h.voxel[2] = mo.k[2];
+        h.steps = mo.steps;
+        h.d = d;
+        h.status = (uint8_t)mo.status;
+        h.pad = 0;
+        h.blocks = (uint16_t)mo.blocks;
+        hits[j] = h;
+      }
+      if (per_ray) {
+        float* o = per_ray + 9 * (size_t)j;
+        o[0] = f[0]; o[1] = f[1]; o[2] = f[2];
+        o[3] = A[0]; o[4] = A[1]; o[5] = A[2]; o[6] = A[3]; o[7] = A[4]; o[8] = A[5];
+      }
+    }
+  }
+  double part[9];
+  BlockReduce<RED>::reduce(acc, part);
+  const unsigned bh = block_sum_u32(n_hit);
+  const unsigned ba = block_sum_u32(n_act);
+  grid_finish(part, bh, ba, ws, parts, out, k.n_rays, cs.bad ? RMP_ERR_INVALID_ARG : RMP_OK);
+}
+
+// ------------------------------------------------------------------ LiDAR scan kernel (Sec. III-G)
+template <int RED>
+__global__ void __launch_bounds__(256) scan_rmp_kernel(const float* __restrict__ pts,
+                                                       EvalConsts k,
+                                                       const double* __restrict__ state,
+                                                       WsHeader* ws, CtaPartial* parts,
+                                                       rmp_result_t* out, float* per_ray) {
+  __shared__ CtaState cs;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cs.xf[a] = __double2float_rn(state[a]);
+    split_velocity(state, cs);
+    cs.bad = 0;
+  }
+  __syncthreads();
+  typename BlockReduce<RED>::Acc acc;
+  BlockReduce<RED>::init(acc);
+  unsigned n_hit = 0, n_act = 0;
+  const float v[3] = {cs.v[0], cs.v[1], cs.v[2]};
+  const float vl[3] = {cs.vl[0], cs.vl[1], cs.vl[2]};
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < k.n_rays;
+       j += gridDim.x * blockDim.x) {
+    float q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q[a] = __fsub_rn(__ldg(pts + 3 * (size_t)j + a), cs.xf[a]);
+    float f[3] = {0.f, 0.f, 0.f}, A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, af[3];
+    bool valid = isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]);
+    float d = 0.0f;
+    if (valid) {
+      d = __fsqrt_rn(__fmaf_rn(q[2], q[2], __fmaf_rn(q[1], q[1], __fmul_rn(q[0], q[0]))));
+      valid = d > 0.0f && d >= k.min_up && d <= k.max_dn;
+    }
+    if (valid) {
+      const float u[3] = {__fdiv_rn(q[0], d), __fdiv_rn(q[1], d), __fdiv_rn(q[2], d)};
+      const bool act = active32(v, u);
+      const bool inr = d < k.r_up;
+      n_hit += 1;
+      n_act += (act && inr) ? 1u : 0u;
+      obstacle_policy(k, u, d, v, vl, act, inr, f, A, af);
+      const float vals[9] = {A[0], A[1], A[2], A[3], A[4], A[5], af[0], af[1], af[2]};
+      BlockReduce<RED>::add(acc, vals);
+    }
+    if (per_ray) {
+      float* o = per_ray + 9 * (size_t)j;
+      o[0] = f[0]; o[1] = f[1]; o[2] = f[2];
+      o[3] = A[0]; o[4] = A[1]; o[5] = A[2]; o[6] = A[3]; o[7] = A[4]; o[8] = A[5];
+    }
+  }
+  double part[9];
+  BlockReduce<RED>::reduce(acc, part);
+  const unsigned bh = block_sum_u32(n_hit);
+  const unsigned ba = block_sum_u32(n_act);
+  grid_finish(part, bh, ba, ws, parts, out, k.n_rays, RMP_OK);
+}
+
+// ------------------------------------------------------------------ map build kernels
+// Dense grid -> bricks: thread per (brick, word); word w covers lz = w/2 and
+// ly = 4 (w&1) .. +3, lx = 0..7.
+__global__ void dense_bricks_kernel(const uint8_t* __restrict__ occ, int dx, int dy, int dz,
+                                    int nbx, int nby, int nbz, uint32_t* __restrict__ bricks) {
+  const size_t total = (size_t)nbx * nby * nbz * kBrickWords;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t brick = idx / kBrickWords;
+    const int w = (int)(idx % kBrickWords);
+    const int bx = (int)(brick % nbx), by = (int)((brick / nbx) % nby), bz = (int)(brick / ((size_t)nbx * nby));
+    const int z = bz * 8 + (w >> 1);
+    uint32_t word = 0;
+    for (int r = 0; r < 4; ++r) {
+      const int y = by * 8 + 4 * (w & 1) + r;
+      for (int lx = 0; lx < 8; ++lx) {
+        const int x = bx * 8 + lx;
+        if (x < dx && y < dy && z < dz && occ[(size_t)x + (size_t)dx * ((size_t)y + (size_t)dy * z)] != 0)
+          word |= 1u << (lx + 8 * r);
+      }
+    }
+    bricks[idx] = word;
+  }
+}
+
+// TSDF blocks -> bricks: bit b of block n is tsdf[n*512 + b] <= 0 (the TSDF voxel order
+// lx + 8 ly + 64 lz is the brick's bit order).
+__global__ void tsdf_bricks_kernel(const float* __restrict__ tsdf, uint32_t n_blocks,
+                                   uint32_t* __restrict__ bricks) {
+  const size_t total = (size_t)n_blocks * kBrickWords;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const float* t = tsdf + idx * 32;
+    uint32_t word = 0;
+#pragma unroll 8
+    for (int b = 0; b < 32; ++b) word |= (t[b] <= 0.0f ? 1u : 0u) << b;
+    bricks[idx] = word;
+  }
+}
+
+// Insert block keys into the open-addressing table (linear probing, bounded).
+// err bits: 1 key out of range, 2 duplicate key, 4 table full.
+__global__ void hash_build_kernel(const int32_t* __restrict__ keys, uint32_t n_blocks,
+                                  HashEntry* table, uint32_t cap_mask, int hash_shift,
+                                  unsigned int* err) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks;
+       b += gridDim.x * blockDim.x) {
+    const int bx = keys[3 * (size_t)b], by = keys[3 * (size_t)b + 1], bz = keys[3 * (size_t)b + 2];
+    if (bx < -kKeyBias || bx >= kKeyBias || by < -kKeyBias || by >= kKeyBias ||
+        bz < -kKeyBias || bz >= kKeyBias) {
+      atomicOr(err, 1u);
+      continue;
+    }
+    const unsigned long long key = (unsigned long long)(uint32_t)(bx + kKeyBias) |
+                                   ((unsigned long long)(uint32_t)(by + kKeyBias) << 21) |
+                                   ((unsigned long long)(uint32_t)(bz + kKeyBias) << 42);
+    uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> hash_shift);
+    bool done = false;
+    for (uint32_t probe = 0; probe <= cap_mask; ++probe) {
+      const unsigned long long prev = atomicCAS(&table[h].key, kEmptyKey, key);
+      if (prev == kEmptyKey) {
+        table[h].slot = b;
+        done = true;
+        break;
+      }
+      if (prev == key) {
+        atomicOr(err, 2u);
+        done = true;
+        break;
+      }
+      h = (h + 1) & cap_mask;
+    }
+    if (!done) atomicOr(err, 4u);
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,
+                           void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
+                           float* per_ray, int block, int grid, cudaStream_t stream) {
+  WsHeader* hdr = (WsHeader*)ws;
+  CtaPartial* parts = (CtaPartial*)((char*)ws + kWsHeaderBytes);
+  const size_t smem = (size_t)kBrickWords * sizeof(uint32_t) * block;
+  if (m.kind == RMP_MAP_DENSE_U8) {
+    if (k.reduce_mode == RMP_REDUCE_FP64)
+      raycast_rmp_kernel<RMP_MAP_DENSE_U8, RMP_REDUCE_FP64><<<grid, block, smem, stream>>>(
+          m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
+    else
+      raycast_rmp_kernel<RMP_MAP_DENSE_U8, RMP_REDUCE_KAHAN32><<<grid, block, smem, stream>>>(
+          m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
+  } else {
+    if (k.reduce_mode == RMP_REDUCE_FP64)
+      raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, RMP_REDUCE_FP64><<<grid, block, smem, stream>>>(
+          m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
+    else
+      raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, RMP_REDUCE_KAHAN32><<<grid, block, smem, stream>>>(
+          m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const float* pts, const EvalConsts& k, const double* state_dev,
+                        void* ws, rmp_result_t* out_dev, float* per_ray, int block, int grid,
+                        cudaStream_t stream) {
+  WsHeader* hdr = (WsHeader*)ws;
+  CtaPartial* parts = (CtaPartial*)((char*)ws + kWsHeaderBytes);
+  if (k.reduce_mode == RMP_REDUCE_FP64)
+    scan_rmp_kernel<RMP_REDUCE_FP64><<<grid, block, 0, stream>>>(pts, k, state_dev, hdr, parts,
+                                                                 out_dev, per_ray);
+  else
+    scan_rmp_kernel<RMP_REDUCE_KAHAN32><<<grid, block, 0, stream>>>(pts, k, state_dev, hdr, parts,
+                                                                    out_dev, per_ray);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_bricks(const uint8_t* occ, const int dims[3], const int nb[3],
+                                uint32_t* bricks, cudaStream_t stream) {
+  const size_t total = (size_t)nb[0] * nb[1] * nb[2] * kBrickWords;
+  const int grid = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
+  dense_bricks_kernel<<<grid, 256, 0, stream>>>(occ, dims[0], dims[1], dims[2], nb[0], nb[1],
+                                                nb[2], bricks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tsdf_bricks(const float* tsdf, uint32_t n_blocks, uint32_t* bricks,
+                               cudaStream_t stream) {
+  const size_t total = (size_t)n_blocks * kBrickWords;
+  const int grid = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
+  tsdf_bricks_kernel<<<grid, 256, 0, stream>>>(tsdf, n_blocks, bricks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hash_build(const int32_t* keys, uint32_t n_blocks, HashEntry* table,
+                              uint32_t cap_mask, int hash_shift, unsigned int* err,
+                              cudaStream_t stream) {
+  const int grid = (int)((n_blocks + 255) / 256 < 65535 ? (n_blocks + 255) / 256 : 65535);
+  hash_build_kernel<<<grid > 0 ? grid : 1, 256, 0, stream>>>(keys, n_blocks, table, cap_mask,
+                                                             hash_shift, err);
+  return cudaGetLastError();
+}
+
+}  // namespace rmp

@@ -1,0 +1,324 @@
+"""Thin ctypes binding of librmp.so (include/rmp.h): the same names as the C ABI, argument
+marshalling only.  Device buffers are passed as torch CUDA tensors (their data_ptr) and
+streams as torch.cuda.Stream objects (or raw cudaStream_t integers); every step of the
+computation runs in the library's kernels.
+
+Loading fails loudly (RuntimeError) when the library has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+RMP_OK = 0
+STATUS_NAMES = {0: "RMP_OK", 1: "RMP_ERR_INVALID_ARG", 2: "RMP_ERR_NO_MEMORY", 3: "RMP_ERR_CUDA",
+                4: "RMP_ERR_TIMEOUT", 5: "RMP_ERR_BUSY", 6: "RMP_ERR_UNKNOWN_MAP",
+                7: "RMP_ERR_NOT_READY"}
+RMP_RAY_HIT, RMP_RAY_MISS_RANGE, RMP_RAY_MISS_EXIT = 1, 2, 3
+RMP_MAP_DENSE_U8, RMP_MAP_HASHED_TSDF = 0, 1
+RMP_PRESET_STATIC_MAP, RMP_PRESET_LIDAR = 0, 1
+RMP_REDUCE_KAHAN32, RMP_REDUCE_FP64 = 0, 1
+
+
+class RmpError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s failed: %s (%d)" % (what, STATUS_NAMES.get(status, "?"), status))
+        self.status = status
+
+
+class rmp_params_t(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("eta_rep", "nu_rep", "eta_damp", "nu_damp", "r", "c",
+                                          "eps", "max_range", "min_range")] + \
+               [(n, C.c_uint32) for n in ("halton_offset", "w_mode", "reduce_mode", "flags")]
+
+
+class rmp_result_t(C.Structure):
+    _fields_ = [("f", C.c_double * 3), ("A", C.c_double * 6), ("Af", C.c_double * 3),
+                ("eig", C.c_double * 3), ("n_rays", C.c_uint32), ("n_hits", C.c_uint32),
+                ("n_active", C.c_uint32), ("rank", C.c_uint32), ("status", C.c_int32),
+                ("reserved", C.c_uint32)]
+
+
+class rmp_ray_hit_t(C.Structure):
+    _fields_ = [("voxel", C.c_int32 * 3), ("steps", C.c_uint32), ("d", C.c_float),
+                ("status", C.c_uint8), ("pad", C.c_uint8), ("blocks", C.c_uint16)]
+
+
+class rmp_map_desc_t(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("data_on_device", C.c_int32), ("voxel_size", C.c_double),
+                ("origin", C.c_double * 3), ("dims", C.c_int32 * 3), ("n_blocks", C.c_uint32),
+                ("occ", C.c_void_p), ("block_keys", C.c_void_p), ("tsdf", C.c_void_p)]
+
+
+class rmp_map_info_t(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_bricks", C.c_uint32), ("hash_capacity", C.c_uint32),
+                ("reserved", C.c_uint32), ("device_bytes", C.c_uint64)]
+
+
+assert C.sizeof(rmp_result_t) == 144 and C.sizeof(rmp_ray_hit_t) == 24
+
+RESULT_BYTES = C.sizeof(rmp_result_t)
+HIT_DTYPE = np.dtype([("voxel", "<i4", (3,)), ("steps", "<u4"), ("d", "<f4"),
+                      ("status", "u1"), ("pad", "u1"), ("blocks", "<u2")])
+
+_P = C.c_void_p
+_SIGNATURES = {
+    "rmp_ctx_create": [C.POINTER(C.c_void_p), C.c_int],
+    "rmp_ctx_destroy": [_P],
+    "rmp_params_preset": [C.c_int, C.POINTER(rmp_params_t)],
+    "rmp_map_upload": [_P, C.POINTER(rmp_map_desc_t), _P, C.POINTER(C.c_uint32)],
+    "rmp_map_release": [_P, C.c_uint32],
+    "rmp_map_info": [_P, C.c_uint32, C.POINTER(rmp_map_info_t)],
+    "rmp_workspace_init": [_P, C.c_size_t, _P],
+    "rmp_raycast_eval": [_P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(rmp_params_t), _P,
+                         C.POINTER(rmp_result_t), _P, _P],
+    "rmp_raycast_eval_async": [_P, C.c_uint32, _P, C.c_uint32, C.POINTER(rmp_params_t), _P,
+                               C.c_size_t, _P, _P, _P, _P],
+    "rmp_scan_eval": [_P, _P, C.c_uint32, _P, _P, C.POINTER(rmp_params_t), _P,
+                      C.POINTER(rmp_result_t), _P],
+    "rmp_scan_eval_async": [_P, _P, C.c_uint32, _P, C.POINTER(rmp_params_t), _P, C.c_size_t, _P,
+                            _P, _P],
+}
+# Symbols every build must export (checked by the not-gpu ABI test against include/rmp.h).
+EXPORTS = sorted(list(_SIGNATURES) + ["rmp_status_string", "rmp_workspace_bytes"])
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib() -> C.CDLL:
+    """Load librmp.so (building it if the sources are newer).  Raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                try:
+                    _build.build()
+                except Exception as e:  # no toolchain: fail loudly, never fall back
+                    raise RuntimeError("librmp.so is missing or stale and could not be built: %s"
+                                       % e) from e
+            L = C.CDLL(path)
+            for name, args in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = C.c_int
+            L.rmp_status_string.argtypes = [C.c_int]
+            L.rmp_status_string.restype = C.c_char_p
+            L.rmp_workspace_bytes.argtypes = []
+            L.rmp_workspace_bytes.restype = C.c_size_t
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != RMP_OK:
+        raise RmpError(status, what)
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _vec3(v):
+    a = (C.c_double * 3)(*[float(x) for x in np.asarray(v, np.float64).reshape(3)])
+    return a
+
+
+def make_params(d: dict, max_range: float) -> rmp_params_t:
+    p = rmp_params_t()
+    for k in ("eta_rep", "nu_rep", "eta_damp", "nu_damp", "r", "c", "eps", "min_range"):
+        setattr(p, k, float(d[k]))
+    p.max_range = float(max_range)
+    p.halton_offset = int(d.get("halton_offset", 1))
+    p.w_mode = int(d.get("w_mode", 0))
+    p.reduce_mode = int(d.get("reduce_mode", 0))
+    p.flags = 0
+    return p
+
+
+def result_dict(r: rmp_result_t) -> dict:
+    return dict(f=np.array(r.f[:]), sumA=np.array(r.A[:]), sumAf=np.array(r.Af[:]),
+                eig=np.array(r.eig[:]), n_rays=r.n_rays, n_hits=r.n_hits, n_active=r.n_active,
+                rank=r.rank, status=r.status)
+
+
+def result_from_bytes(b: bytes) -> dict:
+    return result_dict(rmp_result_t.from_buffer_copy(b))
+
+
+# ----------------------------------------------------------------------------- C-named calls
+def rmp_status_string(status: int) -> str:
+    return lib().rmp_status_string(int(status)).decode()
+
+
+def rmp_params_preset(preset: int) -> rmp_params_t:
+    p = rmp_params_t()
+    _check(lib().rmp_params_preset(int(preset), C.byref(p)), "rmp_params_preset")
+    return p
+
+
+def rmp_workspace_bytes() -> int:
+    return int(lib().rmp_workspace_bytes())
+
+
+def rmp_ctx_create(device: int = 0) -> int:
+    h = C.c_void_p()
+    _check(lib().rmp_ctx_create(C.byref(h), int(device)), "rmp_ctx_create")
+    return h.value
+
+
+def rmp_ctx_destroy(ctx: int):
+    _check(lib().rmp_ctx_destroy(ctx), "rmp_ctx_destroy")
+
+
+def rmp_map_upload(ctx: int, desc: rmp_map_desc_t, stream=None) -> int:
+    mid = C.c_uint32()
+    _check(lib().rmp_map_upload(ctx, C.byref(desc), _stream(stream), C.byref(mid)), "rmp_map_upload")
+    return int(mid.value)
+
+
+def rmp_map_release(ctx: int, map_id: int):
+    _check(lib().rmp_map_release(ctx, int(map_id)), "rmp_map_release")
+
+
+def rmp_map_info(ctx: int, map_id: int) -> dict:
+    info = rmp_map_info_t()
+    _check(lib().rmp_map_info(ctx, int(map_id), C.byref(info)), "rmp_map_info")
+    return dict(kind=info.kind, n_bricks=info.n_bricks, hash_capacity=info.hash_capacity,
+                device_bytes=info.device_bytes)
+
+
+def rmp_workspace_init(workspace, stream=None):
+    _check(lib().rmp_workspace_init(_dptr(workspace), workspace.numel() * workspace.element_size(),
+                                    _stream(stream)), "rmp_workspace_init")
+
+
+def rmp_raycast_eval(ctx: int, map_id: int, x, xdot, n_rays: int, params: rmp_params_t,
+                     stream=None, hits=None, per_ray=None) -> dict:
+    out = rmp_result_t()
+    _check(lib().rmp_raycast_eval(ctx, int(map_id), _vec3(x), _vec3(xdot), int(n_rays),
+                                  C.byref(params), _stream(stream), C.byref(out), _dptr(hits),
+                                  _dptr(per_ray)), "rmp_raycast_eval")
+    return result_dict(out)
+
+
+def rmp_raycast_eval_async(ctx: int, map_id: int, state, n_rays: int, params: rmp_params_t,
+                           workspace, out, stream=None, hits=None, per_ray=None):
+    _check(lib().rmp_raycast_eval_async(ctx, int(map_id), _dptr(state), int(n_rays), C.byref(params),
+                                        _dptr(workspace),
+                                        workspace.numel() * workspace.element_size(),
+                                        _stream(stream), _dptr(out), _dptr(hits), _dptr(per_ray)),
+           "rmp_raycast_eval_async")
+
+
+def rmp_scan_eval(ctx: int, points, x, xdot, params: rmp_params_t, stream=None,
+                  per_ray=None) -> dict:
+    out = rmp_result_t()
+    n = points.shape[0]
+    _check(lib().rmp_scan_eval(ctx, _dptr(points), int(n), _vec3(x), _vec3(xdot), C.byref(params),
+                               _stream(stream), C.byref(out), _dptr(per_ray)), "rmp_scan_eval")
+    return result_dict(out)
+
+
+def rmp_scan_eval_async(ctx: int, points, state, params: rmp_params_t, workspace, out,
+                        stream=None, per_ray=None):
+    n = points.shape[0]
+    _check(lib().rmp_scan_eval_async(ctx, _dptr(points), int(n), _dptr(state), C.byref(params),
+                                     _dptr(workspace), workspace.numel() * workspace.element_size(),
+                                     _stream(stream), _dptr(out), _dptr(per_ray)),
+           "rmp_scan_eval_async")
+
+
+# ----------------------------------------------------------------------------- map descriptors
+def dense_desc(occ, voxel_size: float, origin) -> rmp_map_desc_t:
+    """occ: uint8 array or CUDA tensor shaped (nz, ny, nx) (x fastest)."""
+    d = rmp_map_desc_t()
+    d.kind = RMP_MAP_DENSE_U8
+    d.voxel_size = float(voxel_size)
+    for a in range(3):
+        d.origin[a] = float(origin[a])
+    nz, ny, nx = occ.shape
+    d.dims[0], d.dims[1], d.dims[2] = nx, ny, nz
+    if isinstance(occ, np.ndarray):
+        occ = np.ascontiguousarray(occ, np.uint8)
+        d.data_on_device = 0
+        d.occ = occ.ctypes.data
+        d._keep = occ
+    else:
+        d.data_on_device = 1
+        d.occ = _dptr(occ)
+    return d
+
+
+def hashed_desc(keys, tsdf, voxel_size: float) -> rmp_map_desc_t:
+    """keys: (n, 3) int32, tsdf: (n, 512) float32 -- numpy (host) or CUDA tensors."""
+    d = rmp_map_desc_t()
+    d.kind = RMP_MAP_HASHED_TSDF
+    d.voxel_size = float(voxel_size)
+    d.n_blocks = int(keys.shape[0])
+    if isinstance(keys, np.ndarray):
+        keys = np.ascontiguousarray(keys, np.int32)
+        tsdf = np.ascontiguousarray(tsdf, np.float32)
+        d.data_on_device = 0
+        d.block_keys = keys.ctypes.data if keys.size else None
+        d.tsdf = tsdf.ctypes.data if tsdf.size else None
+        d._keep = (keys, tsdf)
+    else:
+        d.data_on_device = 1
+        d.block_keys = _dptr(keys)
+        d.tsdf = _dptr(tsdf)
+    return d
+
+
+class Context:
+    """Owns one rmp_ctx; convenience wrapper over the C-named calls above."""
+
+    def __init__(self, device: int = 0):
+        self.handle = rmp_ctx_create(device)
+
+    def close(self):
+        if self.handle:
+            rmp_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def upload(self, m, stream=None) -> int:
+        """Upload a workloads.DenseMap / workloads.HashedMap."""
+        if hasattr(m, "occ"):
+            return rmp_map_upload(self.handle, dense_desc(m.occ, m.voxel_size, m.origin), stream)
+        return rmp_map_upload(self.handle, hashed_desc(m.keys, m.tsdf, m.voxel_size), stream)

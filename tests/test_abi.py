@@ -1,0 +1,102 @@
+"""Host-only checks of the C ABI: the library loads, exports every function include/rmp.h
+declares, its structs have the layout the header defines (checked against a C program
+compiled from the header), and pure host calls (presets, status strings) behave.  No
+call here touches a GPU."""
+import ctypes as C
+import json
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rmp.h")
+
+
+@pytest.fixture(scope="module")
+def rmp():
+    from paper_2301_08068_gb300 import build, rmp as R
+    build.build()
+    R.lib()
+    return R
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*(rmp_[a-z_0-9]+)\s*\(",
+                                 text, flags=re.M)))
+
+
+def test_every_declared_function_is_exported(rmp):
+    names = declared_functions()
+    assert len(names) >= 12
+    L = rmp.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(rmp.EXPORTS) == names
+
+
+def test_struct_layouts_match_header(rmp, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "rmp.h"
+#define O(T, f) printf("\\"%s.%s\\": %zu,\\n", #T, #f, offsetof(T, f))
+int main(void) {
+  printf("{\\n");
+  printf("\\"rmp_params_t\\": %zu, \\"rmp_result_t\\": %zu, \\"rmp_ray_hit_t\\": %zu,\\n",
+         sizeof(rmp_params_t), sizeof(rmp_result_t), sizeof(rmp_ray_hit_t));
+  printf("\\"rmp_map_desc_t\\": %zu, \\"rmp_map_info_t\\": %zu,\\n", sizeof(rmp_map_desc_t),
+         sizeof(rmp_map_info_t));
+  O(rmp_params_t, max_range); O(rmp_params_t, halton_offset); O(rmp_params_t, flags);
+  O(rmp_result_t, A); O(rmp_result_t, eig); O(rmp_result_t, n_rays); O(rmp_result_t, status);
+  O(rmp_ray_hit_t, steps); O(rmp_ray_hit_t, d); O(rmp_ray_hit_t, status);
+  O(rmp_map_desc_t, voxel_size); O(rmp_map_desc_t, dims); O(rmp_map_desc_t, n_blocks);
+  O(rmp_map_desc_t, occ); O(rmp_map_desc_t, tsdf); O(rmp_map_info_t, device_bytes);
+  printf("\\"end\\": 0}\\n");
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    got = json.loads(subprocess.check_output([str(exe)]))
+    for T in ("rmp_params_t", "rmp_result_t", "rmp_ray_hit_t", "rmp_map_desc_t", "rmp_map_info_t"):
+        assert C.sizeof(getattr(rmp, T)) == got[T], T
+    for key, off in got.items():
+        if "." in key:
+            T, f = key.split(".")
+            assert getattr(getattr(rmp, T), f).offset == off, key
+    assert got["rmp_result_t"] == 144 and got["rmp_ray_hit_t"] == 24
+
+
+def test_presets_equal_table_one(rmp):
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "table1_params.json")))
+    for preset, col in ((rmp.RMP_PRESET_STATIC_MAP, "static_map"), (rmp.RMP_PRESET_LIDAR, "lidar")):
+        p = rmp.rmp_params_preset(preset)
+        for k in ("c", "eta_rep", "nu_rep", "eta_damp", "nu_damp", "r"):
+            assert getattr(p, k) == gold[col][k], (col, k)
+        assert p.halton_offset == 1 and p.flags == 0
+    with pytest.raises(rmp.RmpError):
+        rmp.rmp_params_preset(7)
+
+
+def test_status_strings(rmp):
+    assert rmp.rmp_status_string(0) == "ok"
+    assert rmp.rmp_status_string(6) == "unknown map id"
+    assert rmp.rmp_status_string(999) == "unknown status"
+
+
+def test_workspace_size_is_fixed(rmp):
+    assert rmp.rmp_workspace_bytes() == 256 + 80 * 4096
+
+
+def test_null_arguments_rejected_without_gpu(rmp):
+    L = rmp.lib()
+    assert L.rmp_ctx_create(None, 0) == 1
+    assert L.rmp_ctx_destroy(None) == 1
+    assert L.rmp_map_release(None, 1) == 1
+    assert L.rmp_raycast_eval(None, 1, None, None, 1, None, None, None, None, None) == 1
+    assert L.rmp_scan_eval(None, None, 1, None, None, None, None, None, None) == 1

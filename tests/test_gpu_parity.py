@@ -1,0 +1,288 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded
+inputs.  Hit records are compared bit for bit; floats within the tolerances stated in
+gpu_helpers.  Sizes span several CTAs with ragged tails, and the full configurations
+(dense 64^3 x 1024 rays; hashed 40x40x10 m x 65536 rays; 64 x 1024 LiDAR scan) run whole.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2301_08068_gb300 import rmp as R
+from paper_2301_08068_gb300 import workloads as W
+
+from gpu_helpers import (assert_hits_exact, assert_per_ray_close, assert_result_close,
+                         gpu_raycast, gpu_scan, torch_cuda)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch_cuda()
+    c = R.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def dense(ctx):
+    wl = W.dense_box_workload(n_states=8, jitter=True)
+    return wl, ctx.upload(wl.map), O.OracleMap(wl.map)
+
+
+@pytest.fixture(scope="module")
+def hashed(ctx):
+    wl = W.hashed_workload(n_states=6)
+    return wl, ctx.upload(wl.map), O.OracleMap(wl.map)
+
+
+def check_raycast(ctx, mid, om, x, xdot, n, pdict, max_range):
+    pg = R.make_params(pdict, max_range)
+    po = O.make_params(pdict, max_range)
+    rg, hg, pgr = gpu_raycast(ctx, mid, x, xdot, n, pg)
+    ro, ho, por = O.raycast_eval(om, x, xdot, n, po)
+    assert_hits_exact(hg, ho)
+    assert_per_ray_close(pgr, por)
+    assert_result_close(rg, ro, por)
+    return rg, ro
+
+
+# ----------------------------------------------------------------------------- dense map
+def test_dense_box_map_full_config(ctx):
+    wl = W.dense_box_workload()
+    mid = ctx.upload(wl.map)
+    s = wl.states[0]
+    rg, ro = check_raycast(ctx, mid, O.OracleMap(wl.map), s.x, s.xdot, wl.n_rays, wl.params,
+                           wl.max_range)
+    assert ro["n_hits"] > 0 and ro["n_active"] > 0
+
+
+def test_dense_jittered_states(ctx, dense):
+    wl, mid, om = dense
+    for s in wl.states:
+        check_raycast(ctx, mid, om, s.x, s.xdot, 1024, wl.params, wl.max_range)
+
+
+@pytest.mark.parametrize("n", [1, 31, 129, 1000, 4097, 20000])
+def test_dense_ragged_ray_counts(ctx, dense, n):
+    wl, mid, om = dense
+    s = wl.states[n % len(wl.states)]
+    check_raycast(ctx, mid, om, s.x, s.xdot, n, wl.params, wl.max_range)
+
+
+def test_dense_ray_count_sweep_paper_range(ctx, dense):
+    """Sec. IV-A varies the ray count from 4^2 to 256^2."""
+    wl, mid, om = dense
+    s = wl.states[1]
+    for n in (16, 64, 256, 1024, 4096, 16384, 65536):
+        check_raycast(ctx, mid, om, s.x, s.xdot, n, wl.params, wl.max_range)
+
+
+def test_dense_robot_outside_grid_all_exit(ctx, dense):
+    wl, mid, om = dense
+    x = wl.map.origin - 0.35
+    rg, ro = check_raycast(ctx, mid, om, x, np.array([1.0, 0.5, 0.0]), 500, wl.params, wl.max_range)
+    assert ro["n_hits"] == 0 and np.all(rg["f"] == 0)
+
+
+def test_w_mode_cubic_and_pole_ray(ctx, dense):
+    wl, mid, om = dense
+    s = wl.states[2]
+    p = dict(wl.params, w_mode=1, halton_offset=0)
+    check_raycast(ctx, mid, om, s.x, s.xdot, 3000, p, wl.max_range)
+
+
+# ----------------------------------------------------------------------------- hashed map
+def test_hashed_tsdf_full_config(ctx, hashed):
+    wl, mid, om = hashed
+    s = wl.states[0]
+    rg, ro = check_raycast(ctx, mid, om, s.x, s.xdot, 65536, wl.params, wl.max_range)
+    assert ro["n_hits"] > 1000
+
+
+@pytest.mark.parametrize("n", [7, 257, 5000, 12345])
+def test_hashed_ragged(ctx, hashed, n):
+    wl, mid, om = hashed
+    for s in wl.states[1:4]:
+        check_raycast(ctx, mid, om, s.x, s.xdot, n, wl.params, wl.max_range)
+
+
+def test_hashed_fp64_reduction(ctx, hashed):
+    wl, mid, om = hashed
+    s = wl.states[4]
+    p = dict(wl.params, reduce_mode=R.RMP_REDUCE_FP64)
+    rg, ro = check_raycast(ctx, mid, om, s.x, s.xdot, 65536, p, wl.max_range)
+    pk = dict(wl.params, reduce_mode=R.RMP_REDUCE_KAHAN32)
+    rk, _, _ = gpu_raycast(ctx, mid, s.x, s.xdot, 65536, R.make_params(pk, wl.max_range), want=False)
+    # both reductions agree with the FP64 oracle far inside the f tolerance
+    for r in (rg, rk):
+        assert np.linalg.norm(r["f"] - ro["f"]) <= 1e-5 * np.linalg.norm(ro["f"])
+
+
+def test_hashed_zero_velocity(ctx, hashed):
+    wl, mid, om = hashed
+    rg, ro = check_raycast(ctx, mid, om, wl.states[0].x, np.zeros(3), 4096, wl.params, wl.max_range)
+    assert rg["n_active"] == 0 and np.all(rg["f"] == 0) and rg["rank"] == 0
+
+
+def test_hashed_map_from_device_buffers(ctx, hashed):
+    torch = torch_cuda()
+    wl, mid, om = hashed
+    keys = torch.from_numpy(wl.map.keys).cuda()
+    tsdf = torch.from_numpy(wl.map.tsdf).cuda()
+    mid2 = R.rmp_map_upload(ctx.handle, R.hashed_desc(keys, tsdf, wl.map.voxel_size))
+    s = wl.states[5]
+    pg = R.make_params(wl.params, wl.max_range)
+    r1, h1, p1 = gpu_raycast(ctx, mid, s.x, s.xdot, 8192, pg)
+    r2, h2, p2 = gpu_raycast(ctx, mid2, s.x, s.xdot, 8192, pg)
+    assert h1.tobytes() == h2.tobytes() and np.array_equal(p1, p2)
+    assert np.array_equal(r1["f"], r2["f"])
+    R.rmp_map_release(ctx.handle, mid2)
+
+
+def test_empty_hashed_map(ctx):
+    hm = W.HashedMap(np.zeros((0, 3), np.int32), np.zeros((0, 512), np.float32), 0.1)
+    mid = ctx.upload(hm)
+    p = dict(W.PARAMS_STATIC_MAP)
+    rg, ro = check_raycast(ctx, mid, O.OracleMap(hm), np.array([1.0, 2.0, 3.0]),
+                           np.array([1.0, 0.0, 0.0]), 3000, p, 10.0)
+    assert rg["n_hits"] == 0 and np.all(rg["f"] == 0)
+
+
+def test_negative_block_keys(ctx):
+    rng = np.random.default_rng(4)
+    keys = np.array([(x, y, z) for x in (-2, -1, 0) for y in (-1, 0) for z in (-1, 0)], np.int32)
+    tsdf = rng.uniform(-0.05, 0.3, (len(keys), 512)).astype(np.float32)
+    hm = W.HashedMap(keys, tsdf, 0.05)
+    mid = ctx.upload(hm)
+    p = dict(W.PARAMS_STATIC_MAP)
+    check_raycast(ctx, mid, O.OracleMap(hm), np.array([-0.01, 0.013, -0.2]),
+                  np.array([0.3, -1.0, 0.7]), 5000, p, 1.0)
+
+
+# ----------------------------------------------------------------------------- LiDAR
+def test_lidar_scan_full_config(ctx):
+    sw = W.lidar_workload()
+    pg = R.make_params(sw.params, sw.max_range)
+    po = O.make_params(sw.params, sw.max_range)
+    rg, pgr = gpu_scan(ctx, sw.points, sw.x, sw.xdot, pg)
+    ro, por = O.scan_eval(sw.points, sw.x, sw.xdot, po)
+    assert_per_ray_close(pgr, por)
+    assert_result_close(rg, ro, por)
+
+
+@pytest.mark.parametrize("n", [1, 100, 3333])
+def test_lidar_ragged_and_offset_sensor(ctx, n):
+    sw = W.lidar_workload()
+    pts = sw.points[:n] + np.float32(3.0)
+    x = np.array([3.0, 3.0, 3.0])
+    xdot = np.array([0.4, -1.2, 0.3])
+    for red in (0, 1):
+        p = dict(sw.params, reduce_mode=red)
+        rg, pgr = gpu_scan(ctx, pts, x, xdot, R.make_params(p, sw.max_range))
+        ro, por = O.scan_eval(pts, x, xdot, O.make_params(p, sw.max_range))
+        assert_per_ray_close(pgr, por)
+        assert_result_close(rg, ro, por)
+
+
+def test_lidar_centred_sphere(ctx):
+    p = dict(W.PARAMS_LIDAR, min_range=0.0)
+    pts = W.sphere_lattice_scan(65536, 0.8)
+    xdot = np.array([0.36, 0.48, 0.8]) * 1.7
+    rg, pgr = gpu_scan(ctx, pts, np.zeros(3), xdot, R.make_params(p, 30.0))
+    ro, por = O.scan_eval(pts, np.zeros(3), xdot, O.make_params(p, 30.0))
+    assert_per_ray_close(pgr, por)
+    assert_result_close(rg, ro, por)
+
+
+# ----------------------------------------------------------------------------- async / determinism
+def test_async_matches_sync_bitwise(ctx, hashed):
+    torch = torch_cuda()
+    wl, mid, om = hashed
+    s = wl.states[2]
+    pg = R.make_params(wl.params, wl.max_range)
+    r_sync, _, _ = gpu_raycast(ctx, mid, s.x, s.xdot, 30000, pg, want=False)
+    ws = torch.empty(R.rmp_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    R.rmp_workspace_init(ws)
+    state = torch.tensor(np.concatenate([s.x, s.xdot]), dtype=torch.float64, device="cuda")
+    out = torch.empty(R.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        R.rmp_raycast_eval_async(ctx.handle, mid, state, 30000, pg, ws, out)
+        r = R.result_from_bytes(out.cpu().numpy().tobytes())
+        for k in ("f", "sumA", "sumAf", "eig"):
+            assert np.array_equal(r[k], r_sync[k]), k
+        assert (r["n_hits"], r["n_active"], r["rank"]) == (r_sync["n_hits"], r_sync["n_active"],
+                                                            r_sync["rank"])
+
+
+def test_async_bad_state_reports_invalid(ctx, hashed):
+    torch = torch_cuda()
+    wl, mid, om = hashed
+    pg = R.make_params(wl.params, wl.max_range)
+    ws = torch.empty(R.rmp_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    R.rmp_workspace_init(ws)
+    out = torch.empty(R.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for bad in (np.nan, np.inf, 1e12):
+        state = torch.tensor([bad, 1.0, 1.0, 0.0, 0.0, 0.0], dtype=torch.float64, device="cuda")
+        R.rmp_raycast_eval_async(ctx.handle, mid, state, 1000, pg, ws, out)
+        r = R.result_from_bytes(out.cpu().numpy().tobytes())
+        assert r["status"] == 1
+        assert np.all(r["f"] == 0) and r["n_hits"] == 0
+    # the workspace is still usable afterwards
+    s = wl.states[0]
+    state = torch.tensor(np.concatenate([s.x, s.xdot]), dtype=torch.float64, device="cuda")
+    R.rmp_raycast_eval_async(ctx.handle, mid, state, 1000, pg, ws, out)
+    assert R.result_from_bytes(out.cpu().numpy().tobytes())["status"] == 0
+
+
+def test_repeated_runs_bitwise_identical(ctx, hashed):
+    wl, mid, om = hashed
+    s = wl.states[3]
+    pg = R.make_params(wl.params, wl.max_range)
+    a = gpu_raycast(ctx, mid, s.x, s.xdot, 65536, pg)
+    b = gpu_raycast(ctx, mid, s.x, s.xdot, 65536, pg)
+    assert np.array_equal(a[0]["f"], b[0]["f"]) and np.array_equal(a[0]["sumA"], b[0]["sumA"])
+    assert a[1].tobytes() == b[1].tobytes() and np.array_equal(a[2], b[2])
+
+
+# ----------------------------------------------------------------------------- argument errors
+def test_argument_errors(ctx, hashed):
+    wl, mid, om = hashed
+    s = wl.states[0]
+    good = dict(wl.params)
+    with pytest.raises(R.RmpError) as e:
+        R.rmp_raycast_eval(ctx.handle, 9999, s.x, s.xdot, 10, R.make_params(good, 10.0))
+    assert e.value.status == 6
+    for bad in (dict(good, nu_rep=0.0), dict(good, c=-1.0), dict(good, w_mode=2),
+                dict(good, reduce_mode=5), dict(good, eps=float("nan"))):
+        with pytest.raises(R.RmpError) as e:
+            R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, 10, R.make_params(bad, 10.0))
+        assert e.value.status == 1
+    with pytest.raises(R.RmpError):                      # more than 16384 voxels of range
+        R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, 10, R.make_params(good, 1700.0))
+    with pytest.raises(R.RmpError):
+        R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, 0, R.make_params(good, 10.0))
+    with pytest.raises(R.RmpError):
+        R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, 1 << 24, R.make_params(good, 10.0))
+    # the largest accepted range still works: 16384 voxels
+    R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, 64, R.make_params(good, 1638.4))
+
+
+def test_map_upload_errors(ctx):
+    keys = np.array([[0, 0, 0], [1, 0, 0], [0, 0, 0]], np.int32)
+    tsdf = np.ones((3, 512), np.float32)
+    with pytest.raises(R.RmpError) as e:
+        ctx.upload(W.HashedMap(keys, tsdf, 0.1))
+    assert e.value.status == 1
+    keys = np.array([[1 << 20, 0, 0]], np.int32)
+    with pytest.raises(R.RmpError):
+        ctx.upload(W.HashedMap(keys, np.ones((1, 512), np.float32), 0.1))
+    with pytest.raises(R.RmpError):
+        ctx.upload(W.DenseMap(np.zeros((4, 4, 4), np.uint8), 0.0, np.zeros(3)))
+    # the context is still usable
+    mid = ctx.upload(W.DenseMap(np.zeros((4, 4, 4), np.uint8), 0.1, np.zeros(3)))
+    info = R.rmp_map_info(ctx.handle, mid)
+    assert info["n_bricks"] == 1 and info["kind"] == 0
+    R.rmp_map_release(ctx.handle, mid)
+    with pytest.raises(R.RmpError):
+        R.rmp_map_release(ctx.handle, mid)

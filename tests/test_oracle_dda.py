@@ -131,7 +131,8 @@ def slab(k, P, D):
 
 
 def brute(occupied, inside, P, D, R_fx):
-    """Expected (status, voxel, steps, exact entry parameter) by exhaustive search.
+    """Expected (status, voxel, steps, exact entry parameter, distinct 8^3 blocks tested)
+    by exhaustive search.
     Returns None if the ray has a tie (two axes cross at the same parameter)."""
     tmax = Fraction(R_fx, DIRQ)
     # tie detection: boundary crossings of different axes at the same parameter
@@ -165,19 +166,23 @@ def brute(occupied, inside, P, D, R_fx):
     cands.sort()
     start = tuple(int(P[a] // FX) for a in range(3))
     assert cands[0][1] == start
+    l1 = lambda k: sum(abs(k[a] - start[a]) for a in range(3))
+    blk = lambda k: tuple(x // 8 for x in k)
     if not inside(start):
-        return ("exit", start, 0, Fraction(0))
+        return ("exit", start, 0, Fraction(0), 0)
+    tested = {blk(start)}
     if occupied(start):
-        return ("hit", start, 0, Fraction(0))
+        return ("hit", start, 0, Fraction(0), 1)
     prev = (start, Fraction(0))
     for t, k in cands[1:]:
         if not inside(k):
-            return ("exit", k, sum(abs(k[a] - start[a]) for a in range(3)), t)
+            return ("exit", k, l1(k), t, len(tested))
+        tested.add(blk(k))
         if occupied(k):
-            return ("hit", k, sum(abs(k[a] - start[a]) for a in range(3)), t)
+            return ("hit", k, l1(k), t, len(tested))
         prev = (k, t)
     k, t = prev
-    return ("range", k, sum(abs(k[a] - start[a]) for a in range(3)), t)
+    return ("range", k, l1(k), t, len(tested))
 
 
 STATUS = {"hit": 1, "range": 2, "exit": 3}
@@ -191,10 +196,11 @@ def check_against_brute(orc, m, occupied, inside, P, Ds, R_fx, vs):
         exp = brute(occupied, inside, [int(p) for p in P], [int(x) for x in D], R_fx)
         if exp is None:
             continue
-        st, k, steps, t = exp
+        st, k, steps, t, blocks = exp
         assert h["status"] == STATUS[st], (P, D, exp, h)
         assert tuple(h["voxel"]) == k, (P, D, exp, h)
         assert h["steps"] == steps
+        assert h["blocks"] == blocks
         d_exact = float(t * 256 * Fraction(float(np.float32(vs))))
         assert abs(float(h["d"]) - d_exact) <= 4 * np.spacing(np.float32(max(d_exact, 1e-30))), (h, d_exact)
         checked += 1
