@@ -1,6 +1,7 @@
 // rmp_api.cu -- host implementation of the C ABI declared in include/rmp.h: contexts,
 // map upload (Sec. III-F: the map is kept in GPU memory and shared by all evaluations),
 // parameter validation and the evaluation entry points.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -17,6 +18,7 @@ struct MapRec {
   DevMap dm;
   void* bricks = nullptr;
   void* table = nullptr;
+  void* index = nullptr;
   uint32_t n_bricks = 0;
   uint32_t cap = 0;
   uint64_t bytes = 0;
@@ -84,6 +86,30 @@ float round_down_f32(double v) {
   return f;
 }
 
+// Coherent ray order: residue classes modulo M = 2^a 3^b are direction cells (see the
+// kernel's ray_of_slot).  Cells hold >= 32 rays so a warp spans at most two of them, about
+// n/48 cells, shaped close to square on the sphere (3^b ~ pi 2^a).
+void pick_ray_cells(uint32_t n, EvalConsts* k) {
+  uint64_t best = 1;
+  double best_score = 1e300;
+  const double target = n / 48.0;
+  for (int a = 0; a <= 24; ++a) {
+    for (int b = 0; b <= 15; ++b) {
+      double m = std::ldexp(1.0, a) * std::pow(3.0, b);
+      if (m > n / 32.0) continue;
+      double score = std::fabs(std::log(m / std::max(target, 1.0))) +
+                     0.5 * std::fabs(std::log(std::pow(3.0, b) / (3.141592653589793 * std::ldexp(1.0, a))));
+      if (score < best_score) {
+        best_score = score;
+        best = (uint64_t)m;
+      }
+    }
+  }
+  k->perm_M = (uint32_t)best;
+  k->perm_Q = n / k->perm_M;
+  k->perm_R = n % k->perm_M;
+}
+
 // Derive the per-evaluation constants; validates every parameter.
 int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalConsts* k) {
   if (!p) return RMP_ERR_INVALID_ARG;
@@ -117,6 +143,11 @@ int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalCon
     const double vox = p->max_range / vs;
     if (!(vox <= (double)kMaxRangeVoxels)) return RMP_ERR_INVALID_ARG;
     k->R_fx = std::llrint(vox * 65536.0);
+    pick_ray_cells(n, k);
+  } else {
+    k->perm_M = 1;
+    k->perm_Q = n;
+    k->perm_R = 0;
   }
   return RMP_OK;
 }
@@ -134,8 +165,10 @@ void launch_shape(const rmp_ctx* ctx, uint32_t n, int* block, int* grid) {
 void free_map(MapRec& r) {
   if (r.bricks) cudaFree(r.bricks);
   if (r.table) cudaFree(r.table);
-  r.bricks = r.table = nullptr;
+  if (r.index) cudaFree(r.index);
+  r.bricks = r.table = r.index = nullptr;
 }
+
 
 }  // namespace
 
@@ -261,10 +294,12 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
     }
     r.n_bricks = (uint32_t)nbr;
     cudaError_t e = cudaMalloc(&r.bricks, nbr * 64);
-    if (e == cudaSuccess) e = launch_dense_bricks(occ, r.dm.dims, r.dm.nb, (uint32_t*)r.bricks, s);
+    if (e == cudaSuccess) e = cudaMalloc(&r.index, nbr * sizeof(int));
+    if (e == cudaSuccess)
+      e = launch_dense_bricks(occ, r.dm.dims, r.dm.nb, (uint32_t*)r.bricks, (int*)r.index, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(cuda_status(e));
-    r.bytes = nbr * 64;
+    r.bytes = nbr * (64 + sizeof(int));
   } else if (d->kind == RMP_MAP_HASHED_TSDF) {
     const uint32_t n = d->n_blocks;
     if (n > (1u << 26)) return RMP_ERR_INVALID_ARG;
@@ -301,8 +336,8 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
       }
       e = launch_tsdf_bricks(tsdf, n, (uint32_t*)r.bricks, s);
       if (e == cudaSuccess)
-        e = launch_hash_build(keys, n, (HashEntry*)r.table, r.dm.cap_mask, r.dm.hash_shift,
-                              err_dev, s);
+        e = launch_hash_build(keys, n, (const uint32_t*)r.bricks, (HashEntry*)r.table,
+                              r.dm.cap_mask, r.dm.hash_shift, err_dev, s);
       if (e != cudaSuccess) return fail(cuda_status(e));
     }
     unsigned int err_host = 0;
@@ -321,6 +356,7 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
   err_dev = nullptr;
   r.dm.bricks = (const uint4*)r.bricks;
   r.dm.table = (const HashEntry*)r.table;
+  r.dm.brick_index = (const int*)r.index;
   std::lock_guard<std::mutex> lk(c->mu);
   const uint32_t id = c->next_id++;
   c->maps[id] = r;

@@ -6,7 +6,10 @@
 //     (a voxel is occupied iff its TSDF value <= 0), addressed through the hash table.
 //   * hash table: power-of-two array of 16-byte entries {key, slot}; key packs the block
 //     coordinates (21 bits each, offset by 2^20); empty entries hold ~0; linear probing
-//     from a Fibonacci (multiply-shift) hash, load factor <= 1/4.
+//     from a Fibonacci (multiply-shift) hash, load factor <= 1/4.  Blocks whose brick has
+//     no occupied voxel keep their key (duplicate detection) with slot -1, so the march
+//     treats them like missing blocks and crosses them in one step.
+//   * dense brick index: int32 per brick, the brick's slot or -1 when it is all free.
 #pragma once
 
 #include <cstdint>
@@ -39,7 +42,8 @@ struct DevMap {
   int dims[3];              // dense voxels per axis
   int nb[3];                // dense bricks per axis
   const uint4* bricks;      // n_bricks x 4 uint4
-  const HashEntry* table;   // hashed only
+  const int* brick_index;   // dense only: brick -> slot of a non-empty brick, or -1
+  const HashEntry* table;   // hashed only: key -> slot of a non-empty brick, or -1
 };
 
 // Constants of one evaluation derived on the host from rmp_params_t.
@@ -49,6 +53,7 @@ struct EvalConsts {
   float min_up, max_dn;     // scans: d >= min_range <=> d >= min_up; d <= max <=> d <= max_dn
   long long R_fx;           // llrint(max_range / vs * 2^16)
   uint32_t n_rays, halton_offset;
+  uint32_t perm_M, perm_Q, perm_R;   // coherent ray order (see ray_of_slot)
   int w_mode, reduce_mode;
 };
 
@@ -80,11 +85,11 @@ cudaError_t launch_scan(const float* pts, const EvalConsts& k, const double* sta
                         void* ws, rmp_result_t* out_dev, float* per_ray, int block, int grid,
                         cudaStream_t stream);
 cudaError_t launch_dense_bricks(const uint8_t* occ, const int dims[3], const int nb[3],
-                                uint32_t* bricks, cudaStream_t stream);
+                                uint32_t* bricks, int* brick_index, cudaStream_t stream);
 cudaError_t launch_tsdf_bricks(const float* tsdf, uint32_t n_blocks, uint32_t* bricks,
                                cudaStream_t stream);
-cudaError_t launch_hash_build(const int32_t* keys, uint32_t n_blocks, HashEntry* table,
-                              uint32_t cap_mask, int hash_shift, unsigned int* err,
-                              cudaStream_t stream);
+cudaError_t launch_hash_build(const int32_t* keys, uint32_t n_blocks, const uint32_t* bricks,
+                              HashEntry* table, uint32_t cap_mask, int hash_shift,
+                              unsigned int* err, cudaStream_t stream);
 
 }  // namespace rmp

@@ -130,39 +130,21 @@ __device__ __forceinline__ int hash_lookup(const DevMap& m, int bx, int by, int 
   return -1;
 }
 
-// Stage brick (bx,by,bz) of this thread in shared memory (word w at cache[w*stride]).
-// Returns false for a missing or all-free brick (nothing is staged then).
+// Occupancy words of the non-empty brick holding block (bx,by,bz), or nullptr when the
+// block is missing or holds no occupied voxel (both are free space).
 template <int KIND>
-__device__ __forceinline__ bool stage_brick(const DevMap& m, int bx, int by, int bz,
-                                            uint32_t* cache, int stride) {
+__device__ __forceinline__ const uint32_t* brick_words(const DevMap& m, int bx, int by, int bz) {
   int slot;
-  if (KIND == RMP_MAP_DENSE_U8) {
-    slot = bx + m.nb[0] * (by + m.nb[1] * bz);
-  } else {
+  if (KIND == RMP_MAP_DENSE_U8)
+    slot = __ldg(m.brick_index + bx + m.nb[0] * (by + m.nb[1] * bz));
+  else
     slot = hash_lookup(m, bx, by, bz);
-    if (slot < 0) return false;
-  }
-  const uint4* src = m.bricks + 4 * (size_t)slot;
-  const uint4 w0 = __ldg(src), w1 = __ldg(src + 1), w2 = __ldg(src + 2), w3 = __ldg(src + 3);
-  const uint32_t any = w0.x | w0.y | w0.z | w0.w | w1.x | w1.y | w1.z | w1.w | w2.x | w2.y |
-                       w2.z | w2.w | w3.x | w3.y | w3.z | w3.w;
-  if (any == 0) return false;
-  cache[0 * stride] = w0.x;  cache[1 * stride] = w0.y;
-  cache[2 * stride] = w0.z;  cache[3 * stride] = w0.w;
-  cache[4 * stride] = w1.x;  cache[5 * stride] = w1.y;
-  cache[6 * stride] = w1.z;  cache[7 * stride] = w1.w;
-  cache[8 * stride] = w2.x;  cache[9 * stride] = w2.y;
-  cache[10 * stride] = w2.z; cache[11 * stride] = w2.w;
-  cache[12 * stride] = w3.x; cache[13 * stride] = w3.y;
-  cache[14 * stride] = w3.z; cache[15 * stride] = w3.w;
-  return true;
+  return slot < 0 ? nullptr : reinterpret_cast<const uint32_t*>(m.bricks + 4 * (size_t)slot);
 }
 
-__device__ __forceinline__ bool cached_bit(const uint32_t* cache, int stride, int kx, int ky,
-                                           int kz) {
+__device__ __forceinline__ bool voxel_bit(const uint32_t* w, int kx, int ky, int kz) {
   const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
-  const uint32_t w = cache[((ly >> 2) + 2 * lz) * stride];
-  return (w >> (lx + 8 * (ly & 3))) & 1u;
+  return (__ldg(w + (ly >> 2) + 2 * lz) >> (lx + 8 * (ly & 3))) & 1u;
 }
 
 // ------------------------------------------------------------------ exact DDA (raycast R)
@@ -171,17 +153,121 @@ __device__ __forceinline__ bool cached_bit(const uint32_t* cache, int stride, in
 // iteration steps the axis with the smallest t_a (cross-multiplied exactly in 64 bits;
 // ties go to the lowest axis); an axis with D_a = 0 has |D_a| = 0, N_a = 1 and so never
 // wins.  A voxel is entered only if N_a 2^24 <= R_fx |D_a|, i.e. N_a <= L_a.
+// Blocks without occupied voxels are crossed in one step of integer arithmetic that
+// reproduces the voxel-by-voxel crossings exactly (skip_block).
 struct MarchOut {
   int k[3];
   uint32_t steps;
-  uint32_t blocks;          // distinct blocks whose occupancy was looked up
+  uint32_t blocks;          // distinct blocks entered (each looked up once)
   uint32_t n_last, a_last;  // entry numerator / |D| of the last voxel (0/1 at the start)
   int status;
 };
 
+__device__ __forceinline__ int min_axis(const uint32_t n[3], const uint32_t a[3]) {
+  const bool ylx = (unsigned long long)n[1] * a[0] < (unsigned long long)n[0] * a[1];
+  const uint32_t nw = ylx ? n[1] : n[0];
+  const uint32_t aw = ylx ? a[1] : a[0];
+  const bool zlw = (unsigned long long)n[2] * aw < (unsigned long long)nw * a[2];
+  return zlw ? 2 : (ylx ? 1 : 0);
+}
+
+__device__ __forceinline__ uint32_t sel3(const uint32_t v[3], int i) {
+  return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
+}
+
+template <int KIND>
+__device__ __forceinline__ bool outside(const DevMap& m, const int k[3]) {
+  return KIND == RMP_MAP_DENSE_U8 &&
+         ((unsigned)k[0] >= (unsigned)m.dims[0] || (unsigned)k[1] >= (unsigned)m.dims[1] ||
+          (unsigned)k[2] >= (unsigned)m.dims[2]);
+}
+
+// The ray is in a block (clipped to the dense grid) that holds no occupied voxel.  Advance
+// the DDA state to the first voxel beyond it exactly as single steps would: the block is
+// left through the axis e whose face crossing F_e/|D_e| comes first (ties: lowest axis);
+// every other axis b crosses its interior boundaries that come strictly before that time
+// (or at the same time if b < e, the tie order).  If the face crossing is out of range,
+// the ray ends inside the block after every in-range crossing; returns true then.
+template <int KIND>
+__device__ __forceinline__ bool skip_block(const DevMap& m, int k[3], const int s[3], uint32_t N[3],
+                                           const uint32_t A[3], const uint32_t L[3],
+                                           uint32_t& steps, uint32_t& n_last, uint32_t& a_last) {
+  uint32_t c[3], F[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int l = k[a] & 7;
+    int ca = s[a] > 0 ? 7 - l : l;
+    if (KIND == RMP_MAP_DENSE_U8) {
+      const int g = s[a] > 0 ? m.dims[a] - 1 - k[a] : k[a];
+      ca = ca < g ? ca : g;
+    }
+    c[a] = (uint32_t)ca;
+    F[a] = N[a] + (c[a] << 16);
+  }
+  const int e = min_axis(F, A);
+  const uint32_t Fe = sel3(F, e), Ae = sel3(A, e), Le = sel3(L, e);
+  if (Fe > Le) {
+    uint32_t bn = 0, ba = 1;
+    bool any = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (A[a] != 0 && N[a] <= L[a]) {
+        uint32_t cnt = ((L[a] - N[a]) >> 16) + 1;
+        cnt = cnt < c[a] ? cnt : c[a];
+        if (cnt > 0) {
+          const uint32_t nl = N[a] + ((cnt - 1) << 16);
+          if (!any || (unsigned long long)nl * ba > (unsigned long long)bn * A[a]) {
+            bn = nl;
+            ba = A[a];
+          }
+          any = true;
+          k[a] += s[a] * (int)cnt;
+          N[a] += cnt << 16;
+          steps += cnt;
+        }
+      }
+    }
+    if (any) {
+      n_last = bn;
+      a_last = ba;
+    }
+    return true;
+  }
+  const unsigned long long unit = (unsigned long long)Ae << 16;     // 2^16 |D_e|
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    if (b == e || A[b] == 0) continue;
+    const unsigned long long X = (unsigned long long)Fe * A[b];
+    const unsigned long long Y = (unsigned long long)N[b] * Ae;
+    const bool le = b < e;
+    // count = #{m >= 0 : Y + m unit < X (<= X if b < e)}, at most 7: binary search
+    uint32_t cnt = 0;
+    unsigned long long t = Y + 3ull * unit;
+    if (le ? t <= X : t < X) cnt = 4;
+    t = Y + (unsigned long long)(cnt + 1) * unit;
+    if (le ? t <= X : t < X) cnt += 2;
+    t = Y + (unsigned long long)cnt * unit;
+    if (le ? t <= X : t < X) cnt += 1;
+    k[b] += s[b] * (int)cnt;
+    N[b] += cnt << 16;
+    steps += cnt;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a == e) {
+      k[a] += s[a] * (int)(c[a] + 1);
+      N[a] = Fe + 65536u;
+    }
+  }
+  steps += sel3(c, e) + 1;
+  n_last = Fe;
+  a_last = Ae;
+  return false;
+}
+
 template <int KIND>
 __device__ __forceinline__ MarchOut march(const DevMap& m, const long long P[3], const int D[3],
-                                          long long R_fx, uint32_t* cache, int stride) {
+                                          long long R_fx) {
   int k[3], s[3];
   uint32_t N[3], A[3], L[3];
 #pragma unroll
@@ -198,27 +284,33 @@ __device__ __forceinline__ MarchOut march(const DevMap& m, const long long P[3],
   o.blocks = 0;
   o.n_last = 0;
   o.a_last = 1;
-  if (KIND == RMP_MAP_DENSE_U8 &&
-      ((unsigned)k[0] >= (unsigned)m.dims[0] || (unsigned)k[1] >= (unsigned)m.dims[1] ||
-       (unsigned)k[2] >= (unsigned)m.dims[2])) {
-    o.status = RMP_RAY_MISS_EXIT;
-  } else {
-    bool staged = stage_brick<KIND>(m, k[0] >> 3, k[1] >> 3, k[2] >> 3, cache, stride);
-    o.blocks = 1;
-    if (staged && cached_bit(cache, stride, k[0], k[1], k[2])) {
-      o.status = RMP_RAY_HIT;
-    } else {
-      o.status = RMP_RAY_MISS_RANGE;
-      for (uint32_t guard = 0; guard < 3u * (kMaxRangeVoxels + 2); ++guard) {
-        const bool ylx = (unsigned long long)N[1] * A[0] < (unsigned long long)N[0] * A[1];
-        const uint32_t nw = ylx ? N[1] : N[0];
-        const uint32_t aw = ylx ? A[1] : A[0];
-        const bool zlw = (unsigned long long)N[2] * aw < (unsigned long long)nw * A[2];
-        const int ax = zlw ? 2 : (ylx ? 1 : 0);
-        const uint32_t na = zlw ? N[2] : nw;
-        const uint32_t aa = zlw ? A[2] : aw;
-        const uint32_t la = ax == 0 ? L[0] : (ax == 1 ? L[1] : L[2]);
-        if (na > la) break;                                   // next voxel beyond range
+  o.status = RMP_RAY_MISS_EXIT;
+  if (!outside<KIND>(m, k)) {
+    o.status = RMP_RAY_MISS_RANGE;
+    for (uint32_t guard = 0; guard < 3u * (kMaxRangeVoxels + 2); ++guard) {
+      o.blocks += 1;
+      const uint32_t* w = brick_words<KIND>(m, k[0] >> 3, k[1] >> 3, k[2] >> 3);
+      if (w == nullptr) {
+        if (skip_block<KIND>(m, k, s, N, A, L, o.steps, o.n_last, o.a_last)) break;  // range
+        if (outside<KIND>(m, k)) {
+          o.status = RMP_RAY_MISS_EXIT;
+          break;
+        }
+        continue;
+      }
+      if (voxel_bit(w, k[0], k[1], k[2])) {
+        o.status = RMP_RAY_HIT;
+        break;
+      }
+      bool done = false;
+      // at most 21 interior steps and one exit step inside an 8^3 block
+      for (int it = 0; it < 24; ++it) {
+        const int ax = min_axis(N, A);
+        const uint32_t na = sel3(N, ax), aa = sel3(A, ax), la = sel3(L, ax);
+        if (na > la) {                                  // next voxel beyond range
+          done = true;
+          break;
+        }
         o.n_last = na;
         o.a_last = aa;
         o.steps += 1;
@@ -232,21 +324,19 @@ __device__ __forceinline__ MarchOut march(const DevMap& m, const long long P[3],
             N[a] += 65536u;
           }
         }
-        if (KIND == RMP_MAP_DENSE_U8 &&
-            ((unsigned)k[0] >= (unsigned)m.dims[0] || (unsigned)k[1] >= (unsigned)m.dims[1] ||
-             (unsigned)k[2] >= (unsigned)m.dims[2])) {
+        if (outside<KIND>(m, k)) {
           o.status = RMP_RAY_MISS_EXIT;
+          done = true;
           break;
         }
-        if (crossed) {
-          staged = stage_brick<KIND>(m, k[0] >> 3, k[1] >> 3, k[2] >> 3, cache, stride);
-          o.blocks += 1;
-        }
-        if (staged && cached_bit(cache, stride, k[0], k[1], k[2])) {
+        if (crossed) break;
+        if (voxel_bit(w, k[0], k[1], k[2])) {
           o.status = RMP_RAY_HIT;
+          done = true;
           break;
         }
       }
+      if (done) break;
     }
   }
   o.k[0] = k[0];
@@ -293,7 +383,7 @@ __device__ __forceinline__ void obstacle_policy(const EvalConsts& k, const float
   const float frep = k.eta_rep * expf(-d * k.inv_nu_rep);
   const float xr = dot2(vh, vl, r);
   const float mm = active ? xr * xr : 0.0f;
-  const float kd = k.eta_damp / (d * k.inv_nu_damp + k.eps);
+  const float kd = __fdividef(k.eta_damp, d * k.inv_nu_damp + k.eps);
   const float z = kd * mm;                       // |f_damp| (|r| = 1)
   const float fr = frep + z;                     // f = (f_rep + |f_damp|) r
   f[0] = fr * r[0];
@@ -306,7 +396,7 @@ __device__ __forceinline__ void obstacle_policy(const EvalConsts& k, const float
     w = k.w_mode == 0 ? y * y : y * y * (1.0f + 2.0f * x);      // (1-x)^2 ; 1-3x^2+2x^3
   }
   const float h = z + k.c * log1pf(expf(-2.0f * k.c * z));
-  const float sc = z / h;                        // s(f_damp) = sc * r
+  const float sc = __fdividef(z, h);            // s(f_damp) = sc * r
   const float alpha = w * sc * sc;               // A = alpha r r^T
   A[0] = alpha * r[0] * r[0];
   A[1] = alpha * r[0] * r[1];
@@ -448,61 +538,102 @@ __device__ __forceinline__ unsigned block_sum_u32(unsigned v) {
 }
 
 // ------------------------------------------------------------------ FP64 resolve (Eq. 1)
-// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations, then
-// f = sum over eigenvalues > 1e-12 lambda_max of (q^T b / lambda) q.
+// f = (sum A)^+ (sum A f) with eigenvalues <= 1e-12 lambda_max treated as zero.  FP64
+// division and square root cost hundreds of cycles each on this GPU, so the
+// eigenvectors come from cyclic Jacobi rotations in FP32 (on the matrix scaled by a power
+// of two), and FP64 then only refines: each eigenvalue is the Rayleigh quotient
+// v^T S v / v^T v of its FP32 eigenvector (second-order accurate, ~1e-14 lambda_max),
+// with 1 / v^T v = 2 - v^T v to first order (v^T v = 1 + O(1e-7)).  A full-rank matrix is
+// solved with the FP64 adjugate (one FP64 division); a rank-deficient one by projecting
+// on the kept eigenvectors.
 __device__ void resolve_pinv(const double S[6], const double b[3], rmp_result_t& r) {
-  double a00 = S[0], a01 = S[1], a02 = S[2], a11 = S[3], a12 = S[4], a22 = S[5];
-  double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-  for (int sweep = 0; sweep < 32; ++sweep) {
-    const double off = fabs(a01) + fabs(a02) + fabs(a12);
-    const double dia = fabs(a00) + fabs(a11) + fabs(a22);
-    if (off == 0.0 || off <= 1e-18 * dia) break;
+  double smax = fmax(fmax(fabs(S[0]), fabs(S[1])), fmax(fmax(fabs(S[2]), fabs(S[3])),
+                                                         fmax(fabs(S[4]), fabs(S[5]))));
+  r.f[0] = r.f[1] = r.f[2] = 0.0;
+  r.eig[0] = r.eig[1] = r.eig[2] = 0.0;
+  r.rank = 0;
+  if (!(smax > 1e-300)) return;
+  const double scale = ldexp(1.0, -ilogb(smax));             // exact power of two
+  float a00 = (float)(S[0] * scale), a01 = (float)(S[1] * scale), a02 = (float)(S[2] * scale),
+        a11 = (float)(S[3] * scale), a12 = (float)(S[4] * scale), a22 = (float)(S[5] * scale);
+  float V[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+  for (int sweep = 0; sweep < 10; ++sweep) {
+    const float off = fabsf(a01) + fabsf(a02) + fabsf(a12);
+    const float dia = fabsf(a00) + fabsf(a11) + fabsf(a22);
+    if (off <= 1e-9f * dia) break;
+#pragma unroll
     for (int pq = 0; pq < 3; ++pq) {
-      // rotation in plane (p,q) in {(0,1), (0,2), (1,2)}; o is the remaining index
-      double app, aqq, apq, apo, aqo;
+      float app, aqq, apq, apo, aqo;
       if (pq == 0) { app = a00; aqq = a11; apq = a01; apo = a02; aqo = a12; }
       else if (pq == 1) { app = a00; aqq = a22; apq = a02; apo = a01; aqo = a12; }
       else { app = a11; aqq = a22; apq = a12; apo = a01; aqo = a02; }
-      if (apq == 0.0) continue;
-      const double tau = (aqq - app) / (2.0 * apq);
-      const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-      const double c = rsqrt(1.0 + t * t), s = t * c;
-      const double npp = app - t * apq, nqq = aqq + t * apq;
-      const double npo = c * apo - s * aqo, nqo = s * apo + c * aqo;
+      if (apq == 0.0f) continue;
+      const float tau = __fdividef(aqq - app, 2.0f * apq);
+      const float at = fabsf(tau);
+      const float root = at < 1e18f ? (1.0f + at * at) * rsqrtf(1.0f + at * at) : at;
+      const float t = copysignf(__fdividef(1.0f, at + root), tau);
+      const float c = rsqrtf(1.0f + t * t), sn = t * c;
+      const float npp = app - t * apq, nqq = aqq + t * apq;
+      const float npo = c * apo - sn * aqo, nqo = sn * apo + c * aqo;
       const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
-      if (pq == 0) { a00 = npp; a11 = nqq; a01 = 0.0; a02 = npo; a12 = nqo; }
-      else if (pq == 1) { a00 = npp; a22 = nqq; a02 = 0.0; a01 = npo; a12 = nqo; }
-      else { a11 = npp; a22 = nqq; a12 = 0.0; a01 = npo; a02 = nqo; }
+      if (pq == 0) { a00 = npp; a11 = nqq; a01 = 0.f; a02 = npo; a12 = nqo; }
+      else if (pq == 1) { a00 = npp; a22 = nqq; a02 = 0.f; a01 = npo; a12 = nqo; }
+      else { a11 = npp; a22 = nqq; a12 = 0.f; a01 = npo; a02 = nqo; }
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const double vp = V[i][p], vq = V[i][q];
-        V[i][p] = c * vp - s * vq;
-        V[i][q] = s * vp + c * vq;
+        const float vp = V[i][p], vq = V[i][q];
+        V[i][p] = c * vp - sn * vq;
+        V[i][q] = sn * vp + c * vq;
       }
     }
   }
-  double lam[3] = {a00, a11, a22};
+  double lam[3], den[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const double v0 = V[0][e], v1 = V[1][e], v2 = V[2][e];
+    const double u0 = S[0] * v0 + S[1] * v1 + S[2] * v2;
+    const double u1 = S[1] * v0 + S[3] * v1 + S[4] * v2;
+    const double u2 = S[2] * v0 + S[4] * v1 + S[5] * v2;
+    den[e] = v0 * v0 + v1 * v1 + v2 * v2;
+    lam[e] = (v0 * u0 + v1 * u1 + v2 * u2) * (2.0 - den[e]);
+  }
   int idx[3] = {0, 1, 2};
   if (lam[idx[1]] < lam[idx[0]]) { int t = idx[0]; idx[0] = idx[1]; idx[1] = t; }
   if (lam[idx[2]] < lam[idx[1]]) { int t = idx[1]; idx[1] = idx[2]; idx[2] = t; }
   if (lam[idx[1]] < lam[idx[0]]) { int t = idx[0]; idx[0] = idx[1]; idx[1] = t; }
   const double lmax = lam[idx[2]];
-  double f[3] = {0.0, 0.0, 0.0};
   uint32_t rank = 0;
+  bool keep[3];
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const int e = idx[i];
-    r.eig[i] = lam[e];
-    if (!(lmax > 1e-300) || lam[e] <= 1e-12 * lmax) continue;
-    ++rank;
-    const double proj = (V[0][e] * b[0] + V[1][e] * b[1] + V[2][e] * b[2]) / lam[e];
-    f[0] += proj * V[0][e];
-    f[1] += proj * V[1][e];
-    f[2] += proj * V[2][e];
+    r.eig[i] = lam[idx[i]];
+    keep[i] = lmax > 1e-300 && lam[idx[i]] > 1e-12 * lmax;
+    rank += keep[i] ? 1u : 0u;
   }
-  r.f[0] = f[0];
-  r.f[1] = f[1];
-  r.f[2] = f[2];
   r.rank = rank;
+  if (rank == 3) {
+    const double c00 = S[3] * S[5] - S[4] * S[4], c01 = S[2] * S[4] - S[1] * S[5],
+                 c02 = S[1] * S[4] - S[2] * S[3], c11 = S[0] * S[5] - S[2] * S[2],
+                 c12 = S[1] * S[2] - S[0] * S[4], c22 = S[0] * S[3] - S[1] * S[1];
+    const double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
+    if (det > 0.0) {
+      const double inv = 1.0 / det;
+      r.f[0] = (c00 * b[0] + c01 * b[1] + c02 * b[2]) * inv;
+      r.f[1] = (c01 * b[0] + c11 * b[1] + c12 * b[2]) * inv;
+      r.f[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
+      return;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (!keep[i]) continue;
+    const int e = idx[i];
+    const double v0 = V[0][e], v1 = V[1][e], v2 = V[2][e];
+    const double proj = (v0 * b[0] + v1 * b[1] + v2 * b[2]) / (lam[e] * den[e]);
+    r.f[0] += proj * v0;
+    r.f[1] += proj * v1;
+    r.f[2] += proj * v2;
+  }
 }
 
 // Grid completion: every CTA stores its partial; the last one (ticket) sums all partials
@@ -559,22 +690,40 @@ __device__ void grid_finish(const double part[9], unsigned hits, unsigned act, W
   }
 }
 
-// Per-CTA state: quantised position (FP64, once per CTA) and FP32 velocity.
+// Per-CTA state: quantised position (FP64, threads 0-2 one axis each) and the velocity
+// as an FP32 pair (threads 3-5).
 struct CtaState {
   long long P[3];
   float v[3];     // RN32(xdot)
   float vl[3];    // RN32(xdot - v)
   float xf[3];
-  int bad;
+  int bad[3];
 };
 
-__device__ __forceinline__ void split_velocity(const double* state, CtaState& cs) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double x = state[3 + a];
-    cs.v[a] = __double2float_rn(x);
-    cs.vl[a] = __double2float_rn(__dsub_rn(x, (double)cs.v[a]));
+__device__ __forceinline__ void split_velocity(const double* state, CtaState& cs, int a) {
+  const double x = state[3 + a];
+  cs.v[a] = __double2float_rn(x);
+  cs.vl[a] = __double2float_rn(__dsub_rn(x, (double)cs.v[a]));
+}
+
+// Coherent ray order: thread slot j -> ray index.  Ray indices i with the same residue
+// i mod M (M = 2^a 3^b) share the first a binary digits of H(i,2) and the first b ternary
+// digits of H(i,3), so they point into one cell of the sphere; slots enumerate residue
+// classes one after the other, so a warp covers at most two cells.  Q = n / M, R = n % M:
+// classes r < R hold Q + 1 rays, the others Q.  M = 1 is the identity.
+__device__ __forceinline__ uint32_t ray_of_slot(uint32_t j, const EvalConsts& k) {
+  const uint32_t big = k.perm_R * (k.perm_Q + 1);
+  uint32_t r, q;
+  if (j < big) {
+    r = j / (k.perm_Q + 1);
+    q = j - r * (k.perm_Q + 1);
+  } else {
+    const uint32_t jj = j - big;
+    const uint32_t t = jj / k.perm_Q;
+    r = k.perm_R + t;
+    q = jj - t * k.perm_Q;
   }
+  return r + k.perm_M * q;
 }
 
 // ------------------------------------------------------------------ fused raycast kernel
@@ -584,35 +733,33 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
                                                           WsHeader* ws, CtaPartial* parts,
                                                           rmp_result_t* out, rmp_ray_hit_t* hits,
                                                           float* per_ray) {
-  extern __shared__ uint32_t brick_cache[];
   __shared__ CtaState cs;
-  if (threadIdx.x == 0) {
-    int bad = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double o = KIND == RMP_MAP_DENSE_U8 ? m.origin[a] : 0.0;
-      const double q = __dmul_rn(__ddiv_rn(__dsub_rn(state[a], o), m.vs), 65536.0);
-      // |voxel| < 2^22 keeps block keys and fixed-point products in range; NaN fails too
-      if (!(fabs(q) < 274877906944.0)) bad = 1;
-      cs.P[a] = bad ? 0 : __double2ll_rn(q);
-    }
-    split_velocity(state, cs);
-    cs.bad = bad;
+  if (threadIdx.x < 3) {
+    const int a = threadIdx.x;
+    const double o = KIND != RMP_MAP_DENSE_U8 ? 0.0
+                     : (a == 0 ? m.origin[0] : (a == 1 ? m.origin[1] : m.origin[2]));
+    const double q = __dmul_rn(__ddiv_rn(__dsub_rn(state[a], o), m.vs), 65536.0);
+    // |voxel| < 2^22 keeps block keys and fixed-point products in range; NaN fails too
+    const int bad = !(fabs(q) < 274877906944.0);
+    cs.bad[a] = bad;
+    cs.P[a] = bad ? 0 : __double2ll_rn(q);
+  } else if (threadIdx.x < 6) {
+    split_velocity(state, cs, threadIdx.x - 3);
   }
   __syncthreads();
+  const bool bad = cs.bad[0] | cs.bad[1] | cs.bad[2];
   typename BlockReduce<RED>::Acc acc;
   BlockReduce<RED>::init(acc);
   unsigned n_hit = 0, n_act = 0;
-  uint32_t* cache = brick_cache + threadIdx.x;
-  const int stride = blockDim.x;
-  if (!cs.bad) {
+  if (!bad) {
     const long long P[3] = {cs.P[0], cs.P[1], cs.P[2]};
     const float v[3] = {cs.v[0], cs.v[1], cs.v[2]};
     const float vl[3] = {cs.vl[0], cs.vl[1], cs.vl[2]};
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < k.n_rays;
          j += gridDim.x * blockDim.x) {
-      const Ray ray = make_ray(j + k.halton_offset);
-      const MarchOut mo = march<KIND>(m, P, ray.D, k.R_fx, cache, stride);
+      const uint32_t ray_idx = ray_of_slot(j, k);
+      const Ray ray = make_ray(ray_idx + k.halton_offset);
+      const MarchOut mo = march<KIND>(m, P, ray.D, k.R_fx);
       const float d = mo.n_last == 0 ? 0.0f : entry_distance(mo.n_last, mo.a_last, m.vs_f);
       float f[3] = {0.f, 0.f, 0.f}, A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, af[3];
       if (mo.status == RMP_RAY_HIT) {
@@ -634,10 +781,10 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
         h.status = (uint8_t)mo.status;
         h.pad = 0;
         h.blocks = (uint16_t)mo.blocks;
-        hits[j] = h;
+        hits[ray_idx] = h;
       }
       if (per_ray) {
-        float* o = per_ray + 9 * (size_t)j;
+        float* o = per_ray + 9 * (size_t)ray_idx;
         o[0] = f[0]; o[1] = f[1]; o[2] = f[2];
         o[3] = A[0]; o[4] = A[1]; o[5] = A[2]; o[6] = A[3]; o[7] = A[4]; o[8] = A[5];
       }
@@ -647,7 +794,7 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
   BlockReduce<RED>::reduce(acc, part);
   const unsigned bh = block_sum_u32(n_hit);
   const unsigned ba = block_sum_u32(n_act);
-  grid_finish(part, bh, ba, ws, parts, out, k.n_rays, cs.bad ? RMP_ERR_INVALID_ARG : RMP_OK);
+  grid_finish(part, bh, ba, ws, parts, out, k.n_rays, bad ? RMP_ERR_INVALID_ARG : RMP_OK);
 }
 
 // ------------------------------------------------------------------ LiDAR scan kernel (Sec. III-G)
@@ -658,11 +805,10 @@ __global__ void __launch_bounds__(256) scan_rmp_kernel(const float* __restrict__
                                                        WsHeader* ws, CtaPartial* parts,
                                                        rmp_result_t* out, float* per_ray) {
   __shared__ CtaState cs;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) cs.xf[a] = __double2float_rn(state[a]);
-    split_velocity(state, cs);
-    cs.bad = 0;
+  if (threadIdx.x < 3) {
+    cs.xf[threadIdx.x] = __double2float_rn(state[threadIdx.x]);
+  } else if (threadIdx.x < 6) {
+    split_velocity(state, cs, threadIdx.x - 3);
   }
   __syncthreads();
   typename BlockReduce<RED>::Acc acc;
@@ -730,6 +876,22 @@ __global__ void dense_bricks_kernel(const uint8_t* __restrict__ occ, int dx, int
   }
 }
 
+// Brick index of a dense map: the brick's slot, or -1 when all its voxels are free.
+__global__ void dense_index_kernel(const uint4* __restrict__ bricks, uint32_t n_bricks,
+                                   int* __restrict__ index) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_bricks;
+       b += gridDim.x * blockDim.x) {
+    const uint4* w = bricks + 4 * (size_t)b;
+    uint32_t any = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 x = w[q];
+      any |= x.x | x.y | x.z | x.w;
+    }
+    index[b] = any ? (int)b : -1;
+  }
+}
+
 // TSDF blocks -> bricks: bit b of block n is tsdf[n*512 + b] <= 0 (the TSDF voxel order
 // lx + 8 ly + 64 lz is the brick's bit order).
 __global__ void tsdf_bricks_kernel(const float* __restrict__ tsdf, uint32_t n_blocks,
@@ -748,8 +910,8 @@ __global__ void tsdf_bricks_kernel(const float* __restrict__ tsdf, uint32_t n_bl
 // Insert block keys into the open-addressing table (linear probing, bounded).
 // err bits: 1 key out of range, 2 duplicate key, 4 table full.
 __global__ void hash_build_kernel(const int32_t* __restrict__ keys, uint32_t n_blocks,
-                                  HashEntry* table, uint32_t cap_mask, int hash_shift,
-                                  unsigned int* err) {
+                                  const uint4* __restrict__ bricks, HashEntry* table,
+                                  uint32_t cap_mask, int hash_shift, unsigned int* err) {
   for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks;
        b += gridDim.x * blockDim.x) {
     const int bx = keys[3 * (size_t)b], by = keys[3 * (size_t)b + 1], bz = keys[3 * (size_t)b + 2];
@@ -766,7 +928,14 @@ __global__ void hash_build_kernel(const int32_t* __restrict__ keys, uint32_t n_b
     for (uint32_t probe = 0; probe <= cap_mask; ++probe) {
       const unsigned long long prev = atomicCAS(&table[h].key, kEmptyKey, key);
       if (prev == kEmptyKey) {
-        table[h].slot = b;
+        const uint4* w = bricks + 4 * (size_t)b;
+        uint32_t any = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 x = w[q];
+          any |= x.x | x.y | x.z | x.w;
+        }
+        table[h].slot = any ? b : 0xFFFFFFFFu;   // all-free bricks read as missing
         done = true;
         break;
       }
@@ -789,7 +958,7 @@ cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* s
                            float* per_ray, int block, int grid, cudaStream_t stream) {
   WsHeader* hdr = (WsHeader*)ws;
   CtaPartial* parts = (CtaPartial*)((char*)ws + kWsHeaderBytes);
-  const size_t smem = (size_t)kBrickWords * sizeof(uint32_t) * block;
+  const size_t smem = 0;
   if (m.kind == RMP_MAP_DENSE_U8) {
     if (k.reduce_mode == RMP_REDUCE_FP64)
       raycast_rmp_kernel<RMP_MAP_DENSE_U8, RMP_REDUCE_FP64><<<grid, block, smem, stream>>>(
@@ -823,11 +992,16 @@ cudaError_t launch_scan(const float* pts, const EvalConsts& k, const double* sta
 }
 
 cudaError_t launch_dense_bricks(const uint8_t* occ, const int dims[3], const int nb[3],
-                                uint32_t* bricks, cudaStream_t stream) {
-  const size_t total = (size_t)nb[0] * nb[1] * nb[2] * kBrickWords;
+                                uint32_t* bricks, int* brick_index, cudaStream_t stream) {
+  const size_t nbr = (size_t)nb[0] * nb[1] * nb[2];
+  const size_t total = nbr * kBrickWords;
   const int grid = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
   dense_bricks_kernel<<<grid, 256, 0, stream>>>(occ, dims[0], dims[1], dims[2], nb[0], nb[1],
                                                 nb[2], bricks);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int g2 = (int)((nbr + 255) / 256 < 65535 ? (nbr + 255) / 256 : 65535);
+  dense_index_kernel<<<g2, 256, 0, stream>>>((const uint4*)bricks, (uint32_t)nbr, brick_index);
   return cudaGetLastError();
 }
 
@@ -839,12 +1013,12 @@ cudaError_t launch_tsdf_bricks(const float* tsdf, uint32_t n_blocks, uint32_t* b
   return cudaGetLastError();
 }
 
-cudaError_t launch_hash_build(const int32_t* keys, uint32_t n_blocks, HashEntry* table,
-                              uint32_t cap_mask, int hash_shift, unsigned int* err,
-                              cudaStream_t stream) {
+cudaError_t launch_hash_build(const int32_t* keys, uint32_t n_blocks, const uint32_t* bricks,
+                              HashEntry* table, uint32_t cap_mask, int hash_shift,
+                              unsigned int* err, cudaStream_t stream) {
   const int grid = (int)((n_blocks + 255) / 256 < 65535 ? (n_blocks + 255) / 256 : 65535);
-  hash_build_kernel<<<grid > 0 ? grid : 1, 256, 0, stream>>>(keys, n_blocks, table, cap_mask,
-                                                             hash_shift, err);
+  hash_build_kernel<<<grid > 0 ? grid : 1, 256, 0, stream>>>(keys, n_blocks, (const uint4*)bricks,
+                                                             table, cap_mask, hash_shift, err);
   return cudaGetLastError();
 }
 

@@ -286,3 +286,25 @@ def test_map_upload_errors(ctx):
     R.rmp_map_release(ctx.handle, mid)
     with pytest.raises(R.RmpError):
         R.rmp_map_release(ctx.handle, mid)
+
+
+# ----------------------------------------------------------------------------- block skipping
+@pytest.mark.parametrize("max_range", [0.37, 1.33, 3.3, 7.77])
+def test_hashed_ranges_ending_inside_skipped_blocks(ctx, hashed, max_range):
+    wl, mid, om = hashed
+    for s in wl.states[:3]:
+        check_raycast(ctx, mid, om, s.x, s.xdot, 6000, wl.params, max_range)
+
+
+def test_dense_grid_not_multiple_of_eight(ctx):
+    rng = W.SplitMix64(W.SEED_BASE + 99)
+    prims = W.random_boxes(rng, 12, np.zeros(3), np.array([4.5, 3.7, 2.9]), 0.2, 1.0)
+    m = W.voxelise_boxes_dense(prims, (45, 37, 29), 0.1)
+    mid = ctx.upload(m)
+    om = O.OracleMap(m)
+    free = np.argwhere(m.occ == 0)
+    for t in range(4):
+        z, y, x = free[(t * 7919) % len(free)]
+        c = (np.array([x, y, z]) + 0.5) * 0.1                      # voxel centre: tie-prone
+        check_raycast(ctx, mid, om, c, np.array([0.5, -1.0, 0.3]), 4000, W.PARAMS_STATIC_MAP, 5.0)
+        check_raycast(ctx, mid, om, c + 0.0123, np.array([-0.2, 0.4, 1.1]), 4000, W.PARAMS_STATIC_MAP, 2.2)
