@@ -140,8 +140,9 @@ typedef struct {
 typedef struct {
   int32_t kind;
   uint32_t n_bricks;        /* 8^3 occupancy bricks held on the device */
-  uint32_t hash_capacity;   /* hashed maps: table entries (power of two) */
-  uint32_t reserved;
+  uint32_t hash_capacity;   /* hash layout: table entries (power of two); else 0 */
+  uint32_t layout;          /* 0: grid (bricks over the bounding box of occupied blocks plus a
+                               1-bit block bitmap); 1: hash table of blocks */
   uint64_t device_bytes;    /* device memory held by the map */
 } rmp_map_info_t;
 

@@ -2,6 +2,7 @@
 // map upload (Sec. III-F: the map is kept in GPU memory and shared by all evaluations),
 // parameter validation and the evaluation entry points.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -18,7 +19,7 @@ struct MapRec {
   DevMap dm;
   void* bricks = nullptr;
   void* table = nullptr;
-  void* index = nullptr;
+  void* bitmap = nullptr;
   uint32_t n_bricks = 0;
   uint32_t cap = 0;
   uint64_t bytes = 0;
@@ -165,8 +166,13 @@ void launch_shape(const rmp_ctx* ctx, uint32_t n, int* block, int* grid) {
 void free_map(MapRec& r) {
   if (r.bricks) cudaFree(r.bricks);
   if (r.table) cudaFree(r.table);
-  if (r.index) cudaFree(r.index);
-  r.bricks = r.table = r.index = nullptr;
+  if (r.bitmap) cudaFree(r.bitmap);
+  r.bricks = r.table = r.bitmap = nullptr;
+}
+
+uint32_t bitmap_words_for(uint64_t n_bricks) {
+  const uint64_t w = (n_bricks + 31) / 32;
+  return (uint32_t)((w + 3) / 4 * 4);            // whole uint4s
 }
 
 
@@ -265,11 +271,23 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
   r.dm.vs_f = (float)d->voxel_size;
   void* tmp_a = nullptr;
   void* tmp_b = nullptr;
+  void* compact = nullptr;
+  void* table = nullptr;
   unsigned int* err_dev = nullptr;
-  auto fail = [&](int st) {
+  int* bbox_dev = nullptr;
+  auto cleanup = [&]() {
     if (tmp_a) cudaFree(tmp_a);
     if (tmp_b) cudaFree(tmp_b);
+    if (compact) cudaFree(compact);
+    if (table) cudaFree(table);
     if (err_dev) cudaFree(err_dev);
+    if (bbox_dev) cudaFree(bbox_dev);
+    tmp_a = tmp_b = compact = table = nullptr;
+    err_dev = nullptr;
+    bbox_dev = nullptr;
+  };
+  auto fail = [&](int st) {
+    cleanup();
     free_map(r);
     return st;
   };
@@ -278,13 +296,14 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
       if (d->dims[a] <= 0 || d->dims[a] > (1 << 20) || !std::isfinite(d->origin[a]))
         return RMP_ERR_INVALID_ARG;
       r.dm.dims[a] = d->dims[a];
-      r.dm.nb[a] = (d->dims[a] + 7) / 8;
+      r.dm.gdim[a] = (d->dims[a] + 7) / 8;
+      r.dm.gmin[a] = 0;
       r.dm.origin[a] = d->origin[a];
     }
     if (!d->occ) return RMP_ERR_INVALID_ARG;
     const uint64_t nvox = (uint64_t)d->dims[0] * d->dims[1] * d->dims[2];
-    const uint64_t nbr = (uint64_t)r.dm.nb[0] * r.dm.nb[1] * r.dm.nb[2];
-    if (nbr > (1ull << 31)) return RMP_ERR_INVALID_ARG;
+    const uint64_t nbr = (uint64_t)r.dm.gdim[0] * r.dm.gdim[1] * r.dm.gdim[2];
+    if (nbr > kMaxGridBricks) return RMP_ERR_INVALID_ARG;
     const uint8_t* occ = d->occ;
     if (!d->data_on_device) {
       cudaError_t e = cudaMalloc(&tmp_a, nvox);
@@ -292,14 +311,18 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
       if (e != cudaSuccess) return fail(cuda_status(e));
       occ = (const uint8_t*)tmp_a;
     }
+    r.dm.layout = kLayoutGrid;
     r.n_bricks = (uint32_t)nbr;
+    r.dm.bitmap_words = bitmap_words_for(nbr);
     cudaError_t e = cudaMalloc(&r.bricks, nbr * 64);
-    if (e == cudaSuccess) e = cudaMalloc(&r.index, nbr * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&r.bitmap, (size_t)r.dm.bitmap_words * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r.bitmap, 0, (size_t)r.dm.bitmap_words * 4, s);
+    if (e == cudaSuccess) e = launch_dense_bricks(occ, r.dm.dims, r.dm.gdim, (uint32_t*)r.bricks, s);
     if (e == cudaSuccess)
-      e = launch_dense_bricks(occ, r.dm.dims, r.dm.nb, (uint32_t*)r.bricks, (int*)r.index, s);
+      e = launch_grid_bitmap((const uint32_t*)r.bricks, (uint32_t)nbr, (uint32_t*)r.bitmap, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(cuda_status(e));
-    r.bytes = nbr * (64 + sizeof(int));
+    r.bytes = nbr * 64 + (uint64_t)r.dm.bitmap_words * 4;
   } else if (d->kind == RMP_MAP_HASHED_TSDF) {
     const uint32_t n = d->n_blocks;
     if (n > (1u << 26)) return RMP_ERR_INVALID_ARG;
@@ -308,18 +331,22 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
     while (cap < 4ull * n) cap <<= 1;
     int log2cap = 0;
     while ((1u << log2cap) < cap) ++log2cap;
-    r.cap = cap;
     r.dm.cap_mask = cap - 1;
     r.dm.hash_shift = 64 - log2cap;
-    r.n_bricks = n;
-    cudaError_t e = cudaMalloc(&r.table, (size_t)cap * sizeof(HashEntry));
-    if (e == cudaSuccess) e = cudaMemsetAsync(r.table, 0xFF, (size_t)cap * sizeof(HashEntry), s);
-    if (e == cudaSuccess && n > 0) e = cudaMalloc(&r.bricks, (size_t)n * 64);
+    // 1) bricks of every block, and the hash table (validates keys and duplicates)
+    cudaError_t e = cudaMalloc(&table, (size_t)cap * sizeof(HashEntry));
+    if (e == cudaSuccess) e = cudaMemsetAsync(table, 0xFF, (size_t)cap * sizeof(HashEntry), s);
+    if (e == cudaSuccess && n > 0) e = cudaMalloc(&compact, (size_t)n * 64);
     if (e == cudaSuccess) e = cudaMalloc((void**)&err_dev, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemsetAsync(err_dev, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&bbox_dev, 6 * sizeof(int));
+    const int bbox_init[6] = {INT32_MAX, INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN, INT32_MIN};
+    int bbox[6];
+    std::memcpy(bbox, bbox_init, sizeof(bbox));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bbox_dev, bbox, sizeof(bbox), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(cuda_status(e));
+    const int32_t* keys = d->block_keys;
     if (n > 0) {
-      const int32_t* keys = d->block_keys;
       const float* tsdf = d->tsdf;
       if (!d->data_on_device) {
         e = cudaMalloc(&tmp_a, (size_t)n * 3 * sizeof(int32_t));
@@ -334,29 +361,68 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
         keys = (const int32_t*)tmp_a;
         tsdf = (const float*)tmp_b;
       }
-      e = launch_tsdf_bricks(tsdf, n, (uint32_t*)r.bricks, s);
+      e = launch_tsdf_bricks(tsdf, n, (uint32_t*)compact, s);
       if (e == cudaSuccess)
-        e = launch_hash_build(keys, n, (const uint32_t*)r.bricks, (HashEntry*)r.table,
-                              r.dm.cap_mask, r.dm.hash_shift, err_dev, s);
+        e = launch_hash_build(keys, n, (const uint32_t*)compact, (HashEntry*)table, r.dm.cap_mask,
+                              r.dm.hash_shift, err_dev, s);
+      if (e == cudaSuccess) e = launch_key_bbox(keys, (const uint32_t*)compact, n, bbox_dev, s);
       if (e != cudaSuccess) return fail(cuda_status(e));
     }
     unsigned int err_host = 0;
     e = cudaMemcpyAsync(&err_host, err_dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bbox, bbox_dev, sizeof(bbox), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(cuda_status(e));
     if (err_host != 0) return fail(RMP_ERR_INVALID_ARG);
-    r.bytes = (uint64_t)cap * sizeof(HashEntry) + (uint64_t)n * 64;
+    // 2) layout: a grid over the bounding box of the occupied blocks unless it is much
+    //    larger than the blocks themselves; otherwise keep the hash table
+    const bool none = bbox[0] > bbox[3];
+    uint64_t gprod = 1;
+    int gdim[3] = {1, 1, 1}, gmin[3] = {0, 0, 0};
+    if (!none) {
+      for (int a = 0; a < 3; ++a) {
+        gmin[a] = bbox[a];
+        gdim[a] = bbox[3 + a] - bbox[a] + 1;
+        gprod *= (uint64_t)gdim[a];
+      }
+    }
+    const uint64_t grid_bytes = gprod * 64;
+    const bool use_grid = gprod <= kMaxGridBricks &&
+                          (grid_bytes <= (256ull << 20) || grid_bytes <= 16ull * 64 * n);
+    if (use_grid) {
+      r.dm.layout = kLayoutGrid;
+      for (int a = 0; a < 3; ++a) {
+        r.dm.gmin[a] = gmin[a];
+        r.dm.gdim[a] = gdim[a];
+      }
+      r.n_bricks = (uint32_t)gprod;
+      r.dm.bitmap_words = bitmap_words_for(gprod);
+      e = cudaMalloc(&r.bricks, grid_bytes);
+      if (e == cudaSuccess) e = cudaMemsetAsync(r.bricks, 0, grid_bytes, s);
+      if (e == cudaSuccess) e = cudaMalloc(&r.bitmap, (size_t)r.dm.bitmap_words * 4);
+      if (e == cudaSuccess) e = cudaMemsetAsync(r.bitmap, 0, (size_t)r.dm.bitmap_words * 4, s);
+      if (e == cudaSuccess && n > 0 && !none)
+        e = launch_grid_scatter(keys, (const uint32_t*)compact, n, gmin, gdim, (uint32_t*)r.bricks,
+                                (uint32_t*)r.bitmap, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return fail(cuda_status(e));
+      r.bytes = grid_bytes + (uint64_t)r.dm.bitmap_words * 4;
+    } else {
+      r.dm.layout = kLayoutHash;
+      r.bricks = compact;
+      r.table = table;
+      compact = table = nullptr;
+      r.cap = cap;
+      r.n_bricks = n;
+      r.bytes = (uint64_t)cap * sizeof(HashEntry) + (uint64_t)n * 64;
+    }
   } else {
     return RMP_ERR_INVALID_ARG;
   }
-  if (tmp_a) cudaFree(tmp_a);
-  if (tmp_b) cudaFree(tmp_b);
-  if (err_dev) cudaFree(err_dev);
-  tmp_a = tmp_b = nullptr;
-  err_dev = nullptr;
+  cleanup();
   r.dm.bricks = (const uint4*)r.bricks;
   r.dm.table = (const HashEntry*)r.table;
-  r.dm.brick_index = (const int*)r.index;
+  r.dm.bitmap = (const uint32_t*)r.bitmap;
   std::lock_guard<std::mutex> lk(c->mu);
   const uint32_t id = c->next_id++;
   c->maps[id] = r;
@@ -382,6 +448,7 @@ int rmp_map_info(rmp_ctx* c, uint32_t map_id, rmp_map_info_t* out) {
   if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
   std::memset(out, 0, sizeof(*out));
   out->kind = it->second.dm.kind;
+  out->layout = (uint32_t)it->second.dm.layout;
   out->n_bricks = it->second.n_bricks;
   out->hash_capacity = it->second.cap;
   out->device_bytes = it->second.bytes;

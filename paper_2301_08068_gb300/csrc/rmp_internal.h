@@ -1,15 +1,16 @@
 // rmp_internal.h -- types shared by the library's host code and kernels (not part of the
 // public ABI).  Layouts in HBM:
-//   * occupancy bricks: one 8^3 voxel brick = 512 bits = 64 bytes = 16 uint32 words;
-//     bit b = lx + 8 ly + 64 lz lives in word b >> 5, bit b & 31.  Dense maps store
-//     ceil(dims/8) bricks in x-fastest order; hashed maps store one brick per TSDF block
-//     (a voxel is occupied iff its TSDF value <= 0), addressed through the hash table.
-//   * hash table: power-of-two array of 16-byte entries {key, slot}; key packs the block
-//     coordinates (21 bits each, offset by 2^20); empty entries hold ~0; linear probing
-//     from a Fibonacci (multiply-shift) hash, load factor <= 1/4.  Blocks whose brick has
-//     no occupied voxel keep their key (duplicate detection) with slot -1, so the march
-//     treats them like missing blocks and crosses them in one step.
-//   * dense brick index: int32 per brick, the brick's slot or -1 when it is all free.
+//   * occupancy brick: one 8^3 voxel block = 512 bits = 64 bytes = 16 uint32 words; bit
+//     b = lx + 8 ly + 64 lz lives in word b >> 5, bit b & 31 (a TSDF voxel is occupied iff
+//     its value is <= 0; a dense voxel iff it is nonzero).
+//   * grid layout (dense maps, and hashed maps whose block bounding box is moderate): the
+//     bricks of every block in the bounding box, x fastest (all-zero where free), plus a
+//     1-bit-per-block bitmap of the blocks that hold an occupied voxel.  The march stages
+//     the bitmap in shared memory, so free blocks cost no global access at all.
+//   * hash layout (fallback for very large extents): power-of-two array of 16-byte entries
+//     {key, slot}; key packs the block coordinates (21 bits each, offset by 2^20); empty
+//     entries hold ~0; linear probing from a Fibonacci (multiply-shift) hash, load factor
+//     <= 1/4; blocks without occupied voxels keep their key with slot -1.
 #pragma once
 
 #include <cstdint>
@@ -32,18 +33,26 @@ struct HashEntry {
   uint32_t pad;
 };
 
+constexpr int kLayoutGrid = 0;
+constexpr int kLayoutHash = 1;
+constexpr uint32_t kMaxSmemBitmapBytes = 48 * 1024;   // staged in shared memory up to this
+constexpr uint64_t kMaxGridBricks = 1ull << 26;       // grid layout up to 4 GiB of bricks
+
 struct DevMap {
-  int kind;                 // RMP_MAP_DENSE_U8 / RMP_MAP_HASHED_TSDF
+  int kind;                 // RMP_MAP_DENSE_U8 (rays exit at the grid) / RMP_MAP_HASHED_TSDF
+  int layout;               // kLayoutGrid / kLayoutHash
   int hash_shift;           // 64 - log2(capacity)
-  float vs_f;               // RN32(voxel size)
   uint32_t cap_mask;
+  float vs_f;               // RN32(voxel size)
+  uint32_t bitmap_words;    // grid: uint32 words of the block bitmap (multiple of 4)
   double vs;
   double origin[3];         // dense only (hashed maps are world-anchored)
   int dims[3];              // dense voxels per axis
-  int nb[3];                // dense bricks per axis
-  const uint4* bricks;      // n_bricks x 4 uint4
-  const int* brick_index;   // dense only: brick -> slot of a non-empty brick, or -1
-  const HashEntry* table;   // hashed only: key -> slot of a non-empty brick, or -1
+  int gmin[3];              // grid: block coordinates of the grid's first brick
+  int gdim[3];              // grid: bricks per axis
+  const uint4* bricks;      // grid: brick (x + gdim0 (y + gdim1 z)); hash: by slot
+  const uint32_t* bitmap;   // grid: bit idx set iff brick idx holds an occupied voxel
+  const HashEntry* table;   // hash layout only
 };
 
 // Constants of one evaluation derived on the host from rmp_params_t.
@@ -78,6 +87,7 @@ inline unsigned long long pack_key(int bx, int by, int bz) {
 }
 
 // Launchers (rmp_kernels.cu).  All enqueue on `stream` and return cudaGetLastError().
+size_t raycast_smem_bytes(const DevMap& m);
 cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,
                            void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
                            float* per_ray, int block, int grid, cudaStream_t stream);
@@ -85,7 +95,14 @@ cudaError_t launch_scan(const float* pts, const EvalConsts& k, const double* sta
                         void* ws, rmp_result_t* out_dev, float* per_ray, int block, int grid,
                         cudaStream_t stream);
 cudaError_t launch_dense_bricks(const uint8_t* occ, const int dims[3], const int nb[3],
-                                uint32_t* bricks, int* brick_index, cudaStream_t stream);
+                                uint32_t* bricks, cudaStream_t stream);
+cudaError_t launch_grid_bitmap(const uint32_t* bricks, uint32_t n_bricks, uint32_t* bitmap,
+                               cudaStream_t stream);
+cudaError_t launch_key_bbox(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,
+                            int* bbox, cudaStream_t stream);
+cudaError_t launch_grid_scatter(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,
+                                const int gmin[3], const int gdim[3], uint32_t* grid_bricks,
+                                uint32_t* bitmap, cudaStream_t stream);
 cudaError_t launch_tsdf_bricks(const float* tsdf, uint32_t n_blocks, uint32_t* bricks,
                                cudaStream_t stream);
 cudaError_t launch_hash_build(const int32_t* keys, uint32_t n_blocks, const uint32_t* bricks,

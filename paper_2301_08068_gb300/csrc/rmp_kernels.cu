@@ -130,21 +130,46 @@ __device__ __forceinline__ int hash_lookup(const DevMap& m, int bx, int by, int 
   return -1;
 }
 
-// Occupancy words of the non-empty brick holding block (bx,by,bz), or nullptr when the
-// block is missing or holds no occupied voxel (both are free space).
-template <int KIND>
-__device__ __forceinline__ const uint32_t* brick_words(const DevMap& m, int bx, int by, int bz) {
-  int slot;
-  if (KIND == RMP_MAP_DENSE_U8)
-    slot = __ldg(m.brick_index + bx + m.nb[0] * (by + m.nb[1] * bz));
-  else
-    slot = hash_lookup(m, bx, by, bz);
-  return slot < 0 ? nullptr : reinterpret_cast<const uint32_t*>(m.bricks + 4 * (size_t)slot);
+// A brick held in registers: 16 occupancy words, loaded with four 128-bit loads.
+struct Brick {
+  uint4 q0, q1, q2, q3;
+};
+
+// Load the brick of block (bx,by,bz) into registers; false when the block holds no
+// occupied voxel (missing, all free, or outside the grid's bounding box).  In the grid
+// layout the test reads the block bitmap `bm` (shared memory when it fits).
+template <int LAYOUT>
+__device__ __forceinline__ bool fetch_brick(const DevMap& m, const uint32_t* bm, int bx, int by,
+                                            int bz, Brick& br) {
+  const uint4* src;
+  if (LAYOUT == kLayoutGrid) {
+    const int x = bx - m.gmin[0], y = by - m.gmin[1], z = bz - m.gmin[2];
+    if ((unsigned)x >= (unsigned)m.gdim[0] || (unsigned)y >= (unsigned)m.gdim[1] ||
+        (unsigned)z >= (unsigned)m.gdim[2])
+      return false;
+    const uint32_t idx = (uint32_t)x + (uint32_t)m.gdim[0] * ((uint32_t)y + (uint32_t)m.gdim[1] * (uint32_t)z);
+    if (!((bm[idx >> 5] >> (idx & 31)) & 1u)) return false;
+    src = m.bricks + 4 * (size_t)idx;
+  } else {
+    const int slot = hash_lookup(m, bx, by, bz);
+    if (slot < 0) return false;
+    src = m.bricks + 4 * (size_t)slot;
+  }
+  br.q0 = __ldg(src);
+  br.q1 = __ldg(src + 1);
+  br.q2 = __ldg(src + 2);
+  br.q3 = __ldg(src + 3);
+  return true;
 }
 
-__device__ __forceinline__ bool voxel_bit(const uint32_t* w, int kx, int ky, int kz) {
+// Occupancy of voxel k in the register brick: word (ly>>2) + 2 lz picked by a select
+// tree (no local memory), bit lx + 8 (ly & 3).
+__device__ __forceinline__ bool brick_bit(const Brick& b, int kx, int ky, int kz) {
   const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
-  return (__ldg(w + (ly >> 2) + 2 * lz) >> (lx + 8 * (ly & 3))) & 1u;
+  const int wi = (ly >> 2) + 2 * lz;
+  const uint4 q = (wi & 8) ? ((wi & 4) ? b.q3 : b.q2) : ((wi & 4) ? b.q1 : b.q0);
+  const uint32_t w = (wi & 2) ? ((wi & 1) ? q.w : q.z) : ((wi & 1) ? q.y : q.x);
+  return (w >> (lx + 8 * (ly & 3))) & 1u;
 }
 
 // ------------------------------------------------------------------ exact DDA (raycast R)
@@ -265,9 +290,9 @@ __device__ __forceinline__ bool skip_block(const DevMap& m, int k[3], const int 
   return false;
 }
 
-template <int KIND>
-__device__ __forceinline__ MarchOut march(const DevMap& m, const long long P[3], const int D[3],
-                                          long long R_fx) {
+template <int KIND, int LAYOUT>
+__device__ __forceinline__ MarchOut march(const DevMap& m, const uint32_t* bm, const long long P[3],
+                                          const int D[3], long long R_fx) {
   int k[3], s[3];
   uint32_t N[3], A[3], L[3];
 #pragma unroll
@@ -289,8 +314,8 @@ __device__ __forceinline__ MarchOut march(const DevMap& m, const long long P[3],
     o.status = RMP_RAY_MISS_RANGE;
     for (uint32_t guard = 0; guard < 3u * (kMaxRangeVoxels + 2); ++guard) {
       o.blocks += 1;
-      const uint32_t* w = brick_words<KIND>(m, k[0] >> 3, k[1] >> 3, k[2] >> 3);
-      if (w == nullptr) {
+      Brick w;
+      if (!fetch_brick<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, w)) {
         if (skip_block<KIND>(m, k, s, N, A, L, o.steps, o.n_last, o.a_last)) break;  // range
         if (outside<KIND>(m, k)) {
           o.status = RMP_RAY_MISS_EXIT;
@@ -298,7 +323,7 @@ __device__ __forceinline__ MarchOut march(const DevMap& m, const long long P[3],
         }
         continue;
       }
-      if (voxel_bit(w, k[0], k[1], k[2])) {
+      if (brick_bit(w, k[0], k[1], k[2])) {
         o.status = RMP_RAY_HIT;
         break;
       }
@@ -330,7 +355,7 @@ __device__ __forceinline__ MarchOut march(const DevMap& m, const long long P[3],
           break;
         }
         if (crossed) break;
-        if (voxel_bit(w, k[0], k[1], k[2])) {
+        if (brick_bit(w, k[0], k[1], k[2])) {
           o.status = RMP_RAY_HIT;
           done = true;
           break;
@@ -727,13 +752,21 @@ __device__ __forceinline__ uint32_t ray_of_slot(uint32_t j, const EvalConsts& k)
 }
 
 // ------------------------------------------------------------------ fused raycast kernel
-template <int KIND, int RED>
+template <int KIND, int LAYOUT, int RED>
 __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k,
                                                           const double* __restrict__ state,
                                                           WsHeader* ws, CtaPartial* parts,
                                                           rmp_result_t* out, rmp_ray_hit_t* hits,
                                                           float* per_ray) {
+  extern __shared__ uint4 smem_bitmap[];
   __shared__ CtaState cs;
+  const uint32_t* bm = m.bitmap;
+  if (LAYOUT == kLayoutGrid && m.bitmap_words * 4u <= kMaxSmemBitmapBytes) {
+    // stage the block bitmap (128-bit loads, coalesced) while threads 0-5 set up the state
+    const uint4* g = reinterpret_cast<const uint4*>(m.bitmap);
+    for (uint32_t i = threadIdx.x; i < m.bitmap_words / 4; i += blockDim.x) smem_bitmap[i] = __ldg(g + i);
+    bm = reinterpret_cast<const uint32_t*>(smem_bitmap);
+  }
   if (threadIdx.x < 3) {
     const int a = threadIdx.x;
     const double o = KIND != RMP_MAP_DENSE_U8 ? 0.0
@@ -759,7 +792,7 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
          j += gridDim.x * blockDim.x) {
       const uint32_t ray_idx = ray_of_slot(j, k);
       const Ray ray = make_ray(ray_idx + k.halton_offset);
-      const MarchOut mo = march<KIND>(m, P, ray.D, k.R_fx);
+      const MarchOut mo = march<KIND, LAYOUT>(m, bm, P, ray.D, k.R_fx);
       const float d = mo.n_last == 0 ? 0.0f : entry_distance(mo.n_last, mo.a_last, m.vs_f);
       float f[3] = {0.f, 0.f, 0.f}, A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, af[3];
       if (mo.status == RMP_RAY_HIT) {
@@ -876,9 +909,9 @@ __global__ void dense_bricks_kernel(const uint8_t* __restrict__ occ, int dx, int
   }
 }
 
-// Brick index of a dense map: the brick's slot, or -1 when all its voxels are free.
-__global__ void dense_index_kernel(const uint4* __restrict__ bricks, uint32_t n_bricks,
-                                   int* __restrict__ index) {
+// Block bitmap of a grid: bit b set iff brick b holds an occupied voxel.
+__global__ void grid_bitmap_kernel(const uint4* __restrict__ bricks, uint32_t n_bricks,
+                                   uint32_t* __restrict__ bitmap) {
   for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_bricks;
        b += gridDim.x * blockDim.x) {
     const uint4* w = bricks + 4 * (size_t)b;
@@ -888,7 +921,51 @@ __global__ void dense_index_kernel(const uint4* __restrict__ bricks, uint32_t n_
       const uint4 x = w[q];
       any |= x.x | x.y | x.z | x.w;
     }
-    index[b] = any ? (int)b : -1;
+    if (any) atomicOr(bitmap + (b >> 5), 1u << (b & 31));
+  }
+}
+
+// Bounding box (min xyz, max xyz) of the blocks whose brick holds an occupied voxel.
+__global__ void key_bbox_kernel(const int32_t* __restrict__ keys, const uint4* __restrict__ bricks,
+                                uint32_t n_blocks, int* bbox) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks;
+       b += gridDim.x * blockDim.x) {
+    const uint4* w = bricks + 4 * (size_t)b;
+    uint32_t any = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 x = w[q];
+      any |= x.x | x.y | x.z | x.w;
+    }
+    if (!any) continue;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(bbox + a, keys[3 * (size_t)b + a]);
+      atomicMax(bbox + 3 + a, keys[3 * (size_t)b + a]);
+    }
+  }
+}
+
+// Scatter the non-empty bricks of a hashed map into the grid layout.
+__global__ void grid_scatter_kernel(const int32_t* __restrict__ keys, const uint4* __restrict__ bricks,
+                                    uint32_t n_blocks, int gx, int gy, int gz, int dx, int dy,
+                                    uint4* __restrict__ grid, uint32_t* __restrict__ bitmap) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks;
+       b += gridDim.x * blockDim.x) {
+    const uint4* w = bricks + 4 * (size_t)b;
+    const uint4 w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3];
+    const uint32_t any = w0.x | w0.y | w0.z | w0.w | w1.x | w1.y | w1.z | w1.w | w2.x | w2.y |
+                         w2.z | w2.w | w3.x | w3.y | w3.z | w3.w;
+    if (!any) continue;
+    const uint32_t idx = (uint32_t)(keys[3 * (size_t)b] - gx) +
+                         (uint32_t)dx * ((uint32_t)(keys[3 * (size_t)b + 1] - gy) +
+                                         (uint32_t)dy * (uint32_t)(keys[3 * (size_t)b + 2] - gz));
+    uint4* dst = grid + 4 * (size_t)idx;
+    dst[0] = w0;
+    dst[1] = w1;
+    dst[2] = w2;
+    dst[3] = w3;
+    atomicOr(bitmap + (idx >> 5), 1u << (idx & 31));
   }
 }
 
@@ -953,27 +1030,40 @@ __global__ void hash_build_kernel(const int32_t* __restrict__ keys, uint32_t n_b
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
+size_t raycast_smem_bytes(const DevMap& m) {
+  if (m.layout == kLayoutGrid && m.bitmap_words * 4u <= kMaxSmemBitmapBytes)
+    return (size_t)m.bitmap_words * 4u;
+  return 0;
+}
+
+template <int KIND, int LAYOUT>
+static void launch_raycast_t(const DevMap& m, const EvalConsts& k, const double* state_dev,
+                             WsHeader* hdr, CtaPartial* parts, rmp_result_t* out_dev,
+                             rmp_ray_hit_t* hits, float* per_ray, int block, int grid,
+                             size_t smem, cudaStream_t stream) {
+  if (k.reduce_mode == RMP_REDUCE_FP64)
+    raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_FP64><<<grid, block, smem, stream>>>(
+        m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
+  else
+    raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_KAHAN32><<<grid, block, smem, stream>>>(
+        m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
+}
+
 cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,
                            void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
                            float* per_ray, int block, int grid, cudaStream_t stream) {
   WsHeader* hdr = (WsHeader*)ws;
   CtaPartial* parts = (CtaPartial*)((char*)ws + kWsHeaderBytes);
-  const size_t smem = 0;
-  if (m.kind == RMP_MAP_DENSE_U8) {
-    if (k.reduce_mode == RMP_REDUCE_FP64)
-      raycast_rmp_kernel<RMP_MAP_DENSE_U8, RMP_REDUCE_FP64><<<grid, block, smem, stream>>>(
-          m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
-    else
-      raycast_rmp_kernel<RMP_MAP_DENSE_U8, RMP_REDUCE_KAHAN32><<<grid, block, smem, stream>>>(
-          m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
-  } else {
-    if (k.reduce_mode == RMP_REDUCE_FP64)
-      raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, RMP_REDUCE_FP64><<<grid, block, smem, stream>>>(
-          m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
-    else
-      raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, RMP_REDUCE_KAHAN32><<<grid, block, smem, stream>>>(
-          m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
-  }
+  const size_t smem = raycast_smem_bytes(m);
+  if (m.kind == RMP_MAP_DENSE_U8)
+    launch_raycast_t<RMP_MAP_DENSE_U8, kLayoutGrid>(m, k, state_dev, hdr, parts, out_dev, hits,
+                                                    per_ray, block, grid, smem, stream);
+  else if (m.layout == kLayoutGrid)
+    launch_raycast_t<RMP_MAP_HASHED_TSDF, kLayoutGrid>(m, k, state_dev, hdr, parts, out_dev, hits,
+                                                       per_ray, block, grid, smem, stream);
+  else
+    launch_raycast_t<RMP_MAP_HASHED_TSDF, kLayoutHash>(m, k, state_dev, hdr, parts, out_dev, hits,
+                                                       per_ray, block, grid, smem, stream);
   return cudaGetLastError();
 }
 
@@ -992,16 +1082,34 @@ cudaError_t launch_scan(const float* pts, const EvalConsts& k, const double* sta
 }
 
 cudaError_t launch_dense_bricks(const uint8_t* occ, const int dims[3], const int nb[3],
-                                uint32_t* bricks, int* brick_index, cudaStream_t stream) {
-  const size_t nbr = (size_t)nb[0] * nb[1] * nb[2];
-  const size_t total = nbr * kBrickWords;
+                                uint32_t* bricks, cudaStream_t stream) {
+  const size_t total = (size_t)nb[0] * nb[1] * nb[2] * kBrickWords;
   const int grid = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
   dense_bricks_kernel<<<grid, 256, 0, stream>>>(occ, dims[0], dims[1], dims[2], nb[0], nb[1],
                                                 nb[2], bricks);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int g2 = (int)((nbr + 255) / 256 < 65535 ? (nbr + 255) / 256 : 65535);
-  dense_index_kernel<<<g2, 256, 0, stream>>>((const uint4*)bricks, (uint32_t)nbr, brick_index);
+  return cudaGetLastError();
+}
+
+static int grid_for(size_t n) { return (int)((n + 255) / 256 < 65535 ? ((n + 255) / 256 > 0 ? (n + 255) / 256 : 1) : 65535); }
+
+cudaError_t launch_grid_bitmap(const uint32_t* bricks, uint32_t n_bricks, uint32_t* bitmap,
+                               cudaStream_t stream) {
+  grid_bitmap_kernel<<<grid_for(n_bricks), 256, 0, stream>>>((const uint4*)bricks, n_bricks, bitmap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_key_bbox(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,
+                            int* bbox, cudaStream_t stream) {
+  key_bbox_kernel<<<grid_for(n_blocks), 256, 0, stream>>>(keys, (const uint4*)bricks, n_blocks, bbox);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_scatter(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,
+                                const int gmin[3], const int gdim[3], uint32_t* grid_bricks,
+                                uint32_t* bitmap, cudaStream_t stream) {
+  grid_scatter_kernel<<<grid_for(n_blocks), 256, 0, stream>>>(keys, (const uint4*)bricks, n_blocks,
+                                                              gmin[0], gmin[1], gmin[2], gdim[0],
+                                                              gdim[1], (uint4*)grid_bricks, bitmap);
   return cudaGetLastError();
 }
 

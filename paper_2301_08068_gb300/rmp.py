@@ -62,7 +62,7 @@ class rmp_map_desc_t(C.Structure):
 
 class rmp_map_info_t(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_bricks", C.c_uint32), ("hash_capacity", C.c_uint32),
-                ("reserved", C.c_uint32), ("device_bytes", C.c_uint64)]
+                ("layout", C.c_uint32), ("device_bytes", C.c_uint64)]
 
 
 assert C.sizeof(rmp_result_t) == 144 and C.sizeof(rmp_ray_hit_t) == 24
@@ -215,7 +215,7 @@ def rmp_map_info(ctx: int, map_id: int) -> dict:
     info = rmp_map_info_t()
     _check(lib().rmp_map_info(ctx, int(map_id), C.byref(info)), "rmp_map_info")
     return dict(kind=info.kind, n_bricks=info.n_bricks, hash_capacity=info.hash_capacity,
-                device_bytes=info.device_bytes)
+                layout=info.layout, device_bytes=info.device_bytes)
 
 
 def rmp_workspace_init(workspace, stream=None):

@@ -308,3 +308,29 @@ def test_dense_grid_not_multiple_of_eight(ctx):
         c = (np.array([x, y, z]) + 0.5) * 0.1                      # voxel centre: tie-prone
         check_raycast(ctx, mid, om, c, np.array([0.5, -1.0, 0.3]), 4000, W.PARAMS_STATIC_MAP, 5.0)
         check_raycast(ctx, mid, om, c + 0.0123, np.array([-0.2, 0.4, 1.1]), 4000, W.PARAMS_STATIC_MAP, 2.2)
+
+
+def test_layouts_grid_and_hash_fallback(ctx, hashed):
+    wl, mid, om = hashed
+    info = R.rmp_map_info(ctx.handle, mid)
+    assert info["layout"] == 0 and info["hash_capacity"] == 0        # grid over the bbox
+    rng = np.random.default_rng(8)
+    keys = np.array([(x, y, z) for x in (-2, -1, 0) for y in (-1, 0) for z in (-1, 0)]
+                    + [(5000, 4000, 700), (-6000, 10, -900)], np.int32)
+    tsdf = rng.uniform(-0.05, 0.3, (len(keys), 512)).astype(np.float32)
+    hm = W.HashedMap(keys, tsdf, 0.05)
+    mid2 = ctx.upload(hm)
+    info2 = R.rmp_map_info(ctx.handle, mid2)
+    assert info2["layout"] == 1 and info2["hash_capacity"] >= 4 * len(keys)
+    p = dict(W.PARAMS_STATIC_MAP)
+    for x in (np.array([-0.01, 0.013, -0.2]), np.array([0.11, -0.05, 0.02])):
+        check_raycast(ctx, mid2, O.OracleMap(hm), x, np.array([0.3, -1.0, 0.7]), 5000, p, 1.0)
+    # the same blocks without the far ones use the grid layout and give identical hits
+    hm3 = W.HashedMap(keys[:-2], tsdf[:-2], 0.05)
+    mid3 = ctx.upload(hm3)
+    assert R.rmp_map_info(ctx.handle, mid3)["layout"] == 0
+    pg = R.make_params(p, 1.0)
+    x = np.array([-0.01, 0.013, -0.2])
+    a = gpu_raycast(ctx, mid2, x, np.array([0.3, -1.0, 0.7]), 5000, pg)
+    b = gpu_raycast(ctx, mid3, x, np.array([0.3, -1.0, 0.7]), 5000, pg)
+    assert a[1].tobytes() == b[1].tobytes()
