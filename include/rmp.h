@@ -216,6 +216,18 @@ int rmp_scan_eval_async(rmp_ctx* ctx, const float* points_dev, uint32_t n,
                         void* workspace_dev, size_t workspace_bytes, rmp_stream_t stream,
                         rmp_result_t* out_dev, float* per_ray_dev);
 
+/* ------------------------------------------------------------------ launch tuning
+ * Knobs of the evaluation kernels (per context; picked by the batch autotuner, settable by
+ * hand).  They change the launch shape only: results are identical up to the order of
+ * the floating-point reduction, hit records are identical.
+ *  RMP_TUNE_BLOCK        threads per CTA: 64, 128 (default) or 256
+ *  RMP_TUNE_LG_SEGMENTS  log2 of the segments each ray is split into and marched by that
+ *                        many threads (0..2), or -1 (default) to choose from the ray count */
+#define RMP_TUNE_BLOCK 1
+#define RMP_TUNE_LG_SEGMENTS 2
+int rmp_tune_set(rmp_ctx* ctx, int knob, int value);
+int rmp_tune_get(rmp_ctx* ctx, int knob, int* value);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,8 @@ struct rmp_ctx {
   std::mutex mu;
   std::map<uint32_t, MapRec> maps;
   uint32_t next_id = 1;
+  int tune_block = 128;      // threads per CTA of the evaluation kernels
+  int tune_lg_segs = -1;     // log2 segments per ray (-1: chosen from the ray count)
   // scratch of the synchronous calls (serialised by mu)
   void* ws = nullptr;
   double* state_dev = nullptr;
@@ -112,7 +114,8 @@ void pick_ray_cells(uint32_t n, EvalConsts* k) {
 }
 
 // Derive the per-evaluation constants; validates every parameter.
-int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalConsts* k) {
+int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalConsts* k,
+                int lg_segs_override = -1) {
   if (!p) return RMP_ERR_INVALID_ARG;
   if (!(std::isfinite(p->eta_rep) && p->eta_rep >= 0.0) || !finite_pos(p->nu_rep) ||
       !(std::isfinite(p->eta_damp) && p->eta_damp >= 0.0) || !finite_pos(p->nu_damp) ||
@@ -145,6 +148,10 @@ int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalCon
     if (!(vox <= (double)kMaxRangeVoxels)) return RMP_ERR_INVALID_ARG;
     k->R_fx = std::llrint(vox * 65536.0);
     pick_ray_cells(n, k);
+    // march each ray as 4 (2) segments while that keeps the thread count modest, so a
+    // single evaluation fills more of the GPU and each thread's serial chain is shorter
+    k->lg_segs = n <= (1u << 17) ? 2u : (n <= (1u << 18) ? 1u : 0u);
+    if (lg_segs_override >= 0) k->lg_segs = (uint32_t)lg_segs_override;
   } else {
     k->perm_M = 1;
     k->perm_Q = n;
@@ -153,10 +160,10 @@ int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalCon
   return RMP_OK;
 }
 
-void launch_shape(const rmp_ctx* ctx, uint32_t n, int* block, int* grid) {
-  (void)ctx;
-  const int b = 128;
-  uint64_t g = ((uint64_t)n + b - 1) / b;
+// n_threads: rays (or points) times segments per ray
+void launch_shape(const rmp_ctx* ctx, uint64_t n_threads, int* block, int* grid) {
+  const int b = ctx->tune_block;
+  uint64_t g = (n_threads + b - 1) / b;
   if (g > (uint64_t)kMaxGrid) g = kMaxGrid;
   if (g < 1) g = 1;
   *block = b;
@@ -457,6 +464,30 @@ int rmp_map_info(rmp_ctx* c, uint32_t map_id, rmp_map_info_t* out) {
 
 size_t rmp_workspace_bytes(void) { return workspace_bytes(); }
 
+int rmp_tune_set(rmp_ctx* c, int knob, int value) {
+  if (!c) return RMP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (knob == RMP_TUNE_BLOCK) {
+    if (value != 64 && value != 128 && value != 256) return RMP_ERR_INVALID_ARG;
+    c->tune_block = value;
+  } else if (knob == RMP_TUNE_LG_SEGMENTS) {
+    if (value < -1 || value > 2) return RMP_ERR_INVALID_ARG;
+    c->tune_lg_segs = value;
+  } else {
+    return RMP_ERR_INVALID_ARG;
+  }
+  return RMP_OK;
+}
+
+int rmp_tune_get(rmp_ctx* c, int knob, int* value) {
+  if (!c || !value) return RMP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (knob == RMP_TUNE_BLOCK) *value = c->tune_block;
+  else if (knob == RMP_TUNE_LG_SEGMENTS) *value = c->tune_lg_segs;
+  else return RMP_ERR_INVALID_ARG;
+  return RMP_OK;
+}
+
 int rmp_workspace_init(void* ws, size_t bytes, rmp_stream_t stream) {
   if (!ws || bytes < workspace_bytes()) return RMP_ERR_INVALID_ARG;
   RMP_CUDA(cudaMemsetAsync(ws, 0, workspace_bytes(), (cudaStream_t)stream));
@@ -477,12 +508,12 @@ int rmp_raycast_eval_async(rmp_ctx* c, uint32_t map_id, const double* state_dev,
     dm = it->second.dm;
   }
   EvalConsts k;
-  int st = make_consts(params, dm.vs, n_rays, false, &k);
+  int st = make_consts(params, dm.vs, n_rays, false, &k, c->tune_lg_segs);
   if (st != RMP_OK) return st;
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   int block, grid;
-  launch_shape(c, n_rays, &block, &grid);
+  launch_shape(c, (uint64_t)n_rays << k.lg_segs, &block, &grid);
   RMP_CUDA(launch_raycast(dm, k, state_dev, ws, out_dev, hits_dev, per_ray_dev, block, grid,
                           (cudaStream_t)stream));
   return RMP_OK;
@@ -497,7 +528,7 @@ int rmp_raycast_eval(rmp_ctx* c, uint32_t map_id, const double x[3], const doubl
   if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
   const DevMap dm = it->second.dm;
   EvalConsts k;
-  int st = make_consts(params, dm.vs, n_rays, false, &k);
+  int st = make_consts(params, dm.vs, n_rays, false, &k, c->tune_lg_segs);
   if (st != RMP_OK) return st;
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
@@ -507,7 +538,7 @@ int rmp_raycast_eval(rmp_ctx* c, uint32_t map_id, const double x[3], const doubl
     c->state_host[3 + a] = xdot[a];
   }
   int block, grid;
-  launch_shape(c, n_rays, &block, &grid);
+  launch_shape(c, (uint64_t)n_rays << k.lg_segs, &block, &grid);
   RMP_CUDA(cudaMemcpyAsync(c->state_dev, c->state_host, 6 * sizeof(double),
                            cudaMemcpyHostToDevice, s));
   RMP_CUDA(launch_raycast(dm, k, c->state_dev, c->ws, c->result_dev, hits_dev, per_ray_dev,

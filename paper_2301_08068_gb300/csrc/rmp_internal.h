@@ -63,6 +63,7 @@ struct EvalConsts {
   long long R_fx;           // llrint(max_range / vs * 2^16)
   uint32_t n_rays, halton_offset;
   uint32_t perm_M, perm_Q, perm_R;   // coherent ray order (see ray_of_slot)
+  uint32_t lg_segs;                  // each ray is marched as 2^lg_segs segments
   int w_mode, reduce_mode;
 };
 

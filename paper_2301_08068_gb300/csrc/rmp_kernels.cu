@@ -180,12 +180,14 @@ __device__ __forceinline__ bool brick_bit(const Brick& b, int kx, int ky, int kz
 // wins.  A voxel is entered only if N_a 2^24 <= R_fx |D_a|, i.e. N_a <= L_a.
 // Blocks without occupied voxels are crossed in one step of integer arithmetic that
 // reproduces the voxel-by-voxel crossings exactly (skip_block).
-struct MarchOut {
+constexpr int kSegContinues = 0;   // segment ended at its upper parameter bound
+
+struct SegOut {
   int k[3];
-  uint32_t steps;
-  uint32_t blocks;          // distinct blocks entered (each looked up once)
+  uint32_t steps;           // steps from the ray's start voxel
   uint32_t n_last, a_last;  // entry numerator / |D| of the last voxel (0/1 at the start)
-  int status;
+  int ax_last;              // axis of the last step (for map exits)
+  int status;               // RMP_RAY_* or kSegContinues
 };
 
 __device__ __forceinline__ int min_axis(const uint32_t n[3], const uint32_t a[3]) {
@@ -290,11 +292,28 @@ __device__ __forceinline__ bool skip_block(const DevMap& m, int k[3], const int 
   return false;
 }
 
+// One segment of a ray.  A ray's parameter range (0, R], R = R_fx / 2^24, is split into S
+// = 2^lgS equal segments; segment `seg` handles the crossings with t in (T_seg, T_seg+1],
+// T_s = s R / S, so the S segments of a ray can be marched by S threads at once.  A
+// crossing numerator n of axis a (t = n / |D_a|) satisfies t <= T_s iff
+// n S 2^24 <= s R_fx |D_a|; the segment's start state (all crossings with t <= T_seg
+// applied) and its limits L_a follow from that in integer arithmetic.  Within a segment:
+// free blocks are crossed by skip_block, occupied ones voxel by voxel, with the order of
+// the next crossings kept in the exact differences E_ab = N_a |D_b| - N_b |D_a|.
 template <int KIND, int LAYOUT>
-__device__ __forceinline__ MarchOut march(const DevMap& m, const uint32_t* bm, const long long P[3],
-                                          const int D[3], long long R_fx) {
+__device__ __forceinline__ SegOut march_segment(const DevMap& m, const uint32_t* bm,
+                                                const long long P[3], const int D[3],
+                                                long long R_fx, uint32_t seg, uint32_t lgS) {
   int k[3], s[3];
   uint32_t N[3], A[3], L[3];
+  SegOut o;
+  o.steps = 0;
+  o.n_last = 0;
+  o.a_last = 1;
+  o.ax_last = 0;
+  const bool last_seg = seg == (1u << lgS) - 1;
+  uint32_t bn = 0, ba = 1;
+  bool any = false;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     k[a] = (int)(P[a] >> 16);
@@ -302,23 +321,40 @@ __device__ __forceinline__ MarchOut march(const DevMap& m, const uint32_t* bm, c
     A[a] = (uint32_t)abs(D[a]);
     const long long lo = (long long)k[a] << 16;
     N[a] = D[a] > 0 ? (uint32_t)(lo + 65536 - P[a]) : (D[a] < 0 ? (uint32_t)(P[a] - lo) : 1u);
-    L[a] = (uint32_t)(((unsigned long long)R_fx * A[a]) >> 24);
+    L[a] = (uint32_t)(((unsigned long long)(seg + 1) * (unsigned long long)R_fx * A[a]) >> (24 + lgS));
+    if (seg > 0 && A[a] != 0) {
+      const unsigned long long X = (unsigned long long)seg * (unsigned long long)R_fx * A[a];
+      const unsigned long long Y = (unsigned long long)N[a] << (24 + lgS);
+      if (X >= Y) {
+        const uint32_t cnt = (uint32_t)((X - Y) >> (40 + lgS)) + 1;
+        const uint32_t nl = N[a] + ((cnt - 1) << 16);
+        if (!any || (unsigned long long)nl * ba > (unsigned long long)bn * A[a]) {
+          bn = nl;
+          ba = A[a];
+        }
+        any = true;
+        k[a] += s[a] * (int)cnt;
+        N[a] += cnt << 16;
+        o.steps += cnt;
+      }
+    }
   }
-  MarchOut o;
-  o.steps = 0;
-  o.blocks = 0;
-  o.n_last = 0;
-  o.a_last = 1;
+  if (any) {
+    o.n_last = bn;
+    o.a_last = ba;
+  }
   o.status = RMP_RAY_MISS_EXIT;
   if (!outside<KIND>(m, k)) {
-    o.status = RMP_RAY_MISS_RANGE;
+    o.status = last_seg ? RMP_RAY_MISS_RANGE : kSegContinues;
     for (uint32_t guard = 0; guard < 3u * (kMaxRangeVoxels + 2); ++guard) {
-      o.blocks += 1;
       Brick w;
       if (!fetch_brick<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, w)) {
-        if (skip_block<KIND>(m, k, s, N, A, L, o.steps, o.n_last, o.a_last)) break;  // range
+        if (skip_block<KIND>(m, k, s, N, A, L, o.steps, o.n_last, o.a_last)) break;  // limit
         if (outside<KIND>(m, k)) {
           o.status = RMP_RAY_MISS_EXIT;
+          // the exit step is the one that left the block: the axis whose voxel is outside
+          o.ax_last = ((unsigned)k[0] >= (unsigned)m.dims[0]) ? 0
+                      : (((unsigned)k[1] >= (unsigned)m.dims[1]) ? 1 : 2);
           break;
         }
         continue;
@@ -327,27 +363,49 @@ __device__ __forceinline__ MarchOut march(const DevMap& m, const uint32_t* bm, c
         o.status = RMP_RAY_HIT;
         break;
       }
+      // exact order of the next crossings: E_xy > 0 <=> t_y < t_x, etc.
+      long long exy = (long long)N[0] * A[1] - (long long)N[1] * A[0];
+      long long exz = (long long)N[0] * A[2] - (long long)N[2] * A[0];
+      long long eyz = (long long)N[1] * A[2] - (long long)N[2] * A[1];
+      const long long u0 = (long long)A[0] << 16, u1 = (long long)A[1] << 16,
+                      u2 = (long long)A[2] << 16;
       bool done = false;
       // at most 21 interior steps and one exit step inside an 8^3 block
       for (int it = 0; it < 24; ++it) {
-        const int ax = min_axis(N, A);
+        const bool ylx = exy > 0;
+        const bool zlw = ylx ? (eyz > 0) : (exz > 0);
+        const int ax = zlw ? 2 : (ylx ? 1 : 0);
         const uint32_t na = sel3(N, ax), aa = sel3(A, ax), la = sel3(L, ax);
-        if (na > la) {                                  // next voxel beyond range
+        if (na > la) {                                  // next crossing beyond the limit
           done = true;
           break;
         }
         o.n_last = na;
         o.a_last = aa;
+        o.ax_last = ax;
         o.steps += 1;
         bool crossed = false;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          if (ax == a) {
-            const int kn = k[a] + s[a];
-            crossed = ((kn ^ k[a]) & ~7) != 0;
-            k[a] = kn;
-            N[a] += 65536u;
-          }
+        if (ax == 0) {
+          const int kn = k[0] + s[0];
+          crossed = ((kn ^ k[0]) & ~7) != 0;
+          k[0] = kn;
+          N[0] += 65536u;
+          exy += u1;
+          exz += u2;
+        } else if (ax == 1) {
+          const int kn = k[1] + s[1];
+          crossed = ((kn ^ k[1]) & ~7) != 0;
+          k[1] = kn;
+          N[1] += 65536u;
+          exy -= u0;
+          eyz += u2;
+        } else {
+          const int kn = k[2] + s[2];
+          crossed = ((kn ^ k[2]) & ~7) != 0;
+          k[2] = kn;
+          N[2] += 65536u;
+          exz -= u0;
+          eyz -= u1;
         }
         if (outside<KIND>(m, k)) {
           o.status = RMP_RAY_MISS_EXIT;
@@ -368,6 +426,22 @@ __device__ __forceinline__ MarchOut march(const DevMap& m, const uint32_t* bm, c
   o.k[1] = k[1];
   o.k[2] = k[2];
   return o;
+}
+
+// Distinct 8^3 blocks whose occupancy the march tested: the voxel path is monotone on
+// each axis and blocks are convex, so this is 1 + the block changes along each axis up to
+// the last tested voxel (for a map exit the voxel before the exit step; none if the ray
+// starts outside the map).
+__device__ __forceinline__ uint32_t blocks_tested(const int k0[3], const SegOut& o, const int s[3]) {
+  int kf[3] = {o.k[0], o.k[1], o.k[2]};
+  if (o.status == RMP_RAY_MISS_EXIT) {
+    if (o.steps == 0) return 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a == o.ax_last) kf[a] -= s[a];
+  }
+  return 1u + (uint32_t)(abs((kf[0] >> 3) - (k0[0] >> 3)) + abs((kf[1] >> 3) - (k0[1] >> 3)) +
+                         abs((kf[2] >> 3) - (k0[2] >> 3)));
 }
 
 __device__ __forceinline__ float entry_distance(uint32_t n, uint32_t a, float vs_f) {
@@ -582,10 +656,10 @@ __device__ void resolve_pinv(const double S[6], const double b[3], rmp_result_t&
   float a00 = (float)(S[0] * scale), a01 = (float)(S[1] * scale), a02 = (float)(S[2] * scale),
         a11 = (float)(S[3] * scale), a12 = (float)(S[4] * scale), a22 = (float)(S[5] * scale);
   float V[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
-  for (int sweep = 0; sweep < 10; ++sweep) {
+  for (int sweep = 0; sweep < 6; ++sweep) {
     const float off = fabsf(a01) + fabsf(a02) + fabsf(a12);
     const float dia = fabsf(a00) + fabsf(a11) + fabsf(a22);
-    if (off <= 1e-9f * dia) break;
+    if (off <= 1e-6f * dia) break;                  // FP32 accuracy; FP64 refines below
 #pragma unroll
     for (int pq = 0; pq < 3; ++pq) {
       float app, aqq, apq, apo, aqo;
@@ -751,7 +825,53 @@ __device__ __forceinline__ uint32_t ray_of_slot(uint32_t j, const EvalConsts& k)
   return r + k.perm_M * q;
 }
 
+// ------------------------------------------------------------------ shared-memory staging
+// The block bitmap is copied into shared memory by one TMA bulk copy (cp.async.bulk,
+// completion counted on an mbarrier) issued at kernel entry, so it overlaps the state
+// set-up and ray generation.  The wait is bounded: on expiry the CTA reports a timeout
+// (after waiting, again bounded, for the copy to land) instead of hanging.
+constexpr uint32_t kWaitSpins = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void bulk_load_begin(uint64_t* bar, void* dst, const void* src,
+                                                uint32_t bytes) {
+  const uint32_t b = smem_u32(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(b)
+      : "memory");
+}
+
+// true once phase 0 of the barrier completed; false if the bounded wait expired
+__device__ __forceinline__ bool bulk_load_wait(uint64_t* bar) {
+  const uint32_t b = smem_u32(bar);
+  for (uint32_t i = 0; i < kWaitSpins; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(b)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // ------------------------------------------------------------------ fused raycast kernel
+// Thread g of the launch handles segment g % S of the ray in slot g / S; the S segments of a
+// ray sit in adjacent lanes, and the ray's result is the first segment (lowest index) that
+// hit or left the map, else the last one -- found with a warp ballot and moved to the
+// ray's first lane by shuffles.  That lane evaluates the policy and writes the outputs.
 template <int KIND, int LAYOUT, int RED>
 __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k,
                                                           const double* __restrict__ state,
@@ -760,12 +880,13 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
                                                           float* per_ray) {
   extern __shared__ uint4 smem_bitmap[];
   __shared__ CtaState cs;
-  const uint32_t* bm = m.bitmap;
-  if (LAYOUT == kLayoutGrid && m.bitmap_words * 4u <= kMaxSmemBitmapBytes) {
-    // stage the block bitmap (128-bit loads, coalesced) while threads 0-5 set up the state
-    const uint4* g = reinterpret_cast<const uint4*>(m.bitmap);
-    for (uint32_t i = threadIdx.x; i < m.bitmap_words / 4; i += blockDim.x) smem_bitmap[i] = __ldg(g + i);
-    bm = reinterpret_cast<const uint32_t*>(smem_bitmap);
+  __shared__ __align__(8) uint64_t bm_bar;
+  __shared__ int bm_timeout;
+  const bool staged = LAYOUT == kLayoutGrid && m.bitmap_words * 4u <= kMaxSmemBitmapBytes;
+  const uint32_t* bm = staged ? reinterpret_cast<const uint32_t*>(smem_bitmap) : m.bitmap;
+  if (threadIdx.x == 0) {
+    bm_timeout = 0;
+    if (staged) bulk_load_begin(&bm_bar, smem_bitmap, m.bitmap, m.bitmap_words * 4u);
   }
   if (threadIdx.x < 3) {
     const int a = threadIdx.x;
@@ -779,55 +900,98 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
   } else if (threadIdx.x < 6) {
     split_velocity(state, cs, threadIdx.x - 3);
   }
-  __syncthreads();
-  const bool bad = cs.bad[0] | cs.bad[1] | cs.bad[2];
   typename BlockReduce<RED>::Acc acc;
   BlockReduce<RED>::init(acc);
   unsigned n_hit = 0, n_act = 0;
-  if (!bad) {
+  const uint32_t lgS = k.lg_segs, S = 1u << lgS;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t total = k.n_rays << lgS;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+  // the first ray is generated while the bitmap copy and the state set-up are in flight
+  uint32_t ray_idx = ray_of_slot(base + lane < total ? (base + lane) >> lgS : 0, k);
+  Ray ray = make_ray(ray_idx + k.halton_offset);
+  __syncthreads();                                  // state ready, barrier initialised
+  if (staged && !bulk_load_wait(&bm_bar)) bm_timeout = 1;
+  __syncthreads();
+  const bool bad = (cs.bad[0] | cs.bad[1] | cs.bad[2] | bm_timeout) != 0;
+  bool first = true;
+  // warp-uniform trip count: every lane takes part in each ballot / shuffle
+  for (; base < total; base += stride) {
+    const uint32_t g = base + lane;
+    const bool active = g < total;
+    const uint32_t seg = g & (S - 1);
+    if (!first) {
+      ray_idx = ray_of_slot(active ? (g >> lgS) : 0, k);
+      ray = make_ray(ray_idx + k.halton_offset);
+    }
+    first = false;
     const long long P[3] = {cs.P[0], cs.P[1], cs.P[2]};
+    SegOut so;
+    so.k[0] = so.k[1] = so.k[2] = 0;
+    so.steps = so.n_last = 0;
+    so.a_last = 1;
+    so.ax_last = 0;
+    so.status = kSegContinues;
+    if (active && !bad) so = march_segment<KIND, LAYOUT>(m, bm, P, ray.D, k.R_fx, seg, lgS);
+    // combine the ray's segments into its first lane
+    const bool fin = active && (so.status == RMP_RAY_HIT || so.status == RMP_RAY_MISS_EXIT);
+    const uint32_t ballot = __ballot_sync(0xffffffffu, fin);
+    const uint32_t grp0 = lane & ~(S - 1);
+    const uint32_t gmask = (S == 32 ? 0xffffffffu : ((1u << S) - 1u)) << grp0;
+    const uint32_t fb = ballot & gmask;
+    const int src = fb ? (__ffs(fb) - 1) : (int)(grp0 + S - 1);
+    SegOut mo;
+    mo.k[0] = __shfl_sync(0xffffffffu, so.k[0], src);
+    mo.k[1] = __shfl_sync(0xffffffffu, so.k[1], src);
+    mo.k[2] = __shfl_sync(0xffffffffu, so.k[2], src);
+    mo.steps = __shfl_sync(0xffffffffu, so.steps, src);
+    mo.n_last = __shfl_sync(0xffffffffu, so.n_last, src);
+    mo.a_last = __shfl_sync(0xffffffffu, so.a_last, src);
+    mo.ax_last = __shfl_sync(0xffffffffu, so.ax_last, src);
+    mo.status = __shfl_sync(0xffffffffu, so.status, src);
+    if (!active || bad || seg != 0) continue;
+    const float d = mo.n_last == 0 ? 0.0f : entry_distance(mo.n_last, mo.a_last, m.vs_f);
+    float f[3] = {0.f, 0.f, 0.f}, A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, af[3];
     const float v[3] = {cs.v[0], cs.v[1], cs.v[2]};
     const float vl[3] = {cs.vl[0], cs.vl[1], cs.vl[2]};
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < k.n_rays;
-         j += gridDim.x * blockDim.x) {
-      const uint32_t ray_idx = ray_of_slot(j, k);
-      const Ray ray = make_ray(ray_idx + k.halton_offset);
-      const MarchOut mo = march<KIND, LAYOUT>(m, bm, P, ray.D, k.R_fx);
-      const float d = mo.n_last == 0 ? 0.0f : entry_distance(mo.n_last, mo.a_last, m.vs_f);
-      float f[3] = {0.f, 0.f, 0.f}, A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, af[3];
-      if (mo.status == RMP_RAY_HIT) {
-        const bool act = active32(v, ray.dir);
-        const bool inr = d < k.r_up;
-        n_hit += 1;
-        n_act += (act && inr) ? 1u : 0u;
-        obstacle_policy(k, ray.dir, d, v, vl, act, inr, f, A, af);
-        const float vals[9] = {A[0], A[1], A[2], A[3], A[4], A[5], af[0], af[1], af[2]};
-        BlockReduce<RED>::add(acc, vals);
-      }
-      if (hits) {
-        rmp_ray_hit_t h;
-        h.voxel[0] = mo.k[0];
-        h.voxel[1] = mo.k[1];
-        h.voxel[2] = mo.k[2];
-        h.steps = mo.steps;
-        h.d = d;
-        h.status = (uint8_t)mo.status;
-        h.pad = 0;
-        h.blocks = (uint16_t)mo.blocks;
-        hits[ray_idx] = h;
-      }
-      if (per_ray) {
-        float* o = per_ray + 9 * (size_t)ray_idx;
-        o[0] = f[0]; o[1] = f[1]; o[2] = f[2];
-        o[3] = A[0]; o[4] = A[1]; o[5] = A[2]; o[6] = A[3]; o[7] = A[4]; o[8] = A[5];
-      }
+    if (mo.status == RMP_RAY_HIT) {
+      const bool act = active32(v, ray.dir);
+      const bool inr = d < k.r_up;
+      n_hit += 1;
+      n_act += (act && inr) ? 1u : 0u;
+      obstacle_policy(k, ray.dir, d, v, vl, act, inr, f, A, af);
+      const float vals[9] = {A[0], A[1], A[2], A[3], A[4], A[5], af[0], af[1], af[2]};
+      BlockReduce<RED>::add(acc, vals);
+    }
+    if (hits) {
+      const int k0[3] = {(int)(P[0] >> 16), (int)(P[1] >> 16), (int)(P[2] >> 16)};
+      const int sg[3] = {ray.D[0] > 0 ? 1 : -1, ray.D[1] > 0 ? 1 : -1, ray.D[2] > 0 ? 1 : -1};
+      rmp_ray_hit_t h;
+      h.voxel[0] = mo.k[0];
+      h.voxel[1] = mo.k[1];
+      h.voxel[2] = mo.k[2];
+      h.steps = mo.steps;
+      h.d = d;
+      h.status = (uint8_t)mo.status;
+      h.pad = 0;
+      h.blocks = (uint16_t)blocks_tested(k0, mo, sg);
+      hits[ray_idx] = h;
+    }
+    if (per_ray) {
+      float* o = per_ray + 9 * (size_t)ray_idx;
+      o[0] = f[0]; o[1] = f[1]; o[2] = f[2];
+      o[3] = A[0]; o[4] = A[1]; o[5] = A[2]; o[6] = A[3]; o[7] = A[4]; o[8] = A[5];
     }
   }
+  if (staged && bm_timeout) bulk_load_wait(&bm_bar);   // let a late copy land before exit
   double part[9];
   BlockReduce<RED>::reduce(acc, part);
   const unsigned bh = block_sum_u32(n_hit);
   const unsigned ba = block_sum_u32(n_act);
-  grid_finish(part, bh, ba, ws, parts, out, k.n_rays, bad ? RMP_ERR_INVALID_ARG : RMP_OK);
+  const int status = bm_timeout ? RMP_ERR_TIMEOUT
+                     : ((cs.bad[0] | cs.bad[1] | cs.bad[2]) ? RMP_ERR_INVALID_ARG : RMP_OK);
+  grid_finish(part, bh, ba, ws, parts, out, k.n_rays, status);
 }
 
 // ------------------------------------------------------------------ LiDAR scan kernel (Sec. III-G)

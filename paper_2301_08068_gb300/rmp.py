@@ -28,6 +28,7 @@ RMP_RAY_HIT, RMP_RAY_MISS_RANGE, RMP_RAY_MISS_EXIT = 1, 2, 3
 RMP_MAP_DENSE_U8, RMP_MAP_HASHED_TSDF = 0, 1
 RMP_PRESET_STATIC_MAP, RMP_PRESET_LIDAR = 0, 1
 RMP_REDUCE_KAHAN32, RMP_REDUCE_FP64 = 0, 1
+RMP_TUNE_BLOCK, RMP_TUNE_LG_SEGMENTS = 1, 2
 
 
 class RmpError(RuntimeError):
@@ -88,6 +89,8 @@ _SIGNATURES = {
                       C.POINTER(rmp_result_t), _P],
     "rmp_scan_eval_async": [_P, _P, C.c_uint32, _P, C.POINTER(rmp_params_t), _P, C.c_size_t, _P,
                             _P, _P],
+    "rmp_tune_set": [_P, C.c_int, C.c_int],
+    "rmp_tune_get": [_P, C.c_int, C.POINTER(C.c_int)],
 }
 # Symbols every build must export (checked by the not-gpu ABI test against include/rmp.h).
 EXPORTS = sorted(list(_SIGNATURES) + ["rmp_status_string", "rmp_workspace_bytes"])
@@ -257,6 +260,16 @@ def rmp_scan_eval_async(ctx: int, points, state, params: rmp_params_t, workspace
                                      _dptr(workspace), workspace.numel() * workspace.element_size(),
                                      _stream(stream), _dptr(out), _dptr(per_ray)),
            "rmp_scan_eval_async")
+
+
+def rmp_tune_set(ctx: int, knob: int, value: int):
+    _check(lib().rmp_tune_set(ctx, int(knob), int(value)), "rmp_tune_set")
+
+
+def rmp_tune_get(ctx: int, knob: int) -> int:
+    v = C.c_int()
+    _check(lib().rmp_tune_get(ctx, int(knob), C.byref(v)), "rmp_tune_get")
+    return int(v.value)
 
 
 # ----------------------------------------------------------------------------- map descriptors

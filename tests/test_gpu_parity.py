@@ -334,3 +334,21 @@ def test_layouts_grid_and_hash_fallback(ctx, hashed):
     a = gpu_raycast(ctx, mid2, x, np.array([0.3, -1.0, 0.7]), 5000, pg)
     b = gpu_raycast(ctx, mid3, x, np.array([0.3, -1.0, 0.7]), 5000, pg)
     assert a[1].tobytes() == b[1].tobytes()
+
+
+@pytest.mark.parametrize("block,lgs", [(64, 0), (128, 1), (256, 2), (128, -1)])
+def test_tuning_knobs_keep_results(ctx, hashed, block, lgs):
+    """Block size and ray segmentation change the launch shape only: hit records stay
+    bit-identical to the oracle's, values within tolerance."""
+    wl, mid, om = hashed
+    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, block)
+    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, lgs)
+    try:
+        assert R.rmp_tune_get(ctx.handle, R.RMP_TUNE_BLOCK) == block
+        for s, n in ((wl.states[1], 65536), (wl.states[2], 777)):
+            check_raycast(ctx, mid, om, s.x, s.xdot, n, wl.params, wl.max_range)
+    finally:
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 128)
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, -1)
+    with pytest.raises(R.RmpError):
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 100)
