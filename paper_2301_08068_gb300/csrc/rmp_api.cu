@@ -148,9 +148,9 @@ int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalCon
     if (!(vox <= (double)kMaxRangeVoxels)) return RMP_ERR_INVALID_ARG;
     k->R_fx = std::llrint(vox * 65536.0);
     pick_ray_cells(n, k);
-    // march each ray as 4 (2) segments while that keeps the thread count modest, so a
-    // single evaluation fills more of the GPU and each thread's serial chain is shorter
-    k->lg_segs = n <= (1u << 17) ? 2u : (n <= (1u << 18) ? 1u : 0u);
+    // small evaluations are latency-bound: marching each ray as 4 (2) segments shortens
+    // every thread's serial chain; large ones are issue-bound, where segments only add work
+    k->lg_segs = n <= 4096u ? 2u : (n <= 16384u ? 1u : 0u);
     if (lg_segs_override >= 0) k->lg_segs = (uint32_t)lg_segs_override;
   } else {
     k->perm_M = 1;
