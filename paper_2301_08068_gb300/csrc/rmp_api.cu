@@ -182,6 +182,18 @@ uint32_t bitmap_words_for(uint64_t n_bricks) {
   return (uint32_t)((w + 3) / 4 * 4);            // whole uint4s
 }
 
+// Superblock (4^3 blocks) extent covering the grid gmin .. gmin + gdim - 1, and the size of
+// both bitmaps.
+void set_superblocks(DevMap& dm) {
+  uint64_t n = 1;
+  for (int a = 0; a < 3; ++a) {
+    dm.sgmin[a] = dm.gmin[a] >> 2;                          // floor for negatives too
+    dm.sgdim[a] = ((dm.gmin[a] + dm.gdim[a] - 1) >> 2) - dm.sgmin[a] + 1;
+    n *= (uint64_t)dm.sgdim[a];
+  }
+  dm.sbitmap_words = bitmap_words_for(n);
+}
+
 
 }  // namespace
 
@@ -321,15 +333,17 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
     r.dm.layout = kLayoutGrid;
     r.n_bricks = (uint32_t)nbr;
     r.dm.bitmap_words = bitmap_words_for(nbr);
+    set_superblocks(r.dm);
+    const size_t bm_bytes = (size_t)(r.dm.bitmap_words + r.dm.sbitmap_words) * 4;
     cudaError_t e = cudaMalloc(&r.bricks, nbr * 64);
-    if (e == cudaSuccess) e = cudaMalloc(&r.bitmap, (size_t)r.dm.bitmap_words * 4);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r.bitmap, 0, (size_t)r.dm.bitmap_words * 4, s);
+    if (e == cudaSuccess) e = cudaMalloc(&r.bitmap, bm_bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r.bitmap, 0, bm_bytes, s);
     if (e == cudaSuccess) e = launch_dense_bricks(occ, r.dm.dims, r.dm.gdim, (uint32_t*)r.bricks, s);
     if (e == cudaSuccess)
-      e = launch_grid_bitmap((const uint32_t*)r.bricks, (uint32_t)nbr, (uint32_t*)r.bitmap, s);
+      e = launch_grid_bitmap((const uint32_t*)r.bricks, r.dm, (uint32_t*)r.bitmap, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(cuda_status(e));
-    r.bytes = nbr * 64 + (uint64_t)r.dm.bitmap_words * 4;
+    r.bytes = nbr * 64 + bm_bytes;
   } else if (d->kind == RMP_MAP_HASHED_TSDF) {
     const uint32_t n = d->n_blocks;
     if (n > (1u << 26)) return RMP_ERR_INVALID_ARG;
@@ -404,16 +418,18 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
       }
       r.n_bricks = (uint32_t)gprod;
       r.dm.bitmap_words = bitmap_words_for(gprod);
+      set_superblocks(r.dm);
+      const size_t bm_bytes = (size_t)(r.dm.bitmap_words + r.dm.sbitmap_words) * 4;
       e = cudaMalloc(&r.bricks, grid_bytes);
       if (e == cudaSuccess) e = cudaMemsetAsync(r.bricks, 0, grid_bytes, s);
-      if (e == cudaSuccess) e = cudaMalloc(&r.bitmap, (size_t)r.dm.bitmap_words * 4);
-      if (e == cudaSuccess) e = cudaMemsetAsync(r.bitmap, 0, (size_t)r.dm.bitmap_words * 4, s);
+      if (e == cudaSuccess) e = cudaMalloc(&r.bitmap, bm_bytes);
+      if (e == cudaSuccess) e = cudaMemsetAsync(r.bitmap, 0, bm_bytes, s);
       if (e == cudaSuccess && n > 0 && !none)
-        e = launch_grid_scatter(keys, (const uint32_t*)compact, n, gmin, gdim, (uint32_t*)r.bricks,
+        e = launch_grid_scatter(keys, (const uint32_t*)compact, n, r.dm, (uint32_t*)r.bricks,
                                 (uint32_t*)r.bitmap, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return fail(cuda_status(e));
-      r.bytes = grid_bytes + (uint64_t)r.dm.bitmap_words * 4;
+      r.bytes = grid_bytes + bm_bytes;
     } else {
       r.dm.layout = kLayoutHash;
       r.bricks = compact;

@@ -5,8 +5,10 @@
 //     its value is <= 0; a dense voxel iff it is nonzero).
 //   * grid layout (dense maps, and hashed maps whose block bounding box is moderate): the
 //     bricks of every block in the bounding box, x fastest (all-zero where free), plus a
-//     1-bit-per-block bitmap of the blocks that hold an occupied voxel.  The march stages
-//     the bitmap in shared memory, so free blocks cost no global access at all.
+//     1-bit-per-block bitmap of the blocks that hold an occupied voxel, followed by a
+//     1-bit-per-superblock bitmap (4^3 blocks = 32^3 voxels, aligned to multiples of 32
+//     voxels).  The march stages both in shared memory, so free space costs no global
+//     access and is crossed 32 voxels at a time where a whole superblock is free.
 //   * hash layout (fallback for very large extents): power-of-two array of 16-byte entries
 //     {key, slot}; key packs the block coordinates (21 bits each, offset by 2^20); empty
 //     entries hold ~0; linear probing from a Fibonacci (multiply-shift) hash, load factor
@@ -50,6 +52,10 @@ struct DevMap {
   int dims[3];              // dense voxels per axis
   int gmin[3];              // grid: block coordinates of the grid's first brick
   int gdim[3];              // grid: bricks per axis
+  int sgmin[3];             // grid: superblock (4^3 blocks, 32^3 voxels) of the first brick
+  int sgdim[3];             // grid: superblocks per axis
+  uint32_t sbitmap_words;   // grid: uint32 words of the superblock bitmap (multiple of 4),
+                            // stored right after the block bitmap
   const uint4* bricks;      // grid: brick (x + gdim0 (y + gdim1 z)); hash: by slot
   const uint32_t* bitmap;   // grid: bit idx set iff brick idx holds an occupied voxel
   const HashEntry* table;   // hash layout only
@@ -97,13 +103,13 @@ cudaError_t launch_scan(const float* pts, const EvalConsts& k, const double* sta
                         cudaStream_t stream);
 cudaError_t launch_dense_bricks(const uint8_t* occ, const int dims[3], const int nb[3],
                                 uint32_t* bricks, cudaStream_t stream);
-cudaError_t launch_grid_bitmap(const uint32_t* bricks, uint32_t n_bricks, uint32_t* bitmap,
+cudaError_t launch_grid_bitmap(const uint32_t* bricks, const DevMap& m, uint32_t* bitmap,
                                cudaStream_t stream);
 cudaError_t launch_key_bbox(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,
                             int* bbox, cudaStream_t stream);
 cudaError_t launch_grid_scatter(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,
-                                const int gmin[3], const int gdim[3], uint32_t* grid_bricks,
-                                uint32_t* bitmap, cudaStream_t stream);
+                                const DevMap& m, uint32_t* grid_bricks, uint32_t* bitmap,
+                                cudaStream_t stream);
 cudaError_t launch_tsdf_bricks(const float* tsdf, uint32_t n_blocks, uint32_t* bricks,
                                cudaStream_t stream);
 cudaError_t launch_hash_build(const int32_t* keys, uint32_t n_blocks, const uint32_t* bricks,

@@ -179,7 +179,7 @@ __device__ __forceinline__ bool brick_bit(const Brick& b, int kx, int ky, int kz
 // ties go to the lowest axis); an axis with D_a = 0 has |D_a| = 0, N_a = 1 and so never
 // wins.  A voxel is entered only if N_a 2^24 <= R_fx |D_a|, i.e. N_a <= L_a.
 // Blocks without occupied voxels are crossed in one step of integer arithmetic that
-// reproduces the voxel-by-voxel crossings exactly (skip_block).
+// reproduces the voxel-by-voxel crossings exactly (skip_cell).
 constexpr int kSegContinues = 0;   // segment ended at its upper parameter bound
 
 struct SegOut {
@@ -209,21 +209,23 @@ __device__ __forceinline__ bool outside(const DevMap& m, const int k[3]) {
           (unsigned)k[2] >= (unsigned)m.dims[2]);
 }
 
-// The ray is in a block (clipped to the dense grid) that holds no occupied voxel.  Advance
-// the DDA state to the first voxel beyond it exactly as single steps would: the block is
-// left through the axis e whose face crossing F_e/|D_e| comes first (ties: lowest axis);
-// every other axis b crosses its interior boundaries that come strictly before that time
-// (or at the same time if b < e, the tie order).  If the face crossing is out of range,
-// the ray ends inside the block after every in-range crossing; returns true then.
-template <int KIND>
-__device__ __forceinline__ bool skip_block(const DevMap& m, int k[3], const int s[3], uint32_t N[3],
-                                           const uint32_t A[3], const uint32_t L[3],
-                                           uint32_t& steps, uint32_t& n_last, uint32_t& a_last) {
+// The ray is in a free cell of 2^LOG2C voxels per side (a block, or a superblock; cells are
+// aligned to multiples of their size and clipped to the dense grid).  Advance the DDA
+// state to the first voxel beyond it exactly as single steps would: the cell is left
+// through the axis e whose face crossing F_e/|D_e| comes first (ties: lowest axis); every
+// other axis b crosses its interior boundaries that come strictly before that time (or at
+// the same time if b < e, the tie order).  If the face crossing is beyond the limit, the
+// ray ends inside the cell after every crossing within the limit; returns true then.
+template <int KIND, int LOG2C>
+__device__ __forceinline__ bool skip_cell(const DevMap& m, int k[3], const int s[3], uint32_t N[3],
+                                          const uint32_t A[3], const uint32_t L[3],
+                                          uint32_t& steps, uint32_t& n_last, uint32_t& a_last) {
+  constexpr int C = 1 << LOG2C;
   uint32_t c[3], F[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const int l = k[a] & 7;
-    int ca = s[a] > 0 ? 7 - l : l;
+    const int l = k[a] & (C - 1);
+    int ca = s[a] > 0 ? C - 1 - l : l;
     if (KIND == RMP_MAP_DENSE_U8) {
       const int g = s[a] > 0 ? m.dims[a] - 1 - k[a] : k[a];
       ca = ca < g ? ca : g;
@@ -267,14 +269,13 @@ __device__ __forceinline__ bool skip_block(const DevMap& m, int k[3], const int 
     const unsigned long long X = (unsigned long long)Fe * A[b];
     const unsigned long long Y = (unsigned long long)N[b] * Ae;
     const bool le = b < e;
-    // count = #{m >= 0 : Y + m unit < X (<= X if b < e)}, at most 7: binary search
+    // count = #{m >= 0 : Y + m unit < X (<= X if b < e)}, at most C - 1: binary lifting
     uint32_t cnt = 0;
-    unsigned long long t = Y + 3ull * unit;
-    if (le ? t <= X : t < X) cnt = 4;
-    t = Y + (unsigned long long)(cnt + 1) * unit;
-    if (le ? t <= X : t < X) cnt += 2;
-    t = Y + (unsigned long long)cnt * unit;
-    if (le ? t <= X : t < X) cnt += 1;
+#pragma unroll
+    for (int step = C / 2; step > 0; step >>= 1) {
+      const unsigned long long t = Y + (unsigned long long)(cnt + step - 1) * unit;
+      if (le ? t <= X : t < X) cnt += step;
+    }
     k[b] += s[b] * (int)cnt;
     N[b] += cnt << 16;
     steps += cnt;
@@ -298,7 +299,7 @@ __device__ __forceinline__ bool skip_block(const DevMap& m, int k[3], const int 
 // crossing numerator n of axis a (t = n / |D_a|) satisfies t <= T_s iff
 // n S 2^24 <= s R_fx |D_a|; the segment's start state (all crossings with t <= T_seg
 // applied) and its limits L_a follow from that in integer arithmetic.  Within a segment:
-// free blocks are crossed by skip_block, occupied ones voxel by voxel, with the order of
+// free superblocks and blocks are crossed by skip_cell, occupied blocks voxel by voxel, with the order of
 // the next crossings kept in the exact differences E_ab = N_a |D_b| - N_b |D_a|.
 template <int KIND, int LAYOUT>
 __device__ __forceinline__ SegOut march_segment(const DevMap& m, const uint32_t* bm,
@@ -347,9 +348,29 @@ __device__ __forceinline__ SegOut march_segment(const DevMap& m, const uint32_t*
   if (!outside<KIND>(m, k)) {
     o.status = last_seg ? RMP_RAY_MISS_RANGE : kSegContinues;
     for (uint32_t guard = 0; guard < 3u * (kMaxRangeVoxels + 2); ++guard) {
+      if (LAYOUT == kLayoutGrid) {
+        const int sx = (k[0] >> 5) - m.sgmin[0], sy = (k[1] >> 5) - m.sgmin[1],
+                  sz = (k[2] >> 5) - m.sgmin[2];
+        bool sfree = (unsigned)sx >= (unsigned)m.sgdim[0] || (unsigned)sy >= (unsigned)m.sgdim[1] ||
+                     (unsigned)sz >= (unsigned)m.sgdim[2];
+        if (!sfree) {
+          const uint32_t si = (uint32_t)sx + (uint32_t)m.sgdim[0] * ((uint32_t)sy + (uint32_t)m.sgdim[1] * (uint32_t)sz);
+          sfree = !((bm[m.bitmap_words + (si >> 5)] >> (si & 31)) & 1u);
+        }
+        if (sfree) {
+          if (skip_cell<KIND, 5>(m, k, s, N, A, L, o.steps, o.n_last, o.a_last)) break;  // limit
+          if (outside<KIND>(m, k)) {
+            o.status = RMP_RAY_MISS_EXIT;
+            o.ax_last = ((unsigned)k[0] >= (unsigned)m.dims[0]) ? 0
+                        : (((unsigned)k[1] >= (unsigned)m.dims[1]) ? 1 : 2);
+            break;
+          }
+          continue;
+        }
+      }
       Brick w;
       if (!fetch_brick<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, w)) {
-        if (skip_block<KIND>(m, k, s, N, A, L, o.steps, o.n_last, o.a_last)) break;  // limit
+        if (skip_cell<KIND, 3>(m, k, s, N, A, L, o.steps, o.n_last, o.a_last)) break;  // limit
         if (outside<KIND>(m, k)) {
           o.status = RMP_RAY_MISS_EXIT;
           // the exit step is the one that left the block: the axis whose voxel is outside
@@ -756,22 +777,49 @@ __device__ void grid_finish(const double part[9], unsigned hits, unsigned act, W
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // Every thread sums the partials g = t, t + blockDim, ... (independent loads, fixed order),
+  // then a fixed xor-shuffle tree within warps and warp order through shared memory.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int G = gridDim.x;
-  for (int q = warp; q < 11; q += nw) {
-    if (q < 9) {
-      double s = 0.0;
-      for (int g = lane; g < G; g += 32) s += __ldcg(&parts[g].v[q]);
+  double acc[9];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-      if (lane == 0) tot[q] = s;
-    } else {
-      unsigned s = 0;
-      for (int g = lane; g < G; g += 32)
-        s += __ldcg(q == 9 ? &parts[g].n_hits : &parts[g].n_active);
-      s = __reduce_add_sync(0xffffffffu, s);
-      if (lane == 0) (q == 9 ? tot_h : tot_a) = s;
+  for (int q = 0; q < 9; ++q) acc[q] = 0.0;
+  unsigned ah = 0, aa = 0;
+#pragma unroll 4
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    const CtaPartial* pp = parts + g;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] += __ldcg(&pp->v[q]);
+    ah += __ldcg(&pp->n_hits);
+    aa += __ldcg(&pp->n_active);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+  ah = __reduce_add_sync(0xffffffffu, ah);
+  aa = __reduce_add_sync(0xffffffffu, aa);
+  __shared__ double wsum[8][9];
+  __shared__ unsigned wcnt[8][2];
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) wsum[warp][q] = acc[q];
+    wcnt[warp][0] = ah;
+    wcnt[warp][1] = aa;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += wsum[w][threadIdx.x];
+    tot[threadIdx.x] = t;
+  } else if (threadIdx.x == 32) {
+    unsigned th = 0, ta = 0;
+    for (int w = 0; w < nw; ++w) {
+      th += wcnt[w][0];
+      ta += wcnt[w][1];
     }
+    tot_h = th;
+    tot_a = ta;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -882,11 +930,12 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
   __shared__ CtaState cs;
   __shared__ __align__(8) uint64_t bm_bar;
   __shared__ int bm_timeout;
-  const bool staged = LAYOUT == kLayoutGrid && m.bitmap_words * 4u <= kMaxSmemBitmapBytes;
+  const uint32_t bm_bytes = (m.bitmap_words + m.sbitmap_words) * 4u;
+  const bool staged = LAYOUT == kLayoutGrid && bm_bytes <= kMaxSmemBitmapBytes;
   const uint32_t* bm = staged ? reinterpret_cast<const uint32_t*>(smem_bitmap) : m.bitmap;
   if (threadIdx.x == 0) {
     bm_timeout = 0;
-    if (staged) bulk_load_begin(&bm_bar, smem_bitmap, m.bitmap, m.bitmap_words * 4u);
+    if (staged) bulk_load_begin(&bm_bar, smem_bitmap, m.bitmap, bm_bytes);
   }
   if (threadIdx.x < 3) {
     const int a = threadIdx.x;
@@ -1073,9 +1122,21 @@ __global__ void dense_bricks_kernel(const uint8_t* __restrict__ occ, int dx, int
   }
 }
 
-// Block bitmap of a grid: bit b set iff brick b holds an occupied voxel.
-__global__ void grid_bitmap_kernel(const uint4* __restrict__ bricks, uint32_t n_bricks,
+// Mark grid brick idx (grid coordinates x, y, z) as holding an occupied voxel, in the block
+// bitmap and in the superblock bitmap that follows it.
+__device__ __forceinline__ void mark_brick(const DevMap& m, uint32_t* bitmap, uint32_t idx, int x,
+                                           int y, int z) {
+  atomicOr(bitmap + (idx >> 5), 1u << (idx & 31));
+  const int sx = ((m.gmin[0] + x) >> 2) - m.sgmin[0], sy = ((m.gmin[1] + y) >> 2) - m.sgmin[1],
+            sz = ((m.gmin[2] + z) >> 2) - m.sgmin[2];
+  const uint32_t si = (uint32_t)sx + (uint32_t)m.sgdim[0] * ((uint32_t)sy + (uint32_t)m.sgdim[1] * (uint32_t)sz);
+  atomicOr(bitmap + m.bitmap_words + (si >> 5), 1u << (si & 31));
+}
+
+// Bitmaps of a dense grid: brick b holds an occupied voxel.
+__global__ void grid_bitmap_kernel(const uint4* __restrict__ bricks, DevMap m,
                                    uint32_t* __restrict__ bitmap) {
+  const uint32_t n_bricks = (uint32_t)m.gdim[0] * m.gdim[1] * m.gdim[2];
   for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_bricks;
        b += gridDim.x * blockDim.x) {
     const uint4* w = bricks + 4 * (size_t)b;
@@ -1085,7 +1146,12 @@ __global__ void grid_bitmap_kernel(const uint4* __restrict__ bricks, uint32_t n_
       const uint4 x = w[q];
       any |= x.x | x.y | x.z | x.w;
     }
-    if (any) atomicOr(bitmap + (b >> 5), 1u << (b & 31));
+    if (any) {
+      const int x = (int)(b % (uint32_t)m.gdim[0]);
+      const int y = (int)((b / (uint32_t)m.gdim[0]) % (uint32_t)m.gdim[1]);
+      const int z = (int)(b / ((uint32_t)m.gdim[0] * m.gdim[1]));
+      mark_brick(m, bitmap, b, x, y, z);
+    }
   }
 }
 
@@ -1112,8 +1178,9 @@ __global__ void key_bbox_kernel(const int32_t* __restrict__ keys, const uint4* _
 
 // Scatter the non-empty bricks of a hashed map into the grid layout.
 __global__ void grid_scatter_kernel(const int32_t* __restrict__ keys, const uint4* __restrict__ bricks,
-                                    uint32_t n_blocks, int gx, int gy, int gz, int dx, int dy,
-                                    uint4* __restrict__ grid, uint32_t* __restrict__ bitmap) {
+                                    uint32_t n_blocks, DevMap m, uint4* __restrict__ grid,
+                                    uint32_t* __restrict__ bitmap) {
+  const int gx = m.gmin[0], gy = m.gmin[1], gz = m.gmin[2], dx = m.gdim[0], dy = m.gdim[1];
   for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks;
        b += gridDim.x * blockDim.x) {
     const uint4* w = bricks + 4 * (size_t)b;
@@ -1121,15 +1188,15 @@ __global__ void grid_scatter_kernel(const int32_t* __restrict__ keys, const uint
     const uint32_t any = w0.x | w0.y | w0.z | w0.w | w1.x | w1.y | w1.z | w1.w | w2.x | w2.y |
                          w2.z | w2.w | w3.x | w3.y | w3.z | w3.w;
     if (!any) continue;
-    const uint32_t idx = (uint32_t)(keys[3 * (size_t)b] - gx) +
-                         (uint32_t)dx * ((uint32_t)(keys[3 * (size_t)b + 1] - gy) +
-                                         (uint32_t)dy * (uint32_t)(keys[3 * (size_t)b + 2] - gz));
+    const int x = keys[3 * (size_t)b] - gx, y = keys[3 * (size_t)b + 1] - gy,
+              z = keys[3 * (size_t)b + 2] - gz;
+    const uint32_t idx = (uint32_t)x + (uint32_t)dx * ((uint32_t)y + (uint32_t)dy * (uint32_t)z);
     uint4* dst = grid + 4 * (size_t)idx;
     dst[0] = w0;
     dst[1] = w1;
     dst[2] = w2;
     dst[3] = w3;
-    atomicOr(bitmap + (idx >> 5), 1u << (idx & 31));
+    mark_brick(m, bitmap, idx, x, y, z);
   }
 }
 
@@ -1195,8 +1262,8 @@ __global__ void hash_build_kernel(const int32_t* __restrict__ keys, uint32_t n_b
 
 // ------------------------------------------------------------------ launchers
 size_t raycast_smem_bytes(const DevMap& m) {
-  if (m.layout == kLayoutGrid && m.bitmap_words * 4u <= kMaxSmemBitmapBytes)
-    return (size_t)m.bitmap_words * 4u;
+  const uint32_t bytes = (m.bitmap_words + m.sbitmap_words) * 4u;
+  if (m.layout == kLayoutGrid && bytes <= kMaxSmemBitmapBytes) return bytes;
   return 0;
 }
 
@@ -1256,9 +1323,10 @@ cudaError_t launch_dense_bricks(const uint8_t* occ, const int dims[3], const int
 
 static int grid_for(size_t n) { return (int)((n + 255) / 256 < 65535 ? ((n + 255) / 256 > 0 ? (n + 255) / 256 : 1) : 65535); }
 
-cudaError_t launch_grid_bitmap(const uint32_t* bricks, uint32_t n_bricks, uint32_t* bitmap,
+cudaError_t launch_grid_bitmap(const uint32_t* bricks, const DevMap& m, uint32_t* bitmap,
                                cudaStream_t stream) {
-  grid_bitmap_kernel<<<grid_for(n_bricks), 256, 0, stream>>>((const uint4*)bricks, n_bricks, bitmap);
+  const size_t n = (size_t)m.gdim[0] * m.gdim[1] * m.gdim[2];
+  grid_bitmap_kernel<<<grid_for(n), 256, 0, stream>>>((const uint4*)bricks, m, bitmap);
   return cudaGetLastError();
 }
 
@@ -1269,11 +1337,10 @@ cudaError_t launch_key_bbox(const int32_t* keys, const uint32_t* bricks, uint32_
 }
 
 cudaError_t launch_grid_scatter(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,
-                                const int gmin[3], const int gdim[3], uint32_t* grid_bricks,
-                                uint32_t* bitmap, cudaStream_t stream) {
+                                const DevMap& m, uint32_t* grid_bricks, uint32_t* bitmap,
+                                cudaStream_t stream) {
   grid_scatter_kernel<<<grid_for(n_blocks), 256, 0, stream>>>(keys, (const uint4*)bricks, n_blocks,
-                                                              gmin[0], gmin[1], gmin[2], gdim[0],
-                                                              gdim[1], (uint4*)grid_bricks, bitmap);
+                                                              m, (uint4*)grid_bricks, bitmap);
   return cudaGetLastError();
 }
 
