@@ -19,7 +19,7 @@ struct MapRec {
   DevMap dm;
   void* bricks = nullptr;
   void* table = nullptr;
-  void* bitmap = nullptr;
+  void* radius = nullptr;
   uint32_t n_bricks = 0;
   uint32_t cap = 0;
   uint64_t bytes = 0;
@@ -173,25 +173,31 @@ void launch_shape(const rmp_ctx* ctx, uint64_t n_threads, int* block, int* grid)
 void free_map(MapRec& r) {
   if (r.bricks) cudaFree(r.bricks);
   if (r.table) cudaFree(r.table);
-  if (r.bitmap) cudaFree(r.bitmap);
-  r.bricks = r.table = r.bitmap = nullptr;
+  if (r.radius) cudaFree(r.radius);
+  r.bricks = r.table = r.radius = nullptr;
 }
 
-uint32_t bitmap_words_for(uint64_t n_bricks) {
-  const uint64_t w = (n_bricks + 31) / 32;
-  return (uint32_t)((w + 3) / 4 * 4);            // whole uint4s
+// uint32 words of a 4-bit-per-brick radius field, in whole uint4s (TMA copy granularity)
+uint32_t radius_words_for(uint64_t n_bricks) {
+  const uint64_t w = (n_bricks + 7) / 8;
+  return (uint32_t)((w + 3) / 4 * 4);
 }
 
-// Superblock (4^3 blocks) extent covering the grid gmin .. gmin + gdim - 1, and the size of
-// both bitmaps.
-void set_superblocks(DevMap& dm) {
-  uint64_t n = 1;
-  for (int a = 0; a < 3; ++a) {
-    dm.sgmin[a] = dm.gmin[a] >> 2;                          // floor for negatives too
-    dm.sgdim[a] = ((dm.gmin[a] + dm.gdim[a] - 1) >> 2) - dm.sgmin[a] + 1;
-    n *= (uint64_t)dm.sgdim[a];
-  }
-  dm.sbitmap_words = bitmap_words_for(n);
+// Free-radius field of a grid layout map whose bricks are in r.bricks.
+int build_radius(MapRec& r, cudaStream_t s) {
+  const uint64_t n = (uint64_t)r.dm.gdim[0] * r.dm.gdim[1] * r.dm.gdim[2];
+  r.dm.radius_words = radius_words_for(n);
+  uint8_t* a = nullptr;
+  uint8_t* b = nullptr;
+  cudaError_t e = cudaMalloc(&r.radius, (size_t)r.dm.radius_words * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&a, n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b, n);
+  if (e == cudaSuccess)
+    e = launch_grid_radius((const uint32_t*)r.bricks, r.dm, a, b, (uint32_t*)r.radius, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (a) cudaFree(a);
+  if (b) cudaFree(b);
+  return e == cudaSuccess ? RMP_OK : cuda_status(e);
 }
 
 
@@ -332,18 +338,12 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
     }
     r.dm.layout = kLayoutGrid;
     r.n_bricks = (uint32_t)nbr;
-    r.dm.bitmap_words = bitmap_words_for(nbr);
-    set_superblocks(r.dm);
-    const size_t bm_bytes = (size_t)(r.dm.bitmap_words + r.dm.sbitmap_words) * 4;
     cudaError_t e = cudaMalloc(&r.bricks, nbr * 64);
-    if (e == cudaSuccess) e = cudaMalloc(&r.bitmap, bm_bytes);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r.bitmap, 0, bm_bytes, s);
     if (e == cudaSuccess) e = launch_dense_bricks(occ, r.dm.dims, r.dm.gdim, (uint32_t*)r.bricks, s);
-    if (e == cudaSuccess)
-      e = launch_grid_bitmap((const uint32_t*)r.bricks, r.dm, (uint32_t*)r.bitmap, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(cuda_status(e));
-    r.bytes = nbr * 64 + bm_bytes;
+    const int rs = build_radius(r, s);
+    if (rs != RMP_OK) return fail(rs);
+    r.bytes = nbr * 64 + (uint64_t)r.dm.radius_words * 4;
   } else if (d->kind == RMP_MAP_HASHED_TSDF) {
     const uint32_t n = d->n_blocks;
     if (n > (1u << 26)) return RMP_ERR_INVALID_ARG;
@@ -417,19 +417,14 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
         r.dm.gdim[a] = gdim[a];
       }
       r.n_bricks = (uint32_t)gprod;
-      r.dm.bitmap_words = bitmap_words_for(gprod);
-      set_superblocks(r.dm);
-      const size_t bm_bytes = (size_t)(r.dm.bitmap_words + r.dm.sbitmap_words) * 4;
       e = cudaMalloc(&r.bricks, grid_bytes);
       if (e == cudaSuccess) e = cudaMemsetAsync(r.bricks, 0, grid_bytes, s);
-      if (e == cudaSuccess) e = cudaMalloc(&r.bitmap, bm_bytes);
-      if (e == cudaSuccess) e = cudaMemsetAsync(r.bitmap, 0, bm_bytes, s);
       if (e == cudaSuccess && n > 0 && !none)
-        e = launch_grid_scatter(keys, (const uint32_t*)compact, n, r.dm, (uint32_t*)r.bricks,
-                                (uint32_t*)r.bitmap, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        e = launch_grid_scatter(keys, (const uint32_t*)compact, n, r.dm, (uint32_t*)r.bricks, s);
       if (e != cudaSuccess) return fail(cuda_status(e));
-      r.bytes = grid_bytes + bm_bytes;
+      const int rs = build_radius(r, s);
+      if (rs != RMP_OK) return fail(rs);
+      r.bytes = grid_bytes + (uint64_t)r.dm.radius_words * 4;
     } else {
       r.dm.layout = kLayoutHash;
       r.bricks = compact;
@@ -445,7 +440,7 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
   cleanup();
   r.dm.bricks = (const uint4*)r.bricks;
   r.dm.table = (const HashEntry*)r.table;
-  r.dm.bitmap = (const uint32_t*)r.bitmap;
+  r.dm.radius = (const uint32_t*)r.radius;
   std::lock_guard<std::mutex> lk(c->mu);
   const uint32_t id = c->next_id++;
   c->maps[id] = r;

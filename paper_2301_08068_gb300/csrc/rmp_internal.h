@@ -5,10 +5,10 @@
 //     its value is <= 0; a dense voxel iff it is nonzero).
 //   * grid layout (dense maps, and hashed maps whose block bounding box is moderate): the
 //     bricks of every block in the bounding box, x fastest (all-zero where free), plus a
-//     1-bit-per-block bitmap of the blocks that hold an occupied voxel, followed by a
-//     1-bit-per-superblock bitmap (4^3 blocks = 32^3 voxels, aligned to multiples of 32
-//     voxels).  The march stages both in shared memory, so free space costs no global
-//     access and is crossed 32 voxels at a time where a whole superblock is free.
+//     4-bit free radius per block: 0 if the block holds an occupied voxel, else
+//     min(15, Chebyshev distance in blocks to the nearest such block), so the blocks
+//     within radius - 1 of it are all free.  The march stages the radii in shared memory
+//     and crosses a whole free box of blocks in one exact step.
 //   * hash layout (fallback for very large extents): power-of-two array of 16-byte entries
 //     {key, slot}; key packs the block coordinates (21 bits each, offset by 2^20); empty
 //     entries hold ~0; linear probing from a Fibonacci (multiply-shift) hash, load factor
@@ -26,7 +26,9 @@ constexpr int kBrickWords = 16;
 constexpr unsigned long long kEmptyKey = ~0ull;
 constexpr int kKeyBias = 1 << 20;
 constexpr int kMaxGrid = 4096;          // CTAs of one evaluation (grid-stride beyond)
-constexpr int kWsHeaderBytes = 256;
+constexpr int kWsHeaderBytes = 1024;
+constexpr int kGroup = 32;                  // CTAs per reduction group (see grid_finish)
+constexpr int kMaxGroups = 4096 / kGroup;
 constexpr int kMaxRangeVoxels = 16384;  // keeps every DDA crossing numerator below 2^31
 
 struct HashEntry {
@@ -37,7 +39,8 @@ struct HashEntry {
 
 constexpr int kLayoutGrid = 0;
 constexpr int kLayoutHash = 1;
-constexpr uint32_t kMaxSmemBitmapBytes = 48 * 1024;   // staged in shared memory up to this
+constexpr uint32_t kMaxSmemRadiusBytes = 48 * 1024;   // staged in shared memory up to this
+constexpr int kMaxFreeRadius = 15;
 constexpr uint64_t kMaxGridBricks = 1ull << 26;       // grid layout up to 4 GiB of bricks
 
 struct DevMap {
@@ -46,18 +49,14 @@ struct DevMap {
   int hash_shift;           // 64 - log2(capacity)
   uint32_t cap_mask;
   float vs_f;               // RN32(voxel size)
-  uint32_t bitmap_words;    // grid: uint32 words of the block bitmap (multiple of 4)
+  uint32_t radius_words;    // grid: uint32 words of the radius field (8 per word, multiple of 4)
   double vs;
   double origin[3];         // dense only (hashed maps are world-anchored)
   int dims[3];              // dense voxels per axis
   int gmin[3];              // grid: block coordinates of the grid's first brick
   int gdim[3];              // grid: bricks per axis
-  int sgmin[3];             // grid: superblock (4^3 blocks, 32^3 voxels) of the first brick
-  int sgdim[3];             // grid: superblocks per axis
-  uint32_t sbitmap_words;   // grid: uint32 words of the superblock bitmap (multiple of 4),
-                            // stored right after the block bitmap
   const uint4* bricks;      // grid: brick (x + gdim0 (y + gdim1 z)); hash: by slot
-  const uint32_t* bitmap;   // grid: bit idx set iff brick idx holds an occupied voxel
+  const uint32_t* radius;   // grid: 4-bit free radius of brick idx at bits 4 (idx & 7)
   const HashEntry* table;   // hash layout only
 };
 
@@ -73,18 +72,22 @@ struct EvalConsts {
   int w_mode, reduce_mode;
 };
 
+// Workspace of one evaluation: tickets, one partial per CTA, one partial per group of
+// kGroup CTAs.  Every ticket is reset to 0 by the CTA that completes it.
 struct WsHeader {
-  unsigned int ticket;      // CTAs finished; the last one resets it to 0
-  unsigned int pad[kWsHeaderBytes / 4 - 1];
+  unsigned int ticket;                     // groups completed
+  unsigned int pad0[31];
+  unsigned int group_ticket[kMaxGroups];   // CTAs completed, per group
+  unsigned int pad1[kWsHeaderBytes / 4 - 32 - kMaxGroups];
 };
 
-struct CtaPartial {         // 80 bytes per CTA
+struct CtaPartial {         // 80 bytes per CTA (and per group)
   double v[9];              // sum A (6), sum A f (3)
   unsigned int n_hits, n_active;
 };
 
 inline size_t workspace_bytes() {
-  return kWsHeaderBytes + sizeof(CtaPartial) * (size_t)kMaxGrid;
+  return kWsHeaderBytes + sizeof(CtaPartial) * (size_t)(kMaxGrid + kMaxGroups);
 }
 
 inline unsigned long long pack_key(int bx, int by, int bz) {
@@ -103,13 +106,13 @@ cudaError_t launch_scan(const float* pts, const EvalConsts& k, const double* sta
                         cudaStream_t stream);
 cudaError_t launch_dense_bricks(const uint8_t* occ, const int dims[3], const int nb[3],
                                 uint32_t* bricks, cudaStream_t stream);
-cudaError_t launch_grid_bitmap(const uint32_t* bricks, const DevMap& m, uint32_t* bitmap,
-                               cudaStream_t stream);
+// Free-radius field of a grid from its bricks (scratch: two byte arrays, one per brick).
+cudaError_t launch_grid_radius(const uint32_t* bricks, const DevMap& m, uint8_t* scratch_a,
+                               uint8_t* scratch_b, uint32_t* radius, cudaStream_t stream);
 cudaError_t launch_key_bbox(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,
                             int* bbox, cudaStream_t stream);
 cudaError_t launch_grid_scatter(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,
-                                const DevMap& m, uint32_t* grid_bricks, uint32_t* bitmap,
-                                cudaStream_t stream);
+                                const DevMap& m, uint32_t* grid_bricks, cudaStream_t stream);
 cudaError_t launch_tsdf_bricks(const float* tsdf, uint32_t n_blocks, uint32_t* bricks,
                                cudaStream_t stream);
 cudaError_t launch_hash_build(const int32_t* keys, uint32_t n_blocks, const uint32_t* bricks,

@@ -135,31 +135,39 @@ struct Brick {
   uint4 q0, q1, q2, q3;
 };
 
-// Load the brick of block (bx,by,bz) into registers; false when the block holds no
-// occupied voxel (missing, all free, or outside the grid's bounding box).  In the grid
-// layout the test reads the block bitmap `bm` (shared memory when it fits).
+// Free radius v of block (bx,by,bz): 0 if it holds an occupied voxel (then *src points at
+// its brick), else v >= 1 with every block within Chebyshev distance v - 1 free.  Grid
+// layout: the 4-bit field `rad` (shared memory when it fits); outside the grid's bounding
+// box the radius is the distance to the box.  Hash layout: 1 for free blocks.
 template <int LAYOUT>
-__device__ __forceinline__ bool fetch_brick(const DevMap& m, const uint32_t* bm, int bx, int by,
-                                            int bz, Brick& br) {
-  const uint4* src;
+__device__ __forceinline__ int block_radius(const DevMap& m, const uint32_t* rad, int bx, int by,
+                                            int bz, const uint4** src) {
   if (LAYOUT == kLayoutGrid) {
     const int x = bx - m.gmin[0], y = by - m.gmin[1], z = bz - m.gmin[2];
     if ((unsigned)x >= (unsigned)m.gdim[0] || (unsigned)y >= (unsigned)m.gdim[1] ||
-        (unsigned)z >= (unsigned)m.gdim[2])
-      return false;
+        (unsigned)z >= (unsigned)m.gdim[2]) {
+      const int dx = max(max(-x, x - (m.gdim[0] - 1)), 0);
+      const int dy = max(max(-y, y - (m.gdim[1] - 1)), 0);
+      const int dz = max(max(-z, z - (m.gdim[2] - 1)), 0);
+      return min(max(dx, max(dy, dz)), kMaxFreeRadius);
+    }
     const uint32_t idx = (uint32_t)x + (uint32_t)m.gdim[0] * ((uint32_t)y + (uint32_t)m.gdim[1] * (uint32_t)z);
-    if (!((bm[idx >> 5] >> (idx & 31)) & 1u)) return false;
-    src = m.bricks + 4 * (size_t)idx;
+    const int v = (int)((rad[idx >> 3] >> ((idx & 7) * 4)) & 15u);
+    *src = m.bricks + 4 * (size_t)idx;
+    return v;
   } else {
     const int slot = hash_lookup(m, bx, by, bz);
-    if (slot < 0) return false;
-    src = m.bricks + 4 * (size_t)slot;
+    if (slot < 0) return 1;
+    *src = m.bricks + 4 * (size_t)slot;
+    return 0;
   }
+}
+
+__device__ __forceinline__ void load_brick(const uint4* src, Brick& br) {
   br.q0 = __ldg(src);
   br.q1 = __ldg(src + 1);
   br.q2 = __ldg(src + 2);
   br.q3 = __ldg(src + 3);
-  return true;
 }
 
 // Occupancy of voxel k in the register brick: word (ly>>2) + 2 lz picked by a select
@@ -179,7 +187,7 @@ __device__ __forceinline__ bool brick_bit(const Brick& b, int kx, int ky, int kz
 // ties go to the lowest axis); an axis with D_a = 0 has |D_a| = 0, N_a = 1 and so never
 // wins.  A voxel is entered only if N_a 2^24 <= R_fx |D_a|, i.e. N_a <= L_a.
 // Blocks without occupied voxels are crossed in one step of integer arithmetic that
-// reproduces the voxel-by-voxel crossings exactly (skip_cell).
+// reproduces the voxel-by-voxel crossings exactly (skip_box).
 constexpr int kSegContinues = 0;   // segment ended at its upper parameter bound
 
 struct SegOut {
@@ -209,23 +217,26 @@ __device__ __forceinline__ bool outside(const DevMap& m, const int k[3]) {
           (unsigned)k[2] >= (unsigned)m.dims[2]);
 }
 
-// The ray is in a free cell of 2^LOG2C voxels per side (a block, or a superblock; cells are
-// aligned to multiples of their size and clipped to the dense grid).  Advance the DDA
-// state to the first voxel beyond it exactly as single steps would: the cell is left
-// through the axis e whose face crossing F_e/|D_e| comes first (ties: lowest axis); every
-// other axis b crosses its interior boundaries that come strictly before that time (or at
-// the same time if b < e, the tie order).  If the face crossing is beyond the limit, the
-// ray ends inside the cell after every crossing within the limit; returns true then.
-template <int KIND, int LOG2C>
-__device__ __forceinline__ bool skip_cell(const DevMap& m, int k[3], const int s[3], uint32_t N[3],
-                                          const uint32_t A[3], const uint32_t L[3],
-                                          uint32_t& steps, uint32_t& n_last, uint32_t& a_last) {
-  constexpr int C = 1 << LOG2C;
+// The ray is in a free box of blocks: the blocks within Chebyshev distance R of its
+// current block (clipped to the dense grid).  Advance the DDA state to the first voxel
+// beyond the box exactly as single steps would: the box is left through the axis e whose
+// face crossing F_e/|D_e| comes first (ties: lowest axis); every other axis b crosses its
+// interior boundaries that come strictly before that time (or at the same time if b < e,
+// the tie order).  If the face crossing is beyond the limit, the ray ends inside the box
+// after every crossing within the limit; returns true then.
+//
+// The per-axis counts #{m >= 0 : Y + m u < X (<= X if b < e)}, u = 2^16 |D_e|, are at most
+// 8 (2R + 1) - 1 < 2^8: an FP32 quotient estimate (error far below 1) is corrected once
+// in each direction with exact 64-bit comparisons.
+template <int KIND>
+__device__ __forceinline__ bool skip_box(const DevMap& m, int k[3], const int s[3], uint32_t N[3],
+                                         const uint32_t A[3], const uint32_t L[3], int R,
+                                         uint32_t& steps, uint32_t& n_last, uint32_t& a_last) {
   uint32_t c[3], F[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const int l = k[a] & (C - 1);
-    int ca = s[a] > 0 ? C - 1 - l : l;
+    const int b = k[a] >> 3;
+    int ca = s[a] > 0 ? 8 * (b + R) + 7 - k[a] : k[a] - 8 * (b - R);
     if (KIND == RMP_MAP_DENSE_U8) {
       const int g = s[a] > 0 ? m.dims[a] - 1 - k[a] : k[a];
       ca = ca < g ? ca : g;
@@ -263,18 +274,24 @@ __device__ __forceinline__ bool skip_cell(const DevMap& m, int k[3], const int s
     return true;
   }
   const unsigned long long unit = (unsigned long long)Ae << 16;     // 2^16 |D_e|
+  const float inv_unit = __frcp_rn(__ull2float_rn(unit));
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
     if (b == e || A[b] == 0) continue;
     const unsigned long long X = (unsigned long long)Fe * A[b];
     const unsigned long long Y = (unsigned long long)N[b] * Ae;
     const bool le = b < e;
-    // count = #{m >= 0 : Y + m unit < X (<= X if b < e)}, at most C - 1: binary lifting
     uint32_t cnt = 0;
-#pragma unroll
-    for (int step = C / 2; step > 0; step >>= 1) {
-      const unsigned long long t = Y + (unsigned long long)(cnt + step - 1) * unit;
-      if (le ? t <= X : t < X) cnt += step;
+    if (le ? Y <= X : Y < X) {
+      const uint32_t q = (uint32_t)(__ull2float_rn(X - Y) * inv_unit);   // floor(estimate)
+      cnt = q + 1;
+      unsigned long long t = Y + (unsigned long long)q * unit;         // condition for m = q
+      if (!(le ? t <= X : t < X)) {
+        cnt = q;
+      } else {
+        t += unit;                                                       // m = q + 1
+        if (le ? t <= X : t < X) cnt = q + 2;
+      }
     }
     k[b] += s[b] * (int)cnt;
     N[b] += cnt << 16;
@@ -299,7 +316,7 @@ __device__ __forceinline__ bool skip_cell(const DevMap& m, int k[3], const int s
 // crossing numerator n of axis a (t = n / |D_a|) satisfies t <= T_s iff
 // n S 2^24 <= s R_fx |D_a|; the segment's start state (all crossings with t <= T_seg
 // applied) and its limits L_a follow from that in integer arithmetic.  Within a segment:
-// free superblocks and blocks are crossed by skip_cell, occupied blocks voxel by voxel, with the order of
+// free boxes of blocks are crossed by skip_box, occupied blocks voxel by voxel, with the order of
 // the next crossings kept in the exact differences E_ab = N_a |D_b| - N_b |D_a|.
 template <int KIND, int LAYOUT>
 __device__ __forceinline__ SegOut march_segment(const DevMap& m, const uint32_t* bm,
@@ -348,38 +365,21 @@ __device__ __forceinline__ SegOut march_segment(const DevMap& m, const uint32_t*
   if (!outside<KIND>(m, k)) {
     o.status = last_seg ? RMP_RAY_MISS_RANGE : kSegContinues;
     for (uint32_t guard = 0; guard < 3u * (kMaxRangeVoxels + 2); ++guard) {
-      if (LAYOUT == kLayoutGrid) {
-        const int sx = (k[0] >> 5) - m.sgmin[0], sy = (k[1] >> 5) - m.sgmin[1],
-                  sz = (k[2] >> 5) - m.sgmin[2];
-        bool sfree = (unsigned)sx >= (unsigned)m.sgdim[0] || (unsigned)sy >= (unsigned)m.sgdim[1] ||
-                     (unsigned)sz >= (unsigned)m.sgdim[2];
-        if (!sfree) {
-          const uint32_t si = (uint32_t)sx + (uint32_t)m.sgdim[0] * ((uint32_t)sy + (uint32_t)m.sgdim[1] * (uint32_t)sz);
-          sfree = !((bm[m.bitmap_words + (si >> 5)] >> (si & 31)) & 1u);
-        }
-        if (sfree) {
-          if (skip_cell<KIND, 5>(m, k, s, N, A, L, o.steps, o.n_last, o.a_last)) break;  // limit
-          if (outside<KIND>(m, k)) {
-            o.status = RMP_RAY_MISS_EXIT;
-            o.ax_last = ((unsigned)k[0] >= (unsigned)m.dims[0]) ? 0
-                        : (((unsigned)k[1] >= (unsigned)m.dims[1]) ? 1 : 2);
-            break;
-          }
-          continue;
-        }
-      }
-      Brick w;
-      if (!fetch_brick<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, w)) {
-        if (skip_cell<KIND, 3>(m, k, s, N, A, L, o.steps, o.n_last, o.a_last)) break;  // limit
+      const uint4* src = nullptr;
+      const int v = block_radius<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, &src);
+      if (v > 0) {
+        if (skip_box<KIND>(m, k, s, N, A, L, v - 1, o.steps, o.n_last, o.a_last)) break;  // limit
         if (outside<KIND>(m, k)) {
           o.status = RMP_RAY_MISS_EXIT;
-          // the exit step is the one that left the block: the axis whose voxel is outside
+          // the exit step is the one that left the box: the axis whose voxel is outside
           o.ax_last = ((unsigned)k[0] >= (unsigned)m.dims[0]) ? 0
                       : (((unsigned)k[1] >= (unsigned)m.dims[1]) ? 1 : 2);
           break;
         }
         continue;
       }
+      Brick w;
+      load_brick(src, w);
       if (brick_bit(w, k[0], k[1], k[2])) {
         o.status = RMP_RAY_HIT;
         break;
@@ -659,68 +659,91 @@ __device__ __forceinline__ unsigned block_sum_u32(unsigned v) {
 
 // ------------------------------------------------------------------ FP64 resolve (Eq. 1)
 // f = (sum A)^+ (sum A f) with eigenvalues <= 1e-12 lambda_max treated as zero.  FP64
-// division and square root cost hundreds of cycles each on this GPU, so the
-// eigenvectors come from cyclic Jacobi rotations in FP32 (on the matrix scaled by a power
-// of two), and FP64 then only refines: each eigenvalue is the Rayleigh quotient
-// v^T S v / v^T v of its FP32 eigenvector (second-order accurate, ~1e-14 lambda_max),
-// with 1 / v^T v = 2 - v^T v to first order (v^T v = 1 + O(1e-7)).  A full-rank matrix is
-// solved with the FP64 adjugate (one FP64 division); a rank-deficient one by projecting
-// on the kept eigenvectors.
-__device__ void resolve_pinv(const double S[6], const double b[3], rmp_result_t& r) {
-  double smax = fmax(fmax(fabs(S[0]), fabs(S[1])), fmax(fmax(fabs(S[2]), fabs(S[3])),
-                                                         fmax(fabs(S[4]), fabs(S[5]))));
-  r.f[0] = r.f[1] = r.f[2] = 0.0;
-  r.eig[0] = r.eig[1] = r.eig[2] = 0.0;
-  r.rank = 0;
-  if (!(smax > 1e-300)) return;
-  const double scale = ldexp(1.0, -ilogb(smax));             // exact power of two
-  float a00 = (float)(S[0] * scale), a01 = (float)(S[1] * scale), a02 = (float)(S[2] * scale),
-        a11 = (float)(S[3] * scale), a12 = (float)(S[4] * scale), a22 = (float)(S[5] * scale);
-  float V[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
-  for (int sweep = 0; sweep < 6; ++sweep) {
-    const float off = fabsf(a01) + fabsf(a02) + fabsf(a12);
-    const float dia = fabsf(a00) + fabsf(a11) + fabsf(a22);
-    if (off <= 1e-6f * dia) break;                  // FP32 accuracy; FP64 refines below
+// division and square root cost hundreds of cycles each on this GPU and FP64 issues at a
+// low rate, so the work is split over three threads of the finishing CTA:
+//   thread 0: eigenvectors by cyclic Jacobi rotations in FP32 (matrix scaled by a power of
+//             two); thread 1, meanwhile: the FP64 adjugate solve adj(S) b / det(S);
+//   threads 0-2: each eigenvalue as the FP64 Rayleigh quotient v^T S v / v^T v of its FP32
+//             eigenvector (second-order accurate, ~1e-14 lambda_max), with
+//             1 / v^T v = 2 - v^T v to first order (v^T v = 1 + O(1e-7));
+//   thread 0: rank from the eigenvalues; full rank uses the adjugate solution, a deficient
+//             rank projects b on the kept eigenvectors.
+// Called by every thread of the CTA.
+__device__ void resolve_pinv(const double* S, const double* b, rmp_result_t& r) {
+  __shared__ float V[3][3];
+  __shared__ double lam[3], den[3], fadj[3];
+  __shared__ int adj_ok;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    const double smax = fmax(fmax(fabs(S[0]), fabs(S[1])), fmax(fmax(fabs(S[2]), fabs(S[3])),
+                                                               fmax(fabs(S[4]), fabs(S[5]))));
+    const double scale = smax > 1e-300 ? ldexp(1.0, -ilogb(smax)) : 1.0;   // power of two
+    float a00 = (float)(S[0] * scale), a01 = (float)(S[1] * scale), a02 = (float)(S[2] * scale),
+          a11 = (float)(S[3] * scale), a12 = (float)(S[4] * scale), a22 = (float)(S[5] * scale);
+    float W[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+    for (int sweep = 0; sweep < 6; ++sweep) {
+      const float off = fabsf(a01) + fabsf(a02) + fabsf(a12);
+      const float dia = fabsf(a00) + fabsf(a11) + fabsf(a22);
+      if (!(off > 1e-6f * dia)) break;              // FP32 accuracy; FP64 refines below
 #pragma unroll
-    for (int pq = 0; pq < 3; ++pq) {
-      float app, aqq, apq, apo, aqo;
-      if (pq == 0) { app = a00; aqq = a11; apq = a01; apo = a02; aqo = a12; }
-      else if (pq == 1) { app = a00; aqq = a22; apq = a02; apo = a01; aqo = a12; }
-      else { app = a11; aqq = a22; apq = a12; apo = a01; aqo = a02; }
-      if (apq == 0.0f) continue;
-      const float tau = __fdividef(aqq - app, 2.0f * apq);
-      const float at = fabsf(tau);
-      const float root = at < 1e18f ? (1.0f + at * at) * rsqrtf(1.0f + at * at) : at;
-      const float t = copysignf(__fdividef(1.0f, at + root), tau);
-      const float c = rsqrtf(1.0f + t * t), sn = t * c;
-      const float npp = app - t * apq, nqq = aqq + t * apq;
-      const float npo = c * apo - sn * aqo, nqo = sn * apo + c * aqo;
-      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
-      if (pq == 0) { a00 = npp; a11 = nqq; a01 = 0.f; a02 = npo; a12 = nqo; }
-      else if (pq == 1) { a00 = npp; a22 = nqq; a02 = 0.f; a01 = npo; a12 = nqo; }
-      else { a11 = npp; a22 = nqq; a12 = 0.f; a01 = npo; a02 = nqo; }
+      for (int pq = 0; pq < 3; ++pq) {
+        float app, aqq, apq, apo, aqo;
+        if (pq == 0) { app = a00; aqq = a11; apq = a01; apo = a02; aqo = a12; }
+        else if (pq == 1) { app = a00; aqq = a22; apq = a02; apo = a01; aqo = a12; }
+        else { app = a11; aqq = a22; apq = a12; apo = a01; aqo = a02; }
+        if (apq == 0.0f) continue;
+        const float tau = __fdividef(aqq - app, 2.0f * apq);
+        const float at = fabsf(tau);
+        const float root = at < 1e18f ? (1.0f + at * at) * rsqrtf(1.0f + at * at) : at;
+        const float tt = copysignf(__fdividef(1.0f, at + root), tau);
+        const float c = rsqrtf(1.0f + tt * tt), sn = tt * c;
+        const float npp = app - tt * apq, nqq = aqq + tt * apq;
+        const float npo = c * apo - sn * aqo, nqo = sn * apo + c * aqo;
+        const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+        if (pq == 0) { a00 = npp; a11 = nqq; a01 = 0.f; a02 = npo; a12 = nqo; }
+        else if (pq == 1) { a00 = npp; a22 = nqq; a02 = 0.f; a01 = npo; a12 = nqo; }
+        else { a11 = npp; a22 = nqq; a12 = 0.f; a01 = npo; a02 = nqo; }
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const float vp = V[i][p], vq = V[i][q];
-        V[i][p] = c * vp - sn * vq;
-        V[i][q] = sn * vp + c * vq;
+        for (int i = 0; i < 3; ++i) {
+          const float vp = W[i][p], vq = W[i][q];
+          W[i][p] = c * vp - sn * vq;
+          W[i][q] = sn * vp + c * vq;
+        }
       }
     }
-  }
-  double lam[3], den[3];
 #pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    const double v0 = V[0][e], v1 = V[1][e], v2 = V[2][e];
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) V[i][j] = W[i][j];
+  } else if (t == 1) {
+    const double c00 = S[3] * S[5] - S[4] * S[4], c01 = S[2] * S[4] - S[1] * S[5],
+                 c02 = S[1] * S[4] - S[2] * S[3], c11 = S[0] * S[5] - S[2] * S[2],
+                 c12 = S[1] * S[2] - S[0] * S[4], c22 = S[0] * S[3] - S[1] * S[1];
+    const double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
+    adj_ok = det > 0.0;
+    if (det > 0.0) {
+      const double inv = 1.0 / det;
+      fadj[0] = (c00 * b[0] + c01 * b[1] + c02 * b[2]) * inv;
+      fadj[1] = (c01 * b[0] + c11 * b[1] + c12 * b[2]) * inv;
+      fadj[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
+    }
+  }
+  __syncthreads();
+  if (t < 3) {
+    const double v0 = V[0][t], v1 = V[1][t], v2 = V[2][t];
     const double u0 = S[0] * v0 + S[1] * v1 + S[2] * v2;
     const double u1 = S[1] * v0 + S[3] * v1 + S[4] * v2;
     const double u2 = S[2] * v0 + S[4] * v1 + S[5] * v2;
-    den[e] = v0 * v0 + v1 * v1 + v2 * v2;
-    lam[e] = (v0 * u0 + v1 * u1 + v2 * u2) * (2.0 - den[e]);
+    const double dn = v0 * v0 + v1 * v1 + v2 * v2;
+    den[t] = dn;
+    lam[t] = (v0 * u0 + v1 * u1 + v2 * u2) * (2.0 - dn);
   }
+  __syncthreads();
+  if (t != 0) return;
   int idx[3] = {0, 1, 2};
-  if (lam[idx[1]] < lam[idx[0]]) { int t = idx[0]; idx[0] = idx[1]; idx[1] = t; }
-  if (lam[idx[2]] < lam[idx[1]]) { int t = idx[1]; idx[1] = idx[2]; idx[2] = t; }
-  if (lam[idx[1]] < lam[idx[0]]) { int t = idx[0]; idx[0] = idx[1]; idx[1] = t; }
+  if (lam[idx[1]] < lam[idx[0]]) { int u = idx[0]; idx[0] = idx[1]; idx[1] = u; }
+  if (lam[idx[2]] < lam[idx[1]]) { int u = idx[1]; idx[1] = idx[2]; idx[2] = u; }
+  if (lam[idx[1]] < lam[idx[0]]) { int u = idx[0]; idx[0] = idx[1]; idx[1] = u; }
   const double lmax = lam[idx[2]];
   uint32_t rank = 0;
   bool keep[3];
@@ -731,18 +754,12 @@ __device__ void resolve_pinv(const double S[6], const double b[3], rmp_result_t&
     rank += keep[i] ? 1u : 0u;
   }
   r.rank = rank;
-  if (rank == 3) {
-    const double c00 = S[3] * S[5] - S[4] * S[4], c01 = S[2] * S[4] - S[1] * S[5],
-                 c02 = S[1] * S[4] - S[2] * S[3], c11 = S[0] * S[5] - S[2] * S[2],
-                 c12 = S[1] * S[2] - S[0] * S[4], c22 = S[0] * S[3] - S[1] * S[1];
-    const double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
-    if (det > 0.0) {
-      const double inv = 1.0 / det;
-      r.f[0] = (c00 * b[0] + c01 * b[1] + c02 * b[2]) * inv;
-      r.f[1] = (c01 * b[0] + c11 * b[1] + c12 * b[2]) * inv;
-      r.f[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
-      return;
-    }
+  r.f[0] = r.f[1] = r.f[2] = 0.0;
+  if (rank == 3 && adj_ok) {
+    r.f[0] = fadj[0];
+    r.f[1] = fadj[1];
+    r.f[2] = fadj[2];
+    return;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -756,13 +773,53 @@ __device__ void resolve_pinv(const double S[6], const double b[3], rmp_result_t&
   }
 }
 
-// Grid completion: every CTA stores its partial; the last one (ticket) sums all partials
-// in index order in FP64 and resolves.  Called by all threads of every CTA.
+// Sum `count` partials in a fixed order: thread (q, j) of the CTA (q < 11 terms, j < J =
+// blockDim / 16) adds partials j, j + J, ... of term q; then thread q adds its J sums in
+// order.  Result in tot / tot_h / tot_a.  Called by every thread.
+__device__ void sum_partials(const CtaPartial* p, int count, double* tot, unsigned* tot_h,
+                             unsigned* tot_a) {
+  __shared__ double part_d[9][16];
+  __shared__ unsigned part_u[2][16];
+  const int J = blockDim.x >> 4;
+  const int q = threadIdx.x / J, j = threadIdx.x - q * J;
+  if (q < 9) {
+    double s = 0.0;
+    for (int i = j; i < count; i += J) s += __ldcg(&p[i].v[q]);
+    part_d[q][j] = s;
+  } else if (q < 11) {
+    unsigned s = 0;
+    for (int i = j; i < count; i += J) s += __ldcg(q == 9 ? &p[i].n_hits : &p[i].n_active);
+    part_u[q - 9][j] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double s = 0.0;
+    for (int i = 0; i < J; ++i) s += part_d[threadIdx.x][i];
+    tot[threadIdx.x] = s;
+  } else if (threadIdx.x < 11) {
+    unsigned s = 0;
+    for (int i = 0; i < J; ++i) s += part_u[threadIdx.x - 9][i];
+    if (threadIdx.x == 9) *tot_h = s; else *tot_a = s;
+  }
+  __syncthreads();
+}
+
+// Grid completion, deterministic and without one thread walking every CTA: each CTA stores
+// its partial; the last CTA of each group of kGroup CTAs (group ticket) sums the group's
+// partials in index order and stores a group partial; the last group to finish (grid
+// ticket) sums the group partials in index order in FP64 and resolves.  Tickets are reset
+// by the CTA that completes them.  Called by all threads of every CTA.
 __device__ void grid_finish(const double part[9], unsigned hits, unsigned act, WsHeader* ws,
                             CtaPartial* parts, rmp_result_t* out, uint32_t n_rays, int status) {
-  __shared__ bool last;
+  __shared__ int stage;
   __shared__ double tot[9];
   __shared__ unsigned tot_h, tot_a;
+  CtaPartial* groups = parts + kMaxGrid;
+  const int G = gridDim.x;
+  const int gi = blockIdx.x / kGroup;
+  const int n_groups = (G + kGroup - 1) / kGroup;
+  const int g0 = gi * kGroup;
+  const int gsz = min(kGroup, G - g0);
   if (threadIdx.x == 0) {
     CtaPartial p;
 #pragma unroll
@@ -771,59 +828,31 @@ __device__ void grid_finish(const double part[9], unsigned hits, unsigned act, W
     p.n_active = act;
     parts[blockIdx.x] = p;
     __threadfence();
-    const unsigned t = atomicAdd(&ws->ticket, 1u);
-    last = (t == gridDim.x - 1);
+    const unsigned t = atomicAdd(&ws->group_ticket[gi], 1u);
+    stage = (t == (unsigned)gsz - 1) ? 1 : 0;
   }
   __syncthreads();
-  if (!last) return;
+  if (stage == 0) return;
   __threadfence();
-  // Every thread sums the partials g = t, t + blockDim, ... (independent loads, fixed order),
-  // then a fixed xor-shuffle tree within warps and warp order through shared memory.
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int G = gridDim.x;
-  double acc[9];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) acc[q] = 0.0;
-  unsigned ah = 0, aa = 0;
-#pragma unroll 4
-  for (int g = threadIdx.x; g < G; g += blockDim.x) {
-    const CtaPartial* pp = parts + g;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) acc[q] += __ldcg(&pp->v[q]);
-    ah += __ldcg(&pp->n_hits);
-    aa += __ldcg(&pp->n_active);
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-    for (int q = 0; q < 9; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
-  ah = __reduce_add_sync(0xffffffffu, ah);
-  aa = __reduce_add_sync(0xffffffffu, aa);
-  __shared__ double wsum[8][9];
-  __shared__ unsigned wcnt[8][2];
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < 9; ++q) wsum[warp][q] = acc[q];
-    wcnt[warp][0] = ah;
-    wcnt[warp][1] = aa;
-  }
-  __syncthreads();
-  if (threadIdx.x < 9) {
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += wsum[w][threadIdx.x];
-    tot[threadIdx.x] = t;
-  } else if (threadIdx.x == 32) {
-    unsigned th = 0, ta = 0;
-    for (int w = 0; w < nw; ++w) {
-      th += wcnt[w][0];
-      ta += wcnt[w][1];
-    }
-    tot_h = th;
-    tot_a = ta;
-  }
-  __syncthreads();
+  sum_partials(parts + g0, gsz, tot, &tot_h, &tot_a);
   if (threadIdx.x == 0) {
-    rmp_result_t r;
+    CtaPartial p;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) p.v[q] = tot[q];
+    p.n_hits = tot_h;
+    p.n_active = tot_a;
+    groups[gi] = p;
+    ws->group_ticket[gi] = 0;
+    __threadfence();
+    const unsigned t = atomicAdd(&ws->ticket, 1u);
+    stage = (t == (unsigned)n_groups - 1) ? 2 : 0;
+  }
+  __syncthreads();
+  if (stage != 2) return;
+  __threadfence();
+  sum_partials(groups, n_groups, tot, &tot_h, &tot_a);
+  __shared__ rmp_result_t r;
+  if (threadIdx.x == 0) {
     for (int q = 0; q < 6; ++q) r.A[q] = tot[q];
     for (int q = 0; q < 3; ++q) r.Af[q] = tot[6 + q];
     r.n_rays = n_rays;
@@ -831,7 +860,10 @@ __device__ void grid_finish(const double part[9], unsigned hits, unsigned act, W
     r.n_active = tot_a;
     r.status = status;
     r.reserved = 0;
-    resolve_pinv(r.A, r.Af, r);
+  }
+  __syncthreads();
+  resolve_pinv(r.A, r.Af, r);
+  if (threadIdx.x == 0) {
     *out = r;
     ws->ticket = 0;                   // ready for the next evaluation
   }
@@ -874,7 +906,7 @@ __device__ __forceinline__ uint32_t ray_of_slot(uint32_t j, const EvalConsts& k)
 }
 
 // ------------------------------------------------------------------ shared-memory staging
-// The block bitmap is copied into shared memory by one TMA bulk copy (cp.async.bulk,
+// The free-radius field is copied into shared memory by one TMA bulk copy (cp.async.bulk,
 // completion counted on an mbarrier) issued at kernel entry, so it overlaps the state
 // set-up and ray generation.  The wait is bounded: on expiry the CTA reports a timeout
 // (after waiting, again bounded, for the copy to land) instead of hanging.
@@ -926,16 +958,16 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
                                                           WsHeader* ws, CtaPartial* parts,
                                                           rmp_result_t* out, rmp_ray_hit_t* hits,
                                                           float* per_ray) {
-  extern __shared__ uint4 smem_bitmap[];
+  extern __shared__ uint4 smem_radius[];
   __shared__ CtaState cs;
   __shared__ __align__(8) uint64_t bm_bar;
   __shared__ int bm_timeout;
-  const uint32_t bm_bytes = (m.bitmap_words + m.sbitmap_words) * 4u;
-  const bool staged = LAYOUT == kLayoutGrid && bm_bytes <= kMaxSmemBitmapBytes;
-  const uint32_t* bm = staged ? reinterpret_cast<const uint32_t*>(smem_bitmap) : m.bitmap;
+  const uint32_t bm_bytes = m.radius_words * 4u;
+  const bool staged = LAYOUT == kLayoutGrid && bm_bytes <= kMaxSmemRadiusBytes;
+  const uint32_t* bm = staged ? reinterpret_cast<const uint32_t*>(smem_radius) : m.radius;
   if (threadIdx.x == 0) {
     bm_timeout = 0;
-    if (staged) bulk_load_begin(&bm_bar, smem_bitmap, m.bitmap, bm_bytes);
+    if (staged) bulk_load_begin(&bm_bar, smem_radius, m.radius, bm_bytes);
   }
   if (threadIdx.x < 3) {
     const int a = threadIdx.x;
@@ -957,7 +989,7 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
   const uint32_t total = k.n_rays << lgS;
   const uint32_t stride = gridDim.x * blockDim.x;
   uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-  // the first ray is generated while the bitmap copy and the state set-up are in flight
+  // the first ray is generated while the radius copy and the state set-up are in flight
   uint32_t ray_idx = ray_of_slot(base + lane < total ? (base + lane) >> lgS : 0, k);
   Ray ray = make_ray(ray_idx + k.halton_offset);
   __syncthreads();                                  // state ready, barrier initialised
@@ -1122,21 +1154,12 @@ __global__ void dense_bricks_kernel(const uint8_t* __restrict__ occ, int dx, int
   }
 }
 
-// Mark grid brick idx (grid coordinates x, y, z) as holding an occupied voxel, in the block
-// bitmap and in the superblock bitmap that follows it.
-__device__ __forceinline__ void mark_brick(const DevMap& m, uint32_t* bitmap, uint32_t idx, int x,
-                                           int y, int z) {
-  atomicOr(bitmap + (idx >> 5), 1u << (idx & 31));
-  const int sx = ((m.gmin[0] + x) >> 2) - m.sgmin[0], sy = ((m.gmin[1] + y) >> 2) - m.sgmin[1],
-            sz = ((m.gmin[2] + z) >> 2) - m.sgmin[2];
-  const uint32_t si = (uint32_t)sx + (uint32_t)m.sgdim[0] * ((uint32_t)sy + (uint32_t)m.sgdim[1] * (uint32_t)sz);
-  atomicOr(bitmap + m.bitmap_words + (si >> 5), 1u << (si & 31));
-}
-
-// Bitmaps of a dense grid: brick b holds an occupied voxel.
-__global__ void grid_bitmap_kernel(const uint4* __restrict__ bricks, DevMap m,
-                                   uint32_t* __restrict__ bitmap) {
-  const uint32_t n_bricks = (uint32_t)m.gdim[0] * m.gdim[1] * m.gdim[2];
+// Free-radius field of a grid, in three steps: radius 0 for bricks with an occupied voxel
+// and 15 otherwise; kMaxFreeRadius - 1 relaxation passes v(b) = min(v(b), 1 + min over the
+// 26 neighbours v(n)) (neighbours outside the grid count as free), which yields the
+// Chebyshev distance to the nearest occupied brick capped at 15; then packing to 4 bits.
+__global__ void radius_init_kernel(const uint4* __restrict__ bricks, uint32_t n_bricks,
+                                   uint8_t* __restrict__ v) {
   for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_bricks;
        b += gridDim.x * blockDim.x) {
     const uint4* w = bricks + 4 * (size_t)b;
@@ -1146,12 +1169,41 @@ __global__ void grid_bitmap_kernel(const uint4* __restrict__ bricks, DevMap m,
       const uint4 x = w[q];
       any |= x.x | x.y | x.z | x.w;
     }
-    if (any) {
-      const int x = (int)(b % (uint32_t)m.gdim[0]);
-      const int y = (int)((b / (uint32_t)m.gdim[0]) % (uint32_t)m.gdim[1]);
-      const int z = (int)(b / ((uint32_t)m.gdim[0] * m.gdim[1]));
-      mark_brick(m, bitmap, b, x, y, z);
+    v[b] = any ? 0 : (uint8_t)kMaxFreeRadius;
+  }
+}
+
+__global__ void radius_relax_kernel(const uint8_t* __restrict__ vin, uint8_t* __restrict__ vout,
+                                    int gx, int gy, int gz) {
+  const uint32_t n = (uint32_t)gx * gy * gz;
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
+    const int x = (int)(b % (uint32_t)gx), y = (int)((b / (uint32_t)gx) % (uint32_t)gy),
+              z = (int)(b / ((uint32_t)gx * gy));
+    int best = vin[b];
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int xx = x + dx, yy = y + dy, zz = z + dz;
+          if ((unsigned)xx >= (unsigned)gx || (unsigned)yy >= (unsigned)gy || (unsigned)zz >= (unsigned)gz)
+            continue;
+          const int c = vin[(uint32_t)xx + (uint32_t)gx * ((uint32_t)yy + (uint32_t)gy * (uint32_t)zz)] + 1;
+          best = c < best ? c : best;
+        }
+    vout[b] = (uint8_t)best;
+  }
+}
+
+__global__ void radius_pack_kernel(const uint8_t* __restrict__ v, uint32_t n, uint32_t words,
+                                   uint32_t* __restrict__ radius) {
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < words; w += gridDim.x * blockDim.x) {
+    uint32_t word = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t b = w * 8 + i;
+      const uint32_t r = b < n ? v[b] : (uint32_t)kMaxFreeRadius;
+      word |= (r & 15u) << (4 * i);
     }
+    radius[w] = word;
   }
 }
 
@@ -1178,8 +1230,7 @@ __global__ void key_bbox_kernel(const int32_t* __restrict__ keys, const uint4* _
 
 // Scatter the non-empty bricks of a hashed map into the grid layout.
 __global__ void grid_scatter_kernel(const int32_t* __restrict__ keys, const uint4* __restrict__ bricks,
-                                    uint32_t n_blocks, DevMap m, uint4* __restrict__ grid,
-                                    uint32_t* __restrict__ bitmap) {
+                                    uint32_t n_blocks, DevMap m, uint4* __restrict__ grid) {
   const int gx = m.gmin[0], gy = m.gmin[1], gz = m.gmin[2], dx = m.gdim[0], dy = m.gdim[1];
   for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks;
        b += gridDim.x * blockDim.x) {
@@ -1196,7 +1247,6 @@ __global__ void grid_scatter_kernel(const int32_t* __restrict__ keys, const uint
     dst[1] = w1;
     dst[2] = w2;
     dst[3] = w3;
-    mark_brick(m, bitmap, idx, x, y, z);
   }
 }
 
@@ -1262,8 +1312,8 @@ __global__ void hash_build_kernel(const int32_t* __restrict__ keys, uint32_t n_b
 
 // ------------------------------------------------------------------ launchers
 size_t raycast_smem_bytes(const DevMap& m) {
-  const uint32_t bytes = (m.bitmap_words + m.sbitmap_words) * 4u;
-  if (m.layout == kLayoutGrid && bytes <= kMaxSmemBitmapBytes) return bytes;
+  const uint32_t bytes = m.radius_words * 4u;
+  if (m.layout == kLayoutGrid && bytes <= kMaxSmemRadiusBytes) return bytes;
   return 0;
 }
 
@@ -1323,10 +1373,20 @@ cudaError_t launch_dense_bricks(const uint8_t* occ, const int dims[3], const int
 
 static int grid_for(size_t n) { return (int)((n + 255) / 256 < 65535 ? ((n + 255) / 256 > 0 ? (n + 255) / 256 : 1) : 65535); }
 
-cudaError_t launch_grid_bitmap(const uint32_t* bricks, const DevMap& m, uint32_t* bitmap,
-                               cudaStream_t stream) {
+cudaError_t launch_grid_radius(const uint32_t* bricks, const DevMap& m, uint8_t* scratch_a,
+                               uint8_t* scratch_b, uint32_t* radius, cudaStream_t stream) {
   const size_t n = (size_t)m.gdim[0] * m.gdim[1] * m.gdim[2];
-  grid_bitmap_kernel<<<grid_for(n), 256, 0, stream>>>((const uint4*)bricks, m, bitmap);
+  radius_init_kernel<<<grid_for(n), 256, 0, stream>>>((const uint4*)bricks, (uint32_t)n, scratch_a);
+  uint8_t* a = scratch_a;
+  uint8_t* b = scratch_b;
+  for (int it = 0; it < kMaxFreeRadius - 1; ++it) {
+    radius_relax_kernel<<<grid_for(n), 256, 0, stream>>>(a, b, m.gdim[0], m.gdim[1], m.gdim[2]);
+    uint8_t* t = a;
+    a = b;
+    b = t;
+  }
+  radius_pack_kernel<<<grid_for(m.radius_words), 256, 0, stream>>>(a, (uint32_t)n, m.radius_words,
+                                                                   radius);
   return cudaGetLastError();
 }
 
@@ -1337,10 +1397,9 @@ cudaError_t launch_key_bbox(const int32_t* keys, const uint32_t* bricks, uint32_
 }
 
 cudaError_t launch_grid_scatter(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,
-                                const DevMap& m, uint32_t* grid_bricks, uint32_t* bitmap,
-                                cudaStream_t stream) {
+                                const DevMap& m, uint32_t* grid_bricks, cudaStream_t stream) {
   grid_scatter_kernel<<<grid_for(n_blocks), 256, 0, stream>>>(keys, (const uint4*)bricks, n_blocks,
-                                                              m, (uint4*)grid_bricks, bitmap);
+                                                              m, (uint4*)grid_bricks);
   return cudaGetLastError();
 }
 

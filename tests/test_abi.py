@@ -90,7 +90,7 @@ def test_status_strings(rmp):
 
 
 def test_workspace_size_is_fixed(rmp):
-    assert rmp.rmp_workspace_bytes() == 256 + 80 * 4096
+    assert rmp.rmp_workspace_bytes() == 1024 + 80 * (4096 + 128)
 
 
 def test_null_arguments_rejected_without_gpu(rmp):
