@@ -246,7 +246,8 @@ def main():
         h = hits.cpu().numpy().view(R.HIT_DTYPE)
         alg.append(float(((h["steps"].astype(np.int64) + 1) * 4).sum() +
                          16 * h["blocks"].astype(np.int64).sum()))
-    grid = min((N_RAYS + 127) // 128, 4096)
+    launch = R.rmp_eval_launch_info(ctx.handle, mid, N_RAYS, params)
+    grid = launch["grid"]
     alg_bytes = float(np.mean(alg)) + grid * 80 + 48 + 144
 
     def step(i):
@@ -322,7 +323,7 @@ def main():
             "config": {"workload": WORKLOAD, "n_rays": N_RAYS, "states": N_STATES,
                        "map_blocks": wl.map.n_blocks, "parallelism": "replicas x%d" % world,
                        "l2": "flushed between timed steps (256 MiB write outside the events)",
-                       "launch": {"block": 128, "grid": grid}},
+                       "launch": launch},
             "evals_per_s": world * 1e3 / ms_max,
             "ms_per_step_p50": float(np.percentile(per, 50)),
             "ms_per_step_p99": float(np.percentile(per, 99)),

@@ -228,6 +228,16 @@ int rmp_scan_eval_async(rmp_ctx* ctx, const float* points_dev, uint32_t n,
 int rmp_tune_set(rmp_ctx* ctx, int knob, int value);
 int rmp_tune_get(rmp_ctx* ctx, int knob, int* value);
 
+/* Launch shape rmp_raycast_eval[_async] would use for this map, ray count and parameters:
+ * threads per CTA, CTAs, log2 segments per ray, resident CTAs per SM (occupancy), SMs,
+ * dynamic shared memory per CTA (the staged free-radius field) and the number of
+ * direction cells of the ray order.  Host-side only; launches nothing. */
+typedef struct {
+  int32_t block, grid, lg_segments, ctas_per_sm, sm_count, smem_bytes, ray_cells, reserved;
+} rmp_launch_info_t;
+int rmp_eval_launch_info(rmp_ctx* ctx, uint32_t map_id, uint32_t n_rays,
+                         const rmp_params_t* params, rmp_launch_info_t* out);
+
 #ifdef __cplusplus
 }
 #endif

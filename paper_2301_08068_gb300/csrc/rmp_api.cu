@@ -490,6 +490,31 @@ int rmp_tune_set(rmp_ctx* c, int knob, int value) {
   return RMP_OK;
 }
 
+int rmp_eval_launch_info(rmp_ctx* c, uint32_t map_id, uint32_t n_rays, const rmp_params_t* params,
+                         rmp_launch_info_t* out) {
+  if (!c || !out) return RMP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->maps.find(map_id);
+  if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
+  const DevMap dm = it->second.dm;
+  EvalConsts k;
+  int st = make_consts(params, dm.vs, n_rays, false, &k, c->tune_lg_segs);
+  if (st != RMP_OK) return st;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  int block, grid;
+  launch_shape(c, (uint64_t)n_rays << k.lg_segs, &block, &grid);
+  std::memset(out, 0, sizeof(*out));
+  out->block = block;
+  out->grid = grid;
+  out->lg_segments = (int)k.lg_segs;
+  out->ctas_per_sm = raycast_occupancy(dm, k.reduce_mode, block);
+  out->sm_count = c->sm_count;
+  out->smem_bytes = (int)raycast_smem_bytes(dm);
+  out->ray_cells = (int)k.perm_M;
+  return RMP_OK;
+}
+
 int rmp_tune_get(rmp_ctx* c, int knob, int* value) {
   if (!c || !value) return RMP_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(c->mu);

@@ -98,6 +98,7 @@ inline unsigned long long pack_key(int bx, int by, int bz) {
 
 // Launchers (rmp_kernels.cu).  All enqueue on `stream` and return cudaGetLastError().
 size_t raycast_smem_bytes(const DevMap& m);
+int raycast_occupancy(const DevMap& m, int reduce_mode, int block);   // CTAs per SM
 cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,
                            void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
                            float* per_ray, int block, int grid, cudaStream_t stream);

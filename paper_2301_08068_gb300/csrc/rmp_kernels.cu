@@ -1317,17 +1317,50 @@ size_t raycast_smem_bytes(const DevMap& m) {
   return 0;
 }
 
+// The kernels keep up to 48 KB of the map's radius field in shared memory: ask for the
+// largest shared-memory carveout once per device so that register use, not the L1/shared
+// split, bounds the CTAs resident per SM (a whole evaluation should fit in one wave).
+template <typename F>
+static void prefer_shared(F* fn) {
+  static uint64_t done_mask = 0;   // one bit per device id < 64
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return;
+  if (__atomic_load_n(&done_mask, __ATOMIC_ACQUIRE) & (1ull << dev)) return;
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
+  __atomic_fetch_or(&done_mask, 1ull << dev, __ATOMIC_ACQ_REL);
+}
+
 template <int KIND, int LAYOUT>
 static void launch_raycast_t(const DevMap& m, const EvalConsts& k, const double* state_dev,
                              WsHeader* hdr, CtaPartial* parts, rmp_result_t* out_dev,
                              rmp_ray_hit_t* hits, float* per_ray, int block, int grid,
                              size_t smem, cudaStream_t stream) {
-  if (k.reduce_mode == RMP_REDUCE_FP64)
+  if (k.reduce_mode == RMP_REDUCE_FP64) {
+    prefer_shared(raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_FP64>);
     raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_FP64><<<grid, block, smem, stream>>>(
         m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
-  else
+  } else {
+    prefer_shared(raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_KAHAN32>);
     raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_KAHAN32><<<grid, block, smem, stream>>>(
         m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
+  }
+}
+
+int raycast_occupancy(const DevMap& m, int reduce_mode, int block) {
+  int n = 0;
+  const size_t smem = raycast_smem_bytes(m);
+  cudaError_t e;
+  if (m.kind == RMP_MAP_DENSE_U8)
+    e = reduce_mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_FP64>, block, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_KAHAN32>, block, smem);
+  else if (m.layout == kLayoutGrid)
+    e = reduce_mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutGrid, RMP_REDUCE_FP64>, block, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutGrid, RMP_REDUCE_KAHAN32>, block, smem);
+  else
+    e = reduce_mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutHash, RMP_REDUCE_FP64>, block, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutHash, RMP_REDUCE_KAHAN32>, block, smem);
+  return e == cudaSuccess ? n : -1;
 }
 
 cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,

@@ -61,6 +61,11 @@ class rmp_map_desc_t(C.Structure):
                 ("occ", C.c_void_p), ("block_keys", C.c_void_p), ("tsdf", C.c_void_p)]
 
 
+class rmp_launch_info_t(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("block", "grid", "lg_segments", "ctas_per_sm", "sm_count",
+                                         "smem_bytes", "ray_cells", "reserved")]
+
+
 class rmp_map_info_t(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_bricks", C.c_uint32), ("hash_capacity", C.c_uint32),
                 ("layout", C.c_uint32), ("device_bytes", C.c_uint64)]
@@ -90,6 +95,8 @@ _SIGNATURES = {
     "rmp_scan_eval_async": [_P, _P, C.c_uint32, _P, C.POINTER(rmp_params_t), _P, C.c_size_t, _P,
                             _P, _P],
     "rmp_tune_set": [_P, C.c_int, C.c_int],
+    "rmp_eval_launch_info": [_P, C.c_uint32, C.c_uint32, C.POINTER(rmp_params_t),
+                             C.POINTER(rmp_launch_info_t)],
     "rmp_tune_get": [_P, C.c_int, C.POINTER(C.c_int)],
 }
 # Symbols every build must export (checked by the not-gpu ABI test against include/rmp.h).
@@ -264,6 +271,13 @@ def rmp_scan_eval_async(ctx: int, points, state, params: rmp_params_t, workspace
 
 def rmp_tune_set(ctx: int, knob: int, value: int):
     _check(lib().rmp_tune_set(ctx, int(knob), int(value)), "rmp_tune_set")
+
+
+def rmp_eval_launch_info(ctx: int, map_id: int, n_rays: int, params: rmp_params_t) -> dict:
+    info = rmp_launch_info_t()
+    _check(lib().rmp_eval_launch_info(ctx, int(map_id), int(n_rays), C.byref(params), C.byref(info)),
+           "rmp_eval_launch_info")
+    return {n: getattr(info, n) for n, _ in rmp_launch_info_t._fields_ if n != "reserved"}
 
 
 def rmp_tune_get(ctx: int, knob: int) -> int:

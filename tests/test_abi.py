@@ -49,13 +49,14 @@ int main(void) {
   printf("{\\n");
   printf("\\"rmp_params_t\\": %zu, \\"rmp_result_t\\": %zu, \\"rmp_ray_hit_t\\": %zu,\\n",
          sizeof(rmp_params_t), sizeof(rmp_result_t), sizeof(rmp_ray_hit_t));
-  printf("\\"rmp_map_desc_t\\": %zu, \\"rmp_map_info_t\\": %zu,\\n", sizeof(rmp_map_desc_t),
-         sizeof(rmp_map_info_t));
+  printf("\\"rmp_map_desc_t\\": %zu, \\"rmp_map_info_t\\": %zu, \\"rmp_launch_info_t\\": %zu,\\n",
+         sizeof(rmp_map_desc_t), sizeof(rmp_map_info_t), sizeof(rmp_launch_info_t));
   O(rmp_params_t, max_range); O(rmp_params_t, halton_offset); O(rmp_params_t, flags);
   O(rmp_result_t, A); O(rmp_result_t, eig); O(rmp_result_t, n_rays); O(rmp_result_t, status);
   O(rmp_ray_hit_t, steps); O(rmp_ray_hit_t, d); O(rmp_ray_hit_t, status);
   O(rmp_map_desc_t, voxel_size); O(rmp_map_desc_t, dims); O(rmp_map_desc_t, n_blocks);
   O(rmp_map_desc_t, occ); O(rmp_map_desc_t, tsdf); O(rmp_map_info_t, device_bytes);
+  O(rmp_map_info_t, layout); O(rmp_launch_info_t, ctas_per_sm); O(rmp_launch_info_t, ray_cells);
   printf("\\"end\\": 0}\\n");
   return 0;
 }
@@ -63,7 +64,8 @@ int main(void) {
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
     got = json.loads(subprocess.check_output([str(exe)]))
-    for T in ("rmp_params_t", "rmp_result_t", "rmp_ray_hit_t", "rmp_map_desc_t", "rmp_map_info_t"):
+    for T in ("rmp_params_t", "rmp_result_t", "rmp_ray_hit_t", "rmp_map_desc_t", "rmp_map_info_t",
+              "rmp_launch_info_t"):
         assert C.sizeof(getattr(rmp, T)) == got[T], T
     for key, off in got.items():
         if "." in key:
