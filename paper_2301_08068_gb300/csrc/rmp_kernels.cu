@@ -130,6 +130,28 @@ __device__ __forceinline__ int hash_lookup(const DevMap& m, int bx, int by, int 
   return -1;
 }
 
+// A brick held in registers: 16 occupancy words, loaded with four 128-bit loads.
+struct Brick {
+  uint4 q0, q1, q2, q3;
+};
+
+__device__ __forceinline__ void load_brick(const uint4* src, Brick& br) {
+  br.q0 = __ldg(src);
+  br.q1 = __ldg(src + 1);
+  br.q2 = __ldg(src + 2);
+  br.q3 = __ldg(src + 3);
+}
+
+// Occupancy of voxel k in the register brick: word (ly>>2) + 2 lz picked by a select
+// tree (no local memory), bit lx + 8 (ly & 3).
+__device__ __forceinline__ bool brick_bit(const Brick& b, int kx, int ky, int kz) {
+  const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
+  const int wi = (ly >> 2) + 2 * lz;
+  const uint4 q = (wi & 8) ? ((wi & 4) ? b.q3 : b.q2) : ((wi & 4) ? b.q1 : b.q0);
+  const uint32_t w = (wi & 2) ? ((wi & 1) ? q.w : q.z) : ((wi & 1) ? q.y : q.x);
+  return (w >> (lx + 8 * (ly & 3))) & 1u;
+}
+
 // Free radius v of block (bx,by,bz): 0 if it holds an occupied voxel (then *src points at
 // its brick), else v >= 1 with every block within Chebyshev distance v - 1 free.  Grid
 // layout: the 4-bit field `rad` (shared memory when it fits); outside the grid's bounding
@@ -195,17 +217,17 @@ __device__ __forceinline__ bool outside(const DevMap& m, const int k[3]) {
           (unsigned)k[2] >= (unsigned)m.dims[2]);
 }
 
-// The ray is in a free box: the blocks within Chebyshev distance R of its current block, or
-// for R < 0 just its current voxel (clipped to the dense grid).  Advance the DDA state to the first voxel
-// beyond the box exactly as single steps would: the box is left through the axis e whose
-// face crossing F_e/|D_e| comes first (ties: lowest axis); every other axis b crosses its
-// interior boundaries that come strictly before that time (or at the same time if b < e,
-// the tie order).  If the face crossing is beyond the limit, the ray ends inside the box
-// after every crossing within the limit; returns true then.
+// The ray is in a free box: the blocks within Chebyshev distance R of its current block
+// (clipped to the dense grid).  Advance the DDA state to the first voxel beyond the box
+// exactly as single steps would: the box is left through the axis e whose face crossing
+// F_e/|D_e| comes first (ties: lowest axis); every other axis b crosses its interior
+// boundaries that come strictly before that time (or at the same time if b < e, the tie
+// order).  If the face crossing is beyond the limit, the ray ends inside the box after
+// every crossing within the limit; returns true then.
 //
-// The per-axis counts #{m >= 0 : Y + m u < X (<= X if b < e)}, u = 2^16 |D_e|, are at most
-// 8 (2R + 1) - 1 < 2^8: an FP32 quotient estimate (error far below 1) is corrected once
-// in each direction with exact 64-bit comparisons.
+// Per axis b the crossing count is #{m >= 0 : (N_b + 2^16 m) |D_e| < F_e |D_b|} (<= for
+// b < e), at most 8 (2R + 1) - 1.  It is estimated from 32-bit values in FP32 (error far
+// below one crossing) and corrected once, up or down, with exact 64-bit comparisons.
 template <int KIND>
 __device__ __forceinline__ bool skip_box(const DevMap& m, int k[3], const int s[3], uint32_t N[3],
                                          const uint32_t A[3], const uint32_t L[3], int R,
@@ -214,7 +236,7 @@ __device__ __forceinline__ bool skip_box(const DevMap& m, int k[3], const int s[
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int b = k[a] >> 3;
-    int ca = R < 0 ? 0 : (s[a] > 0 ? 8 * (b + R) + 7 - k[a] : k[a] - 8 * (b - R));
+    int ca = s[a] > 0 ? 8 * (b + R) + 7 - k[a] : k[a] - 8 * (b - R);
     if (KIND == RMP_MAP_DENSE_U8) {
       const int g = s[a] > 0 ? m.dims[a] - 1 - k[a] : k[a];
       ca = ca < g ? ca : g;
@@ -251,29 +273,31 @@ __device__ __forceinline__ bool skip_box(const DevMap& m, int k[3], const int s[
     }
     return true;
   }
-  const unsigned long long unit = (unsigned long long)Ae << 16;     // 2^16 |D_e|
-  const float inv_unit = __frcp_rn(__ull2float_rn(unit));
+  const float te = __fdividef(__uint2float_rn(Fe), __uint2float_rn(Ae));   // ~ exit time
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
     if (b == e || A[b] == 0) continue;
-    const unsigned long long X = (unsigned long long)Fe * A[b];
-    const unsigned long long Y = (unsigned long long)N[b] * Ae;
     const bool le = b < e;
-    uint32_t cnt = 0;
-    if (le ? Y <= X : Y < X) {
-      const uint32_t q = (uint32_t)(__ull2float_rn(X - Y) * inv_unit);   // floor(estimate)
-      cnt = q + 1;
-      unsigned long long t = Y + (unsigned long long)q * unit;         // condition for m = q
-      if (!(le ? t <= X : t < X)) {
-        cnt = q;
+    const unsigned long long X = (unsigned long long)Fe * A[b];
+    // estimate (t_e |D_b| - N_b) / 2^16, then the candidate count floor(.) + 1
+    const float est = (te * __uint2float_rn(A[b]) - __uint2float_rn(N[b])) * (1.0f / 65536.0f);
+    int cnt = est < 0.0f ? 0 : (int)est + 1;
+    cnt = cnt < (int)c[b] + 1 ? cnt : (int)c[b] + 1;
+    if (cnt > 0) {
+      const unsigned long long y = (unsigned long long)(N[b] + ((uint32_t)(cnt - 1) << 16)) * Ae;
+      if (!(le ? y <= X : y < X)) {
+        cnt -= 1;
       } else {
-        t += unit;                                                       // m = q + 1
-        if (le ? t <= X : t < X) cnt = q + 2;
+        const unsigned long long y1 = y + ((unsigned long long)Ae << 16);
+        if (le ? y1 <= X : y1 < X) cnt += 1;
       }
+    } else {
+      const unsigned long long y0 = (unsigned long long)N[b] * Ae;
+      if (le ? y0 <= X : y0 < X) cnt = 1;
     }
-    k[b] += s[b] * (int)cnt;
-    N[b] += cnt << 16;
-    steps += cnt;
+    k[b] += s[b] * cnt;
+    N[b] += (uint32_t)cnt << 16;
+    steps += (uint32_t)cnt;
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -294,8 +318,9 @@ __device__ __forceinline__ bool skip_box(const DevMap& m, int k[3], const int s[
 // crossing numerator n of axis a (t = n / |D_a|) satisfies t <= T_s iff
 // n S 2^24 <= s R_fx |D_a|; the segment's start state (all crossings with t <= T_seg
 // applied) and its limits L_a follow from that in integer arithmetic.  Within a segment:
-// free boxes of blocks are crossed by skip_box, occupied blocks voxel by voxel (a box of
-// one voxel), so all lanes of a warp run the same instructions in every iteration.
+// free boxes of blocks are crossed by skip_box, occupied blocks voxel by voxel with the brick
+// in registers and the order of the next crossings kept in the exact differences
+// E_ab = N_a |D_b| - N_b |D_a|.
 template <int KIND, int LAYOUT>
 __device__ __forceinline__ SegOut march_segment(const DevMap& m, const uint32_t* bm,
                                                 const long long P[3], const int D[3],
@@ -342,28 +367,83 @@ __device__ __forceinline__ SegOut march_segment(const DevMap& m, const uint32_t*
   o.status = RMP_RAY_MISS_EXIT;
   if (!outside<KIND>(m, k)) {
     o.status = last_seg ? RMP_RAY_MISS_RANGE : kSegContinues;
-    // Every iteration is the same for all lanes: look up the block's free radius; in an
-    // occupied block test the current voxel and take the voxel itself as the box; then
-    // one exact box crossing (a single voxel step when the box is the voxel).
     for (uint32_t guard = 0; guard < 3u * (kMaxRangeVoxels + 2); ++guard) {
       const uint4* src = nullptr;
       const int v = block_radius<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, &src);
-      if (v == 0) {
-        const int lx = k[0] & 7, ly = k[1] & 7, lz = k[2] & 7;
-        const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(src) + (ly >> 2) + 2 * lz);
-        if ((w >> (lx + 8 * (ly & 3))) & 1u) {
+      if (v > 0) {
+        if (skip_box<KIND>(m, k, s, N, A, L, v - 1, o.steps, o.n_last, o.a_last)) break;  // limit
+        if (outside<KIND>(m, k)) {
+          o.status = RMP_RAY_MISS_EXIT;
+          // only the exit axis can have left the grid
+          o.ax_last = ((unsigned)k[0] >= (unsigned)m.dims[0]) ? 0
+                      : (((unsigned)k[1] >= (unsigned)m.dims[1]) ? 1 : 2);
+          break;
+        }
+        continue;
+      }
+      Brick w;
+      load_brick(src, w);
+      if (brick_bit(w, k[0], k[1], k[2])) {
+        o.status = RMP_RAY_HIT;
+        break;
+      }
+      // exact order of the next crossings: E_xy > 0 <=> t_y < t_x, etc.
+      long long exy = (long long)N[0] * A[1] - (long long)N[1] * A[0];
+      long long exz = (long long)N[0] * A[2] - (long long)N[2] * A[0];
+      long long eyz = (long long)N[1] * A[2] - (long long)N[2] * A[1];
+      const long long u0 = (long long)A[0] << 16, u1 = (long long)A[1] << 16,
+                      u2 = (long long)A[2] << 16;
+      bool done = false;
+      // at most 21 interior steps and one exit step inside an 8^3 block
+      for (int it = 0; it < 24; ++it) {
+        const bool ylx = exy > 0;
+        const bool zlw = ylx ? (eyz > 0) : (exz > 0);
+        const int ax = zlw ? 2 : (ylx ? 1 : 0);
+        const uint32_t na = sel3(N, ax), aa = sel3(A, ax), la = sel3(L, ax);
+        if (na > la) {                                  // next crossing beyond the limit
+          done = true;
+          break;
+        }
+        o.n_last = na;
+        o.a_last = aa;
+        o.ax_last = ax;
+        o.steps += 1;
+        bool crossed = false;
+        if (ax == 0) {
+          const int kn = k[0] + s[0];
+          crossed = ((kn ^ k[0]) & ~7) != 0;
+          k[0] = kn;
+          N[0] += 65536u;
+          exy += u1;
+          exz += u2;
+        } else if (ax == 1) {
+          const int kn = k[1] + s[1];
+          crossed = ((kn ^ k[1]) & ~7) != 0;
+          k[1] = kn;
+          N[1] += 65536u;
+          exy -= u0;
+          eyz += u2;
+        } else {
+          const int kn = k[2] + s[2];
+          crossed = ((kn ^ k[2]) & ~7) != 0;
+          k[2] = kn;
+          N[2] += 65536u;
+          exz -= u0;
+          eyz -= u1;
+        }
+        if (outside<KIND>(m, k)) {
+          o.status = RMP_RAY_MISS_EXIT;
+          done = true;
+          break;
+        }
+        if (crossed) break;
+        if (brick_bit(w, k[0], k[1], k[2])) {
           o.status = RMP_RAY_HIT;
+          done = true;
           break;
         }
       }
-      if (skip_box<KIND>(m, k, s, N, A, L, v - 1, o.steps, o.n_last, o.a_last)) break;  // limit
-      if (outside<KIND>(m, k)) {
-        o.status = RMP_RAY_MISS_EXIT;
-        // only the exit axis can have left the grid
-        o.ax_last = ((unsigned)k[0] >= (unsigned)m.dims[0]) ? 0
-                    : (((unsigned)k[1] >= (unsigned)m.dims[1]) ? 1 : 2);
-        break;
-      }
+      if (done) break;
     }
   }
   o.k[0] = k[0];
