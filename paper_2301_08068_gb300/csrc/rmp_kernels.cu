@@ -367,83 +367,85 @@ __device__ __forceinline__ SegOut march_segment(const DevMap& m, const uint32_t*
   o.status = RMP_RAY_MISS_EXIT;
   if (!outside<KIND>(m, k)) {
     o.status = last_seg ? RMP_RAY_MISS_RANGE : kSegContinues;
-    for (uint32_t guard = 0; guard < 3u * (kMaxRangeVoxels + 2); ++guard) {
-      const uint4* src = nullptr;
-      const int v = block_radius<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, &src);
-      if (v > 0) {
-        if (skip_box<KIND>(m, k, s, N, A, L, v - 1, o.steps, o.n_last, o.a_last)) break;  // limit
-        if (outside<KIND>(m, k)) {
-          o.status = RMP_RAY_MISS_EXIT;
-          // only the exit axis can have left the grid
-          o.ax_last = ((unsigned)k[0] >= (unsigned)m.dims[0]) ? 0
-                      : (((unsigned)k[1] >= (unsigned)m.dims[1]) ? 1 : 2);
+    // One loop, one unit of work per lane and iteration (a free-box crossing, entering an
+    // occupied block, or one voxel step inside it), so lanes in different phases of their
+    // rays share iterations instead of serialising nested loops.
+    Brick w;
+    long long exy = 0, exz = 0, eyz = 0;
+    bool in_block = false;
+    const long long u0 = (long long)A[0] << 16, u1 = (long long)A[1] << 16,
+                    u2 = (long long)A[2] << 16;
+    for (uint32_t guard = 0; guard < 8u * (kMaxRangeVoxels + 2); ++guard) {
+      if (!in_block) {
+        const uint4* src = nullptr;
+        const int v = block_radius<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, &src);
+        if (v > 0) {
+          if (skip_box<KIND>(m, k, s, N, A, L, v - 1, o.steps, o.n_last, o.a_last)) break;  // limit
+          if (outside<KIND>(m, k)) {
+            o.status = RMP_RAY_MISS_EXIT;
+            // only the exit axis can have left the grid
+            o.ax_last = ((unsigned)k[0] >= (unsigned)m.dims[0]) ? 0
+                        : (((unsigned)k[1] >= (unsigned)m.dims[1]) ? 1 : 2);
+            break;
+          }
+          continue;
+        }
+        load_brick(src, w);
+        if (brick_bit(w, k[0], k[1], k[2])) {
+          o.status = RMP_RAY_HIT;
           break;
         }
+        // exact order of the next crossings: E_xy > 0 <=> t_y < t_x, etc.
+        exy = (long long)N[0] * A[1] - (long long)N[1] * A[0];
+        exz = (long long)N[0] * A[2] - (long long)N[2] * A[0];
+        eyz = (long long)N[1] * A[2] - (long long)N[2] * A[1];
+        in_block = true;
         continue;
       }
-      Brick w;
-      load_brick(src, w);
+      const bool ylx = exy > 0;
+      const bool zlw = ylx ? (eyz > 0) : (exz > 0);
+      const int ax = zlw ? 2 : (ylx ? 1 : 0);
+      const uint32_t na = sel3(N, ax), aa = sel3(A, ax), la = sel3(L, ax);
+      if (na > la) break;                                // next crossing beyond the limit
+      o.n_last = na;
+      o.a_last = aa;
+      o.ax_last = ax;
+      o.steps += 1;
+      bool crossed = false;
+      if (ax == 0) {
+        const int kn = k[0] + s[0];
+        crossed = ((kn ^ k[0]) & ~7) != 0;
+        k[0] = kn;
+        N[0] += 65536u;
+        exy += u1;
+        exz += u2;
+      } else if (ax == 1) {
+        const int kn = k[1] + s[1];
+        crossed = ((kn ^ k[1]) & ~7) != 0;
+        k[1] = kn;
+        N[1] += 65536u;
+        exy -= u0;
+        eyz += u2;
+      } else {
+        const int kn = k[2] + s[2];
+        crossed = ((kn ^ k[2]) & ~7) != 0;
+        k[2] = kn;
+        N[2] += 65536u;
+        exz -= u0;
+        eyz -= u1;
+      }
+      if (outside<KIND>(m, k)) {
+        o.status = RMP_RAY_MISS_EXIT;
+        break;
+      }
+      if (crossed) {
+        in_block = false;
+        continue;
+      }
       if (brick_bit(w, k[0], k[1], k[2])) {
         o.status = RMP_RAY_HIT;
         break;
       }
-      // exact order of the next crossings: E_xy > 0 <=> t_y < t_x, etc.
-      long long exy = (long long)N[0] * A[1] - (long long)N[1] * A[0];
-      long long exz = (long long)N[0] * A[2] - (long long)N[2] * A[0];
-      long long eyz = (long long)N[1] * A[2] - (long long)N[2] * A[1];
-      const long long u0 = (long long)A[0] << 16, u1 = (long long)A[1] << 16,
-                      u2 = (long long)A[2] << 16;
-      bool done = false;
-      // at most 21 interior steps and one exit step inside an 8^3 block
-      for (int it = 0; it < 24; ++it) {
-        const bool ylx = exy > 0;
-        const bool zlw = ylx ? (eyz > 0) : (exz > 0);
-        const int ax = zlw ? 2 : (ylx ? 1 : 0);
-        const uint32_t na = sel3(N, ax), aa = sel3(A, ax), la = sel3(L, ax);
-        if (na > la) {                                  // next crossing beyond the limit
-          done = true;
-          break;
-        }
-        o.n_last = na;
-        o.a_last = aa;
-        o.ax_last = ax;
-        o.steps += 1;
-        bool crossed = false;
-        if (ax == 0) {
-          const int kn = k[0] + s[0];
-          crossed = ((kn ^ k[0]) & ~7) != 0;
-          k[0] = kn;
-          N[0] += 65536u;
-          exy += u1;
-          exz += u2;
-        } else if (ax == 1) {
-          const int kn = k[1] + s[1];
-          crossed = ((kn ^ k[1]) & ~7) != 0;
-          k[1] = kn;
-          N[1] += 65536u;
-          exy -= u0;
-          eyz += u2;
-        } else {
-          const int kn = k[2] + s[2];
-          crossed = ((kn ^ k[2]) & ~7) != 0;
-          k[2] = kn;
-          N[2] += 65536u;
-          exz -= u0;
-          eyz -= u1;
-        }
-        if (outside<KIND>(m, k)) {
-          o.status = RMP_RAY_MISS_EXIT;
-          done = true;
-          break;
-        }
-        if (crossed) break;
-        if (brick_bit(w, k[0], k[1], k[2])) {
-          o.status = RMP_RAY_HIT;
-          done = true;
-          break;
-        }
-      }
-      if (done) break;
     }
   }
   o.k[0] = k[0];
