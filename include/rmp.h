@@ -222,9 +222,16 @@ int rmp_scan_eval_async(rmp_ctx* ctx, const float* points_dev, uint32_t n,
  * the floating-point reduction, hit records are identical.
  *  RMP_TUNE_BLOCK        threads per CTA: 64, 128 (default) or 256
  *  RMP_TUNE_LG_SEGMENTS  log2 of the segments each ray is split into and marched by that
- *                        many threads (0..2), or -1 (default) to choose from the ray count */
+ *                        many threads (0..2), or -1 (default) to choose from the ray count
+ *  RMP_TUNE_RAY_ORDER    0 (default): rays of one direction cell share warps (coherent
+ *                        march); 1: Halton index order
+ *  RMP_TUNE_SPLIT_BUDGET block visits after which the pieces still running in a warp are
+ *                        cut into sub-pieces marched by the warp's idle lanes (1..65536),
+ *                        0 never, -1 (default) the library's choice (currently never) */
 #define RMP_TUNE_BLOCK 1
 #define RMP_TUNE_LG_SEGMENTS 2
+#define RMP_TUNE_RAY_ORDER 3
+#define RMP_TUNE_SPLIT_BUDGET 4
 int rmp_tune_set(rmp_ctx* ctx, int knob, int value);
 int rmp_tune_get(rmp_ctx* ctx, int knob, int* value);
 

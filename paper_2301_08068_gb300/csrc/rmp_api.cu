@@ -35,6 +35,8 @@ struct rmp_ctx {
   uint32_t next_id = 1;
   int tune_block = 128;      // threads per CTA of the evaluation kernels
   int tune_lg_segs = -1;     // log2 segments per ray (-1: chosen from the ray count)
+  int tune_ray_order = 0;    // 0: coherent direction cells, 1: Halton index order
+  int tune_split = -1;       // split budget (-1: default, 0: never split)
   // scratch of the synchronous calls (serialised by mu)
   void* ws = nullptr;
   double* state_dev = nullptr;
@@ -114,8 +116,20 @@ void pick_ray_cells(uint32_t n, EvalConsts* k) {
 }
 
 // Derive the per-evaluation constants; validates every parameter.
+struct Tuning {
+  int lg_segs = -1, ray_order = 0, split = -1;
+};
+
+Tuning tuning_of(const rmp_ctx* c) {
+  Tuning t;
+  t.lg_segs = c->tune_lg_segs;
+  t.ray_order = c->tune_ray_order;
+  t.split = c->tune_split;
+  return t;
+}
+
 int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalConsts* k,
-                int lg_segs_override = -1) {
+                const Tuning& tune = Tuning()) {
   if (!p) return RMP_ERR_INVALID_ARG;
   if (!(std::isfinite(p->eta_rep) && p->eta_rep >= 0.0) || !finite_pos(p->nu_rep) ||
       !(std::isfinite(p->eta_damp) && p->eta_damp >= 0.0) || !finite_pos(p->nu_damp) ||
@@ -147,11 +161,19 @@ int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalCon
     const double vox = p->max_range / vs;
     if (!(vox <= (double)kMaxRangeVoxels)) return RMP_ERR_INVALID_ARG;
     k->R_fx = std::llrint(vox * 65536.0);
-    pick_ray_cells(n, k);
+    if (tune.ray_order == 0) {
+      pick_ray_cells(n, k);
+    } else {
+      k->perm_M = 1;
+      k->perm_Q = n;
+      k->perm_R = 0;
+    }
     // small evaluations are latency-bound: marching each ray as 4 (2) segments shortens
     // every thread's serial chain; large ones are issue-bound, where segments only add work
     k->lg_segs = n <= 4096u ? 2u : (n <= 16384u ? 1u : 0u);
-    if (lg_segs_override >= 0) k->lg_segs = (uint32_t)lg_segs_override;
+    if (tune.lg_segs >= 0) k->lg_segs = (uint32_t)tune.lg_segs;
+    k->split_budget = tune.split < 0 ? kDefaultSplitBudget
+                      : (tune.split == 0 ? 0xffffffffu : (uint32_t)tune.split);
   } else {
     k->perm_M = 1;
     k->perm_Q = n;
@@ -484,6 +506,12 @@ int rmp_tune_set(rmp_ctx* c, int knob, int value) {
   } else if (knob == RMP_TUNE_LG_SEGMENTS) {
     if (value < -1 || value > 2) return RMP_ERR_INVALID_ARG;
     c->tune_lg_segs = value;
+  } else if (knob == RMP_TUNE_RAY_ORDER) {
+    if (value < 0 || value > 1) return RMP_ERR_INVALID_ARG;
+    c->tune_ray_order = value;
+  } else if (knob == RMP_TUNE_SPLIT_BUDGET) {
+    if (value < -1 || value > 65536) return RMP_ERR_INVALID_ARG;
+    c->tune_split = value;
   } else {
     return RMP_ERR_INVALID_ARG;
   }
@@ -498,7 +526,7 @@ int rmp_eval_launch_info(rmp_ctx* c, uint32_t map_id, uint32_t n_rays, const rmp
   if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
   const DevMap dm = it->second.dm;
   EvalConsts k;
-  int st = make_consts(params, dm.vs, n_rays, false, &k, c->tune_lg_segs);
+  int st = make_consts(params, dm.vs, n_rays, false, &k, tuning_of(c));
   if (st != RMP_OK) return st;
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
@@ -520,6 +548,8 @@ int rmp_tune_get(rmp_ctx* c, int knob, int* value) {
   std::lock_guard<std::mutex> lk(c->mu);
   if (knob == RMP_TUNE_BLOCK) *value = c->tune_block;
   else if (knob == RMP_TUNE_LG_SEGMENTS) *value = c->tune_lg_segs;
+  else if (knob == RMP_TUNE_RAY_ORDER) *value = c->tune_ray_order;
+  else if (knob == RMP_TUNE_SPLIT_BUDGET) *value = c->tune_split;
   else return RMP_ERR_INVALID_ARG;
   return RMP_OK;
 }
@@ -544,7 +574,7 @@ int rmp_raycast_eval_async(rmp_ctx* c, uint32_t map_id, const double* state_dev,
     dm = it->second.dm;
   }
   EvalConsts k;
-  int st = make_consts(params, dm.vs, n_rays, false, &k, c->tune_lg_segs);
+  int st = make_consts(params, dm.vs, n_rays, false, &k, tuning_of(c));
   if (st != RMP_OK) return st;
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
@@ -564,7 +594,7 @@ int rmp_raycast_eval(rmp_ctx* c, uint32_t map_id, const double x[3], const doubl
   if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
   const DevMap dm = it->second.dm;
   EvalConsts k;
-  int st = make_consts(params, dm.vs, n_rays, false, &k, c->tune_lg_segs);
+  int st = make_consts(params, dm.vs, n_rays, false, &k, tuning_of(c));
   if (st != RMP_OK) return st;
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;

@@ -30,6 +30,9 @@ constexpr int kWsHeaderBytes = 1024;
 constexpr int kGroup = 32;                  // CTAs per reduction group (see grid_finish)
 constexpr int kMaxGroups = 4096 / kGroup;
 constexpr int kMaxRangeVoxels = 16384;  // keeps every DDA crossing numerator below 2^31
+// Block visits before a warp's unfinished pieces are split over its idle lanes; by default
+// never (measured: with coherent ray order the split does not shorten the slowest warps)
+constexpr uint32_t kDefaultSplitBudget = 0xffffffffu;
 
 struct HashEntry {
   unsigned long long key;
@@ -69,6 +72,7 @@ struct EvalConsts {
   uint32_t n_rays, halton_offset;
   uint32_t perm_M, perm_Q, perm_R;   // coherent ray order (see ray_of_slot)
   uint32_t lg_segs;                  // each ray is marched as 2^lg_segs segments
+  uint32_t split_budget;             // block visits before unfinished pieces are split (~0: never)
   int w_mode, reduce_mode;
 };
 

@@ -188,15 +188,7 @@ __device__ __forceinline__ int block_radius(const DevMap& m, const uint32_t* rad
 // wins.  A voxel is entered only if N_a 2^24 <= R_fx |D_a|, i.e. N_a <= L_a.
 // Blocks without occupied voxels are crossed in one step of integer arithmetic that
 // reproduces the voxel-by-voxel crossings exactly (skip_box).
-constexpr int kSegContinues = 0;   // segment ended at its upper parameter bound
-
-struct SegOut {
-  int k[3];
-  uint32_t steps;           // steps from the ray's start voxel
-  uint32_t n_last, a_last;  // entry numerator / |D| of the last voxel (0/1 at the start)
-  int ax_last;              // axis of the last step (for map exits)
-  int status;               // RMP_RAY_* or kSegContinues
-};
+constexpr int kSegContinues = 0;   // piece ended at its upper parameter bound
 
 __device__ __forceinline__ int min_axis(const uint32_t n[3], const uint32_t a[3]) {
   const bool ylx = (unsigned long long)n[1] * a[0] < (unsigned long long)n[0] * a[1];
@@ -328,107 +320,146 @@ __device__ __forceinline__ bool skip_box(const DevMap& m, int k[3], const int s[
   return false;
 }
 
-// One segment of a ray.  A ray's parameter range (0, R], R = R_fx / 2^24, is split into S
-// = 2^lgS equal segments; segment `seg` handles the crossings with t in (T_seg, T_seg+1],
-// T_s = s R / S, so the S segments of a ray can be marched by S threads at once.  A
-// crossing numerator n of axis a (t = n / |D_a|) satisfies t <= T_s iff
-// n S 2^24 <= s R_fx |D_a|; the segment's start state (all crossings with t <= T_seg
-// applied) and its limits L_a follow from that in integer arithmetic.  Within a segment:
-// free boxes of blocks are crossed by skip_box, occupied blocks voxel by voxel with the brick
-// in registers and the order of the next crossings kept in the exact differences
-// E_ab = N_a |D_b| - N_b |D_a|.
-template <int KIND, int LAYOUT>
-__device__ __forceinline__ SegOut march_segment(const DevMap& m, const uint32_t* bm,
-                                                const long long P[3], const int D[3],
-                                                long long R_fx, uint32_t seg, uint32_t lgS) {
-  int k[3], s[3];
-  uint32_t N[3], A[3], L[3];
-  SegOut o;
-  o.steps = 0;
-  o.n_last = 0;
-  o.a_last = 1;
-  o.ax_last = 0;
-  const bool last_seg = seg == (1u << lgS) - 1;
-  uint32_t bn = 0, ba = 1;
-  bool any = false;
+// Pieces of a ray.  The parameter range (0, R], R = R_fx / 2^24 voxel units, is cut at
+// the points T_j = j R / 2^kGridLog (j = 0 .. 2^kGridLog); a piece covers (T_lo, T_hi]
+// between two of them.  A crossing numerator n of axis a (t = n / |D_a|) satisfies
+// t <= T_j iff n 2^(24 + kGridLog) <= j R_fx |D_a|, so a piece's start state (every
+// crossing with t <= T_lo applied) and its limits L_a (the crossings with t <= T_hi are
+// those with N_a <= L_a) are integer functions of j.  Pieces of one ray can be marched by
+// different threads at once; the ray's result is the first piece (in t) that hit or left
+// the map, else the last piece.  With R_fx <= 2^30 and |D_a| <= 2^24 every product stays
+// below 2^62.
+constexpr int kGridLog = 7;
+constexpr int kBudgetOut = 4;      // march_run: iteration budget spent, state resumable
+
+struct MarchState {
+  int k[3];
+  uint32_t N[3];
+  uint32_t steps;           // steps from the ray's start voxel
+  uint32_t n_last, a_last;  // entry numerator / |D| of the current voxel (0/1 at the start)
+  int ax_last;              // axis of the last step (for map exits)
+};
+
+// Per-ray fixed-point constants: step signs, |D_a| and the start voxel's boundary distances.
+struct RayFx {
+  int k0[3], s[3];
+  uint32_t A[3], N0[3];
+};
+
+__device__ __forceinline__ void ray_fx(const long long P[3], const int D[3], RayFx& r) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    k[a] = (int)(P[a] >> 16);
-    s[a] = D[a] > 0 ? 1 : -1;
-    A[a] = (uint32_t)abs(D[a]);
-    const long long lo = (long long)k[a] << 16;
-    N[a] = D[a] > 0 ? (uint32_t)(lo + 65536 - P[a]) : (D[a] < 0 ? (uint32_t)(P[a] - lo) : 1u);
-    L[a] = (uint32_t)(((unsigned long long)(seg + 1) * (unsigned long long)R_fx * A[a]) >> (24 + lgS));
-    if (seg > 0 && A[a] != 0) {
-      const unsigned long long X = (unsigned long long)seg * (unsigned long long)R_fx * A[a];
-      const unsigned long long Y = (unsigned long long)N[a] << (24 + lgS);
+    r.k0[a] = (int)(P[a] >> 16);
+    r.s[a] = D[a] > 0 ? 1 : -1;
+    r.A[a] = (uint32_t)abs(D[a]);
+    const long long lo = (long long)r.k0[a] << 16;
+    r.N0[a] = D[a] > 0 ? (uint32_t)(lo + 65536 - P[a]) : (D[a] < 0 ? (uint32_t)(P[a] - lo) : 1u);
+  }
+}
+
+__device__ __forceinline__ void limits_at(const RayFx& r, long long R_fx, uint32_t j, uint32_t L[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    L[a] = (uint32_t)(((unsigned long long)j * (unsigned long long)R_fx * r.A[a]) >> (24 + kGridLog));
+}
+
+// State after every crossing with t <= T_j: per axis the count of boundaries
+// N0_a + 2^16 m (m >= 0) within the bound; the entry of the current voxel is the latest of
+// the axes' last crossings.
+__device__ __forceinline__ void state_at(const RayFx& r, long long R_fx, uint32_t j, MarchState& st) {
+  uint32_t bn = 0, ba = 1;
+  bool any = false;
+  st.steps = 0;
+  st.ax_last = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    st.k[a] = r.k0[a];
+    st.N[a] = r.N0[a];
+    if (j > 0 && r.A[a] != 0) {
+      const unsigned long long X = (unsigned long long)j * (unsigned long long)R_fx * r.A[a];
+      const unsigned long long Y = (unsigned long long)r.N0[a] << (24 + kGridLog);
       if (X >= Y) {
-        const uint32_t cnt = (uint32_t)((X - Y) >> (40 + lgS)) + 1;
-        const uint32_t nl = N[a] + ((cnt - 1) << 16);
-        if (!any || (unsigned long long)nl * ba > (unsigned long long)bn * A[a]) {
+        const uint32_t cnt = (uint32_t)((X - Y) >> (40 + kGridLog)) + 1;
+        const uint32_t nl = r.N0[a] + ((cnt - 1) << 16);
+        if (!any || (unsigned long long)nl * ba > (unsigned long long)bn * r.A[a]) {
           bn = nl;
-          ba = A[a];
+          ba = r.A[a];
         }
         any = true;
-        k[a] += s[a] * (int)cnt;
-        N[a] += cnt << 16;
-        o.steps += cnt;
+        st.k[a] += r.s[a] * (int)cnt;
+        st.N[a] += cnt << 16;
+        st.steps += cnt;
       }
     }
   }
-  if (any) {
-    o.n_last = bn;
-    o.a_last = ba;
-  }
-  o.status = RMP_RAY_MISS_EXIT;
-  if (!outside<KIND>(m, k)) {
-    o.status = last_seg ? RMP_RAY_MISS_RANGE : kSegContinues;
-    // One loop, one unit of work per lane and iteration (a free-box crossing, entering an
-    // occupied block, or one voxel step inside it), so lanes in different phases of their
-    // rays share iterations instead of serialising nested loops.
+  st.n_last = any ? bn : 0;
+  st.a_last = any ? ba : 1;
+}
+
+// March a piece from state st until a hit, a map exit, the limits L (returns `at_limit`) or
+// `budget` block visits (returns kBudgetOut; st is then a state from which march_run
+// continues exactly).  Each visit of the outer loop either crosses a free box of blocks
+// (skip_box) or enters an occupied block, whose brick is held in registers while the inner
+// loop steps voxel by voxel, the order of the next crossings kept in the exact differences
+// E_ab = N_a |D_b| - N_b |D_a|.
+template <int KIND, int LAYOUT>
+__device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, MarchState& st,
+                                         const RayFx& r, const uint32_t L[3], int at_limit,
+                                         uint32_t budget) {
+  if (outside<KIND>(m, st.k)) return RMP_RAY_MISS_EXIT;
+  const uint32_t* A = r.A;
+  const int* s = r.s;
+  int* k = st.k;
+  uint32_t* N = st.N;
+  const float rA[3] = {__frcp_rn(__uint2float_rn(A[0])), __frcp_rn(__uint2float_rn(A[1])),
+                       __frcp_rn(__uint2float_rn(A[2]))};
+  const uint32_t guard = 8u * (kMaxRangeVoxels + 2);
+  const uint32_t iters = budget < guard ? budget : guard;
+  int status = budget < guard ? kBudgetOut : at_limit;
+  for (uint32_t it = 0; it < iters; ++it) {
+    const uint4* src = nullptr;
+    const int v = block_radius<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, &src);
+    if (v > 0) {
+      if (skip_box<KIND>(m, k, s, N, A, rA, L, v - 1, st.steps, st.n_last, st.a_last)) {
+        status = at_limit;
+        break;
+      }
+      if (outside<KIND>(m, k)) {
+        // only the exit axis can have left the grid
+        st.ax_last = ((unsigned)k[0] >= (unsigned)m.dims[0]) ? 0
+                     : (((unsigned)k[1] >= (unsigned)m.dims[1]) ? 1 : 2);
+        status = RMP_RAY_MISS_EXIT;
+        break;
+      }
+      continue;
+    }
     Brick w;
-    long long exy = 0, exz = 0, eyz = 0;
-    bool in_block = false;
-    const float rA[3] = {__frcp_rn(__uint2float_rn(A[0])), __frcp_rn(__uint2float_rn(A[1])),
-                         __frcp_rn(__uint2float_rn(A[2]))};
+    load_brick(src, w);
+    if (brick_bit(w, k[0], k[1], k[2])) {
+      status = RMP_RAY_HIT;
+      break;
+    }
+    // exact order of the next crossings: E_xy > 0 <=> t_y < t_x, etc.
+    long long exy = (long long)N[0] * A[1] - (long long)N[1] * A[0];
+    long long exz = (long long)N[0] * A[2] - (long long)N[2] * A[0];
+    long long eyz = (long long)N[1] * A[2] - (long long)N[2] * A[1];
     const long long u0 = (long long)A[0] << 16, u1 = (long long)A[1] << 16,
                     u2 = (long long)A[2] << 16;
-    for (uint32_t guard = 0; guard < 8u * (kMaxRangeVoxels + 2); ++guard) {
-      if (!in_block) {
-        const uint4* src = nullptr;
-        const int v = block_radius<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, &src);
-        if (v > 0) {
-          if (skip_box<KIND>(m, k, s, N, A, rA, L, v - 1, o.steps, o.n_last, o.a_last)) break;  // limit
-          if (outside<KIND>(m, k)) {
-            o.status = RMP_RAY_MISS_EXIT;
-            // only the exit axis can have left the grid
-            o.ax_last = ((unsigned)k[0] >= (unsigned)m.dims[0]) ? 0
-                        : (((unsigned)k[1] >= (unsigned)m.dims[1]) ? 1 : 2);
-            break;
-          }
-          continue;
-        }
-        load_brick(src, w);
-        if (brick_bit(w, k[0], k[1], k[2])) {
-          o.status = RMP_RAY_HIT;
-          break;
-        }
-        // exact order of the next crossings: E_xy > 0 <=> t_y < t_x, etc.
-        exy = (long long)N[0] * A[1] - (long long)N[1] * A[0];
-        exz = (long long)N[0] * A[2] - (long long)N[2] * A[0];
-        eyz = (long long)N[1] * A[2] - (long long)N[2] * A[1];
-        in_block = true;
-        continue;
-      }
+    int fin = 0;
+    // at most 21 interior steps and one exit step inside an 8^3 block
+    for (int j = 0; j < 24; ++j) {
       const bool ylx = exy > 0;
       const bool zlw = ylx ? (eyz > 0) : (exz > 0);
       const int ax = zlw ? 2 : (ylx ? 1 : 0);
       const uint32_t na = sel3(N, ax), aa = sel3(A, ax), la = sel3(L, ax);
-      if (na > la) break;                                // next crossing beyond the limit
-      o.n_last = na;
-      o.a_last = aa;
-      o.ax_last = ax;
-      o.steps += 1;
+      if (na > la) {                                   // next crossing beyond the limit
+        fin = 1;
+        break;
+      }
+      st.n_last = na;
+      st.a_last = aa;
+      st.ax_last = ax;
+      st.steps += 1;
       bool crossed = false;
       if (ax == 0) {
         const int kn = k[0] + s[0];
@@ -453,32 +484,137 @@ __device__ __forceinline__ SegOut march_segment(const DevMap& m, const uint32_t*
         eyz -= u1;
       }
       if (outside<KIND>(m, k)) {
-        o.status = RMP_RAY_MISS_EXIT;
+        fin = 2;
         break;
       }
-      if (crossed) {
-        in_block = false;
-        continue;
-      }
+      if (crossed) break;
       if (brick_bit(w, k[0], k[1], k[2])) {
-        o.status = RMP_RAY_HIT;
+        fin = 3;
         break;
       }
     }
+    if (fin) {
+      status = fin == 1 ? at_limit : (fin == 2 ? RMP_RAY_MISS_EXIT : RMP_RAY_HIT);
+      break;
+    }
   }
-  o.k[0] = k[0];
-  o.k[1] = k[1];
-  o.k[2] = k[2];
-  return o;
+  return status;
+}
+
+__device__ __forceinline__ bool piece_final(int status) {
+  return status == RMP_RAY_HIT || status == RMP_RAY_MISS_EXIT;
+}
+
+__device__ __forceinline__ void shfl_state(MarchState& d, const MarchState& st, int src) {
+  d.k[0] = __shfl_sync(0xffffffffu, st.k[0], src);
+  d.k[1] = __shfl_sync(0xffffffffu, st.k[1], src);
+  d.k[2] = __shfl_sync(0xffffffffu, st.k[2], src);
+  d.N[0] = __shfl_sync(0xffffffffu, st.N[0], src);
+  d.N[1] = __shfl_sync(0xffffffffu, st.N[1], src);
+  d.N[2] = __shfl_sync(0xffffffffu, st.N[2], src);
+  d.steps = __shfl_sync(0xffffffffu, st.steps, src);
+  d.n_last = __shfl_sync(0xffffffffu, st.n_last, src);
+  d.a_last = __shfl_sync(0xffffffffu, st.a_last, src);
+  d.ax_last = __shfl_sync(0xffffffffu, st.ax_last, src);
+}
+
+// Smallest j >= j_min with T_j >= t (t = n / a > 0 the current entry parameter):
+// n 2^(24 + kGridLog) <= j R_fx a.  FP32 estimate, then exact 64-bit corrections.
+__device__ __forceinline__ uint32_t grid_index_at_or_after(uint32_t n, uint32_t a, long long R_fx,
+                                                           uint32_t j_min) {
+  if (n == 0) return j_min;
+  const unsigned long long num = (unsigned long long)n << (24 + kGridLog);
+  const unsigned long long den = (unsigned long long)R_fx * a;
+  float e = __fdiv_rn(__ull2float_rn(num), __ull2float_rn(den));
+  uint32_t j = e < 0.0f ? 0u : (e > 129.0f ? 129u : (uint32_t)ceilf(e));
+  if ((unsigned long long)j * den < num) ++j;
+  if (j > 0 && (unsigned long long)(j - 1) * den >= num) --j;
+  return j > j_min ? j : j_min;
+}
+
+// Pieces that spent the first phase's budget are split over the warp's lanes: with u such
+// pieces each gets h = 32 / u lanes.  Piece p (the owner lane's remaining range (t, T_hi],
+// t its current entry parameter) is cut at grid points into up to h sub-pieces; the first
+// continues from the owner's state, the others start from state_at.  The sub-pieces' first
+// final result (else the last one's) becomes the owner's.  Both steps are
+// warp-synchronous: every lane calls them with the same `unfinished` mask.
+struct SplitPlan {
+  uint32_t h;       // lanes per unfinished piece
+  uint32_t p;       // this lane's rank among the unfinished lanes (if it owns one)
+  uint32_t hq;      // sub-pieces of this lane's own piece
+  bool mine;        // this lane owns an unfinished piece
+};
+
+// Number of sub-pieces of a piece whose remaining grid range is j0 .. j_hi.
+__device__ __forceinline__ uint32_t sub_pieces(uint32_t j0, uint32_t j_hi, uint32_t h) {
+  const uint32_t c = j_hi > j0 ? j_hi - j0 : 0u;
+  return c < h ? (c > 0 ? c : 1u) : h;
+}
+
+// Give this lane its sub-piece: on return (st, r, L, at_limit) describe it and the result
+// says whether the lane has one.
+__device__ __forceinline__ bool split_setup(long long R_fx, const long long P[3], int D[3],
+                                            uint32_t j_lo, uint32_t j_hi, int& at_limit,
+                                            uint32_t unfinished, MarchState& st, RayFx& r,
+                                            uint32_t L[3], SplitPlan& plan) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nu = __popc(unfinished);
+  const uint32_t h = 32u / nu;
+  plan.h = h;
+  plan.mine = (unfinished >> lane) & 1u;
+  plan.p = __popc(unfinished & ((1u << lane) - 1u));
+  plan.hq = plan.mine ? sub_pieces(grid_index_at_or_after(st.n_last, st.a_last, R_fx, j_lo), j_hi, h)
+                      : 1u;
+  // the piece this lane works on: group gi = lane / h, sub-piece q
+  const uint32_t gi = lane / h, q = lane - gi * h;
+  const bool in_grp = gi < nu;
+  const int owner = in_grp ? (int)(__fns(unfinished, 0, (int)gi + 1)) : (int)lane;
+  MarchState o;
+  shfl_state(o, st, owner);
+  D[0] = __shfl_sync(0xffffffffu, D[0], owner);
+  D[1] = __shfl_sync(0xffffffffu, D[1], owner);
+  D[2] = __shfl_sync(0xffffffffu, D[2], owner);
+  const uint32_t jl = __shfl_sync(0xffffffffu, j_lo, owner);
+  const uint32_t jh = __shfl_sync(0xffffffffu, j_hi, owner);
+  const int lim = __shfl_sync(0xffffffffu, at_limit, owner);
+  const uint32_t j0 = grid_index_at_or_after(o.n_last, o.a_last, R_fx, jl);
+  const uint32_t hq = sub_pieces(j0, jh, h);
+  if (!in_grp || q >= hq) return false;
+  ray_fx(P, D, r);
+  const uint32_t c = jh - j0;
+  const uint32_t b1 = q + 1 == hq ? jh : j0 + (c * (q + 1)) / hq;
+  if (q > 0) state_at(r, R_fx, j0 + (c * q) / hq, st);
+  else st = o;
+  limits_at(r, R_fx, b1, L);
+  at_limit = q + 1 == hq ? lim : kSegContinues;
+  return true;
+}
+
+// Move each split piece's result to its owner lane; the other lanes get back their own
+// result (own, own_status) from before the split.
+__device__ __forceinline__ void split_combine(const SplitPlan& plan, bool worked, MarchState& st,
+                                              int& status, const MarchState& own, int own_status) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t fin = __ballot_sync(0xffffffffu, worked && piece_final(status));
+  const uint32_t gmask = (plan.hq >= 32 ? 0xffffffffu : ((1u << plan.hq) - 1u)) << (plan.p * plan.h);
+  const uint32_t fb = fin & gmask;
+  const int src = !plan.mine ? (int)lane
+                             : (fb ? __ffs(fb) - 1 : (int)(plan.p * plan.h + plan.hq - 1));
+  MarchState res;
+  shfl_state(res, st, src);
+  const int rs = __shfl_sync(0xffffffffu, status, src);
+  st = plan.mine ? res : own;
+  status = plan.mine ? rs : own_status;
 }
 
 // Distinct 8^3 blocks whose occupancy the march tested: the voxel path is monotone on
 // each axis and blocks are convex, so this is 1 + the block changes along each axis up to
 // the last tested voxel (for a map exit the voxel before the exit step; none if the ray
 // starts outside the map).
-__device__ __forceinline__ uint32_t blocks_tested(const int k0[3], const SegOut& o, const int s[3]) {
+__device__ __forceinline__ uint32_t blocks_tested(const int k0[3], const MarchState& o, int status,
+                                                 const int s[3]) {
   int kf[3] = {o.k[0], o.k[1], o.k[2]};
-  if (o.status == RMP_RAY_MISS_EXIT) {
+  if (status == RMP_RAY_MISS_EXIT) {
     if (o.steps == 0) return 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -1031,35 +1167,54 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
     }
     first = false;
     const long long P[3] = {cs.P[0], cs.P[1], cs.P[2]};
-    SegOut so;
-    so.k[0] = so.k[1] = so.k[2] = 0;
-    so.steps = so.n_last = 0;
-    so.a_last = 1;
-    so.ax_last = 0;
-    so.status = kSegContinues;
-    if (active && !bad) so = march_segment<KIND, LAYOUT>(m, bm, P, ray.D, k.R_fx, seg, lgS);
+    // this lane's piece: segment seg of the ray, grid points j_lo .. j_hi
+    const uint32_t j_lo = seg << (kGridLog - lgS), j_hi = (seg + 1) << (kGridLog - lgS);
+    const int at_limit = seg == S - 1 ? RMP_RAY_MISS_RANGE : kSegContinues;
+    MarchState so;
+    int sstat = kSegContinues;
+    RayFx r;
+    uint32_t L[3];
+    int lim = at_limit;
+    int D[3] = {ray.D[0], ray.D[1], ray.D[2]};
+    ray_fx(P, D, r);
+    state_at(r, k.R_fx, j_lo, so);
+    limits_at(r, k.R_fx, j_hi, L);
+    bool work = active && !bad;
+    SplitPlan plan;
+    bool split = false;
+    MarchState own;
+    int own_stat = kSegContinues;
+    // phase 0 marches the lane's own piece for split_budget iterations; if pieces are still
+    // running then, phase 1 splits them over the warp and marches the sub-pieces
+    for (int phase = 0; phase < 2; ++phase) {
+      if (work)
+        sstat = march_run<KIND, LAYOUT>(m, bm, so, r, L, lim, phase == 0 ? k.split_budget : 0xffffffffu);
+      if (phase == 1) break;
+      const uint32_t unfinished = __ballot_sync(0xffffffffu, work && sstat == kBudgetOut);
+      if (!unfinished) break;
+      split = true;
+      own = so;
+      own_stat = sstat;
+      work = split_setup(k.R_fx, P, D, j_lo, j_hi, lim, unfinished, so, r, L, plan);
+      if (!work) sstat = kSegContinues;
+    }
+    if (split) split_combine(plan, work, so, sstat, own, own_stat);
     // combine the ray's segments into its first lane
-    const bool fin = active && (so.status == RMP_RAY_HIT || so.status == RMP_RAY_MISS_EXIT);
+    const bool fin = active && piece_final(sstat);
     const uint32_t ballot = __ballot_sync(0xffffffffu, fin);
     const uint32_t grp0 = lane & ~(S - 1);
     const uint32_t gmask = (S == 32 ? 0xffffffffu : ((1u << S) - 1u)) << grp0;
     const uint32_t fb = ballot & gmask;
     const int src = fb ? (__ffs(fb) - 1) : (int)(grp0 + S - 1);
-    SegOut mo;
-    mo.k[0] = __shfl_sync(0xffffffffu, so.k[0], src);
-    mo.k[1] = __shfl_sync(0xffffffffu, so.k[1], src);
-    mo.k[2] = __shfl_sync(0xffffffffu, so.k[2], src);
-    mo.steps = __shfl_sync(0xffffffffu, so.steps, src);
-    mo.n_last = __shfl_sync(0xffffffffu, so.n_last, src);
-    mo.a_last = __shfl_sync(0xffffffffu, so.a_last, src);
-    mo.ax_last = __shfl_sync(0xffffffffu, so.ax_last, src);
-    mo.status = __shfl_sync(0xffffffffu, so.status, src);
+    MarchState mo;
+    shfl_state(mo, so, src);
+    const int mstat = __shfl_sync(0xffffffffu, sstat, src);
     if (!active || bad || seg != 0) continue;
     const float d = mo.n_last == 0 ? 0.0f : entry_distance(mo.n_last, mo.a_last, m.vs_f);
     float f[3] = {0.f, 0.f, 0.f}, A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, af[3];
     const float v[3] = {cs.v[0], cs.v[1], cs.v[2]};
     const float vl[3] = {cs.vl[0], cs.vl[1], cs.vl[2]};
-    if (mo.status == RMP_RAY_HIT) {
+    if (mstat == RMP_RAY_HIT) {
       const bool act = active32(v, ray.dir);
       const bool inr = d < k.r_up;
       n_hit += 1;
@@ -1077,9 +1232,9 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
       h.voxel[2] = mo.k[2];
       h.steps = mo.steps;
       h.d = d;
-      h.status = (uint8_t)mo.status;
+      h.status = (uint8_t)mstat;
       h.pad = 0;
-      h.blocks = (uint16_t)blocks_tested(k0, mo, sg);
+      h.blocks = (uint16_t)blocks_tested(k0, mo, mstat, sg);
       hits[ray_idx] = h;
     }
     if (per_ray) {

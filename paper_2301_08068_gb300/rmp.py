@@ -28,7 +28,7 @@ RMP_RAY_HIT, RMP_RAY_MISS_RANGE, RMP_RAY_MISS_EXIT = 1, 2, 3
 RMP_MAP_DENSE_U8, RMP_MAP_HASHED_TSDF = 0, 1
 RMP_PRESET_STATIC_MAP, RMP_PRESET_LIDAR = 0, 1
 RMP_REDUCE_KAHAN32, RMP_REDUCE_FP64 = 0, 1
-RMP_TUNE_BLOCK, RMP_TUNE_LG_SEGMENTS = 1, 2
+RMP_TUNE_BLOCK, RMP_TUNE_LG_SEGMENTS, RMP_TUNE_RAY_ORDER, RMP_TUNE_SPLIT_BUDGET = 1, 2, 3, 4
 
 
 class RmpError(RuntimeError):

@@ -336,6 +336,35 @@ def test_layouts_grid_and_hash_fallback(ctx, hashed):
     assert a[1].tobytes() == b[1].tobytes()
 
 
+@pytest.mark.parametrize("order,budget,lgs", [(0, 1, 0), (0, 2, 2), (1, 3, 0), (1, 24, 1),
+                                               (0, 0, 0), (1, -1, -1), (0, 7, 1)])
+def test_split_and_ray_order_keep_results(ctx, hashed, dense, order, budget, lgs):
+    """Ray order and the warp split of long pieces (budgets down to one iteration, so that
+    nearly every warp splits, with and without static segments) leave hit records
+    bit-identical to the oracle's and values within tolerance, on the hashed map and on the
+    dense map, whose rays also leave the map."""
+    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_RAY_ORDER, order)
+    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_SPLIT_BUDGET, budget)
+    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, lgs)
+    try:
+        assert R.rmp_tune_get(ctx.handle, R.RMP_TUNE_SPLIT_BUDGET) == budget
+        assert R.rmp_tune_get(ctx.handle, R.RMP_TUNE_RAY_ORDER) == order
+        wl, mid, om = hashed
+        for s, n in ((wl.states[3], 65536), (wl.states[4], 777)):
+            check_raycast(ctx, mid, om, s.x, s.xdot, n, wl.params, wl.max_range)
+        wl, mid, om = dense
+        for s, n in ((wl.states[5], 4097), (wl.states[6], 1024)):
+            check_raycast(ctx, mid, om, s.x, s.xdot, n, wl.params, wl.max_range)
+    finally:
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_RAY_ORDER, 0)
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_SPLIT_BUDGET, -1)
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, -1)
+    for knob, bad in ((R.RMP_TUNE_RAY_ORDER, 2), (R.RMP_TUNE_SPLIT_BUDGET, -2),
+                      (R.RMP_TUNE_SPLIT_BUDGET, 65537)):
+        with pytest.raises(R.RmpError):
+            R.rmp_tune_set(ctx.handle, knob, bad)
+
+
 @pytest.mark.parametrize("block,lgs", [(64, 0), (128, 1), (256, 2), (128, -1)])
 def test_tuning_knobs_keep_results(ctx, hashed, block, lgs):
     """Block size and ray segmentation change the launch shape only: hit records stay
