@@ -335,7 +335,8 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "kernel": "raycast_rmp_kernel<HASHED_TSDF, KAHAN32>",
+                         "kernel": "raycast_rmp_kernel<hashed TSDF, grid layout, "
+                                   "compensated FP32 reduction>",
                          "kernel_source_sha256_16": src},
             "cpu_baseline": cpu,
             "gpu_launches": args.steps,

@@ -216,6 +216,58 @@ int rmp_scan_eval_async(rmp_ctx* ctx, const float* points_dev, uint32_t n,
                         void* workspace_dev, size_t workspace_bytes, rmp_stream_t stream,
                         rmp_result_t* out_dev, float* per_ray_dev);
 
+/* ------------------------------------------------------------------ batched evaluation
+ * Many independent evaluations in one launch: state b (x then xdot, 6 doubles at
+ * states_dev + 6 b) casts n_rays_dev[b] rays (Halton indices halton_offset ..
+ * halton_offset + n_b - 1, as rmp_raycast_eval) with the shared map and params; result b
+ * goes to out_dev[b], exactly what rmp_raycast_eval computes for that state up to the
+ * order of the floating-point reduction.  The paper evaluates one state per call; the
+ * batch is this library's throughput form of the same computation (candidate states of
+ * a planner, or many robots).  Work is cut into chunks of 32 threads that a persistent
+ * grid takes from a counter, so states of any ray counts share the device evenly.
+ *
+ * Capacity: n_states in [1, 65536]; every n_rays_dev[b] <= max_rays, max_rays +
+ * halton_offset <= 2^24.  A state with n_b > max_rays or an invalid position gets
+ * status RMP_ERR_INVALID_ARG in its result (the others are unaffected); n_b = 0 gives a
+ * zero result with status RMP_OK.  hits_dev / per_ray_dev (nullable): the records of
+ * state b start at index b * max_rays (same layout as rmp_raycast_eval per state); for a
+ * state with an error status they are not written. */
+
+/* Bytes of device workspace a batch of n_states states of at most max_rays rays needs
+ * (any tuning); 0 for out-of-range arguments.  No initialisation is needed: every launch
+ * resets what it uses. */
+size_t rmp_batch_workspace_bytes(uint32_t n_states, uint32_t max_rays);
+
+/* Enqueues two kernels on `stream` (per-state set-up, then the persistent evaluation);
+ * no host synchronisation and no allocation, so the call may be captured in a CUDA graph
+ * and the graph replayed with new contents of states_dev / n_rays_dev.  The workspace
+ * must not be shared by batches that may run concurrently. */
+int rmp_raycast_eval_batch_async(rmp_ctx* ctx, uint32_t map_id, const double* states_dev,
+                                 const uint32_t* n_rays_dev, uint32_t n_states,
+                                 uint32_t max_rays, const rmp_params_t* params,
+                                 void* workspace_dev, size_t workspace_bytes,
+                                 rmp_stream_t stream, rmp_result_t* out_dev,
+                                 rmp_ray_hit_t* hits_dev, float* per_ray_dev);
+
+/* Synchronous batch with host arrays (states: 6 n_states doubles, n_rays: n_states
+ * counts, out: n_states results); allocates and frees its device buffers. */
+int rmp_raycast_eval_batch(rmp_ctx* ctx, uint32_t map_id, const double* states,
+                           const uint32_t* n_rays, uint32_t n_states,
+                           const rmp_params_t* params, rmp_stream_t stream, rmp_result_t* out);
+
+/* Autotuner of the batch launch: times every combination of threads per CTA {64, 128,
+ * 256}, segments per ray 2^{0,1,2} (rays per thread 1, 1/2, 1/4) and warp split of long
+ * pieces {never, after 8 block visits} on this batch (one untimed launch, then the
+ * median of `reps` timed launches, CUDA events on `stream`; synchronises), and leaves
+ * the fastest in the context's knobs.  times_ms (nullable, n_times entries) receives
+ * the medians in the order block-major, then segments, then split.  The workspace must
+ * be sized for the batch (rmp_batch_workspace_bytes). */
+int rmp_batch_autotune(rmp_ctx* ctx, uint32_t map_id, const double* states_dev,
+                       const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
+                       const rmp_params_t* params, void* workspace_dev, size_t workspace_bytes,
+                       rmp_stream_t stream, rmp_result_t* out_dev, int reps, float* times_ms,
+                       int n_times);
+
 /* ------------------------------------------------------------------ launch tuning
  * Knobs of the evaluation kernels (per context; picked by the batch autotuner, settable by
  * hand).  They change the launch shape only: results are identical up to the order of

@@ -661,4 +661,155 @@ int rmp_scan_eval(rmp_ctx* c, const float* points_dev, uint32_t n, const double 
   return RMP_OK;
 }
 
+// ------------------------------------------------------------------ batched evaluation
+size_t rmp_batch_workspace_bytes(uint32_t n_states, uint32_t max_rays) {
+  if (n_states == 0 || n_states > kMaxBatchStates || max_rays == 0) return 0;
+  return batch_layout(n_states, max_rays).total;
+}
+
+namespace {
+
+// Constants and launch shape of a batch; grid = every CTA that fits on the device at once.
+int batch_setup(rmp_ctx* c, uint32_t map_id, uint32_t n_states, uint32_t max_rays,
+                const rmp_params_t* params, DevMap* dm, EvalConsts* k, int* block, int* grid) {
+  if (n_states == 0 || n_states > kMaxBatchStates || max_rays == 0) return RMP_ERR_INVALID_ARG;
+  Tuning t;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->maps.find(map_id);
+    if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
+    *dm = it->second.dm;
+    t = tuning_of(c);
+    *block = c->tune_block;
+  }
+  int st = make_consts(params, dm->vs, max_rays, false, k, t);
+  if (st != RMP_OK) return st;
+  // many states fill the device without segmenting rays; one state uses the single-state rule
+  if (t.lg_segs < 0 && n_states > 1) k->lg_segs = 0;
+  const int occ = batch_occupancy(*dm, k->reduce_mode, *block);
+  if (occ <= 0) return RMP_ERR_CUDA;
+  *grid = c->sm_count * occ;
+  return RMP_OK;
+}
+
+}  // namespace
+
+int rmp_raycast_eval_batch_async(rmp_ctx* c, uint32_t map_id, const double* states_dev,
+                                 const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
+                                 const rmp_params_t* params, void* ws, size_t ws_bytes,
+                                 rmp_stream_t stream, rmp_result_t* out_dev,
+                                 rmp_ray_hit_t* hits_dev, float* per_ray_dev) {
+  if (!c || !states_dev || !n_rays_dev || !ws || !out_dev) return RMP_ERR_INVALID_ARG;
+  if (n_states == 0 || n_states > kMaxBatchStates || max_rays == 0 ||
+      ws_bytes < batch_layout(n_states, max_rays).total)
+    return RMP_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  DevMap dm;
+  EvalConsts k;
+  int block, grid;
+  int st = batch_setup(c, map_id, n_states, max_rays, params, &dm, &k, &block, &grid);
+  if (st != RMP_OK) return st;
+  RMP_CUDA(launch_batch(dm, k, states_dev, n_rays_dev, n_states, max_rays, ws, out_dev, hits_dev,
+                        per_ray_dev, block, grid, (cudaStream_t)stream));
+  return RMP_OK;
+}
+
+int rmp_raycast_eval_batch(rmp_ctx* c, uint32_t map_id, const double* states, const uint32_t* n_rays,
+                           uint32_t n_states, const rmp_params_t* params, rmp_stream_t stream,
+                           rmp_result_t* out) {
+  if (!c || !states || !n_rays || !out || n_states == 0 || n_states > kMaxBatchStates)
+    return RMP_ERR_INVALID_ARG;
+  uint32_t max_rays = 1;
+  for (uint32_t b = 0; b < n_states; ++b) max_rays = n_rays[b] > max_rays ? n_rays[b] : max_rays;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  const size_t wsb = batch_layout(n_states, max_rays).total;
+  const size_t sb = 6 * sizeof(double) * n_states, nb = 4 * (size_t)n_states,
+               ob = sizeof(rmp_result_t) * n_states;
+  char* buf = nullptr;
+  const size_t o_states = 0, o_n = align256(sb), o_out = o_n + align256(nb),
+               o_ws = o_out + align256(ob);
+  cudaError_t e = cudaMalloc((void**)&buf, o_ws + wsb);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = RMP_OK;
+  e = cudaMemcpyAsync(buf + o_states, states, sb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf + o_n, n_rays, nb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    st = rmp_raycast_eval_batch_async(c, map_id, (const double*)(buf + o_states),
+                                      (const uint32_t*)(buf + o_n), n_states, max_rays, params,
+                                      buf + o_ws, wsb, stream, (rmp_result_t*)(buf + o_out),
+                                      nullptr, nullptr);
+  }
+  if (e == cudaSuccess && st == RMP_OK)
+    e = cudaMemcpyAsync(out, buf + o_out, ob, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(buf);
+  if (st != RMP_OK) return st;
+  return e == cudaSuccess ? RMP_OK : cuda_status(e);
+}
+
+int rmp_batch_autotune(rmp_ctx* c, uint32_t map_id, const double* states_dev,
+                       const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
+                       const rmp_params_t* params, void* ws, size_t ws_bytes, rmp_stream_t stream,
+                       rmp_result_t* out_dev, int reps, float* times_ms, int n_times) {
+  if (!c || reps < 1 || reps > 1000) return RMP_ERR_INVALID_ARG;
+  static const int kBlocks[3] = {64, 128, 256};
+  static const int kSplits[2] = {0, 8};
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RMP_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return RMP_ERR_CUDA;
+  }
+  float best = 3.0e38f;
+  int best_b = 128, best_l = 0, best_s = 0, idx = 0, st = RMP_OK;
+  for (int bi = 0; bi < 3 && st == RMP_OK; ++bi)
+    for (int l = 0; l <= 2 && st == RMP_OK; ++l)
+      for (int si = 0; si < 2 && st == RMP_OK; ++si, ++idx) {
+        {
+          std::lock_guard<std::mutex> lk(c->mu);
+          c->tune_block = kBlocks[bi];
+          c->tune_lg_segs = l;
+          c->tune_split = kSplits[si];
+        }
+        // one untimed launch, then the median of `reps` timed ones
+        st = rmp_raycast_eval_batch_async(c, map_id, states_dev, n_rays_dev, n_states, max_rays,
+                                          params, ws, ws_bytes, stream, out_dev, nullptr, nullptr);
+        float t[1000];
+        for (int r = 0; r < reps && st == RMP_OK; ++r) {
+          if (cudaEventRecord(e0, s) != cudaSuccess) st = RMP_ERR_CUDA;
+          if (st == RMP_OK)
+            st = rmp_raycast_eval_batch_async(c, map_id, states_dev, n_rays_dev, n_states,
+                                              max_rays, params, ws, ws_bytes, stream, out_dev,
+                                              nullptr, nullptr);
+          if (st == RMP_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                               cudaEventSynchronize(e1) != cudaSuccess ||
+                               cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess))
+            st = RMP_ERR_CUDA;
+        }
+        if (st != RMP_OK) break;
+        std::sort(t, t + reps);
+        const float med = t[reps / 2];
+        if (times_ms && idx < n_times) times_ms[idx] = med;
+        if (med < best) {
+          best = med;
+          best_b = kBlocks[bi];
+          best_l = l;
+          best_s = kSplits[si];
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->tune_block = best_b;
+  c->tune_lg_segs = best_l;
+  c->tune_split = best_s;
+  return st;
+}
+
 }  // extern "C"

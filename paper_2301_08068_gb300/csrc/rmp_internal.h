@@ -94,6 +94,51 @@ inline size_t workspace_bytes() {
   return kWsHeaderBytes + sizeof(CtaPartial) * (size_t)(kMaxGrid + kMaxGroups);
 }
 
+// ------------------------------------------------------------------ batched evaluation
+// Work of a batch is cut into chunks of 32 threads (32 / S rays of one state, S segments
+// per ray) that the warps of a persistent grid take from a counter.  Each chunk stores a
+// partial; kBatchGroup consecutive chunks of a state form a group (the last chunk of a
+// group to finish sums them), and the last group of a state sums the groups and resolves.
+constexpr uint32_t kBatchGroup = 32;
+constexpr uint32_t kMaxBatchStates = 1u << 16;
+constexpr uint32_t kMaxBatchSegs = 4;        // workspace is sized for up to 4 segments per ray
+
+struct BatchState {         // 80 bytes, written by the prep kernel
+  long long P[3];           // quantised position (2^-16 voxels)
+  float v[3], vl[3];        // velocity as an FP32 pair
+  uint32_t n_rays, chunk0, n_chunks, group0;
+  uint32_t perm_M, perm_Q, perm_R;
+  int status;               // RMP_OK or RMP_ERR_INVALID_ARG
+};
+
+struct BatchHeader {        // 128 bytes
+  uint32_t next_chunk;      // work counter of the persistent grid
+  uint32_t total_chunks;
+  uint32_t n_states;
+  uint32_t pad[29];
+};
+
+struct BatchLayout {
+  size_t states, sticket, gticket, cparts, gparts, total;
+  uint64_t chunks_per_state, groups_per_state;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+inline BatchLayout batch_layout(uint32_t n_states, uint32_t max_rays) {
+  BatchLayout L;
+  L.chunks_per_state = ((uint64_t)max_rays * kMaxBatchSegs + 31) / 32;
+  L.groups_per_state = (L.chunks_per_state + kBatchGroup - 1) / kBatchGroup;
+  const uint64_t n = n_states;
+  L.states = align256(sizeof(BatchHeader));
+  L.sticket = align256(L.states + sizeof(BatchState) * n);
+  L.gticket = align256(L.sticket + 4 * n);
+  L.cparts = align256(L.gticket + 4 * n * L.groups_per_state);
+  L.gparts = align256(L.cparts + sizeof(CtaPartial) * n * L.chunks_per_state);
+  L.total = align256(L.gparts + sizeof(CtaPartial) * n * L.groups_per_state);
+  return L;
+}
+
 inline unsigned long long pack_key(int bx, int by, int bz) {
   return (unsigned long long)(uint32_t)(bx + kKeyBias) |
          ((unsigned long long)(uint32_t)(by + kKeyBias) << 21) |
@@ -106,6 +151,12 @@ int raycast_occupancy(const DevMap& m, int reduce_mode, int block);   // CTAs pe
 cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,
                            void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
                            float* per_ray, int block, int grid, cudaStream_t stream);
+int batch_occupancy(const DevMap& m, int reduce_mode, int block);     // CTAs per SM
+// Prep kernel + persistent batch kernel; n_rays_dev / states_dev on the device.
+cudaError_t launch_batch(const DevMap& m, const EvalConsts& k, const double* states_dev,
+                         const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
+                         void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits, float* per_ray,
+                         int block, int grid, cudaStream_t stream);
 cudaError_t launch_scan(const float* pts, const EvalConsts& k, const double* state_dev,
                         void* ws, rmp_result_t* out_dev, float* per_ray, int block, int grid,
                         cudaStream_t stream);

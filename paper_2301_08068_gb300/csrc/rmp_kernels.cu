@@ -819,27 +819,26 @@ __device__ __forceinline__ unsigned block_sum_u32(unsigned v) {
 // ------------------------------------------------------------------ FP64 resolve (Eq. 1)
 // f = (sum A)^+ (sum A f) with eigenvalues <= 1e-12 lambda_max treated as zero.  FP64
 // division and square root cost hundreds of cycles each on this GPU and FP64 issues at a
-// low rate, so the work is split over three threads of the finishing CTA:
-//   thread 0: eigenvectors by cyclic Jacobi rotations in FP32 (matrix scaled by a power of
-//             two); thread 1, meanwhile: the FP64 adjugate solve adj(S) b / det(S);
-//   threads 0-2: each eigenvalue as the FP64 Rayleigh quotient v^T S v / v^T v of its FP32
-//             eigenvector (second-order accurate, ~1e-14 lambda_max), with
-//             1 / v^T v = 2 - v^T v to first order (v^T v = 1 + O(1e-7));
-//   thread 0: rank from the eigenvalues; full rank uses the adjugate solution, a deficient
-//             rank projects b on the kept eigenvectors.
-// Called by every thread of the CTA.
+// low rate, so the work is split over three lanes of one warp:
+//   lane 0: eigenvectors by cyclic Jacobi rotations in FP32 (matrix scaled by a power of
+//           two); lane 1, meanwhile: the FP64 adjugate solve adj(S) b / det(S);
+//   lanes 0-2: each eigenvalue as the FP64 Rayleigh quotient v^T S v / v^T v of its FP32
+//           eigenvector (second-order accurate, ~1e-14 lambda_max), with
+//           1 / v^T v = 2 - v^T v to first order (v^T v = 1 + O(1e-7));
+//   lane 0: rank from the eigenvalues; full rank uses the adjugate solution, a deficient
+//           rank projects b on the kept eigenvectors, and writes f, eig, rank into r.
+// Called by all 32 lanes of one warp.
 __device__ void resolve_pinv(const double* S, const double* b, rmp_result_t& r) {
-  __shared__ float V[3][3];
-  __shared__ double lam[3], den[3], fadj[3];
-  __shared__ int adj_ok;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x & 31;
+  float W[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+  double fa0 = 0.0, fa1 = 0.0, fa2 = 0.0;
+  int ok = 0;
   if (t == 0) {
     const double smax = fmax(fmax(fabs(S[0]), fabs(S[1])), fmax(fmax(fabs(S[2]), fabs(S[3])),
                                                                fmax(fabs(S[4]), fabs(S[5]))));
     const double scale = smax > 1e-300 ? ldexp(1.0, -ilogb(smax)) : 1.0;   // power of two
     float a00 = (float)(S[0] * scale), a01 = (float)(S[1] * scale), a02 = (float)(S[2] * scale),
           a11 = (float)(S[3] * scale), a12 = (float)(S[4] * scale), a22 = (float)(S[5] * scale);
-    float W[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
     for (int sweep = 0; sweep < 6; ++sweep) {
       const float off = fabsf(a01) + fabsf(a02) + fabsf(a12);
       const float dia = fabsf(a00) + fabsf(a11) + fabsf(a22);
@@ -870,34 +869,45 @@ __device__ void resolve_pinv(const double* S, const double* b, rmp_result_t& r) 
         }
       }
     }
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) V[i][j] = W[i][j];
   } else if (t == 1) {
     const double c00 = S[3] * S[5] - S[4] * S[4], c01 = S[2] * S[4] - S[1] * S[5],
                  c02 = S[1] * S[4] - S[2] * S[3], c11 = S[0] * S[5] - S[2] * S[2],
                  c12 = S[1] * S[2] - S[0] * S[4], c22 = S[0] * S[3] - S[1] * S[1];
     const double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
-    adj_ok = det > 0.0;
+    ok = det > 0.0;
     if (det > 0.0) {
       const double inv = 1.0 / det;
-      fadj[0] = (c00 * b[0] + c01 * b[1] + c02 * b[2]) * inv;
-      fadj[1] = (c01 * b[0] + c11 * b[1] + c12 * b[2]) * inv;
-      fadj[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
+      fa0 = (c00 * b[0] + c01 * b[1] + c02 * b[2]) * inv;
+      fa1 = (c01 * b[0] + c11 * b[1] + c12 * b[2]) * inv;
+      fa2 = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
     }
   }
-  __syncthreads();
+  float V[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) V[i][j] = __shfl_sync(0xffffffffu, W[i][j], 0);
+  fa0 = __shfl_sync(0xffffffffu, fa0, 1);
+  fa1 = __shfl_sync(0xffffffffu, fa1, 1);
+  fa2 = __shfl_sync(0xffffffffu, fa2, 1);
+  ok = __shfl_sync(0xffffffffu, ok, 1);
+  double lam_t = 0.0, den_t = 0.0;
   if (t < 3) {
-    const double v0 = V[0][t], v1 = V[1][t], v2 = V[2][t];
+    const double v0 = t == 0 ? V[0][0] : (t == 1 ? V[0][1] : V[0][2]);
+    const double v1 = t == 0 ? V[1][0] : (t == 1 ? V[1][1] : V[1][2]);
+    const double v2 = t == 0 ? V[2][0] : (t == 1 ? V[2][1] : V[2][2]);
     const double u0 = S[0] * v0 + S[1] * v1 + S[2] * v2;
     const double u1 = S[1] * v0 + S[3] * v1 + S[4] * v2;
     const double u2 = S[2] * v0 + S[4] * v1 + S[5] * v2;
-    const double dn = v0 * v0 + v1 * v1 + v2 * v2;
-    den[t] = dn;
-    lam[t] = (v0 * u0 + v1 * u1 + v2 * u2) * (2.0 - dn);
+    den_t = v0 * v0 + v1 * v1 + v2 * v2;
+    lam_t = (v0 * u0 + v1 * u1 + v2 * u2) * (2.0 - den_t);
   }
-  __syncthreads();
+  double lam[3], den[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    lam[i] = __shfl_sync(0xffffffffu, lam_t, i);
+    den[i] = __shfl_sync(0xffffffffu, den_t, i);
+  }
   if (t != 0) return;
   int idx[3] = {0, 1, 2};
   if (lam[idx[1]] < lam[idx[0]]) { int u = idx[0]; idx[0] = idx[1]; idx[1] = u; }
@@ -914,10 +924,10 @@ __device__ void resolve_pinv(const double* S, const double* b, rmp_result_t& r) 
   }
   r.rank = rank;
   r.f[0] = r.f[1] = r.f[2] = 0.0;
-  if (rank == 3 && adj_ok) {
-    r.f[0] = fadj[0];
-    r.f[1] = fadj[1];
-    r.f[2] = fadj[2];
+  if (rank == 3 && ok) {
+    r.f[0] = fa0;
+    r.f[1] = fa1;
+    r.f[2] = fa2;
     return;
   }
 #pragma unroll
@@ -1021,7 +1031,7 @@ __device__ void grid_finish(const double part[9], unsigned hits, unsigned act, W
     r.reserved = 0;
   }
   __syncthreads();
-  resolve_pinv(r.A, r.Af, r);
+  if (threadIdx.x < 32) resolve_pinv(r.A, r.Af, r);
   if (threadIdx.x == 0) {
     *out = r;
     ws->ticket = 0;                   // ready for the next evaluation
@@ -1106,6 +1116,101 @@ __device__ __forceinline__ bool bulk_load_wait(uint64_t* bar) {
   return false;
 }
 
+// ------------------------------------------------------------------ per-ray march and outputs
+// One thread's segment `seg` (of S = 2^lg_segs) of the ray `ray` from position P: march the
+// piece (phase 0: split_budget block visits; pieces still running are then split over the
+// warp and finished, phase 1), then combine the ray's S segments -- adjacent lanes -- into
+// the first final one (lowest index), else the last one.  Warp-synchronous: every lane of
+// the warp calls it (work = false for lanes without a segment).  Returns the ray's status;
+// mo is its final state (valid in every lane of the ray's segment group).
+template <int KIND, int LAYOUT>
+__device__ __forceinline__ int march_ray(const DevMap& m, const uint32_t* bm, const EvalConsts& k,
+                                         const long long P[3], const Ray& ray, uint32_t seg,
+                                         bool work, MarchState& mo) {
+  const uint32_t lgS = k.lg_segs, S = 1u << lgS;
+  const uint32_t lane = threadIdx.x & 31;
+  // this lane's piece: segment seg of the ray, grid points j_lo .. j_hi
+  const uint32_t j_lo = seg << (kGridLog - lgS), j_hi = (seg + 1) << (kGridLog - lgS);
+  const int at_limit = seg == S - 1 ? RMP_RAY_MISS_RANGE : kSegContinues;
+  MarchState so;
+  int sstat = kSegContinues;
+  RayFx r;
+  uint32_t L[3];
+  int lim = at_limit;
+  int D[3] = {ray.D[0], ray.D[1], ray.D[2]};
+  ray_fx(P, D, r);
+  state_at(r, k.R_fx, j_lo, so);
+  limits_at(r, k.R_fx, j_hi, L);
+  const bool work0 = work;
+  SplitPlan plan;
+  bool split = false;
+  MarchState own;
+  int own_stat = kSegContinues;
+  for (int phase = 0; phase < 2; ++phase) {
+    if (work)
+      sstat = march_run<KIND, LAYOUT>(m, bm, so, r, L, lim, phase == 0 ? k.split_budget : 0xffffffffu);
+    if (phase == 1) break;
+    const uint32_t unfinished = __ballot_sync(0xffffffffu, work && sstat == kBudgetOut);
+    if (!unfinished) break;
+    split = true;
+    own = so;
+    own_stat = sstat;
+    work = split_setup(k.R_fx, P, D, j_lo, j_hi, lim, unfinished, so, r, L, plan);
+    if (!work) sstat = kSegContinues;
+  }
+  if (split) split_combine(plan, work, so, sstat, own, own_stat);
+  const bool fin = work0 && piece_final(sstat);
+  const uint32_t ballot = __ballot_sync(0xffffffffu, fin);
+  const uint32_t grp0 = lane & ~(S - 1);
+  const uint32_t gmask = (S == 32 ? 0xffffffffu : ((1u << S) - 1u)) << grp0;
+  const uint32_t fb = ballot & gmask;
+  const int src = fb ? (__ffs(fb) - 1) : (int)(grp0 + S - 1);
+  shfl_state(mo, so, src);
+  return __shfl_sync(0xffffffffu, sstat, src);
+}
+
+// The ray's obstacle policy (Sec. III-C) from its final state: vals = A_i (6) and A_i f_i
+// (3), all zero unless it hit; counts hits and active rays; writes the optional hit record
+// and per-ray (f_i, A_i).
+__device__ __forceinline__ void ray_outputs(const DevMap& m, const EvalConsts& k,
+                                            const long long P[3], const Ray& ray,
+                                            const MarchState& mo, int mstat, const float v[3],
+                                            const float vl[3], rmp_ray_hit_t* hit, float* per,
+                                            float vals[9], unsigned& n_hit, unsigned& n_act) {
+  const float d = mo.n_last == 0 ? 0.0f : entry_distance(mo.n_last, mo.a_last, m.vs_f);
+  float f[3] = {0.f, 0.f, 0.f}, A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, af[3] = {0.f, 0.f, 0.f};
+  if (mstat == RMP_RAY_HIT) {
+    const bool act = active32(v, ray.dir);
+    const bool inr = d < k.r_up;
+    n_hit += 1;
+    n_act += (act && inr) ? 1u : 0u;
+    obstacle_policy(k, ray.dir, d, v, vl, act, inr, f, A, af);
+  }
+#pragma unroll
+  for (int q = 0; q < 6; ++q) vals[q] = A[q];
+  vals[6] = af[0];
+  vals[7] = af[1];
+  vals[8] = af[2];
+  if (hit) {
+    const int k0[3] = {(int)(P[0] >> 16), (int)(P[1] >> 16), (int)(P[2] >> 16)};
+    const int sg[3] = {ray.D[0] > 0 ? 1 : -1, ray.D[1] > 0 ? 1 : -1, ray.D[2] > 0 ? 1 : -1};
+    rmp_ray_hit_t h;
+    h.voxel[0] = mo.k[0];
+    h.voxel[1] = mo.k[1];
+    h.voxel[2] = mo.k[2];
+    h.steps = mo.steps;
+    h.d = d;
+    h.status = (uint8_t)mstat;
+    h.pad = 0;
+    h.blocks = (uint16_t)blocks_tested(k0, mo, mstat, sg);
+    *hit = h;
+  }
+  if (per) {
+    per[0] = f[0]; per[1] = f[1]; per[2] = f[2];
+    per[3] = A[0]; per[4] = A[1]; per[5] = A[2]; per[6] = A[3]; per[7] = A[4]; per[8] = A[5];
+  }
+}
+
 // ------------------------------------------------------------------ fused raycast kernel
 // Thread g of the launch handles segment g % S of the ray in slot g / S; the S segments of a
 // ray sit in adjacent lanes, and the ray's result is the first segment (lowest index) that
@@ -1167,81 +1272,13 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
     }
     first = false;
     const long long P[3] = {cs.P[0], cs.P[1], cs.P[2]};
-    // this lane's piece: segment seg of the ray, grid points j_lo .. j_hi
-    const uint32_t j_lo = seg << (kGridLog - lgS), j_hi = (seg + 1) << (kGridLog - lgS);
-    const int at_limit = seg == S - 1 ? RMP_RAY_MISS_RANGE : kSegContinues;
-    MarchState so;
-    int sstat = kSegContinues;
-    RayFx r;
-    uint32_t L[3];
-    int lim = at_limit;
-    int D[3] = {ray.D[0], ray.D[1], ray.D[2]};
-    ray_fx(P, D, r);
-    state_at(r, k.R_fx, j_lo, so);
-    limits_at(r, k.R_fx, j_hi, L);
-    bool work = active && !bad;
-    SplitPlan plan;
-    bool split = false;
-    MarchState own;
-    int own_stat = kSegContinues;
-    // phase 0 marches the lane's own piece for split_budget iterations; if pieces are still
-    // running then, phase 1 splits them over the warp and marches the sub-pieces
-    for (int phase = 0; phase < 2; ++phase) {
-      if (work)
-        sstat = march_run<KIND, LAYOUT>(m, bm, so, r, L, lim, phase == 0 ? k.split_budget : 0xffffffffu);
-      if (phase == 1) break;
-      const uint32_t unfinished = __ballot_sync(0xffffffffu, work && sstat == kBudgetOut);
-      if (!unfinished) break;
-      split = true;
-      own = so;
-      own_stat = sstat;
-      work = split_setup(k.R_fx, P, D, j_lo, j_hi, lim, unfinished, so, r, L, plan);
-      if (!work) sstat = kSegContinues;
-    }
-    if (split) split_combine(plan, work, so, sstat, own, own_stat);
-    // combine the ray's segments into its first lane
-    const bool fin = active && piece_final(sstat);
-    const uint32_t ballot = __ballot_sync(0xffffffffu, fin);
-    const uint32_t grp0 = lane & ~(S - 1);
-    const uint32_t gmask = (S == 32 ? 0xffffffffu : ((1u << S) - 1u)) << grp0;
-    const uint32_t fb = ballot & gmask;
-    const int src = fb ? (__ffs(fb) - 1) : (int)(grp0 + S - 1);
     MarchState mo;
-    shfl_state(mo, so, src);
-    const int mstat = __shfl_sync(0xffffffffu, sstat, src);
+    const int mstat = march_ray<KIND, LAYOUT>(m, bm, k, P, ray, seg, active && !bad, mo);
     if (!active || bad || seg != 0) continue;
-    const float d = mo.n_last == 0 ? 0.0f : entry_distance(mo.n_last, mo.a_last, m.vs_f);
-    float f[3] = {0.f, 0.f, 0.f}, A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, af[3];
-    const float v[3] = {cs.v[0], cs.v[1], cs.v[2]};
-    const float vl[3] = {cs.vl[0], cs.vl[1], cs.vl[2]};
-    if (mstat == RMP_RAY_HIT) {
-      const bool act = active32(v, ray.dir);
-      const bool inr = d < k.r_up;
-      n_hit += 1;
-      n_act += (act && inr) ? 1u : 0u;
-      obstacle_policy(k, ray.dir, d, v, vl, act, inr, f, A, af);
-      const float vals[9] = {A[0], A[1], A[2], A[3], A[4], A[5], af[0], af[1], af[2]};
-      BlockReduce<RED>::add(acc, vals);
-    }
-    if (hits) {
-      const int k0[3] = {(int)(P[0] >> 16), (int)(P[1] >> 16), (int)(P[2] >> 16)};
-      const int sg[3] = {ray.D[0] > 0 ? 1 : -1, ray.D[1] > 0 ? 1 : -1, ray.D[2] > 0 ? 1 : -1};
-      rmp_ray_hit_t h;
-      h.voxel[0] = mo.k[0];
-      h.voxel[1] = mo.k[1];
-      h.voxel[2] = mo.k[2];
-      h.steps = mo.steps;
-      h.d = d;
-      h.status = (uint8_t)mstat;
-      h.pad = 0;
-      h.blocks = (uint16_t)blocks_tested(k0, mo, mstat, sg);
-      hits[ray_idx] = h;
-    }
-    if (per_ray) {
-      float* o = per_ray + 9 * (size_t)ray_idx;
-      o[0] = f[0]; o[1] = f[1]; o[2] = f[2];
-      o[3] = A[0]; o[4] = A[1]; o[5] = A[2]; o[6] = A[3]; o[7] = A[4]; o[8] = A[5];
-    }
+    float vals[9];
+    ray_outputs(m, k, P, ray, mo, mstat, cs.v, cs.vl, hits ? hits + ray_idx : nullptr,
+                per_ray ? per_ray + 9 * (size_t)ray_idx : nullptr, vals, n_hit, n_act);
+    if (mstat == RMP_RAY_HIT) BlockReduce<RED>::add(acc, vals);
   }
   if (staged && bm_timeout) bulk_load_wait(&bm_bar);   // let a late copy land before exit
   double part[9];
@@ -1251,6 +1288,352 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
   const int status = bm_timeout ? RMP_ERR_TIMEOUT
                      : ((cs.bad[0] | cs.bad[1] | cs.bad[2]) ? RMP_ERR_INVALID_ARG : RMP_OK);
   grid_finish(part, bh, ba, ws, parts, out, k.n_rays, status);
+}
+
+// ------------------------------------------------------------------ batched evaluation
+// Device form of the host's direction-cell choice: M = 2^a 3^b <= n / 32 minimising
+// |log M - log(n / 48)| + 0.5 |log(3^b / (pi 2^a))| (cells close to square on the
+// sphere).  The score is piecewise linear in b with its steeper kink where M = n / 48,
+// so for each a only the b next to that kink, b = 0 and the largest b allowed by the
+// bound need checking.  Only the work schedule and the summation grouping depend on it.
+__device__ __forceinline__ uint32_t pick_cells_dev(uint32_t n) {
+  const float L3 = 1.5849625f, LPI = 1.6514961f;   // log2(3), log2(pi)
+  const float lt = __log2f(fmaxf((float)n * (1.0f / 48.0f), 1.0f));
+  const float lm = __log2f((float)n * (1.0f / 32.0f));
+  uint32_t best = 1;
+  float best_score = 3.0e38f;
+  for (int a = 0; a <= 24; ++a) {
+    if ((32ull << a) > n) break;
+    const int bk = (int)floorf(((lt - (float)a) / L3));
+    const int bm = (int)floorf(((lm - (float)a) / L3)) + 1;
+    const int cand[4] = {0, bk, bk + 1, bm};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int bb = cand[i] < 0 ? 0 : (cand[i] > 15 ? 15 : cand[i]);
+      unsigned long long mm = 1ull << a;
+      for (int j = 0; j < bb; ++j) mm *= 3ull;
+      while (bb > 0 && mm * 32ull > n) {          // largest feasible b <= the candidate
+        mm /= 3ull;
+        --bb;
+      }
+      if (mm * 32ull > n) continue;
+      const float score = fabsf((float)a + (float)bb * L3 - lt) +
+                          0.5f * fabsf((float)bb * L3 - LPI - (float)a);
+      if (score < best_score) {
+        best_score = score;
+        best = (uint32_t)mm;
+      }
+    }
+  }
+  return best;
+}
+
+__device__ __forceinline__ uint32_t ray_of_slot_p(uint32_t j, uint32_t M, uint32_t Q, uint32_t R) {
+  const uint32_t big = R * (Q + 1);
+  uint32_t r, q;
+  if (j < big) {
+    r = j / (Q + 1);
+    q = j - r * (Q + 1);
+  } else {
+    const uint32_t jj = j - big;
+    const uint32_t t = jj / Q;
+    r = R + t;
+    q = jj - t * Q;
+  }
+  return r + M * q;
+}
+
+// Per-state set-up of a batch (one CTA of 1024 threads): validates each ray count,
+// quantises the position, splits the velocity, counts chunks and groups, assigns them
+// consecutive index ranges (block-wide exclusive scans), clears the tickets and the work
+// counter, and writes the result of every state that has no chunks (no rays, or invalid).
+__global__ void __launch_bounds__(1024) batch_prep_kernel(
+    const double* __restrict__ states, const uint32_t* __restrict__ n_rays, uint32_t n_states,
+    uint32_t max_rays, DevMap m, EvalConsts k, BatchHeader* hdr, BatchState* bs,
+    uint32_t* sticket, uint32_t* gticket, rmp_result_t* out) {
+  __shared__ uint32_t wsum_c[32], wsum_g[32];
+  __shared__ uint32_t carry_c, carry_g;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t S = 1u << k.lg_segs;
+  if (tid == 0) {
+    carry_c = 0;
+    carry_g = 0;
+  }
+  __syncthreads();
+  for (uint32_t base = 0; base < n_states; base += blockDim.x) {
+    const uint32_t b = base + tid;
+    BatchState st;
+    uint32_t chunks = 0, groups = 0;
+    if (b < n_states) {
+      const uint32_t n = n_rays[b];
+      int bad = n > max_rays;
+      const double* x = states + 6 * (size_t)b;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double o = m.kind != RMP_MAP_DENSE_U8 ? 0.0
+                         : (a == 0 ? m.origin[0] : (a == 1 ? m.origin[1] : m.origin[2]));
+        const double q = __dmul_rn(__ddiv_rn(__dsub_rn(x[a], o), m.vs), 65536.0);
+        const int ba = !(fabs(q) < 274877906944.0);
+        bad |= ba;
+        st.P[a] = ba ? 0 : __double2ll_rn(q);
+        const double v = x[3 + a];
+        st.v[a] = __double2float_rn(v);
+        st.vl[a] = __double2float_rn(__dsub_rn(v, (double)st.v[a]));
+      }
+      st.n_rays = n;
+      st.status = bad ? RMP_ERR_INVALID_ARG : RMP_OK;
+      if (!bad && n > 0) {
+        chunks = (n * S + 31) / 32;
+        groups = (chunks + kBatchGroup - 1) / kBatchGroup;
+      }
+      st.n_chunks = chunks;
+      st.perm_M = n >= 32 ? pick_cells_dev(n) : 1u;
+      st.perm_Q = n / st.perm_M;
+      st.perm_R = n - st.perm_Q * st.perm_M;
+    }
+    // exclusive scans of chunks and groups over this tile
+    uint32_t ic = chunks, ig = groups;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t c2 = __shfl_up_sync(0xffffffffu, ic, off);
+      const uint32_t g2 = __shfl_up_sync(0xffffffffu, ig, off);
+      if (lane >= (uint32_t)off) {
+        ic += c2;
+        ig += g2;
+      }
+    }
+    if (lane == 31) {
+      wsum_c[warp] = ic;
+      wsum_g[warp] = ig;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t wc = lane < (blockDim.x >> 5) ? wsum_c[lane] : 0u;
+      uint32_t wg = lane < (blockDim.x >> 5) ? wsum_g[lane] : 0u;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t c2 = __shfl_up_sync(0xffffffffu, wc, off);
+        const uint32_t g2 = __shfl_up_sync(0xffffffffu, wg, off);
+        if (lane >= (uint32_t)off) {
+          wc += c2;
+          wg += g2;
+        }
+      }
+      wsum_c[lane] = wc;   // inclusive over warps
+      wsum_g[lane] = wg;
+    }
+    __syncthreads();
+    const uint32_t pre_c = carry_c + (warp ? wsum_c[warp - 1] : 0u) + ic - chunks;
+    const uint32_t pre_g = carry_g + (warp ? wsum_g[warp - 1] : 0u) + ig - groups;
+    if (b < n_states) {
+      st.chunk0 = pre_c;
+      st.group0 = pre_g;
+      bs[b] = st;
+      sticket[b] = 0;
+      if (chunks == 0) {
+        rmp_result_t r;
+        memset(&r, 0, sizeof(r));
+        r.n_rays = st.n_rays;
+        r.status = st.status;
+        out[b] = r;
+      }
+    }
+    __syncthreads();
+    if (tid == blockDim.x - 1) {
+      carry_c = pre_c + chunks;
+      carry_g = pre_g + groups;
+    }
+    __syncthreads();
+  }
+  for (uint32_t i = tid; i < carry_g; i += blockDim.x) gticket[i] = 0;
+  if (tid == 0) {
+    hdr->next_chunk = 0;
+    hdr->total_chunks = carry_c;
+    hdr->n_states = n_states;
+  }
+}
+
+// Sum of a partial over the lanes of a warp (lane i holds p_i; lanes without one hold 0):
+// FP64 shuffle tree in a fixed order, result in lane 0.
+__device__ __forceinline__ void warp_sum_partial(double v[9], unsigned& h, unsigned& a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
+  h = __reduce_add_sync(0xffffffffu, h);
+  a = __reduce_add_sync(0xffffffffu, a);
+}
+
+__device__ __forceinline__ void load_partial(const CtaPartial* p, double v[9], unsigned& h,
+                                             unsigned& a) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) v[q] = __ldcg(&p->v[q]);
+  h = __ldcg(&p->n_hits);
+  a = __ldcg(&p->n_active);
+}
+
+// Persistent batched evaluation: every warp takes chunks from the work counter until none
+// is left; a chunk is 32 / S rays of one state (coherent ray order of that state), marched
+// and evaluated as in the single-state kernel.  The chunk's 9 terms are summed over the
+// warp (compensated FP32 or FP64 tree), stored, and the chunk's group and state tickets
+// decide which warp sums a group (<= 32 chunk partials, one per lane) and which one sums
+// the state's groups and resolves it -- every sum in a fixed order, so results do not
+// depend on which warp ran which chunk.
+template <int KIND, int LAYOUT, int RED>
+__global__ void __launch_bounds__(256) raycast_batch_kernel(
+    DevMap m, EvalConsts k, BatchHeader* hdr, const BatchState* __restrict__ bs,
+    uint32_t* sticket, uint32_t* gticket, CtaPartial* cparts, CtaPartial* gparts,
+    rmp_result_t* out, rmp_ray_hit_t* hits, float* per_ray, uint32_t max_rays) {
+  extern __shared__ uint4 smem_radius[];
+  __shared__ __align__(8) uint64_t bm_bar;
+  __shared__ int bm_timeout;
+  const uint32_t bm_bytes = m.radius_words * 4u;
+  const bool staged = LAYOUT == kLayoutGrid && bm_bytes <= kMaxSmemRadiusBytes;
+  if (threadIdx.x == 0) {
+    bm_timeout = 0;
+    if (staged) bulk_load_begin(&bm_bar, smem_radius, m.radius, bm_bytes);
+  }
+  __syncthreads();
+  if (staged && threadIdx.x == 0 && !bulk_load_wait(&bm_bar)) bm_timeout = 1;
+  __syncthreads();
+  // a copy that did not land in time leaves the CTA on the global copy of the field
+  const uint32_t* bm = (staged && !bm_timeout) ? reinterpret_cast<const uint32_t*>(smem_radius)
+                                               : m.radius;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t lgS = k.lg_segs, S = 1u << lgS;
+  const uint32_t total = *(volatile const uint32_t*)&hdr->total_chunks;
+  const uint32_t nst = *(volatile const uint32_t*)&hdr->n_states;
+  uint32_t c = 0;
+  if (lane == 0) c = atomicAdd(&hdr->next_chunk, 1u);
+  c = __shfl_sync(0xffffffffu, c, 0);
+  while (c < total) {
+    uint32_t cn = 0;
+    if (lane == 0) cn = atomicAdd(&hdr->next_chunk, 1u);   // next chunk, fetched early
+    // the chunk's state: the last one whose first chunk is <= c
+    uint32_t lo = 0, hi = nst;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(&bs[mid].chunk0) <= c) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t b = lo;
+    const BatchState* sp = bs + b;
+    const long long P[3] = {__ldg(&sp->P[0]), __ldg(&sp->P[1]), __ldg(&sp->P[2])};
+    const float v[3] = {__ldg(&sp->v[0]), __ldg(&sp->v[1]), __ldg(&sp->v[2])};
+    const float vl[3] = {__ldg(&sp->vl[0]), __ldg(&sp->vl[1]), __ldg(&sp->vl[2])};
+    const uint32_t n_b = __ldg(&sp->n_rays), chunk0 = __ldg(&sp->chunk0);
+    const uint32_t n_chunks = __ldg(&sp->n_chunks), group0 = __ldg(&sp->group0);
+    const uint32_t q = c - chunk0;
+    const uint32_t g = q * 32 + lane;
+    const uint32_t slot = g >> lgS, seg = g & (S - 1);
+    const bool active = slot < n_b;
+    const uint32_t ray_idx = ray_of_slot_p(active ? slot : 0, __ldg(&sp->perm_M),
+                                           __ldg(&sp->perm_Q), __ldg(&sp->perm_R));
+    const Ray ray = make_ray(ray_idx + k.halton_offset);
+    MarchState mo;
+    const int mstat = march_ray<KIND, LAYOUT>(m, bm, k, P, ray, seg, active, mo);
+    float vals[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    unsigned nh = 0, na = 0;
+    if (active && seg == 0) {
+      const size_t ro = (size_t)b * max_rays + ray_idx;
+      ray_outputs(m, k, P, ray, mo, mstat, v, vl, hits ? hits + ro : nullptr,
+                  per_ray ? per_ray + 9 * ro : nullptr, vals, nh, na);
+    }
+    // chunk partial
+    double pv[9];
+    if (RED == RMP_REDUCE_FP64) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) pv[i] = (double)vals[i];
+      warp_sum_partial(pv, nh, na);
+    } else {
+      Acc32 acc;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        acc.s[i] = vals[i];
+        acc.c[i] = 0.0f;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const float s2 = __shfl_down_sync(0xffffffffu, acc.s[i], off);
+          const float c2 = __shfl_down_sync(0xffffffffu, acc.c[i], off);
+          acc_merge(acc, s2, c2, i);
+        }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) pv[i] = (double)acc.s[i] + (double)acc.c[i];
+      nh = __reduce_add_sync(0xffffffffu, nh);
+      na = __reduce_add_sync(0xffffffffu, na);
+    }
+    const uint32_t gi = q / kBatchGroup;
+    const uint32_t gsz = min(kBatchGroup, n_chunks - gi * kBatchGroup);
+    uint32_t stage = 0;
+    if (lane == 0) {
+      CtaPartial p;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) p.v[i] = pv[i];
+      p.n_hits = nh;
+      p.n_active = na;
+      cparts[chunk0 + q] = p;
+      __threadfence();
+      stage = atomicAdd(&gticket[group0 + gi], 1u) == gsz - 1 ? 1u : 0u;
+    }
+    stage = __shfl_sync(0xffffffffu, stage, 0);
+    if (stage) {
+      // last chunk of its group: sum the group's chunk partials (lane i: chunk i)
+      __threadfence();
+      double gv[9] = {0., 0., 0., 0., 0., 0., 0., 0., 0.};
+      unsigned gh = 0, ga = 0;
+      if (lane < gsz) load_partial(cparts + chunk0 + gi * kBatchGroup + lane, gv, gh, ga);
+      warp_sum_partial(gv, gh, ga);
+      const uint32_t n_groups = (n_chunks + kBatchGroup - 1) / kBatchGroup;
+      if (lane == 0) {
+        CtaPartial p;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) p.v[i] = gv[i];
+        p.n_hits = gh;
+        p.n_active = ga;
+        gparts[group0 + gi] = p;
+        __threadfence();
+        stage = atomicAdd(&sticket[b], 1u) == n_groups - 1 ? 2u : 0u;
+      }
+      stage = __shfl_sync(0xffffffffu, stage, 0);
+      if (stage == 2) {
+        // last group of the state: lane i sums groups i, i + 32, ... in order, then the tree
+        __threadfence();
+        double tv[9] = {0., 0., 0., 0., 0., 0., 0., 0., 0.};
+        unsigned th = 0, ta = 0;
+        for (uint32_t j = lane; j < n_groups; j += 32) {
+          double pv2[9];
+          unsigned h2, a2;
+          load_partial(gparts + group0 + j, pv2, h2, a2);
+#pragma unroll
+          for (int i = 0; i < 9; ++i) tv[i] += pv2[i];
+          th += h2;
+          ta += a2;
+        }
+        warp_sum_partial(tv, th, ta);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) tv[i] = __shfl_sync(0xffffffffu, tv[i], 0);
+        rmp_result_t r;
+        resolve_pinv(tv, tv + 6, r);
+        if (lane == 0) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) r.A[i] = tv[i];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) r.Af[i] = tv[6 + i];
+          r.n_rays = n_b;
+          r.n_hits = th;
+          r.n_active = ta;
+          r.status = RMP_OK;
+          r.reserved = 0;
+          out[b] = r;
+        }
+      }
+    }
+    c = __shfl_sync(0xffffffffu, cn, 0);
+  }
+  if (staged && bm_timeout && threadIdx.x == 0) bulk_load_wait(&bm_bar);   // let a late copy land
 }
 
 // ------------------------------------------------------------------ LiDAR scan kernel (Sec. III-G)
@@ -1498,13 +1881,13 @@ size_t raycast_smem_bytes(const DevMap& m) {
 // The kernels keep up to 48 KB of the map's radius field in shared memory: ask for the
 // largest shared-memory carveout once per device so that register use, not the L1/shared
 // split, bounds the CTAs resident per SM (a whole evaluation should fit in one wave).
-template <typename F>
-static void prefer_shared(F* fn) {
-  static uint64_t done_mask = 0;   // one bit per device id < 64
+template <auto Fn>
+static void prefer_shared() {
+  static uint64_t done_mask = 0;   // one bit per device id < 64, per kernel
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return;
   if (__atomic_load_n(&done_mask, __ATOMIC_ACQUIRE) & (1ull << dev)) return;
-  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+  cudaFuncSetAttribute(Fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                        (int)cudaSharedmemCarveoutMaxShared);
   __atomic_fetch_or(&done_mask, 1ull << dev, __ATOMIC_ACQ_REL);
 }
@@ -1515,11 +1898,11 @@ static void launch_raycast_t(const DevMap& m, const EvalConsts& k, const double*
                              rmp_ray_hit_t* hits, float* per_ray, int block, int grid,
                              size_t smem, cudaStream_t stream) {
   if (k.reduce_mode == RMP_REDUCE_FP64) {
-    prefer_shared(raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_FP64>);
+    prefer_shared<raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_FP64>>();
     raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_FP64><<<grid, block, smem, stream>>>(
         m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
   } else {
-    prefer_shared(raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_KAHAN32>);
+    prefer_shared<raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_KAHAN32>>();
     raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_KAHAN32><<<grid, block, smem, stream>>>(
         m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
   }
@@ -1556,6 +1939,83 @@ cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* s
   else
     launch_raycast_t<RMP_MAP_HASHED_TSDF, kLayoutHash>(m, k, state_dev, hdr, parts, out_dev, hits,
                                                        per_ray, block, grid, smem, stream);
+  return cudaGetLastError();
+}
+
+template <int KIND, int LAYOUT, int RED>
+static int batch_occupancy_t(int block, size_t smem) {
+  int n = 0;
+  prefer_shared<raycast_batch_kernel<KIND, LAYOUT, RED>>();
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_batch_kernel<KIND, LAYOUT, RED>,
+                                                       block, smem) == cudaSuccess ? n : -1;
+}
+
+int batch_occupancy(const DevMap& m, int reduce_mode, int block) {
+  const size_t smem = raycast_smem_bytes(m);
+  if (m.kind == RMP_MAP_DENSE_U8)
+    return reduce_mode ? batch_occupancy_t<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_FP64>(block, smem)
+                       : batch_occupancy_t<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_KAHAN32>(block, smem);
+  if (m.layout == kLayoutGrid)
+    return reduce_mode ? batch_occupancy_t<RMP_MAP_HASHED_TSDF, kLayoutGrid, RMP_REDUCE_FP64>(block, smem)
+                       : batch_occupancy_t<RMP_MAP_HASHED_TSDF, kLayoutGrid, RMP_REDUCE_KAHAN32>(block, smem);
+  return reduce_mode ? batch_occupancy_t<RMP_MAP_HASHED_TSDF, kLayoutHash, RMP_REDUCE_FP64>(block, smem)
+                     : batch_occupancy_t<RMP_MAP_HASHED_TSDF, kLayoutHash, RMP_REDUCE_KAHAN32>(block, smem);
+}
+
+template <int KIND, int LAYOUT, int RED>
+static void launch_batch_t(const DevMap& m, const EvalConsts& k, BatchHeader* hdr,
+                           const BatchState* bs, uint32_t* sticket, uint32_t* gticket,
+                           CtaPartial* cparts, CtaPartial* gparts, rmp_result_t* out,
+                           rmp_ray_hit_t* hits, float* per_ray, uint32_t max_rays, int block,
+                           int grid, size_t smem, cudaStream_t stream) {
+  prefer_shared<raycast_batch_kernel<KIND, LAYOUT, RED>>();
+  raycast_batch_kernel<KIND, LAYOUT, RED><<<grid, block, smem, stream>>>(
+      m, k, hdr, bs, sticket, gticket, cparts, gparts, out, hits, per_ray, max_rays);
+}
+
+template <int KIND, int LAYOUT>
+static void launch_batch_r(const DevMap& m, const EvalConsts& k, BatchHeader* hdr,
+                           const BatchState* bs, uint32_t* sticket, uint32_t* gticket,
+                           CtaPartial* cparts, CtaPartial* gparts, rmp_result_t* out,
+                           rmp_ray_hit_t* hits, float* per_ray, uint32_t max_rays, int block,
+                           int grid, size_t smem, cudaStream_t stream) {
+  if (k.reduce_mode == RMP_REDUCE_FP64)
+    launch_batch_t<KIND, LAYOUT, RMP_REDUCE_FP64>(m, k, hdr, bs, sticket, gticket, cparts, gparts,
+                                                  out, hits, per_ray, max_rays, block, grid, smem,
+                                                  stream);
+  else
+    launch_batch_t<KIND, LAYOUT, RMP_REDUCE_KAHAN32>(m, k, hdr, bs, sticket, gticket, cparts,
+                                                     gparts, out, hits, per_ray, max_rays, block,
+                                                     grid, smem, stream);
+}
+
+cudaError_t launch_batch(const DevMap& m, const EvalConsts& k, const double* states_dev,
+                         const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
+                         void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits, float* per_ray,
+                         int block, int grid, cudaStream_t stream) {
+  const BatchLayout L = batch_layout(n_states, max_rays);
+  char* w = (char*)ws;
+  BatchHeader* hdr = (BatchHeader*)w;
+  BatchState* bs = (BatchState*)(w + L.states);
+  uint32_t* sticket = (uint32_t*)(w + L.sticket);
+  uint32_t* gticket = (uint32_t*)(w + L.gticket);
+  CtaPartial* cparts = (CtaPartial*)(w + L.cparts);
+  CtaPartial* gparts = (CtaPartial*)(w + L.gparts);
+  batch_prep_kernel<<<1, 1024, 0, stream>>>(states_dev, n_rays_dev, n_states, max_rays, m, k, hdr,
+                                            bs, sticket, gticket, out_dev);
+  const size_t smem = raycast_smem_bytes(m);
+  if (m.kind == RMP_MAP_DENSE_U8)
+    launch_batch_r<RMP_MAP_DENSE_U8, kLayoutGrid>(m, k, hdr, bs, sticket, gticket, cparts, gparts,
+                                                  out_dev, hits, per_ray, max_rays, block, grid,
+                                                  smem, stream);
+  else if (m.layout == kLayoutGrid)
+    launch_batch_r<RMP_MAP_HASHED_TSDF, kLayoutGrid>(m, k, hdr, bs, sticket, gticket, cparts,
+                                                     gparts, out_dev, hits, per_ray, max_rays,
+                                                     block, grid, smem, stream);
+  else
+    launch_batch_r<RMP_MAP_HASHED_TSDF, kLayoutHash>(m, k, hdr, bs, sticket, gticket, cparts,
+                                                     gparts, out_dev, hits, per_ray, max_rays,
+                                                     block, grid, smem, stream);
   return cudaGetLastError();
 }
 

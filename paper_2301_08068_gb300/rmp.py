@@ -20,7 +20,7 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-RMP_OK = 0
+RMP_OK, RMP_ERR_INVALID_ARG = 0, 1
 STATUS_NAMES = {0: "RMP_OK", 1: "RMP_ERR_INVALID_ARG", 2: "RMP_ERR_NO_MEMORY", 3: "RMP_ERR_CUDA",
                 4: "RMP_ERR_TIMEOUT", 5: "RMP_ERR_BUSY", 6: "RMP_ERR_UNKNOWN_MAP",
                 7: "RMP_ERR_NOT_READY"}
@@ -98,9 +98,16 @@ _SIGNATURES = {
     "rmp_eval_launch_info": [_P, C.c_uint32, C.c_uint32, C.POINTER(rmp_params_t),
                              C.POINTER(rmp_launch_info_t)],
     "rmp_tune_get": [_P, C.c_int, C.POINTER(C.c_int)],
+    "rmp_raycast_eval_batch_async": [_P, C.c_uint32, _P, _P, C.c_uint32, C.c_uint32,
+                                     C.POINTER(rmp_params_t), _P, C.c_size_t, _P, _P, _P, _P],
+    "rmp_raycast_eval_batch": [_P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(rmp_params_t), _P,
+                               _P],
+    "rmp_batch_autotune": [_P, C.c_uint32, _P, _P, C.c_uint32, C.c_uint32, C.POINTER(rmp_params_t),
+                           _P, C.c_size_t, _P, _P, C.c_int, _P, C.c_int],
 }
 # Symbols every build must export (checked by the not-gpu ABI test against include/rmp.h).
-EXPORTS = sorted(list(_SIGNATURES) + ["rmp_status_string", "rmp_workspace_bytes"])
+EXPORTS = sorted(list(_SIGNATURES) + ["rmp_status_string", "rmp_workspace_bytes",
+                                       "rmp_batch_workspace_bytes"])
 
 
 def lib_path() -> str:
@@ -128,6 +135,8 @@ def lib() -> C.CDLL:
             L.rmp_status_string.restype = C.c_char_p
             L.rmp_workspace_bytes.argtypes = []
             L.rmp_workspace_bytes.restype = C.c_size_t
+            L.rmp_batch_workspace_bytes.argtypes = [C.c_uint32, C.c_uint32]
+            L.rmp_batch_workspace_bytes.restype = C.c_size_t
             _lib = L
     return _lib
 
@@ -267,6 +276,47 @@ def rmp_scan_eval_async(ctx: int, points, state, params: rmp_params_t, workspace
                                      _dptr(workspace), workspace.numel() * workspace.element_size(),
                                      _stream(stream), _dptr(out), _dptr(per_ray)),
            "rmp_scan_eval_async")
+
+
+def rmp_batch_workspace_bytes(n_states: int, max_rays: int) -> int:
+    return int(lib().rmp_batch_workspace_bytes(int(n_states), int(max_rays)))
+
+
+def rmp_raycast_eval_batch_async(ctx: int, map_id: int, states, n_rays, n_states: int,
+                                 max_rays: int, params: rmp_params_t, workspace, out, stream=None,
+                                 hits=None, per_ray=None):
+    """states: device float64 (n_states, 6); n_rays: device int32/uint32 (n_states,);
+    out: device buffer of n_states results (RESULT_BYTES each)."""
+    _check(lib().rmp_raycast_eval_batch_async(
+        ctx, int(map_id), _dptr(states), _dptr(n_rays), int(n_states), int(max_rays),
+        C.byref(params), _dptr(workspace), workspace.numel() * workspace.element_size(),
+        _stream(stream), _dptr(out), _dptr(hits), _dptr(per_ray)), "rmp_raycast_eval_batch_async")
+
+
+def rmp_raycast_eval_batch(ctx: int, map_id: int, states, n_rays, params: rmp_params_t,
+                           stream=None) -> list:
+    """states: host (n_states, 6) float64 [x, xdot]; n_rays: host counts.  Returns one result
+    dict per state."""
+    st = np.ascontiguousarray(states, np.float64).reshape(-1, 6)
+    nr = np.ascontiguousarray(n_rays, np.uint32).reshape(-1)
+    assert st.shape[0] == nr.shape[0]
+    out = (rmp_result_t * st.shape[0])()
+    _check(lib().rmp_raycast_eval_batch(ctx, int(map_id), st.ctypes.data, nr.ctypes.data,
+                                        int(st.shape[0]), C.byref(params), _stream(stream), out),
+           "rmp_raycast_eval_batch")
+    return [result_dict(r) for r in out]
+
+
+def rmp_batch_autotune(ctx: int, map_id: int, states, n_rays, n_states: int, max_rays: int,
+                       params: rmp_params_t, workspace, out, reps: int = 5, stream=None) -> list:
+    """Runs the autotuner (leaves the fastest knobs in the context); returns the 18 median
+    times in ms (block-major, then segments, then split)."""
+    times = (C.c_float * 18)()
+    _check(lib().rmp_batch_autotune(
+        ctx, int(map_id), _dptr(states), _dptr(n_rays), int(n_states), int(max_rays),
+        C.byref(params), _dptr(workspace), workspace.numel() * workspace.element_size(),
+        _stream(stream), _dptr(out), int(reps), times, 18), "rmp_batch_autotune")
+    return [float(t) for t in times]
 
 
 def rmp_tune_set(ctx: int, knob: int, value: int):

@@ -95,6 +95,25 @@ def test_workspace_size_is_fixed(rmp):
     assert rmp.rmp_workspace_bytes() == 1024 + 80 * (4096 + 128)
 
 
+def test_batch_workspace_size(rmp):
+    """Header + states + tickets + one 80-byte partial per chunk (32 threads, up to 4
+    segments per ray) and per group of 32 chunks, each region 256-byte aligned."""
+    al = lambda x: (x + 255) // 256 * 256
+    for B, mr in ((1, 1), (3, 1000), (256, 65536)):
+        cps = (mr * 4 + 31) // 32
+        gps = (cps + 31) // 32
+        o = al(128)
+        o = al(o + 80 * B)
+        o = al(o + 4 * B)
+        o = al(o + 4 * B * gps)
+        o = al(o + 80 * B * cps)
+        o = al(o + 80 * B * gps)
+        assert rmp.rmp_batch_workspace_bytes(B, mr) == o
+    assert rmp.rmp_batch_workspace_bytes(0, 10) == 0
+    assert rmp.rmp_batch_workspace_bytes(10, 0) == 0
+    assert rmp.rmp_batch_workspace_bytes(65537, 10) == 0
+
+
 def test_null_arguments_rejected_without_gpu(rmp):
     L = rmp.lib()
     assert L.rmp_ctx_create(None, 0) == 1
@@ -102,3 +121,8 @@ def test_null_arguments_rejected_without_gpu(rmp):
     assert L.rmp_map_release(None, 1) == 1
     assert L.rmp_raycast_eval(None, 1, None, None, 1, None, None, None, None, None) == 1
     assert L.rmp_scan_eval(None, None, 1, None, None, None, None, None, None) == 1
+    assert L.rmp_raycast_eval_batch_async(None, 1, None, None, 1, 1, None, None, 0, None, None,
+                                          None, None) == 1
+    assert L.rmp_raycast_eval_batch(None, 1, None, None, 1, None, None, None) == 1
+    assert L.rmp_batch_autotune(None, 1, None, None, 1, 1, None, None, 0, None, None, 1, None,
+                                0) == 1
