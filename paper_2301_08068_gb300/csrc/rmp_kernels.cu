@@ -1291,21 +1291,23 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
 }
 
 // ------------------------------------------------------------------ batched evaluation
-// Device form of the host's direction-cell choice: M = 2^a 3^b <= n / 32 minimising
-// |log M - log(n / 48)| + 0.5 |log(3^b / (pi 2^a))| (cells close to square on the
-// sphere).  The score is piecewise linear in b with its steeper kink where M = n / 48,
-// so for each a only the b next to that kink, b = 0 and the largest b allowed by the
-// bound need checking.  Only the work schedule and the summation grouping depend on it.
-__device__ __forceinline__ uint32_t pick_cells_dev(uint32_t n) {
+// Device form of the host's direction-cell choice, one warp per state: M = 2^a 3^b <=
+// n / 32 minimising |log M - log(n / 48)| + 0.5 |log(3^b / (pi 2^a))| (cells close to
+// square on the sphere).  The score is piecewise linear in b with its steeper kink where
+// M = n / 48, so for a given a only the b next to that kink, b = 0 and the largest b the
+// bound allows need checking; lane a checks those, the warp keeps the best (lowest a on
+// ties).  Only the work schedule and the summation grouping depend on the choice.
+__device__ __forceinline__ uint32_t pick_cells_warp(uint32_t n) {
+  const uint32_t lane = threadIdx.x & 31;
   const float L3 = 1.5849625f, LPI = 1.6514961f;   // log2(3), log2(pi)
   const float lt = __log2f(fmaxf((float)n * (1.0f / 48.0f), 1.0f));
   const float lm = __log2f((float)n * (1.0f / 32.0f));
-  uint32_t best = 1;
   float best_score = 3.0e38f;
-  for (int a = 0; a <= 24; ++a) {
-    if ((32ull << a) > n) break;
-    const int bk = (int)floorf(((lt - (float)a) / L3));
-    const int bm = (int)floorf(((lm - (float)a) / L3)) + 1;
+  uint32_t best = 1;
+  const int a = (int)lane;
+  if (a <= 24 && (32ull << a) <= n) {
+    const int bk = (int)floorf((lt - (float)a) / L3);
+    const int bm = (int)floorf((lm - (float)a) / L3) + 1;
     const int cand[4] = {0, bk, bk + 1, bm};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -1316,7 +1318,6 @@ __device__ __forceinline__ uint32_t pick_cells_dev(uint32_t n) {
         mm /= 3ull;
         --bb;
       }
-      if (mm * 32ull > n) continue;
       const float score = fabsf((float)a + (float)bb * L3 - lt) +
                           0.5f * fabsf((float)bb * L3 - LPI - (float)a);
       if (score < best_score) {
@@ -1325,7 +1326,16 @@ __device__ __forceinline__ uint32_t pick_cells_dev(uint32_t n) {
       }
     }
   }
-  return best;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float s2 = __shfl_down_sync(0xffffffffu, best_score, off);
+    const uint32_t m2 = __shfl_down_sync(0xffffffffu, best, off);
+    if (s2 < best_score) {                          // strict: the lower lane wins ties
+      best_score = s2;
+      best = m2;
+    }
+  }
+  return __shfl_sync(0xffffffffu, best, 0);
 }
 
 __device__ __forceinline__ uint32_t ray_of_slot_p(uint32_t j, uint32_t M, uint32_t Q, uint32_t R) {
@@ -1343,55 +1353,68 @@ __device__ __forceinline__ uint32_t ray_of_slot_p(uint32_t j, uint32_t M, uint32
   return r + M * q;
 }
 
-// Per-state set-up of a batch (one CTA of 1024 threads): validates each ray count,
-// quantises the position, splits the velocity, counts chunks and groups, assigns them
-// consecutive index ranges (block-wide exclusive scans), clears the tickets and the work
-// counter, and writes the result of every state that has no chunks (no rays, or invalid).
+// Per-state set-up of a batch (one CTA of 1024 threads).  Phase A, one warp per state:
+// validate the ray count, quantise the position (lanes 0-2, FP64), split the velocity
+// (lanes 3-5), choose the direction cells, count chunks and groups.  Phase B, one thread
+// per state: exclusive block scans assign consecutive chunk and group ranges.  Then the
+// tickets and the work counter are cleared and every state without chunks (no rays, or
+// invalid) gets its result here.
 __global__ void __launch_bounds__(1024) batch_prep_kernel(
     const double* __restrict__ states, const uint32_t* __restrict__ n_rays, uint32_t n_states,
     uint32_t max_rays, DevMap m, EvalConsts k, BatchHeader* hdr, BatchState* bs,
     uint32_t* sticket, uint32_t* gticket, rmp_result_t* out) {
+  __shared__ uint32_t s_chunks[1024], s_groups[1024];
   __shared__ uint32_t wsum_c[32], wsum_g[32];
   __shared__ uint32_t carry_c, carry_g;
-  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const uint32_t S = 1u << k.lg_segs;
   if (tid == 0) {
     carry_c = 0;
     carry_g = 0;
   }
-  __syncthreads();
   for (uint32_t base = 0; base < n_states; base += blockDim.x) {
-    const uint32_t b = base + tid;
-    BatchState st;
-    uint32_t chunks = 0, groups = 0;
-    if (b < n_states) {
+    const uint32_t tile = min(blockDim.x, n_states - base);
+    for (uint32_t j = warp; j < tile; j += nwarps) {
+      const uint32_t b = base + j;
       const uint32_t n = n_rays[b];
-      int bad = n > max_rays;
       const double* x = states + 6 * (size_t)b;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
+      long long Pa = 0;
+      int bad_a = 0;
+      float va = 0.f, vla = 0.f;
+      if (lane < 3) {
         const double o = m.kind != RMP_MAP_DENSE_U8 ? 0.0
-                         : (a == 0 ? m.origin[0] : (a == 1 ? m.origin[1] : m.origin[2]));
-        const double q = __dmul_rn(__ddiv_rn(__dsub_rn(x[a], o), m.vs), 65536.0);
-        const int ba = !(fabs(q) < 274877906944.0);
-        bad |= ba;
-        st.P[a] = ba ? 0 : __double2ll_rn(q);
-        const double v = x[3 + a];
-        st.v[a] = __double2float_rn(v);
-        st.vl[a] = __double2float_rn(__dsub_rn(v, (double)st.v[a]));
+                         : (lane == 0 ? m.origin[0] : (lane == 1 ? m.origin[1] : m.origin[2]));
+        const double q = __dmul_rn(__ddiv_rn(__dsub_rn(x[lane], o), m.vs), 65536.0);
+        bad_a = !(fabs(q) < 274877906944.0);
+        Pa = bad_a ? 0 : __double2ll_rn(q);
+      } else if (lane < 6) {
+        const double v = x[lane];
+        va = __double2float_rn(v);
+        vla = __double2float_rn(__dsub_rn(v, (double)va));
       }
-      st.n_rays = n;
-      st.status = bad ? RMP_ERR_INVALID_ARG : RMP_OK;
-      if (!bad && n > 0) {
-        chunks = (n * S + 31) / 32;
-        groups = (chunks + kBatchGroup - 1) / kBatchGroup;
+      const bool bad = (__ballot_sync(0xffffffffu, bad_a != 0) != 0) || n > max_rays;
+      const uint32_t M = n >= 32 ? pick_cells_warp(n) : 1u;
+      BatchState* sp = bs + b;
+      if (lane < 3) sp->P[lane] = Pa;
+      else if (lane < 6) {
+        sp->v[lane - 3] = va;
+        sp->vl[lane - 3] = vla;
       }
-      st.n_chunks = chunks;
-      st.perm_M = n >= 32 ? pick_cells_dev(n) : 1u;
-      st.perm_Q = n / st.perm_M;
-      st.perm_R = n - st.perm_Q * st.perm_M;
+      if (lane == 0) {
+        const uint32_t chunks = (!bad && n > 0) ? (n * S + 31) / 32 : 0u;
+        sp->n_rays = n;
+        sp->status = bad ? RMP_ERR_INVALID_ARG : RMP_OK;
+        sp->n_chunks = chunks;
+        sp->perm_M = M;
+        sp->perm_Q = n / M;
+        sp->perm_R = n - (n / M) * M;
+        s_chunks[j] = chunks;
+        s_groups[j] = (chunks + kBatchGroup - 1) / kBatchGroup;
+      }
     }
-    // exclusive scans of chunks and groups over this tile
+    __syncthreads();
+    const uint32_t chunks = tid < tile ? s_chunks[tid] : 0u;
+    const uint32_t groups = tid < tile ? s_groups[tid] : 0u;
     uint32_t ic = chunks, ig = groups;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -1408,8 +1431,8 @@ __global__ void __launch_bounds__(1024) batch_prep_kernel(
     }
     __syncthreads();
     if (warp == 0) {
-      uint32_t wc = lane < (blockDim.x >> 5) ? wsum_c[lane] : 0u;
-      uint32_t wg = lane < (blockDim.x >> 5) ? wsum_g[lane] : 0u;
+      uint32_t wc = lane < nwarps ? wsum_c[lane] : 0u;
+      uint32_t wg = lane < nwarps ? wsum_g[lane] : 0u;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
         const uint32_t c2 = __shfl_up_sync(0xffffffffu, wc, off);
@@ -1425,16 +1448,16 @@ __global__ void __launch_bounds__(1024) batch_prep_kernel(
     __syncthreads();
     const uint32_t pre_c = carry_c + (warp ? wsum_c[warp - 1] : 0u) + ic - chunks;
     const uint32_t pre_g = carry_g + (warp ? wsum_g[warp - 1] : 0u) + ig - groups;
-    if (b < n_states) {
-      st.chunk0 = pre_c;
-      st.group0 = pre_g;
-      bs[b] = st;
+    if (tid < tile) {
+      const uint32_t b = base + tid;
+      bs[b].chunk0 = pre_c;
+      bs[b].group0 = pre_g;
       sticket[b] = 0;
       if (chunks == 0) {
         rmp_result_t r;
         memset(&r, 0, sizeof(r));
-        r.n_rays = st.n_rays;
-        r.status = st.status;
+        r.n_rays = bs[b].n_rays;
+        r.status = bs[b].status;
         out[b] = r;
       }
     }
@@ -1472,8 +1495,8 @@ __device__ __forceinline__ void load_partial(const CtaPartial* p, double v[9], u
   a = __ldcg(&p->n_active);
 }
 
-// Persistent batched evaluation: every warp takes chunks from the work counter until none
-// is left; a chunk is 32 / S rays of one state (coherent ray order of that state), marched
+// Persistent batched evaluation: every warp takes chunks (its own index first, then from
+// the work counter) until none is left; a chunk is 32 / S rays of one state (coherent ray order of that state), marched
 // and evaluated as in the single-state kernel.  The chunk's 9 terms are summed over the
 // warp (compensated FP32 or FP64 tree), stored, and the chunk's group and state tickets
 // decide which warp sums a group (<= 32 chunk partials, one per lane) and which one sums
@@ -1503,12 +1526,15 @@ __global__ void __launch_bounds__(256) raycast_batch_kernel(
   const uint32_t lgS = k.lg_segs, S = 1u << lgS;
   const uint32_t total = *(volatile const uint32_t*)&hdr->total_chunks;
   const uint32_t nst = *(volatile const uint32_t*)&hdr->n_states;
-  uint32_t c = 0;
-  if (lane == 0) c = atomicAdd(&hdr->next_chunk, 1u);
-  c = __shfl_sync(0xffffffffu, c, 0);
+  // first chunk: the warp's index in the grid; later ones from the counter (offset by the
+  // number of warps), requested as soon as a chunk starts so the atomic's latency is
+  // hidden.  (Same-address atomics are serialised, several ns each: a grid-wide rush on
+  // the counter at kernel start would delay every warp's first chunk.)
+  const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+  uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   while (c < total) {
-    uint32_t cn = 0;
-    if (lane == 0) cn = atomicAdd(&hdr->next_chunk, 1u);   // next chunk, fetched early
+    uint32_t cn = 0xffffffffu;
+    if (lane == 0 && total > n_warps) cn = n_warps + atomicAdd(&hdr->next_chunk, 1u);
     // the chunk's state: the last one whose first chunk is <= c
     uint32_t lo = 0, hi = nst;
     while (hi - lo > 1) {
