@@ -268,6 +268,56 @@ int rmp_batch_autotune(rmp_ctx* ctx, uint32_t map_id, const double* states_dev,
                        rmp_stream_t stream, rmp_result_t* out_dev, int reps, float* times_ms,
                        int n_times);
 
+/* ------------------------------------------------------------------ request server
+ * Continuous batching of single-state requests (a serving layer over the batched
+ * evaluation; the paper evaluates one state per control step and has no counterpart).
+ * Requests are submitted from any thread and complete asynchronously; a worker thread
+ * keeps up to `slots` batches in flight on separate CUDA streams, admitting the oldest
+ * pending request together with later pending ones of the same map and params (up to
+ * max_batch_states) whenever a slot and enough of the device-memory budget are free.
+ * Batches in flight overlap on the device.  Each request's result is what
+ * rmp_raycast_eval returns for it, up to the order of the floating-point reduction.
+ * A request whose batch alone exceeds the budget completes with RMP_ERR_NO_MEMORY; a
+ * parameter or map error, or a CUDA error, completes the batch's requests with that
+ * status.  Each result is delivered once (poll or wait). */
+typedef struct rmp_server rmp_server;
+
+typedef struct {
+  uint32_t slots;              /* batches in flight at most (streams), 1..16 */
+  uint32_t max_batch_states;   /* requests per batch, 1..65536 */
+  uint32_t max_rays;           /* largest accepted request */
+  uint32_t reserved;
+  uint64_t mem_budget_bytes;   /* device memory for all batches in flight (allocated once) */
+} rmp_server_config_t;
+
+typedef struct {
+  uint64_t submitted, completed, rejected;   /* rejected: completed with an error status */
+  uint64_t batches, batched_states;          /* batches launched, requests in them */
+  uint64_t pending;                          /* waiting for admission now */
+  uint64_t max_inflight;                     /* most batches in flight at once */
+  uint64_t mem_high_water;                   /* most budget bytes in use at once */
+} rmp_server_stats_t;
+
+/* Defaults: 4 slots, 256 states per batch, 262144 rays, 1 GiB. */
+int rmp_server_config_default(rmp_server_config_t* cfg);
+/* Start a server on the context's device (allocates the budget, streams, pinned staging
+ * and the worker thread).  The context must outlive the server. */
+int rmp_server_create(rmp_ctx* ctx, const rmp_server_config_t* cfg, rmp_server** out);
+/* Finish every submitted request, then stop and free everything. */
+int rmp_server_destroy(rmp_server* server);
+/* Queue one evaluation (x, xdot: host, 3 doubles each; n_rays in [1, max_rays]);
+ * *ticket identifies it.  Never blocks on the device. */
+int rmp_server_submit(rmp_server* server, uint32_t map_id, const double x[3],
+                      const double xdot[3], uint32_t n_rays, const rmp_params_t* params,
+                      uint64_t* ticket);
+/* RMP_OK and the result (and its submit-to-completion latency in seconds, nullable) if
+ * done; RMP_ERR_NOT_READY if not yet; RMP_ERR_INVALID_ARG for a ticket never issued. */
+int rmp_server_poll(rmp_server* server, uint64_t ticket, rmp_result_t* out, double* latency_s);
+/* Like poll, but waits up to timeout_ms; RMP_ERR_TIMEOUT if the result is not there then. */
+int rmp_server_wait(rmp_server* server, uint64_t ticket, uint32_t timeout_ms, rmp_result_t* out,
+                    double* latency_s);
+int rmp_server_stats(rmp_server* server, rmp_server_stats_t* out);
+
 /* ------------------------------------------------------------------ launch tuning
  * Knobs of the evaluation kernels (per context; picked by the batch autotuner, settable by
  * hand).  They change the launch shape only: results are identical up to the order of

@@ -662,6 +662,12 @@ int rmp_scan_eval(rmp_ctx* c, const float* points_dev, uint32_t n, const double 
 }
 
 // ------------------------------------------------------------------ batched evaluation
+}  // extern "C"
+
+int rmp::ctx_device(const rmp_ctx* c) { return c->device; }
+
+extern "C" {
+
 size_t rmp_batch_workspace_bytes(uint32_t n_states, uint32_t max_rays) {
   if (n_states == 0 || n_states > kMaxBatchStates || max_rays == 0) return 0;
   return batch_layout(n_states, max_rays).total;

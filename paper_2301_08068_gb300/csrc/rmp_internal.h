@@ -151,6 +151,7 @@ int raycast_occupancy(const DevMap& m, int reduce_mode, int block);   // CTAs pe
 cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,
                            void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
                            float* per_ray, int block, int grid, cudaStream_t stream);
+int ctx_device(const rmp_ctx* ctx);                                  // CUDA device of a context
 int batch_occupancy(const DevMap& m, int reduce_mode, int block);     // CTAs per SM
 // Prep kernel + persistent batch kernel; n_rays_dev / states_dev on the device.
 cudaError_t launch_batch(const DevMap& m, const EvalConsts& k, const double* states_dev,

@@ -24,6 +24,7 @@ RMP_OK, RMP_ERR_INVALID_ARG = 0, 1
 STATUS_NAMES = {0: "RMP_OK", 1: "RMP_ERR_INVALID_ARG", 2: "RMP_ERR_NO_MEMORY", 3: "RMP_ERR_CUDA",
                 4: "RMP_ERR_TIMEOUT", 5: "RMP_ERR_BUSY", 6: "RMP_ERR_UNKNOWN_MAP",
                 7: "RMP_ERR_NOT_READY"}
+STATUS_CODES = {v: k for k, v in STATUS_NAMES.items()}
 RMP_RAY_HIT, RMP_RAY_MISS_RANGE, RMP_RAY_MISS_EXIT = 1, 2, 3
 RMP_MAP_DENSE_U8, RMP_MAP_HASHED_TSDF = 0, 1
 RMP_PRESET_STATIC_MAP, RMP_PRESET_LIDAR = 0, 1
@@ -66,6 +67,17 @@ class rmp_launch_info_t(C.Structure):
                                          "smem_bytes", "ray_cells", "reserved")]
 
 
+class rmp_server_config_t(C.Structure):
+    _fields_ = [("slots", C.c_uint32), ("max_batch_states", C.c_uint32), ("max_rays", C.c_uint32),
+                ("reserved", C.c_uint32), ("mem_budget_bytes", C.c_uint64)]
+
+
+class rmp_server_stats_t(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "rejected", "batches",
+                                          "batched_states", "pending", "max_inflight",
+                                          "mem_high_water")]
+
+
 class rmp_map_info_t(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_bricks", C.c_uint32), ("hash_capacity", C.c_uint32),
                 ("layout", C.c_uint32), ("device_bytes", C.c_uint64)]
@@ -102,6 +114,14 @@ _SIGNATURES = {
                                      C.POINTER(rmp_params_t), _P, C.c_size_t, _P, _P, _P, _P],
     "rmp_raycast_eval_batch": [_P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(rmp_params_t), _P,
                                _P],
+    "rmp_server_config_default": [C.POINTER(rmp_server_config_t)],
+    "rmp_server_create": [_P, C.POINTER(rmp_server_config_t), C.POINTER(C.c_void_p)],
+    "rmp_server_destroy": [_P],
+    "rmp_server_submit": [_P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(rmp_params_t),
+                          C.POINTER(C.c_uint64)],
+    "rmp_server_poll": [_P, C.c_uint64, C.POINTER(rmp_result_t), C.POINTER(C.c_double)],
+    "rmp_server_wait": [_P, C.c_uint64, C.c_uint32, C.POINTER(rmp_result_t), C.POINTER(C.c_double)],
+    "rmp_server_stats": [_P, C.POINTER(rmp_server_stats_t)],
     "rmp_batch_autotune": [_P, C.c_uint32, _P, _P, C.c_uint32, C.c_uint32, C.POINTER(rmp_params_t),
                            _P, C.c_size_t, _P, _P, C.c_int, _P, C.c_int],
 }
@@ -375,6 +395,88 @@ def hashed_desc(keys, tsdf, voxel_size: float) -> rmp_map_desc_t:
         d.block_keys = _dptr(keys)
         d.tsdf = _dptr(tsdf)
     return d
+
+
+def rmp_server_config_default() -> rmp_server_config_t:
+    cfg = rmp_server_config_t()
+    _check(lib().rmp_server_config_default(C.byref(cfg)), "rmp_server_config_default")
+    return cfg
+
+
+def rmp_server_create(ctx: int, cfg: rmp_server_config_t) -> int:
+    h = C.c_void_p()
+    _check(lib().rmp_server_create(ctx, C.byref(cfg), C.byref(h)), "rmp_server_create")
+    return h.value
+
+
+def rmp_server_destroy(server: int):
+    _check(lib().rmp_server_destroy(server), "rmp_server_destroy")
+
+
+def rmp_server_submit(server: int, map_id: int, x, xdot, n_rays: int, params: rmp_params_t) -> int:
+    t = C.c_uint64()
+    _check(lib().rmp_server_submit(server, int(map_id), _vec3(x), _vec3(xdot), int(n_rays),
+                                   C.byref(params), C.byref(t)), "rmp_server_submit")
+    return int(t.value)
+
+
+def rmp_server_poll(server: int, ticket: int):
+    """(result dict, latency s) or None if not ready."""
+    out = rmp_result_t()
+    lat = C.c_double()
+    st = lib().rmp_server_poll(server, int(ticket), C.byref(out), C.byref(lat))
+    if st == 7:                               # RMP_ERR_NOT_READY
+        return None
+    _check(st, "rmp_server_poll")
+    return result_dict(out), float(lat.value)
+
+
+def rmp_server_wait(server: int, ticket: int, timeout_ms: int = 10000):
+    out = rmp_result_t()
+    lat = C.c_double()
+    _check(lib().rmp_server_wait(server, int(ticket), int(timeout_ms), C.byref(out), C.byref(lat)),
+           "rmp_server_wait")
+    return result_dict(out), float(lat.value)
+
+
+def rmp_server_stats(server: int) -> dict:
+    st = rmp_server_stats_t()
+    _check(lib().rmp_server_stats(server, C.byref(st)), "rmp_server_stats")
+    return {n: int(getattr(st, n)) for n, _ in rmp_server_stats_t._fields_}
+
+
+class Server:
+    """Owns one rmp_server (continuous-batching request server) of a Context."""
+
+    def __init__(self, ctx: "Context", slots: int = 4, max_batch_states: int = 256,
+                 max_rays: int = 262144, mem_budget_bytes: int = 1 << 30):
+        cfg = rmp_server_config_default()
+        cfg.slots, cfg.max_batch_states, cfg.max_rays = slots, max_batch_states, max_rays
+        cfg.mem_budget_bytes = mem_budget_bytes
+        self.handle = rmp_server_create(ctx.handle, cfg)
+
+    def submit(self, map_id, x, xdot, n_rays, params) -> int:
+        return rmp_server_submit(self.handle, map_id, x, xdot, n_rays, params)
+
+    def poll(self, ticket):
+        return rmp_server_poll(self.handle, ticket)
+
+    def wait(self, ticket, timeout_ms: int = 10000):
+        return rmp_server_wait(self.handle, ticket, timeout_ms)
+
+    def stats(self) -> dict:
+        return rmp_server_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            rmp_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Context:

@@ -57,6 +57,9 @@ int main(void) {
   O(rmp_map_desc_t, voxel_size); O(rmp_map_desc_t, dims); O(rmp_map_desc_t, n_blocks);
   O(rmp_map_desc_t, occ); O(rmp_map_desc_t, tsdf); O(rmp_map_info_t, device_bytes);
   O(rmp_map_info_t, layout); O(rmp_launch_info_t, ctas_per_sm); O(rmp_launch_info_t, ray_cells);
+  printf("\\"rmp_server_config_t\\": %zu, \\"rmp_server_stats_t\\": %zu,\\n",
+         sizeof(rmp_server_config_t), sizeof(rmp_server_stats_t));
+  O(rmp_server_config_t, mem_budget_bytes); O(rmp_server_stats_t, max_inflight);
   printf("\\"end\\": 0}\\n");
   return 0;
 }
@@ -65,7 +68,7 @@ int main(void) {
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
     got = json.loads(subprocess.check_output([str(exe)]))
     for T in ("rmp_params_t", "rmp_result_t", "rmp_ray_hit_t", "rmp_map_desc_t", "rmp_map_info_t",
-              "rmp_launch_info_t"):
+              "rmp_launch_info_t", "rmp_server_config_t", "rmp_server_stats_t"):
         assert C.sizeof(getattr(rmp, T)) == got[T], T
     for key, off in got.items():
         if "." in key:
@@ -126,3 +129,12 @@ def test_null_arguments_rejected_without_gpu(rmp):
     assert L.rmp_raycast_eval_batch(None, 1, None, None, 1, None, None, None) == 1
     assert L.rmp_batch_autotune(None, 1, None, None, 1, 1, None, None, 0, None, None, 1, None,
                                 0) == 1
+    assert L.rmp_server_create(None, None, None) == 1
+    assert L.rmp_server_destroy(None) == 1
+    assert L.rmp_server_submit(None, 1, None, None, 1, None, None) == 1
+    assert L.rmp_server_poll(None, 1, None, None) == 1
+    assert L.rmp_server_wait(None, 1, 0, None, None) == 1
+    assert L.rmp_server_stats(None, None) == 1
+    cfg = rmp.rmp_server_config_default()
+    assert (cfg.slots, cfg.max_batch_states, cfg.max_rays, cfg.mem_budget_bytes) == \
+        (4, 256, 262144, 1 << 30)
