@@ -268,6 +268,25 @@ int rmp_batch_autotune(rmp_ctx* ctx, uint32_t map_id, const double* states_dev,
                        rmp_stream_t stream, rmp_result_t* out_dev, int reps, float* times_ms,
                        int n_times);
 
+/* Batched evaluation without caller-provided memory (no counterpart in the paper: a
+ * deployment form of rmp_raycast_eval_batch_async).  The workspace is a 4 MiB array owned
+ * by the library on each device, so the call allocates nothing and needs no workspace
+ * argument -- for callers that must not allocate device memory after start-up, such as a
+ * control loop with a fixed memory footprint (cudaMalloc may synchronise the device and
+ * has no bounded latency).  Per-ray outputs are not offered.
+ * Limit: batches whose workspace (rmp_batch_workspace_bytes(n_states, max_rays)) exceeds
+ * 4 MiB are rejected with RMP_ERR_NO_MEMORY (one state of up to 406016 rays, or up to six
+ * states of 65536).  Nothing in the array has to start at zero: each call's set-up kernel clears
+ * what it uses.  The first call on a device looks up the array's address with that device
+ * current (which can load module data), so make one call before any stream capture.
+ * All calls on a device share the one array: calls that may overlap in time (different
+ * streams without ordering, other threads) race on it and give wrong results; order them
+ * on one stream or synchronise between them. */
+int rmp_raycast_eval_batch_static(rmp_ctx* ctx, uint32_t map_id, const double* states_dev,
+                                  const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
+                                  const rmp_params_t* params, rmp_stream_t stream,
+                                  rmp_result_t* out_dev);
+
 /* ------------------------------------------------------------------ request server
  * Continuous batching of single-state requests (a serving layer over the batched
  * evaluation; the paper evaluates one state per control step and has no counterpart).

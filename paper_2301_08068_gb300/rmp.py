@@ -114,6 +114,8 @@ _SIGNATURES = {
                                      C.POINTER(rmp_params_t), _P, C.c_size_t, _P, _P, _P, _P],
     "rmp_raycast_eval_batch": [_P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(rmp_params_t), _P,
                                _P],
+    "rmp_raycast_eval_batch_static": [_P, C.c_uint32, _P, _P, C.c_uint32, C.c_uint32,
+                                      C.POINTER(rmp_params_t), _P, _P],
     "rmp_server_config_default": [C.POINTER(rmp_server_config_t)],
     "rmp_server_create": [_P, C.POINTER(rmp_server_config_t), C.POINTER(C.c_void_p)],
     "rmp_server_destroy": [_P],
@@ -311,6 +313,16 @@ def rmp_raycast_eval_batch_async(ctx: int, map_id: int, states, n_rays, n_states
         ctx, int(map_id), _dptr(states), _dptr(n_rays), int(n_states), int(max_rays),
         C.byref(params), _dptr(workspace), workspace.numel() * workspace.element_size(),
         _stream(stream), _dptr(out), _dptr(hits), _dptr(per_ray)), "rmp_raycast_eval_batch_async")
+
+
+def rmp_raycast_eval_batch_static(ctx: int, map_id: int, states, n_rays, n_states: int,
+                                  max_rays: int, params: rmp_params_t, out, stream=None):
+    """As rmp_raycast_eval_batch_async with the library's static device scratch (no
+    workspace argument; batches up to 4 MiB of workspace)."""
+    _check(lib().rmp_raycast_eval_batch_static(ctx, int(map_id), _dptr(states), _dptr(n_rays),
+                                               int(n_states), int(max_rays), C.byref(params),
+                                               _stream(stream), _dptr(out)),
+           "rmp_raycast_eval_batch_static")
 
 
 def rmp_raycast_eval_batch(ctx: int, map_id: int, states, n_rays, params: rmp_params_t,
