@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched and served sections (rank 0, N=1 only)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="length of the Poisson request stream of the served section")
     return ap.parse_args()
 
 
@@ -164,6 +168,154 @@ def measured_peak_hbm():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def timed_device(fn, flush, reps: int):
+    """Median CUDA-event time (ms) of fn() over `reps` runs, L2 flushed before each."""
+    import torch
+    for i in range(3):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for i in range(reps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record()
+        fn()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in ev]))
+
+
+def batch_section(ctx, mid, flush) -> dict:
+    """Batched evaluation: 256 states over the same hashed map with ray counts drawn
+    log-uniform in [4096, 65536]; autotuned launch, captured once in a CUDA graph and
+    replayed; against the plain single-state kernel called once per state; both
+    reductions (compensated FP32, FP64)."""
+    import torch
+    from paper_2301_08068_gb300 import rmp as R, workloads as W
+    wl = W.hashed_workload(n_states=256, uneven_rays=(4096, 65536))
+    counts = np.asarray(wl.n_rays, np.int32)
+    B, mr = len(counts), int(counts.max())
+    st = torch.tensor(np.stack([np.concatenate([s.x, s.xdot]) for s in wl.states]),
+                      dtype=torch.float64, device="cuda")
+    nr = torch.tensor(counts, device="cuda")
+    ws = torch.empty(R.rmp_batch_workspace_bytes(B, mr), dtype=torch.uint8, device="cuda")
+    out = torch.empty((B, R.RESULT_BYTES), dtype=torch.uint8, device="cuda")
+    knobs = [R.rmp_tune_get(ctx.handle, k) for k in (1, 2, 4)]
+    res = {"workload": "256 states on the hashed 40x40x10 m map, rays log-uniform in "
+                       "[4096, 65536] (total %d)" % int(counts.sum())}
+    try:
+        for mode, name in ((0, "kahan_fp32"), (1, "fp64")):
+            p = R.make_params(dict(wl.params, reduce_mode=mode), wl.max_range)
+            times = R.rmp_batch_autotune(ctx.handle, mid, st, nr, B, mr, p, ws, out, reps=3)
+            tuned = {"block": R.rmp_tune_get(ctx.handle, 1),
+                     "lg_segments": R.rmp_tune_get(ctx.handle, 2),
+                     "split_budget": R.rmp_tune_get(ctx.handle, 4)}
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                R.rmp_raycast_eval_batch_async(ctx.handle, mid, st, nr, B, mr, p, ws, out)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                R.rmp_raycast_eval_batch_async(ctx.handle, mid, st, nr, B, mr, p, ws, out)
+            ms = timed_device(g.replay, flush, 20)
+            res[name] = {"ms_per_batch": ms, "Grays_per_s": float(counts.sum()) / ms / 1e6,
+                         "evals_per_s": B / ms * 1e3, "tuned": tuned,
+                         "autotune_ms": [round(t, 4) for t in times]}
+        # the plain single-state kernel, one launch per state, same states and counts
+        R.rmp_tune_set(ctx.handle, 1, 128)
+        R.rmp_tune_set(ctx.handle, 2, -1)
+        R.rmp_tune_set(ctx.handle, 4, -1)
+        p = R.make_params(wl.params, wl.max_range)
+        wss = torch.empty(R.rmp_workspace_bytes(), dtype=torch.uint8, device="cuda")
+        R.rmp_workspace_init(wss)
+        outs = torch.empty((B, R.RESULT_BYTES), dtype=torch.uint8, device="cuda")
+
+        def loop():
+            for b in range(B):
+                R.rmp_raycast_eval_async(ctx.handle, mid, st[b], int(counts[b]), p, wss, outs[b])
+        ms = timed_device(loop, flush, 5)
+        res["plain_per_state"] = {"ms_per_batch": ms,
+                                  "Grays_per_s": float(counts.sum()) / ms / 1e6,
+                                  "evals_per_s": B / ms * 1e3}
+        res["speedup_vs_plain"] = res["plain_per_state"]["ms_per_batch"] / \
+            res["kahan_fp32"]["ms_per_batch"]
+    finally:
+        for k, v in zip((1, 2, 4), knobs):
+            R.rmp_tune_set(ctx.handle, k, v)
+    return res
+
+
+def serve_section(ctx, seconds: float) -> dict:
+    """Served: a Poisson stream (20k requests/s) over three device-resident maps (dense
+    128^3 at 0.05 m, hashed 40x40x10 m at 0.1 m, hashed 100x100x20 m at 0.2 m; max range
+    10 m) with requests of 1024..262144 rays (log-uniform), fed in real time to the
+    continuous-batching server (256 MiB device-memory budget), and the same stream served
+    by the plain kernel one request at a time (FIFO); latency = completion - arrival."""
+    from paper_2301_08068_gb300 import rmp as R, workloads as W
+    wls = [W.dense_box_workload(n_states=64, dims=(128, 128, 128), vs=0.05, n_boxes=40,
+                                max_range=10.0, seed_index=6),
+           W.hashed_workload(n_states=64, state_seed_index=7),
+           W.hashed_workload(n_states=64, extent=(100.0, 100.0, 20.0), vs=0.2, n_prims=2500,
+                             seed_index=5, state_seed_index=8)]
+    mids = [ctx.upload(w.map) for w in wls]
+    params = [R.make_params(w.params, w.max_range) for w in wls]
+    t_arr, maps, rays, vel = W.poisson_requests(3, 20000.0, seconds, 1024, 262144)
+    n = len(t_arr)
+    reqs = []
+    for i in range(n):
+        w = wls[maps[i]]
+        s = w.states[i % len(w.states)]
+        reqs.append((int(maps[i]), s.x, vel[i], int(rays[i])))
+    total_rays = float(np.sum(rays))
+
+    def pct(lat):
+        return {"p50_ms": float(np.percentile(lat, 50)) * 1e3,
+                "p99_ms": float(np.percentile(lat, 99)) * 1e3,
+                "mean_ms": float(np.mean(lat)) * 1e3}
+
+    out = {"workload": "Poisson 20000 req/s for %.2f s (%d requests, %.3g rays), 3 maps, "
+                       "1024..262144 rays log-uniform" % (seconds, n, total_rays)}
+    # warm both paths
+    with R.Server(ctx, slots=4, max_batch_states=256, max_rays=262144,
+                  mem_budget_bytes=256 << 20) as srv:
+        for m in range(3):
+            srv.wait(srv.submit(mids[m], wls[m].states[0].x, wls[m].states[0].xdot, 4096,
+                                params[m]))
+        tickets = []
+        t0 = time.perf_counter()
+        for i, (m, x, v, r) in enumerate(reqs):
+            while time.perf_counter() - t0 < t_arr[i]:
+                pass
+            tickets.append(srv.submit(mids[m], x, v, r, params[m]))
+        lat = []
+        for t in tickets:
+            res, l = srv.wait(t, 60000)
+            assert res["status"] == 0
+            lat.append(l)
+        span = time.perf_counter() - t0
+        st = srv.stats()
+    out["served"] = dict(pct(lat), Grays_per_s=total_rays / span / 1e9, makespan_s=span,
+                         batches=st["batches"], mean_batch=st["batched_states"] / max(1, st["batches"]),
+                         max_inflight=st["max_inflight"], mem_high_water=st["mem_high_water"])
+    # the plain kernel, one request at a time in arrival order
+    for m in range(3):
+        R.rmp_raycast_eval(ctx.handle, mids[m], wls[m].states[0].x, wls[m].states[0].xdot, 4096,
+                           params[m])
+    lat = []
+    t0 = time.perf_counter()
+    for i, (m, x, v, r) in enumerate(reqs):
+        while time.perf_counter() - t0 < t_arr[i]:
+            pass
+        res = R.rmp_raycast_eval(ctx.handle, mids[m], x, v, r, params[m])
+        lat.append(time.perf_counter() - t0 - t_arr[i])
+    span = time.perf_counter() - t0
+    out["plain_per_request"] = dict(pct(lat), Grays_per_s=total_rays / span / 1e9,
+                                    makespan_s=span)
+    for m in mids:
+        R.rmp_map_release(ctx.handle, m)
+    return out
 
 
 def run_reference(args):
@@ -310,6 +462,11 @@ def main():
                "sample": "%d full evaluations (65536 rays each) of the workload's states, "
                          "single-threaded C oracle, %.1f s" % (n, secs)}
 
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra["batched"] = batch_section(ctx, mid, flush)
+        extra["served"] = serve_section(ctx, args.serve_seconds)
+
     src = kernel_source_hash()
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (ms / 1e3) / 1e9
@@ -340,6 +497,7 @@ def main():
                          "kernel_source_sha256_16": src},
             "cpu_baseline": cpu,
             "gpu_launches": args.steps,
+            **extra,
             "clocks": clk,
             "paper_context": {"value": PAPER_RATE, "unit": UNIT,
                               "note": "65536 rays at up to 3 kHz (abstract), unnamed GPU of "
