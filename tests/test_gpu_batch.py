@@ -222,3 +222,36 @@ def test_batch_autotuner(ctx, hashed):
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 128)
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, -1)
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_SPLIT_BUDGET, -1)
+
+
+def test_batch_precision_kahan_vs_fp64_per_state(ctx, hashed, capsys):
+    """Config-4 states (rays log-uniform in [4096, 65536]): per-state error of sum A,
+    sum A f and the resolved f against the FP64 oracle, compensated FP32 against FP64
+    reduction (printed as a table; both within the stated tolerances)."""
+    wl, mid, om = hashed
+    w4 = W.hashed_workload(n_states=256, uneven_rays=(4096, 65536))
+    states, counts = w4.states[:16], np.asarray(w4.n_rays[:16], np.uint32)
+    po = O.make_params(wl.params, wl.max_range)
+    sv = np.stack([np.concatenate([s.x, s.xdot]) for s in states])
+    runs = {}
+    for mode in (0, 1):
+        pg = R.make_params(dict(wl.params, reduce_mode=mode), wl.max_range)
+        runs[mode] = run_batch(ctx, mid, sv, counts, pg, want=False)[0]
+    rows = []
+    for b, s in enumerate(states):
+        ro, _, por = O.raycast_eval(om, s.x, s.xdot, int(counts[b]), po, want_hits=False)
+        row = [b, int(counts[b])]
+        for mode in (0, 1):
+            g = runs[mode][b]
+            assert_result_close(g, ro, por)
+            eA = np.abs(g["sumA"] - ro["sumA"]).max() / max(np.abs(ro["sumA"]).max(), 1e-300)
+            eAf = np.abs(g["sumAf"] - ro["sumAf"]).max() / max(np.abs(ro["sumAf"]).max(), 1e-300)
+            ef = np.linalg.norm(g["f"] - ro["f"]) / max(np.linalg.norm(ro["f"]), 1e-300)
+            row += [eA, eAf, ef]
+        rows.append(row)
+    with capsys.disabled():
+        print("\nstate rays | kahan32: sumA sumAf f | fp64: sumA sumAf f  (relative to the FP64 oracle)")
+        for r in rows:
+            print("%5d %6d | %.1e %.1e %.1e | %.1e %.1e %.1e" % tuple(r))
+        a = np.array([r[2:] for r in rows])
+        print("max        | %.1e %.1e %.1e | %.1e %.1e %.1e" % tuple(a.max(axis=0)))
