@@ -263,6 +263,49 @@ def batch_section(ctx, mid, flush) -> dict:
     return res
 
 
+def lidar_section(ctx, flush) -> dict:
+    """LiDAR variant (config 3): a 64 x 1024 scan (65536 points, FP32, sensor frame), one
+    fused launch per scan (per-point policy, reduction, FP64 resolve).  It is launch- and
+    latency-bound, so it is reported against the same kernel's floor: a one-point scan."""
+    import torch
+    from paper_2301_08068_gb300 import rmp as R, workloads as W
+    sw = W.lidar_workload()
+    p = R.make_params(sw.params, sw.max_range)
+    pts = torch.from_numpy(np.ascontiguousarray(sw.points, np.float32)).cuda()
+    st = torch.tensor(np.concatenate([sw.x, sw.xdot]), dtype=torch.float64, device="cuda")
+    ws = torch.empty(R.rmp_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    R.rmp_workspace_init(ws)
+    out = torch.empty(R.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ms = timed_device(lambda: R.rmp_scan_eval_async(ctx.handle, pts, st, p, ws, out), flush, 200)
+    one = pts[:1].contiguous()
+    ms1 = timed_device(lambda: R.rmp_scan_eval_async(ctx.handle, one, st, p, ws, out), flush, 200)
+    n = int(pts.shape[0])
+    return {"workload": "64 x 1024 scan (65536 points), Table I LiDAR params",
+            "ms_per_scan": ms, "evals_per_s": 1e3 / ms, "Gpoints_per_s": n / ms / 1e6,
+            "floor_ms_one_point": ms1, "frac_of_floor": ms1 / ms}
+
+
+def l2_probe(flush) -> float:
+    """L2 bandwidth probe (GB/s): repeated device copies of a 24 MiB buffer pair, which
+    stays resident in the 129 MB L2; bytes = read + write."""
+    import torch
+    a = torch.empty(24 << 20, dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    a.fill_(1)
+    for _ in range(5):
+        b.copy_(a)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 200
+    e0.record()
+    for _ in range(reps):
+        b.copy_(a)
+    e1.record()
+    torch.cuda.synchronize()
+    return 2.0 * a.numel() * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
 def serve_section(ctx, seconds: float) -> dict:
     """Served: a Poisson stream (20k requests/s) over three device-resident maps (dense
     128^3 at 0.05 m, hashed 40x40x10 m at 0.1 m, hashed 100x100x20 m at 0.2 m; max range
@@ -475,6 +518,7 @@ def main():
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:
+        extra["lidar"] = lidar_section(ctx, flush)
         extra["batched"] = batch_section(ctx, mid, flush)
         extra["served"] = serve_section(ctx, args.serve_seconds)
 
@@ -482,6 +526,7 @@ def main():
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (ms / 1e3) / 1e9
     traffic = committed_traffic(src)
+    l2_gbs = l2_probe(flush) if rank == 0 else None
     if rank == 0:
         value = whole_job_rate(world, N_RAYS, ms_max)
         line = {
@@ -503,6 +548,9 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,
                          "algorithmic_bytes_per_launch": alg_bytes,
+                         "l2": {"achieved": achieved, "peak_probe": l2_gbs, "unit": "GB/s",
+                                "frac": achieved / l2_gbs if l2_gbs else None,
+                                "probe": "24 MiB device-to-device copies resident in L2"},
                          "kernel": "raycast_rmp_kernel<hashed TSDF, grid layout, "
                                    "compensated FP32 reduction>",
                          "kernel_source_sha256_16": src},
