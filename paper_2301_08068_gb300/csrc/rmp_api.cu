@@ -690,8 +690,9 @@ int batch_setup(rmp_ctx* c, uint32_t map_id, uint32_t n_states, uint32_t max_ray
   }
   int st = make_consts(params, dm->vs, max_rays, false, k, t);
   if (st != RMP_OK) return st;
-  // many states fill the device without segmenting rays; one state uses the single-state rule
-  if (t.lg_segs < 0 && n_states > 1) k->lg_segs = 0;
+  // segments per ray: a fixed tuned value for every state, or (default) the single-state
+  // rule applied per state by the prep kernel
+  if (t.lg_segs < 0) k->lg_segs = 0xffffffffu;
   const int occ = batch_occupancy(*dm, k->reduce_mode, *block);
   if (occ <= 0) return RMP_ERR_CUDA;
   *grid = c->sm_count * occ;

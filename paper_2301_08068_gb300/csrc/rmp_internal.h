@@ -96,7 +96,7 @@ inline size_t workspace_bytes() {
 
 // ------------------------------------------------------------------ batched evaluation
 // Work of a batch is cut into chunks of 32 threads (32 / S rays of one state, S segments
-// per ray) that the warps of a persistent grid take from a counter.  Each chunk stores a
+// per ray, S chosen per state) that the warps of a persistent grid take from a counter.  Each chunk stores a
 // partial; kBatchGroup consecutive chunks of a state form a group (the last chunk of a
 // group to finish sums them), and the last group of a state sums the groups and resolves.
 constexpr uint32_t kBatchGroup = 32;
@@ -107,7 +107,8 @@ struct BatchState {         // 80 bytes, written by the prep kernel
   long long P[3];           // quantised position (2^-16 voxels)
   float v[3], vl[3];        // velocity as an FP32 pair
   uint32_t n_rays, chunk0, n_chunks, group0;
-  uint32_t perm_M, perm_Q, perm_R;
+  uint32_t perm_M, perm_Q;  // direction cells (the remainder n_rays - perm_Q perm_M is derived)
+  uint32_t lg_segs;         // log2 segments per ray of this state
   int status;               // RMP_OK or RMP_ERR_INVALID_ARG
 };
 

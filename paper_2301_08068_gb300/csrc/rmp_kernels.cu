@@ -1126,8 +1126,8 @@ __device__ __forceinline__ bool bulk_load_wait(uint64_t* bar) {
 template <int KIND, int LAYOUT>
 __device__ __forceinline__ int march_ray(const DevMap& m, const uint32_t* bm, const EvalConsts& k,
                                          const long long P[3], const Ray& ray, uint32_t seg,
-                                         bool work, MarchState& mo) {
-  const uint32_t lgS = k.lg_segs, S = 1u << lgS;
+                                         uint32_t lgS, bool work, MarchState& mo) {
+  const uint32_t S = 1u << lgS;
   const uint32_t lane = threadIdx.x & 31;
   // this lane's piece: segment seg of the ray, grid points j_lo .. j_hi
   const uint32_t j_lo = seg << (kGridLog - lgS), j_hi = (seg + 1) << (kGridLog - lgS);
@@ -1273,7 +1273,7 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
     first = false;
     const long long P[3] = {cs.P[0], cs.P[1], cs.P[2]};
     MarchState mo;
-    const int mstat = march_ray<KIND, LAYOUT>(m, bm, k, P, ray, seg, active && !bad, mo);
+    const int mstat = march_ray<KIND, LAYOUT>(m, bm, k, P, ray, seg, lgS, active && !bad, mo);
     if (!active || bad || seg != 0) continue;
     float vals[9];
     ray_outputs(m, k, P, ray, mo, mstat, cs.v, cs.vl, hits ? hits + ray_idx : nullptr,
@@ -1367,7 +1367,6 @@ __global__ void __launch_bounds__(1024) batch_prep_kernel(
   __shared__ uint32_t wsum_c[32], wsum_g[32];
   __shared__ uint32_t carry_c, carry_g;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const uint32_t S = 1u << k.lg_segs;
   if (tid == 0) {
     carry_c = 0;
     carry_g = 0;
@@ -1401,13 +1400,18 @@ __global__ void __launch_bounds__(1024) batch_prep_kernel(
         sp->vl[lane - 3] = vla;
       }
       if (lane == 0) {
-        const uint32_t chunks = (!bad && n > 0) ? (n * S + 31) / 32 : 0u;
+        // segments per ray: the launch's fixed choice, or the single-state rule applied to
+        // this state's own ray count -- either way a function of the state alone, so its
+        // result does not depend on the other states of the batch or their order
+        const uint32_t lg = k.lg_segs <= 2u ? k.lg_segs
+                                            : (n <= 4096u ? 2u : (n <= 16384u ? 1u : 0u));
+        const uint32_t chunks = (!bad && n > 0) ? ((n << lg) + 31) / 32 : 0u;
         sp->n_rays = n;
         sp->status = bad ? RMP_ERR_INVALID_ARG : RMP_OK;
         sp->n_chunks = chunks;
         sp->perm_M = M;
         sp->perm_Q = n / M;
-        sp->perm_R = n - (n / M) * M;
+        sp->lg_segs = lg;
         s_chunks[j] = chunks;
         s_groups[j] = (chunks + kBatchGroup - 1) / kBatchGroup;
       }
@@ -1526,7 +1530,6 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
   const uint32_t* bm = (staged && !bm_timeout) ? reinterpret_cast<const uint32_t*>(smem_radius)
                                                : m.radius;
   const uint32_t lane = threadIdx.x & 31;
-  const uint32_t lgS = k.lg_segs, S = 1u << lgS;
   const uint32_t total = *(volatile const uint32_t*)&hdr->total_chunks;
   const uint32_t nst = *(volatile const uint32_t*)&hdr->n_states;
   // first chunk: the warp's index in the grid; later ones from the counter (offset by the
@@ -1553,14 +1556,15 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
     const uint32_t n_b = __ldg(&sp->n_rays), chunk0 = __ldg(&sp->chunk0);
     const uint32_t n_chunks = __ldg(&sp->n_chunks), group0 = __ldg(&sp->group0);
     const uint32_t q = c - chunk0;
+    const uint32_t lgS = __ldg(&sp->lg_segs), S = 1u << lgS;
     const uint32_t g = q * 32 + lane;
     const uint32_t slot = g >> lgS, seg = g & (S - 1);
     const bool active = slot < n_b;
-    const uint32_t ray_idx = ray_of_slot_p(active ? slot : 0, __ldg(&sp->perm_M),
-                                           __ldg(&sp->perm_Q), __ldg(&sp->perm_R));
+    const uint32_t pM = __ldg(&sp->perm_M), pQ = __ldg(&sp->perm_Q);
+    const uint32_t ray_idx = ray_of_slot_p(active ? slot : 0, pM, pQ, n_b - pQ * pM);
     const Ray ray = make_ray(ray_idx + k.halton_offset);
     MarchState mo;
-    const int mstat = march_ray<KIND, LAYOUT>(m, bm, k, P, ray, seg, active, mo);
+    const int mstat = march_ray<KIND, LAYOUT>(m, bm, k, P, ray, seg, lgS, active, mo);
     float vals[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     unsigned nh = 0, na = 0;
     if (active && seg == 0) {

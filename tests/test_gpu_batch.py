@@ -132,6 +132,27 @@ def test_batch_deterministic_and_sync_form(ctx, hashed):
             assert np.array_equal(x[key], y[key]) and np.array_equal(x[key], z[key])
 
 
+def test_batch_results_independent_of_order_and_company(ctx, hashed):
+    """A state's result depends on that state alone: bitwise the same alone, in a batch, and
+    in a permuted batch (segments per ray chosen per state, chunks and groups per state,
+    fixed summation order)."""
+    wl, mid, om = hashed
+    pg = R.make_params(wl.params, wl.max_range)
+    counts = np.array([3000, 65536, 777, 20000, 4096, 12000, 1, 50000], np.uint32)
+    states = np.stack([np.concatenate([s.x, s.xdot]) for s in wl.states[:8]])
+    base = run_batch(ctx, mid, states, counts, pg, want=False)[0]
+    perm = np.random.default_rng(3).permutation(8)
+    permuted = run_batch(ctx, mid, states[perm], counts[perm], pg, want=False)[0]
+    keys = ("f", "sumA", "sumAf", "eig")
+    for j, b in enumerate(perm):
+        for key in keys:
+            assert np.array_equal(permuted[j][key], base[b][key]), (b, key)
+    for b in (0, 1, 6):
+        alone = run_batch(ctx, mid, states[b:b + 1], counts[b:b + 1], pg, want=False)[0][0]
+        for key in keys:
+            assert np.array_equal(alone[key], base[b][key]), (b, key)
+
+
 def test_batch_invalid_states_are_isolated(ctx, hashed):
     wl, mid, om = hashed
     pg = R.make_params(wl.params, wl.max_range)

@@ -1,7 +1,7 @@
 """GPU tests of the continuous-batching request server: results against the CPU oracle,
-the same request alone and inside a mixed stream (identical hits statistics, values within
-the stated tolerances of each other and of the oracle), admission under a small
-device-memory budget, error completion, and concurrent submitters."""
+the same request alone and inside a mixed stream (within the stated tolerances of the
+oracle, and bitwise identical to each other), admission under a small device-memory
+budget, error completion, and concurrent submitters."""
 import threading
 
 import numpy as np
@@ -95,6 +95,8 @@ def test_server_same_result_alone_and_in_mix(env):
     assert_result_close(alone, ro, por)
     assert_result_close(mixed, ro, por)
     close_to_each_other(alone, mixed, por)
+    for key in ("f", "sumA", "sumAf", "eig"):              # and in fact bitwise identical
+        assert np.array_equal(alone[key], mixed[key]), key
 
 
 def test_server_memory_budget_admission(env):
