@@ -12,6 +12,8 @@ import os
 import subprocess
 import threading
 
+from typing import Optional
+
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -87,6 +89,10 @@ def lib():
                 "orc_pinv3": (None, [P, P, P, P]),
                 "orc_raycast_eval": (C.c_int, [P, P, P, C.c_uint32, P, P, P, P]),
                 "orc_scan_eval": (C.c_int, [P, C.c_uint32, P, P, P, P, P]),
+                "orc_attractor": (None, [P, P, P, C.c_double, C.c_double, C.c_double, P]),
+                "orc_combined_eval": (C.c_int, [P, P, P, C.c_uint32, P, P, C.c_double,
+                                                C.c_double, P]),
+                "orc_rollout_step": (None, [P, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -94,6 +100,22 @@ def lib():
                 fn.argtypes = args
             _lib = L
     return _lib
+
+
+class RolloutParams(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("dt", C.c_double),
+                ("goal_tol", C.c_double), ("max_steps", C.c_uint32), ("seg_steps", C.c_uint32),
+                ("n_rays", C.c_uint32), ("pad", C.c_uint32)]
+
+
+class RolloutState(C.Structure):
+    _fields_ = [("x", C.c_double * 3), ("xdot", C.c_double * 3), ("path_length", C.c_double),
+                ("smooth_sum", C.c_double), ("seg_start", C.c_double * 3),
+                ("prev_seg", C.c_double * 3), ("status", C.c_uint32), ("steps", C.c_uint32),
+                ("smooth_n", C.c_uint32), ("have_prev", C.c_uint32)]
+
+
+ROLL_RUNNING, ROLL_REACHED, ROLL_COLLIDED, ROLL_TIMEOUT, ROLL_LEFT_MAP = 0, 1, 2, 3, 4
 
 
 def _ptr(a: np.ndarray):
@@ -218,6 +240,69 @@ def pinv3(S6):
     rank = C.c_uint32(0)
     lib().orc_pinv3(_ptr(S), _ptr(P), _ptr(eig), C.byref(rank))
     return P, eig, int(rank.value)
+
+
+def attractor(x, xdot, goal, alpha: float, beta: float, c: float) -> np.ndarray:
+    """Attractor force f_a (Sec. III-B, Eq. attractorPolicy); its metric is I."""
+    xx = np.ascontiguousarray(x, np.float64)
+    xd = np.ascontiguousarray(xdot, np.float64)
+    g = np.ascontiguousarray(goal, np.float64)
+    fa = np.zeros(3)
+    lib().orc_attractor(_ptr(xx), _ptr(xd), _ptr(g), float(alpha), float(beta), float(c), _ptr(fa))
+    return fa
+
+
+def combined_eval(omap: "OracleMap", x, xdot, n_rays: int, params: Params, goal, alpha: float,
+                  beta: float) -> dict:
+    """Raycasting policy combined with the attractor by Eq. (1); sums include I and f_a."""
+    xx = np.ascontiguousarray(x, np.float64)
+    xd = np.ascontiguousarray(xdot, np.float64)
+    g = np.ascontiguousarray(goal, np.float64)
+    res = Result()
+    lib().orc_combined_eval(omap.ref, _ptr(xx), _ptr(xd), int(n_rays), C.byref(params), _ptr(g),
+                            float(alpha), float(beta), C.byref(res))
+    return _result(res)
+
+
+def rollout_params(alpha, beta, dt, goal_tol, max_steps, seg_steps, n_rays) -> RolloutParams:
+    rp = RolloutParams()
+    rp.alpha, rp.beta, rp.dt, rp.goal_tol = float(alpha), float(beta), float(dt), float(goal_tol)
+    rp.max_steps, rp.seg_steps, rp.n_rays = int(max_steps), int(seg_steps), int(n_rays)
+    return rp
+
+
+def rollout_state(x0, xdot0) -> RolloutState:
+    st = RolloutState()
+    for a in range(3):
+        st.x[a] = float(x0[a])
+        st.xdot[a] = float(xdot0[a])
+        st.seg_start[a] = float(x0[a])
+    return st
+
+
+def rollout_step(omap: "OracleMap", params: Params, rp: RolloutParams, goal, st: RolloutState):
+    g = np.ascontiguousarray(goal, np.float64)
+    lib().orc_rollout_step(omap.ref, C.byref(params), C.byref(rp), _ptr(g), C.byref(st))
+
+
+def rollout(omap: "OracleMap", params: Params, rp: RolloutParams, x0, xdot0, goal,
+            steps: Optional[int] = None, want_path: bool = False):
+    """Closed-loop rollout until the robot stops running (or `steps` steps); returns the
+    final state as a dict (and the positions after each step if want_path)."""
+    st = rollout_state(x0, xdot0)
+    path = []
+    n = rp.max_steps if steps is None else steps
+    for _ in range(n):
+        if st.status != ROLL_RUNNING:
+            break
+        rollout_step(omap, params, rp, goal, st)
+        if want_path:
+            path.append(np.array(st.x[:]))
+    out = dict(x=np.array(st.x[:]), xdot=np.array(st.xdot[:]), status=int(st.status),
+               steps=int(st.steps), path_length=float(st.path_length),
+               smoothness=float(st.smooth_sum / st.smooth_n) if st.smooth_n else 1.0,
+               smooth_n=int(st.smooth_n))
+    return (out, np.array(path)) if want_path else out
 
 
 def _result(res: Result) -> dict:

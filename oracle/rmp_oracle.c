@@ -557,6 +557,86 @@ int orc_scan_eval(const float* pts, uint32_t n, const double x[3], const double 
   return 0;
 }
 
+/* ------------------------------------------------------------------ attractor (Sec. III-B)
+ * f_a = alpha s(goal - x) - beta xdot, s(v) = v / (|v| + c log(1 + exp(-2c|v|))). */
+void orc_attractor(const double x[3], const double xdot[3], const double goal[3], double alpha,
+                   double beta, double c, double fa[3]) {
+  double v[3] = {goal[0] - x[0], goal[1] - x[1], goal[2] - x[2]};
+  double z = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  double h = z + c * log1p(exp(-2.0 * c * z));
+  for (int a = 0; a < 3; ++a) fa[a] = alpha * (v[a] / h) - beta * xdot[a];
+}
+
+/* Eq. (1) over the raycasting policy and the attractor (metric I). */
+int orc_combined_eval(const orc_map_t* m, const double x[3], const double xdot[3],
+                      uint32_t n_rays, const orc_params_t* p, const double goal[3],
+                      double alpha, double beta, orc_result_t* out) {
+  orc_raycast_eval(m, x, xdot, n_rays, p, out, NULL, NULL);
+  double fa[3];
+  orc_attractor(x, xdot, goal, alpha, beta, p->c, fa);
+  out->sumA[0] += 1.0;
+  out->sumA[3] += 1.0;
+  out->sumA[5] += 1.0;
+  for (int a = 0; a < 3; ++a) out->sumAf[a] += fa[a];
+  double P[6];
+  orc_pinv3(out->sumA, P, out->eig, &out->rank);
+  const double* b = out->sumAf;
+  out->f[0] = P[0] * b[0] + P[1] * b[1] + P[2] * b[2];
+  out->f[1] = P[1] * b[0] + P[3] * b[1] + P[4] * b[2];
+  out->f[2] = P[2] * b[0] + P[4] * b[1] + P[5] * b[2];
+  return 0;
+}
+
+/* ------------------------------------------------------------------ closed loop (Sec. IV-A)
+ * A point robot integrates the combined policy's acceleration. */
+void orc_rollout_step(const orc_map_t* m, const orc_params_t* p, const orc_rollout_params_t* rp,
+                      const double goal[3], orc_rollout_t* st) {
+  if (st->status != ORC_ROLL_RUNNING) return;
+  orc_result_t r;
+  orc_combined_eval(m, st->x, st->xdot, rp->n_rays, p, goal, rp->alpha, rp->beta, &r);
+  double xn[3], dl = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    st->xdot[a] = st->xdot[a] + r.f[a] * rp->dt;
+    xn[a] = st->x[a] + st->xdot[a] * rp->dt;
+    dl += (xn[a] - st->x[a]) * (xn[a] - st->x[a]);
+    st->x[a] = xn[a];
+  }
+  st->path_length += sqrt(dl);
+  st->steps += 1;
+  if (rp->seg_steps && st->steps % rp->seg_steps == 0) {
+    double seg[3];
+    for (int a = 0; a < 3; ++a) {
+      seg[a] = st->x[a] - st->seg_start[a];
+      st->seg_start[a] = st->x[a];
+    }
+    if (st->have_prev) {
+      double dot = 0, na = 0, nb = 0;
+      for (int a = 0; a < 3; ++a) {
+        dot += st->prev_seg[a] * seg[a];
+        na += st->prev_seg[a] * st->prev_seg[a];
+        nb += seg[a] * seg[a];
+      }
+      if (na > 0.0 && nb > 0.0) {
+        double cs = dot / (sqrt(na) * sqrt(nb));
+        cs = cs > 1.0 ? 1.0 : (cs < -1.0 ? -1.0 : cs);
+        st->smooth_sum += 1.0 - acos(cs) / 3.14159265358979323846;
+        st->smooth_n += 1;
+      }
+    }
+    for (int a = 0; a < 3; ++a) st->prev_seg[a] = seg[a];
+    st->have_prev = 1;
+  }
+  int64_t k[3];
+  for (int a = 0; a < 3; ++a)
+    k[a] = orc_quantize_pos(st->x[a], m->kind == 0 ? m->origin[a] : 0.0, m->voxel_size) >> 16;
+  double dg = 0.0;
+  for (int a = 0; a < 3; ++a) dg += (st->x[a] - goal[a]) * (st->x[a] - goal[a]);
+  if (m->kind == 0 && !inside_dense(m, k)) st->status = ORC_ROLL_LEFT_MAP;
+  else if (occupied(m, k)) st->status = ORC_ROLL_COLLIDED;
+  else if (sqrt(dg) < rp->goal_tol) st->status = ORC_ROLL_REACHED;
+  else if (st->steps >= rp->max_steps) st->status = ORC_ROLL_TIMEOUT;
+}
+
 /* ------------------------------------------------------------------ batch helpers (tests) */
 void orc_halton_batch(uint32_t n, uint32_t offset, float* u, float* v, uint32_t* num3) {
   for (uint32_t j = 0; j < n; ++j) {

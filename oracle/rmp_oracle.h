@@ -83,6 +83,44 @@ int orc_raycast_eval(const orc_map_t* m, const double x[3], const double xdot[3]
 int orc_scan_eval(const float* pts, uint32_t n, const double x[3], const double xdot[3],
                   const orc_params_t* p, orc_result_t* out, double* per_ray);
 
+/* Attractor policy (Sec. III-B, Eq. attractorPolicy): f_a = alpha s(goal - x) - beta xdot,
+ * A_a = I, with the soft normalisation s of Eq. softmax (parameter c). */
+void orc_attractor(const double x[3], const double xdot[3], const double goal[3], double alpha,
+                   double beta, double c, double fa[3]);
+
+/* Raycasting policy combined with the attractor by Eq. (1):
+ * f_c = (sum A + I)^+ (sum A f + f_a).  out->sumA / sumAf hold the combined sums
+ * (sum A + I, sum A f + f_a), out->eig and out->rank describe sum A + I. */
+int orc_combined_eval(const orc_map_t* m, const double x[3], const double xdot[3],
+                      uint32_t n_rays, const orc_params_t* p, const double goal[3],
+                      double alpha, double beta, orc_result_t* out);
+
+enum { ORC_ROLL_RUNNING = 0, ORC_ROLL_REACHED = 1, ORC_ROLL_COLLIDED = 2, ORC_ROLL_TIMEOUT = 3,
+       ORC_ROLL_LEFT_MAP = 4 };
+
+typedef struct {
+  double alpha, beta, dt, goal_tol;
+  uint32_t max_steps, seg_steps, n_rays, pad;
+} orc_rollout_params_t;
+
+typedef struct {
+  double x[3], xdot[3];
+  double path_length;    /* sum of the step lengths |x' - x| */
+  double smooth_sum;     /* sum of 1 - acos(cos angle)/pi over consecutive segments */
+  double seg_start[3], prev_seg[3];
+  uint32_t status, steps, smooth_n, have_prev;
+} orc_rollout_t;
+
+/* One closed-loop control step of a point robot: f = f_c(x, xdot); then
+ * xdot' = xdot + f dt, x' = x + xdot' dt (semi-implicit Euler).  Then, in this order:
+ * left the dense grid -> LEFT_MAP; the voxel holding x' is occupied -> COLLIDED;
+ * |x' - goal| < goal_tol -> REACHED; steps == max_steps -> TIMEOUT.  Every seg_steps
+ * steps the displacement since the last segment end is a segment; consecutive segments
+ * A, B add 1 - acos(A.B / (|A||B|)) / pi to smooth_sum.  No-op unless RUNNING.  A new
+ * state is all zero except x, xdot and seg_start = x. */
+void orc_rollout_step(const orc_map_t* m, const orc_params_t* p, const orc_rollout_params_t* rp,
+                      const double goal[3], orc_rollout_t* st);
+
 /* batch helpers used by the tests */
 void orc_halton_batch(uint32_t n, uint32_t offset, float* u, float* v, uint32_t* num3);
 void orc_sincos_batch(uint32_t n, const float* v, float* c, float* s);
