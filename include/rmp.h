@@ -287,6 +287,60 @@ int rmp_raycast_eval_batch_static(rmp_ctx* ctx, uint32_t map_id, const double* s
                                   const rmp_params_t* params, rmp_stream_t stream,
                                   rmp_result_t* out_dev);
 
+/* ------------------------------------------------------------------ attractor and closed loop
+ * The raycasting policy combined with a goal attractor (Sec. III-B Eq. attractorPolicy:
+ * f_a = alpha s(goal - x) - beta xdot with the soft normalisation s of Eq. softmax and
+ * parameter params->c, metric I) by Eq. (1): f_c = (sum A + I)^+ (sum A f + f_a).
+ * A result's A and Af then hold the combined sums (sum A + I, sum A f + f_a), f = f_c and
+ * eig / rank describe sum A + I.  alpha, beta: Table I alpha_g, beta_g. */
+int rmp_combined_eval_batch_async(rmp_ctx* ctx, uint32_t map_id, const double* states_dev,
+                                  const uint32_t* n_rays_dev, uint32_t n_states,
+                                  uint32_t max_rays, const rmp_params_t* params,
+                                  const double* goals_dev, double alpha, double beta,
+                                  void* workspace_dev, size_t workspace_bytes,
+                                  rmp_stream_t stream, rmp_result_t* out_dev);
+
+/* Closed-loop rollout of point robots (the map-based experiment of Sec. IV-A): every control
+ * step evaluates f_c for all running robots in one batched launch and integrates it by
+ * semi-implicit Euler in FP64 (xdot' = xdot + f_c dt, x' = x + xdot' dt).  A robot stops
+ * when, in this order, it leaves a dense grid (LEFT_MAP), the voxel holding it is occupied
+ * (COLLIDED), it is within goal_tol of its goal (REACHED), or it has taken max_steps steps
+ * (TIMEOUT); an evaluation error stops it with FAILED.  Smoothness is the mean over
+ * consecutive segments (displacements over seg_steps steps) of the angular similarity
+ * 1 - acos(A.B / (|A||B|)) / pi (1 = straight; the paper's path smoothness). */
+#define RMP_ROLLOUT_RUNNING 0
+#define RMP_ROLLOUT_REACHED 1
+#define RMP_ROLLOUT_COLLIDED 2
+#define RMP_ROLLOUT_TIMEOUT 3
+#define RMP_ROLLOUT_LEFT_MAP 4
+#define RMP_ROLLOUT_FAILED 5
+
+typedef struct {
+  double alpha, beta;      /* attractor gain and damping */
+  double dt;               /* control period, s */
+  double goal_tol;         /* m */
+  uint32_t max_steps;
+  uint32_t seg_steps;      /* smoothness segment length, steps (0: no smoothness) */
+  uint32_t n_rays;         /* rays per evaluation */
+  uint32_t reserved;
+} rmp_rollout_params_t;
+
+typedef struct {
+  double x[3], xdot[3];    /* final state */
+  double path_length;      /* sum of step lengths, m */
+  double smoothness;       /* mean angular similarity of consecutive segments (1 if none) */
+  uint32_t status;         /* RMP_ROLLOUT_* */
+  uint32_t steps;
+  uint32_t smooth_segments;
+  uint32_t reserved;
+} rmp_rollout_result_t;
+
+/* robots: host, 9 doubles per robot (start x, start xdot, goal).  Synchronous: allocates its
+ * device buffers, runs until every robot has stopped, copies the results to out (host). */
+int rmp_rollout(rmp_ctx* ctx, uint32_t map_id, const double* robots, uint32_t n_robots,
+                const rmp_params_t* params, const rmp_rollout_params_t* rollout,
+                rmp_stream_t stream, rmp_rollout_result_t* out);
+
 /* ------------------------------------------------------------------ request server
  * Continuous batching of single-state requests (a serving layer over the batched
  * evaluation; the paper evaluates one state per control step and has no counterpart).

@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "rmp_internal.h"
 
@@ -156,6 +157,7 @@ int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalCon
   k->halton_offset = p->halton_offset;
   k->w_mode = (int)p->w_mode;
   k->reduce_mode = (int)p->reduce_mode;
+  k->c64 = p->c;
   if (!scan) {
     if ((uint64_t)n + p->halton_offset > (1ull << 24)) return RMP_ERR_INVALID_ARG;
     const double vox = p->max_range / vs;
@@ -701,14 +703,18 @@ int batch_setup(rmp_ctx* c, uint32_t map_id, uint32_t n_states, uint32_t max_ray
 
 }  // namespace
 
-int rmp_raycast_eval_batch_async(rmp_ctx* c, uint32_t map_id, const double* states_dev,
-                                 const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
-                                 const rmp_params_t* params, void* ws, size_t ws_bytes,
-                                 rmp_stream_t stream, rmp_result_t* out_dev,
-                                 rmp_ray_hit_t* hits_dev, float* per_ray_dev) {
+namespace {
+
+int batch_async_impl(rmp_ctx* c, uint32_t map_id, const double* states_dev,
+                     const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
+                     const rmp_params_t* params, void* ws, size_t ws_bytes, rmp_stream_t stream,
+                     rmp_result_t* out_dev, rmp_ray_hit_t* hits_dev, float* per_ray_dev,
+                     const double* goals_dev, double alpha, double beta) {
   if (!c || !states_dev || !n_rays_dev || !ws || !out_dev) return RMP_ERR_INVALID_ARG;
   if (n_states == 0 || n_states > kMaxBatchStates || max_rays == 0 ||
       ws_bytes < batch_layout(n_states, max_rays).total)
+    return RMP_ERR_INVALID_ARG;
+  if (goals_dev && !(std::isfinite(alpha) && alpha >= 0.0 && std::isfinite(beta) && beta >= 0.0))
     return RMP_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
@@ -717,9 +723,129 @@ int rmp_raycast_eval_batch_async(rmp_ctx* c, uint32_t map_id, const double* stat
   int block, grid;
   int st = batch_setup(c, map_id, n_states, max_rays, params, &dm, &k, &block, &grid);
   if (st != RMP_OK) return st;
+  k.att_alpha = alpha;
+  k.att_beta = beta;
   RMP_CUDA(launch_batch(dm, k, states_dev, n_rays_dev, n_states, max_rays, ws, out_dev, hits_dev,
-                        per_ray_dev, block, grid, (cudaStream_t)stream));
+                        per_ray_dev, block, grid, (cudaStream_t)stream, goals_dev));
   return RMP_OK;
+}
+
+}  // namespace
+
+int rmp_combined_eval_batch_async(rmp_ctx* c, uint32_t map_id, const double* states_dev,
+                                  const uint32_t* n_rays_dev, uint32_t n_states,
+                                  uint32_t max_rays, const rmp_params_t* params,
+                                  const double* goals_dev, double alpha, double beta, void* ws,
+                                  size_t ws_bytes, rmp_stream_t stream, rmp_result_t* out_dev) {
+  if (!goals_dev) return RMP_ERR_INVALID_ARG;
+  return batch_async_impl(c, map_id, states_dev, n_rays_dev, n_states, max_rays, params, ws,
+                          ws_bytes, stream, out_dev, nullptr, nullptr, goals_dev, alpha, beta);
+}
+
+int rmp_rollout(rmp_ctx* c, uint32_t map_id, const double* robots, uint32_t n,
+                const rmp_params_t* params, const rmp_rollout_params_t* rp, rmp_stream_t stream,
+                rmp_rollout_result_t* out) {
+  if (!c || !robots || !params || !rp || !out || n == 0 || n > kMaxBatchStates)
+    return RMP_ERR_INVALID_ARG;
+  if (!(rp->dt > 0.0 && std::isfinite(rp->dt)) || !(rp->goal_tol >= 0.0) || rp->max_steps == 0 ||
+      rp->n_rays == 0)
+    return RMP_ERR_INVALID_ARG;
+  DevMap dm;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->maps.find(map_id);
+    if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
+    dm = it->second.dm;
+  }
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t wsb = batch_layout(n, rp->n_rays).total;
+  const size_t o_st = 0, o_goal = align256(48 * (size_t)n), o_nr = o_goal + align256(24 * (size_t)n),
+               o_res = o_nr + align256(4 * (size_t)n),
+               o_rs = o_res + align256(sizeof(rmp_result_t) * n),
+               o_cnt = o_rs + align256(sizeof(RolloutDev) * n), o_ws = o_cnt + 256;
+  char* buf = nullptr;
+  cudaError_t e = cudaMalloc((void**)&buf, o_ws + wsb);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::vector<double> st(6 * (size_t)n), goal(3 * (size_t)n);
+  std::vector<uint32_t> nr(n, rp->n_rays);
+  std::vector<RolloutDev> rs(n);
+  for (uint32_t b = 0; b < n; ++b) {
+    for (int a = 0; a < 6; ++a) st[6 * b + a] = robots[9 * (size_t)b + a];
+    for (int a = 0; a < 3; ++a) goal[3 * b + a] = robots[9 * (size_t)b + 6 + a];
+    std::memset(&rs[b], 0, sizeof(RolloutDev));
+    for (int a = 0; a < 3; ++a) rs[b].seg_start[a] = st[6 * b + a];
+  }
+  double* d_st = (double*)(buf + o_st);
+  double* d_goal = (double*)(buf + o_goal);
+  uint32_t* d_nr = (uint32_t*)(buf + o_nr);
+  rmp_result_t* d_res = (rmp_result_t*)(buf + o_res);
+  RolloutDev* d_rs = (RolloutDev*)(buf + o_rs);
+  uint32_t* d_cnt = (uint32_t*)(buf + o_cnt);
+  RolloutConsts rc;
+  rc.dt = rp->dt;
+  rc.goal_tol = rp->goal_tol;
+  rc.max_steps = rp->max_steps;
+  rc.seg_steps = rp->seg_steps;
+  rc.n_rays = rp->n_rays;
+  rc.pad = 0;
+  int status = RMP_OK;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_st, st.data(), 48 * (size_t)n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_goal, goal.data(), 24 * (size_t)n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_nr, nr.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_rs, rs.data(), sizeof(RolloutDev) * n, cudaMemcpyHostToDevice, s);
+  // steps in rounds of 32; after each round the running count decides whether to go on
+  const uint32_t kRound = 32;
+  uint32_t running = n;
+  for (uint32_t step = 0; e == cudaSuccess && status == RMP_OK && running > 0 &&
+                          step < rp->max_steps;) {
+    e = cudaMemsetAsync(d_cnt, 0, 4, s);
+    for (uint32_t i = 0; i < kRound && step < rp->max_steps && e == cudaSuccess; ++i, ++step) {
+      status = batch_async_impl(c, map_id, d_st, d_nr, n, rp->n_rays, params, buf + o_ws, wsb,
+                                stream, d_res, nullptr, nullptr, d_goal, rp->alpha, rp->beta);
+      if (status != RMP_OK) break;
+      e = launch_rollout_step(dm, rc, d_res, d_st, d_goal, d_nr, d_rs, n,
+                              i + 1 == kRound || step + 1 == rp->max_steps ? d_cnt : nullptr, s);
+    }
+    if (e == cudaSuccess && status == RMP_OK) {
+      e = cudaMemcpyAsync(&running, d_cnt, 4, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+  }
+  if (e == cudaSuccess && status == RMP_OK) {
+    e = cudaMemcpyAsync(st.data(), d_st, 48 * (size_t)n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rs.data(), d_rs, sizeof(RolloutDev) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  cudaFree(buf);
+  if (status != RMP_OK) return status;
+  if (e != cudaSuccess) return cuda_status(e);
+  for (uint32_t b = 0; b < n; ++b) {
+    rmp_rollout_result_t& r = out[b];
+    std::memset(&r, 0, sizeof(r));
+    for (int a = 0; a < 3; ++a) {
+      r.x[a] = st[6 * b + a];
+      r.xdot[a] = st[6 * b + 3 + a];
+    }
+    r.path_length = rs[b].path_length;
+    r.smoothness = rs[b].smooth_n ? rs[b].smooth_sum / rs[b].smooth_n : 1.0;
+    r.status = rs[b].status;
+    r.steps = rs[b].steps;
+    r.smooth_segments = rs[b].smooth_n;
+  }
+  return RMP_OK;
+}
+
+int rmp_raycast_eval_batch_async(rmp_ctx* c, uint32_t map_id, const double* states_dev,
+                                 const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
+                                 const rmp_params_t* params, void* ws, size_t ws_bytes,
+                                 rmp_stream_t stream, rmp_result_t* out_dev,
+                                 rmp_ray_hit_t* hits_dev, float* per_ray_dev) {
+  return batch_async_impl(c, map_id, states_dev, n_rays_dev, n_states, max_rays, params, ws,
+                          ws_bytes, stream, out_dev, hits_dev, per_ray_dev, nullptr, 0.0, 0.0);
 }
 
 int rmp_raycast_eval_batch(rmp_ctx* c, uint32_t map_id, const double* states, const uint32_t* n_rays,

@@ -74,6 +74,20 @@ struct EvalConsts {
   uint32_t lg_segs;                  // each ray is marched as 2^lg_segs segments
   uint32_t split_budget;             // block visits before unfinished pieces are split (~0: never)
   int w_mode, reduce_mode;
+  double c64;                        // soft-normalisation c (FP64, attractor)
+  double att_alpha, att_beta;        // attractor gain and damping (combined evaluations)
+};
+
+// Closed-loop rollout of point robots (per robot, device-resident).
+struct RolloutDev {
+  double seg_start[3], prev_seg[3];
+  double path_length, smooth_sum;
+  uint32_t status, steps, smooth_n, have_prev;
+};
+
+struct RolloutConsts {
+  double dt, goal_tol;
+  uint32_t max_steps, seg_steps, n_rays, pad;
 };
 
 // Workspace of one evaluation: tickets, one partial per CTA, one partial per group of
@@ -154,11 +168,19 @@ cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* s
                            float* per_ray, int block, int grid, cudaStream_t stream);
 int ctx_device(const rmp_ctx* ctx);                                  // CUDA device of a context
 int batch_occupancy(const DevMap& m, int reduce_mode, int block);     // CTAs per SM
-// Prep kernel + persistent batch kernel; n_rays_dev / states_dev on the device.
+// Prep kernel + persistent batch kernel; n_rays_dev / states_dev on the device.  With
+// goals_dev (3 doubles per state) each state's rays are combined with its attractor.
 cudaError_t launch_batch(const DevMap& m, const EvalConsts& k, const double* states_dev,
                          const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
                          void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits, float* per_ray,
-                         int block, int grid, cudaStream_t stream);
+                         int block, int grid, cudaStream_t stream,
+                         const double* goals_dev = nullptr);
+// One control step of every robot (see rollout_step_kernel); counts running robots into
+// *running (which the caller zeroes) when running is not null.
+cudaError_t launch_rollout_step(const DevMap& m, const RolloutConsts& rc, const rmp_result_t* res,
+                                double* states, const double* goals, uint32_t* n_rays,
+                                RolloutDev* rs, uint32_t n, uint32_t* running,
+                                cudaStream_t stream);
 cudaError_t launch_scan(const float* pts, const EvalConsts& k, const double* state_dev,
                         void* ws, rmp_result_t* out_dev, float* per_ray, int block, int grid,
                         cudaStream_t stream);

@@ -1499,6 +1499,110 @@ __device__ __forceinline__ void load_partial(const CtaPartial* p, double v[9], u
   a = __ldcg(&p->n_active);
 }
 
+// Attractor policy (Sec. III-B, Eq. attractorPolicy) combined by Eq. (1): its metric I is
+// added to sum A and f_a = alpha s(goal - x) - beta xdot to sum A f, in FP64.
+__device__ __forceinline__ void add_attractor(const EvalConsts& k, const double* st,
+                                              const double* goal, double tv[9]) {
+  const double v0 = goal[0] - st[0], v1 = goal[1] - st[1], v2 = goal[2] - st[2];
+  const double z = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+  const double h = z + k.c64 * log1p(exp(-2.0 * k.c64 * z));
+  tv[0] += 1.0;
+  tv[3] += 1.0;
+  tv[5] += 1.0;
+  tv[6] += k.att_alpha * (v0 / h) - k.att_beta * st[3];
+  tv[7] += k.att_alpha * (v1 / h) - k.att_beta * st[4];
+  tv[8] += k.att_alpha * (v2 / h) - k.att_beta * st[5];
+}
+
+// Occupancy of voxel (kx, ky, kz) (global voxel coordinates, inside the map for dense
+// maps): the block's radius or hash entry, then the brick bit.
+template <int LAYOUT>
+__device__ __forceinline__ bool voxel_occupied(const DevMap& m, int kx, int ky, int kz) {
+  const uint4* src = nullptr;
+  if (block_radius<LAYOUT>(m, m.radius, kx >> 3, ky >> 3, kz >> 3, &src) > 0) return false;
+  Brick w;
+  load_brick(src, w);
+  return brick_bit(w, kx, ky, kz);
+}
+
+// One control step of point robot b (Sec. IV-A closed loop): the combined policy's
+// acceleration f (res[b]) is integrated by semi-implicit Euler in FP64,
+// xdot' = xdot + f dt, x' = x + xdot' dt; then, in this order: outside a dense grid ->
+// LEFT_MAP; the voxel of x' occupied -> COLLIDED; |x' - goal| < goal_tol -> REACHED;
+// steps == max_steps -> TIMEOUT.  Every seg_steps steps the displacement since the last
+// segment end is a segment, and consecutive segments A, B add 1 - acos(cos(A, B)) / pi to
+// the smoothness sum.  A robot that stops running gets 0 rays from then on.
+template <int KIND, int LAYOUT>
+__global__ void rollout_step_kernel(DevMap m, RolloutConsts rc, const rmp_result_t* __restrict__ res,
+                                    double* states, const double* __restrict__ goals,
+                                    uint32_t* n_rays, RolloutDev* rs, uint32_t n,
+                                    uint32_t* running) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  RolloutDev& r = rs[b];
+  if (r.status != RMP_ROLLOUT_RUNNING) {
+    n_rays[b] = 0;
+    return;
+  }
+  double* st = states + 6 * (size_t)b;
+  const rmp_result_t& e = res[b];
+  if (e.status != RMP_OK) {
+    r.status = RMP_ROLLOUT_FAILED;
+    n_rays[b] = 0;
+    return;
+  }
+  double dl = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double vd = st[3 + a] + e.f[a] * rc.dt;
+    const double xn = st[a] + vd * rc.dt;
+    dl += (xn - st[a]) * (xn - st[a]);
+    st[3 + a] = vd;
+    st[a] = xn;
+  }
+  r.path_length += sqrt(dl);
+  r.steps += 1;
+  if (rc.seg_steps && r.steps % rc.seg_steps == 0) {
+    double seg[3];
+    for (int a = 0; a < 3; ++a) {
+      seg[a] = st[a] - r.seg_start[a];
+      r.seg_start[a] = st[a];
+    }
+    if (r.have_prev) {
+      double dot = 0.0, na = 0.0, nb = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        dot += r.prev_seg[a] * seg[a];
+        na += r.prev_seg[a] * r.prev_seg[a];
+        nb += seg[a] * seg[a];
+      }
+      if (na > 0.0 && nb > 0.0) {
+        double cs = dot / (sqrt(na) * sqrt(nb));
+        cs = cs > 1.0 ? 1.0 : (cs < -1.0 ? -1.0 : cs);
+        r.smooth_sum += 1.0 - acos(cs) / 3.14159265358979323846;
+        r.smooth_n += 1;
+      }
+    }
+    for (int a = 0; a < 3; ++a) r.prev_seg[a] = seg[a];
+    r.have_prev = 1;
+  }
+  int k[3];
+  bool far = false;
+  for (int a = 0; a < 3; ++a) {
+    const double o = KIND == RMP_MAP_DENSE_U8 ? (a == 0 ? m.origin[0] : (a == 1 ? m.origin[1] : m.origin[2]))
+                                              : 0.0;
+    const double q = __dmul_rn(__ddiv_rn(__dsub_rn(st[a], o), m.vs), 65536.0);
+    far = far || !(fabs(q) < 274877906944.0);
+    k[a] = far ? 0 : (int)(__double2ll_rn(q) >> 16);
+  }
+  double dg = 0.0;
+  for (int a = 0; a < 3; ++a) dg += (st[a] - goals[3 * (size_t)b + a]) * (st[a] - goals[3 * (size_t)b + a]);
+  if (far || (KIND == RMP_MAP_DENSE_U8 && outside<KIND>(m, k))) r.status = RMP_ROLLOUT_LEFT_MAP;
+  else if (voxel_occupied<LAYOUT>(m, k[0], k[1], k[2])) r.status = RMP_ROLLOUT_COLLIDED;
+  else if (sqrt(dg) < rc.goal_tol) r.status = RMP_ROLLOUT_REACHED;
+  else if (r.steps >= rc.max_steps) r.status = RMP_ROLLOUT_TIMEOUT;
+  if (r.status != RMP_ROLLOUT_RUNNING) n_rays[b] = 0;
+  else if (running) atomicAdd(running, 1u);
+}
+
 // Persistent batched evaluation: every warp takes chunks (its own index first, then from
 // the work counter) until none is left; a chunk is 32 / S rays of one state (coherent ray order of that state), marched
 // and evaluated as in the single-state kernel.  The chunk's 9 terms are summed over the
@@ -1513,7 +1617,8 @@ template <int KIND, int LAYOUT, int RED>
 __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
     DevMap m, EvalConsts k, BatchHeader* hdr, const BatchState* __restrict__ bs,
     uint32_t* sticket, uint32_t* gticket, CtaPartial* cparts, CtaPartial* gparts,
-    rmp_result_t* out, rmp_ray_hit_t* hits, float* per_ray, uint32_t max_rays) {
+    rmp_result_t* out, rmp_ray_hit_t* hits, float* per_ray, uint32_t max_rays,
+    const double* __restrict__ states, const double* __restrict__ goals) {
   extern __shared__ uint4 smem_radius[];
   __shared__ __align__(8) uint64_t bm_bar;
   __shared__ int bm_timeout;
@@ -1646,6 +1751,7 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
           ta += a2;
         }
         warp_sum_partial(tv, th, ta);
+        if (goals && lane == 0) add_attractor(k, states + 6 * (size_t)b, goals + 3 * (size_t)b, tv);
 #pragma unroll
         for (int i = 0; i < 9; ++i) tv[i] = __shfl_sync(0xffffffffu, tv[i], 0);
         rmp_result_t r;
@@ -2000,10 +2106,12 @@ static void launch_batch_t(const DevMap& m, const EvalConsts& k, BatchHeader* hd
                            const BatchState* bs, uint32_t* sticket, uint32_t* gticket,
                            CtaPartial* cparts, CtaPartial* gparts, rmp_result_t* out,
                            rmp_ray_hit_t* hits, float* per_ray, uint32_t max_rays, int block,
-                           int grid, size_t smem, cudaStream_t stream) {
+                           int grid, size_t smem, cudaStream_t stream, const double* states,
+                           const double* goals) {
   prefer_shared<raycast_batch_kernel<KIND, LAYOUT, RED>>();
   raycast_batch_kernel<KIND, LAYOUT, RED><<<grid, block, smem, stream>>>(
-      m, k, hdr, bs, sticket, gticket, cparts, gparts, out, hits, per_ray, max_rays);
+      m, k, hdr, bs, sticket, gticket, cparts, gparts, out, hits, per_ray, max_rays, states,
+      goals);
 }
 
 template <int KIND, int LAYOUT>
@@ -2011,21 +2119,22 @@ static void launch_batch_r(const DevMap& m, const EvalConsts& k, BatchHeader* hd
                            const BatchState* bs, uint32_t* sticket, uint32_t* gticket,
                            CtaPartial* cparts, CtaPartial* gparts, rmp_result_t* out,
                            rmp_ray_hit_t* hits, float* per_ray, uint32_t max_rays, int block,
-                           int grid, size_t smem, cudaStream_t stream) {
+                           int grid, size_t smem, cudaStream_t stream, const double* states,
+                           const double* goals) {
   if (k.reduce_mode == RMP_REDUCE_FP64)
     launch_batch_t<KIND, LAYOUT, RMP_REDUCE_FP64>(m, k, hdr, bs, sticket, gticket, cparts, gparts,
                                                   out, hits, per_ray, max_rays, block, grid, smem,
-                                                  stream);
+                                                  stream, states, goals);
   else
     launch_batch_t<KIND, LAYOUT, RMP_REDUCE_KAHAN32>(m, k, hdr, bs, sticket, gticket, cparts,
                                                      gparts, out, hits, per_ray, max_rays, block,
-                                                     grid, smem, stream);
+                                                     grid, smem, stream, states, goals);
 }
 
 cudaError_t launch_batch(const DevMap& m, const EvalConsts& k, const double* states_dev,
                          const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
                          void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits, float* per_ray,
-                         int block, int grid, cudaStream_t stream) {
+                         int block, int grid, cudaStream_t stream, const double* goals_dev) {
   const BatchLayout L = batch_layout(n_states, max_rays);
   char* w = (char*)ws;
   BatchHeader* hdr = (BatchHeader*)w;
@@ -2040,15 +2149,35 @@ cudaError_t launch_batch(const DevMap& m, const EvalConsts& k, const double* sta
   if (m.kind == RMP_MAP_DENSE_U8)
     launch_batch_r<RMP_MAP_DENSE_U8, kLayoutGrid>(m, k, hdr, bs, sticket, gticket, cparts, gparts,
                                                   out_dev, hits, per_ray, max_rays, block, grid,
-                                                  smem, stream);
+                                                  smem, stream, states_dev, goals_dev);
   else if (m.layout == kLayoutGrid)
     launch_batch_r<RMP_MAP_HASHED_TSDF, kLayoutGrid>(m, k, hdr, bs, sticket, gticket, cparts,
                                                      gparts, out_dev, hits, per_ray, max_rays,
-                                                     block, grid, smem, stream);
+                                                     block, grid, smem, stream, states_dev,
+                                                     goals_dev);
   else
     launch_batch_r<RMP_MAP_HASHED_TSDF, kLayoutHash>(m, k, hdr, bs, sticket, gticket, cparts,
                                                      gparts, out_dev, hits, per_ray, max_rays,
-                                                     block, grid, smem, stream);
+                                                     block, grid, smem, stream, states_dev,
+                                                     goals_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rollout_step(const DevMap& m, const RolloutConsts& rc, const rmp_result_t* res,
+                                double* states, const double* goals, uint32_t* n_rays,
+                                RolloutDev* rs, uint32_t n, uint32_t* running,
+                                cudaStream_t stream) {
+  const int block = 128;
+  const int grid = (int)((n + block - 1) / block);
+  if (m.kind == RMP_MAP_DENSE_U8)
+    rollout_step_kernel<RMP_MAP_DENSE_U8, kLayoutGrid><<<grid, block, 0, stream>>>(
+        m, rc, res, states, goals, n_rays, rs, n, running);
+  else if (m.layout == kLayoutGrid)
+    rollout_step_kernel<RMP_MAP_HASHED_TSDF, kLayoutGrid><<<grid, block, 0, stream>>>(
+        m, rc, res, states, goals, n_rays, rs, n, running);
+  else
+    rollout_step_kernel<RMP_MAP_HASHED_TSDF, kLayoutHash><<<grid, block, 0, stream>>>(
+        m, rc, res, states, goals, n_rays, rs, n, running);
   return cudaGetLastError();
 }
 

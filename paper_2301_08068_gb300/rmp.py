@@ -67,6 +67,22 @@ class rmp_launch_info_t(C.Structure):
                                          "smem_bytes", "ray_cells", "reserved")]
 
 
+class rmp_rollout_params_t(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("dt", C.c_double),
+                ("goal_tol", C.c_double), ("max_steps", C.c_uint32), ("seg_steps", C.c_uint32),
+                ("n_rays", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class rmp_rollout_result_t(C.Structure):
+    _fields_ = [("x", C.c_double * 3), ("xdot", C.c_double * 3), ("path_length", C.c_double),
+                ("smoothness", C.c_double), ("status", C.c_uint32), ("steps", C.c_uint32),
+                ("smooth_segments", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+RMP_ROLLOUT_RUNNING, RMP_ROLLOUT_REACHED, RMP_ROLLOUT_COLLIDED = 0, 1, 2
+RMP_ROLLOUT_TIMEOUT, RMP_ROLLOUT_LEFT_MAP, RMP_ROLLOUT_FAILED = 3, 4, 5
+
+
 class rmp_server_config_t(C.Structure):
     _fields_ = [("slots", C.c_uint32), ("max_batch_states", C.c_uint32), ("max_rays", C.c_uint32),
                 ("reserved", C.c_uint32), ("mem_budget_bytes", C.c_uint64)]
@@ -114,6 +130,11 @@ _SIGNATURES = {
                                      C.POINTER(rmp_params_t), _P, C.c_size_t, _P, _P, _P, _P],
     "rmp_raycast_eval_batch": [_P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(rmp_params_t), _P,
                                _P],
+    "rmp_combined_eval_batch_async": [_P, C.c_uint32, _P, _P, C.c_uint32, C.c_uint32,
+                                      C.POINTER(rmp_params_t), _P, C.c_double, C.c_double, _P,
+                                      C.c_size_t, _P, _P],
+    "rmp_rollout": [_P, C.c_uint32, _P, C.c_uint32, C.POINTER(rmp_params_t),
+                    C.POINTER(rmp_rollout_params_t), _P, _P],
     "rmp_raycast_eval_batch_static": [_P, C.c_uint32, _P, _P, C.c_uint32, C.c_uint32,
                                       C.POINTER(rmp_params_t), _P, _P],
     "rmp_server_config_default": [C.POINTER(rmp_server_config_t)],
@@ -323,6 +344,36 @@ def rmp_raycast_eval_batch_static(ctx: int, map_id: int, states, n_rays, n_state
                                                int(n_states), int(max_rays), C.byref(params),
                                                _stream(stream), _dptr(out)),
            "rmp_raycast_eval_batch_static")
+
+
+def rmp_combined_eval_batch_async(ctx: int, map_id: int, states, n_rays, n_states: int,
+                                  max_rays: int, params: rmp_params_t, goals, alpha: float,
+                                  beta: float, workspace, out, stream=None):
+    """Batched raycasting policy combined with per-state goal attractors (Eq. 1)."""
+    _check(lib().rmp_combined_eval_batch_async(
+        ctx, int(map_id), _dptr(states), _dptr(n_rays), int(n_states), int(max_rays),
+        C.byref(params), _dptr(goals), float(alpha), float(beta), _dptr(workspace),
+        workspace.numel() * workspace.element_size(), _stream(stream), _dptr(out)),
+        "rmp_combined_eval_batch_async")
+
+
+def rollout_params(alpha, beta, dt, goal_tol, max_steps, seg_steps, n_rays) -> rmp_rollout_params_t:
+    rp = rmp_rollout_params_t()
+    rp.alpha, rp.beta, rp.dt, rp.goal_tol = float(alpha), float(beta), float(dt), float(goal_tol)
+    rp.max_steps, rp.seg_steps, rp.n_rays = int(max_steps), int(seg_steps), int(n_rays)
+    return rp
+
+
+def rmp_rollout(ctx: int, map_id: int, robots, params: rmp_params_t, rp: rmp_rollout_params_t,
+                stream=None) -> list:
+    """robots: host (n, 9) float64 [start x, start xdot, goal]; returns one dict per robot."""
+    rb = np.ascontiguousarray(robots, np.float64).reshape(-1, 9)
+    out = (rmp_rollout_result_t * rb.shape[0])()
+    _check(lib().rmp_rollout(ctx, int(map_id), rb.ctypes.data, int(rb.shape[0]), C.byref(params),
+                             C.byref(rp), _stream(stream), out), "rmp_rollout")
+    return [dict(x=np.array(r.x[:]), xdot=np.array(r.xdot[:]), path_length=r.path_length,
+                 smoothness=r.smoothness, status=int(r.status), steps=int(r.steps),
+                 smooth_n=int(r.smooth_segments)) for r in out]
 
 
 def rmp_raycast_eval_batch(ctx: int, map_id: int, states, n_rays, params: rmp_params_t,

@@ -60,6 +60,10 @@ int main(void) {
   printf("\\"rmp_server_config_t\\": %zu, \\"rmp_server_stats_t\\": %zu,\\n",
          sizeof(rmp_server_config_t), sizeof(rmp_server_stats_t));
   O(rmp_server_config_t, mem_budget_bytes); O(rmp_server_stats_t, max_inflight);
+  printf("\\"rmp_rollout_params_t\\": %zu, \\"rmp_rollout_result_t\\": %zu,\\n",
+         sizeof(rmp_rollout_params_t), sizeof(rmp_rollout_result_t));
+  O(rmp_rollout_params_t, max_steps); O(rmp_rollout_result_t, status);
+  O(rmp_rollout_result_t, smooth_segments);
   printf("\\"end\\": 0}\\n");
   return 0;
 }
@@ -68,7 +72,8 @@ int main(void) {
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
     got = json.loads(subprocess.check_output([str(exe)]))
     for T in ("rmp_params_t", "rmp_result_t", "rmp_ray_hit_t", "rmp_map_desc_t", "rmp_map_info_t",
-              "rmp_launch_info_t", "rmp_server_config_t", "rmp_server_stats_t"):
+              "rmp_launch_info_t", "rmp_server_config_t", "rmp_server_stats_t",
+              "rmp_rollout_params_t", "rmp_rollout_result_t"):
         assert C.sizeof(getattr(rmp, T)) == got[T], T
     for key, off in got.items():
         if "." in key:
@@ -135,6 +140,9 @@ def test_null_arguments_rejected_without_gpu(rmp):
     assert L.rmp_server_poll(None, 1, None, None) == 1
     assert L.rmp_server_wait(None, 1, 0, None, None) == 1
     assert L.rmp_server_stats(None, None) == 1
+    assert L.rmp_rollout(None, 1, None, 1, None, None, None, None) == 1
+    assert L.rmp_combined_eval_batch_async(None, 1, None, None, 1, 1, None, None, 1.0, 1.0,
+                                           None, 0, None, None) == 1
     cfg = rmp.rmp_server_config_default()
     assert (cfg.slots, cfg.max_batch_states, cfg.max_rays, cfg.mem_budget_bytes) == \
         (4, 256, 262144, 1 << 30)
