@@ -306,6 +306,48 @@ def l2_probe(flush) -> float:
     return 2.0 * a.numel() * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
+def rollout_section(ctx) -> dict:
+    """Closed loop (Sec. IV-A): 128 start/goal pairs across seeded 10 m maps, point robots
+    driven by the raycasting policy combined with the goal attractor (Table I static-map
+    gains), dt = 10 ms, up to 60 s; success (goal reached without collision) and path
+    smoothness against the ray count N^2 (the paper's Fig. 6-7 sweep), with the time per
+    control step of all 128 robots; both readings of the ray metric in the combination
+    (sum as printed in Eq. raytracing_policy, mean as the text describes)."""
+    from paper_2301_08068_gb300 import rmp as R, workloads as W
+    out = {"workload": "128 start/goal pairs per map (x 0.5-1.5 m -> 8.5-9.5 m), 10 m cube, "
+                       "dt 10 ms, <= 6000 steps, goal tolerance 0.2 m, static-map params, "
+                       "alpha_g 10, beta_g 15"}
+    for n_prims, size in ((200, (0.2, 0.6)), (50, (0.2, 2.0))):
+        t = W.rollout_tasks(128, n_prims=n_prims, size_range=size)
+        mid = ctx.upload(t.map)
+        p = R.make_params(t.params, t.max_range)
+        robots = np.concatenate([t.starts, np.zeros_like(t.starts), t.goals], axis=1)
+        for mean in (True, False):
+            rows = []
+            for side in (4, 8, 16, 32, 64):
+                rp = R.rollout_params(10.0, 15.0, 0.01, 0.2, 6000, 10, side * side,
+                                      metric_mean=mean)
+                t0 = time.perf_counter()
+                res = R.rmp_rollout(ctx.handle, mid, robots, p, rp)
+                wall = time.perf_counter() - t0
+                st = np.array([r["status"] for r in res])
+                steps = np.array([r["steps"] for r in res])
+                ok = st == R.RMP_ROLLOUT_REACHED
+                rows.append({"rays": side * side, "success": float(ok.mean()),
+                             "collided": float((st == R.RMP_ROLLOUT_COLLIDED).mean()),
+                             "timeout": float((st == R.RMP_ROLLOUT_TIMEOUT).mean()),
+                             "smoothness_success_mean":
+                                 float(np.mean([r["smoothness"] for r, o in zip(res, ok) if o]))
+                                 if ok.any() else None,
+                             "steps_max": int(steps.max()), "wall_s": wall,
+                             "ms_per_control_step": 1e3 * wall / max(1, int(steps.max())),
+                             "robot_steps_per_s": float(steps.sum()) / wall})
+            out["%d_prims_%g-%gm_%s" % (n_prims, size[0], size[1],
+                                        "mean" if mean else "sum")] = rows
+        R.rmp_map_release(ctx.handle, mid)
+    return out
+
+
 def serve_section(ctx, seconds: float) -> dict:
     """Served: a Poisson stream (20k requests/s) over three device-resident maps (dense
     128^3 at 0.05 m, hashed 40x40x10 m at 0.1 m, hashed 100x100x20 m at 0.2 m; max range
@@ -521,6 +563,7 @@ def main():
         extra["lidar"] = lidar_section(ctx, flush)
         extra["batched"] = batch_section(ctx, mid, flush)
         extra["served"] = serve_section(ctx, args.serve_seconds)
+        extra["rollout"] = rollout_section(ctx)
 
     src = kernel_source_hash()
     peak, peak_kind = measured_peak_hbm()

@@ -290,15 +290,19 @@ int rmp_raycast_eval_batch_static(rmp_ctx* ctx, uint32_t map_id, const double* s
 /* ------------------------------------------------------------------ attractor and closed loop
  * The raycasting policy combined with a goal attractor (Sec. III-B Eq. attractorPolicy:
  * f_a = alpha s(goal - x) - beta xdot with the soft normalisation s of Eq. softmax and
- * parameter params->c, metric I) by Eq. (1): f_c = (sum A + I)^+ (sum A f + f_a).
- * A result's A and Af then hold the combined sums (sum A + I, sum A f + f_a), f = f_c and
- * eig / rank describe sum A + I.  alpha, beta: Table I alpha_g, beta_g. */
+ * parameter params->c, metric I) by Eq. (1): f_c = (M + I)^+ (M f_ray + f_a), where
+ * M f_ray = sum A f and M = sum A (Eq. raytracing_policy as printed; metric_mean = 0), or
+ * both divided by the state's ray count (metric_mean = 1: the ray policies' mean, as the
+ * text describes the combined acceleration; it keeps the attractor's weight independent of
+ * the ray count).  A result's A and Af then hold the combined sums (M + I, M f_ray + f_a),
+ * f = f_c and eig / rank describe M + I.  alpha, beta: Table I alpha_g, beta_g. */
 int rmp_combined_eval_batch_async(rmp_ctx* ctx, uint32_t map_id, const double* states_dev,
                                   const uint32_t* n_rays_dev, uint32_t n_states,
                                   uint32_t max_rays, const rmp_params_t* params,
                                   const double* goals_dev, double alpha, double beta,
-                                  void* workspace_dev, size_t workspace_bytes,
-                                  rmp_stream_t stream, rmp_result_t* out_dev);
+                                  uint32_t metric_mean, void* workspace_dev,
+                                  size_t workspace_bytes, rmp_stream_t stream,
+                                  rmp_result_t* out_dev);
 
 /* Closed-loop rollout of point robots (the map-based experiment of Sec. IV-A): every control
  * step evaluates f_c for all running robots in one batched launch and integrates it by
@@ -322,7 +326,7 @@ typedef struct {
   uint32_t max_steps;
   uint32_t seg_steps;      /* smoothness segment length, steps (0: no smoothness) */
   uint32_t n_rays;         /* rays per evaluation */
-  uint32_t reserved;
+  uint32_t metric_mean;    /* 0: M = sum A, 1: M = mean of the A_i (see above) */
 } rmp_rollout_params_t;
 
 typedef struct {

@@ -91,7 +91,7 @@ def lib():
                 "orc_scan_eval": (C.c_int, [P, C.c_uint32, P, P, P, P, P]),
                 "orc_attractor": (None, [P, P, P, C.c_double, C.c_double, C.c_double, P]),
                 "orc_combined_eval": (C.c_int, [P, P, P, C.c_uint32, P, P, C.c_double,
-                                                C.c_double, P]),
+                                                C.c_double, C.c_int, P]),
                 "orc_rollout_step": (None, [P, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
@@ -105,7 +105,7 @@ def lib():
 class RolloutParams(C.Structure):
     _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("dt", C.c_double),
                 ("goal_tol", C.c_double), ("max_steps", C.c_uint32), ("seg_steps", C.c_uint32),
-                ("n_rays", C.c_uint32), ("pad", C.c_uint32)]
+                ("n_rays", C.c_uint32), ("metric_mean", C.c_uint32)]
 
 
 class RolloutState(C.Structure):
@@ -253,21 +253,24 @@ def attractor(x, xdot, goal, alpha: float, beta: float, c: float) -> np.ndarray:
 
 
 def combined_eval(omap: "OracleMap", x, xdot, n_rays: int, params: Params, goal, alpha: float,
-                  beta: float) -> dict:
-    """Raycasting policy combined with the attractor by Eq. (1); sums include I and f_a."""
+                  beta: float, metric_mean: bool = False) -> dict:
+    """Raycasting policy combined with the attractor by Eq. (1); sums include I and f_a
+    (ray sums divided by the ray count first when metric_mean)."""
     xx = np.ascontiguousarray(x, np.float64)
     xd = np.ascontiguousarray(xdot, np.float64)
     g = np.ascontiguousarray(goal, np.float64)
     res = Result()
     lib().orc_combined_eval(omap.ref, _ptr(xx), _ptr(xd), int(n_rays), C.byref(params), _ptr(g),
-                            float(alpha), float(beta), C.byref(res))
+                            float(alpha), float(beta), int(bool(metric_mean)), C.byref(res))
     return _result(res)
 
 
-def rollout_params(alpha, beta, dt, goal_tol, max_steps, seg_steps, n_rays) -> RolloutParams:
+def rollout_params(alpha, beta, dt, goal_tol, max_steps, seg_steps, n_rays,
+                   metric_mean: bool = False) -> RolloutParams:
     rp = RolloutParams()
     rp.alpha, rp.beta, rp.dt, rp.goal_tol = float(alpha), float(beta), float(dt), float(goal_tol)
     rp.max_steps, rp.seg_steps, rp.n_rays = int(max_steps), int(seg_steps), int(n_rays)
+    rp.metric_mean = int(bool(metric_mean))
     return rp
 
 

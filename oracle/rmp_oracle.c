@@ -567,11 +567,16 @@ void orc_attractor(const double x[3], const double xdot[3], const double goal[3]
   for (int a = 0; a < 3; ++a) fa[a] = alpha * (v[a] / h) - beta * xdot[a];
 }
 
-/* Eq. (1) over the raycasting policy and the attractor (metric I). */
+/* Eq. (1) over the raycasting policy and the attractor (metric I); with metric_mean the
+ * ray policies' sums are divided by the ray count first (their mean). */
 int orc_combined_eval(const orc_map_t* m, const double x[3], const double xdot[3],
                       uint32_t n_rays, const orc_params_t* p, const double goal[3],
-                      double alpha, double beta, orc_result_t* out) {
+                      double alpha, double beta, int metric_mean, orc_result_t* out) {
   orc_raycast_eval(m, x, xdot, n_rays, p, out, NULL, NULL);
+  if (metric_mean && n_rays > 0) {
+    for (int k = 0; k < 6; ++k) out->sumA[k] /= (double)n_rays;
+    for (int k = 0; k < 3; ++k) out->sumAf[k] /= (double)n_rays;
+  }
   double fa[3];
   orc_attractor(x, xdot, goal, alpha, beta, p->c, fa);
   out->sumA[0] += 1.0;
@@ -593,7 +598,8 @@ void orc_rollout_step(const orc_map_t* m, const orc_params_t* p, const orc_rollo
                       const double goal[3], orc_rollout_t* st) {
   if (st->status != ORC_ROLL_RUNNING) return;
   orc_result_t r;
-  orc_combined_eval(m, st->x, st->xdot, rp->n_rays, p, goal, rp->alpha, rp->beta, &r);
+  orc_combined_eval(m, st->x, st->xdot, rp->n_rays, p, goal, rp->alpha, rp->beta,
+                    (int)rp->metric_mean, &r);
   double xn[3], dl = 0.0;
   for (int a = 0; a < 3; ++a) {
     st->xdot[a] = st->xdot[a] + r.f[a] * rp->dt;

@@ -89,18 +89,20 @@ void orc_attractor(const double x[3], const double xdot[3], const double goal[3]
                    double beta, double c, double fa[3]);
 
 /* Raycasting policy combined with the attractor by Eq. (1):
- * f_c = (sum A + I)^+ (sum A f + f_a).  out->sumA / sumAf hold the combined sums
- * (sum A + I, sum A f + f_a), out->eig and out->rank describe sum A + I. */
+ * f_c = (M + I)^+ (M f_ray + f_a) with M f_ray = sum A f and M = sum A (Eq.
+ * raytracing_policy as printed) or, with metric_mean, M = sum A / n_rays and
+ * M f_ray = sum A f / n_rays (the mean the text describes).  out->sumA / sumAf hold the
+ * combined sums (M + I, M f_ray + f_a), out->eig and out->rank describe M + I. */
 int orc_combined_eval(const orc_map_t* m, const double x[3], const double xdot[3],
                       uint32_t n_rays, const orc_params_t* p, const double goal[3],
-                      double alpha, double beta, orc_result_t* out);
+                      double alpha, double beta, int metric_mean, orc_result_t* out);
 
 enum { ORC_ROLL_RUNNING = 0, ORC_ROLL_REACHED = 1, ORC_ROLL_COLLIDED = 2, ORC_ROLL_TIMEOUT = 3,
        ORC_ROLL_LEFT_MAP = 4 };
 
 typedef struct {
   double alpha, beta, dt, goal_tol;
-  uint32_t max_steps, seg_steps, n_rays, pad;
+  uint32_t max_steps, seg_steps, n_rays, metric_mean;
 } orc_rollout_params_t;
 
 typedef struct {

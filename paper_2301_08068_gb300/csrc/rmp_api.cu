@@ -709,7 +709,7 @@ int batch_async_impl(rmp_ctx* c, uint32_t map_id, const double* states_dev,
                      const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
                      const rmp_params_t* params, void* ws, size_t ws_bytes, rmp_stream_t stream,
                      rmp_result_t* out_dev, rmp_ray_hit_t* hits_dev, float* per_ray_dev,
-                     const double* goals_dev, double alpha, double beta) {
+                     const double* goals_dev, double alpha, double beta, int metric_mean = 0) {
   if (!c || !states_dev || !n_rays_dev || !ws || !out_dev) return RMP_ERR_INVALID_ARG;
   if (n_states == 0 || n_states > kMaxBatchStates || max_rays == 0 ||
       ws_bytes < batch_layout(n_states, max_rays).total)
@@ -725,6 +725,7 @@ int batch_async_impl(rmp_ctx* c, uint32_t map_id, const double* states_dev,
   if (st != RMP_OK) return st;
   k.att_alpha = alpha;
   k.att_beta = beta;
+  k.att_mean = metric_mean ? 1 : 0;
   RMP_CUDA(launch_batch(dm, k, states_dev, n_rays_dev, n_states, max_rays, ws, out_dev, hits_dev,
                         per_ray_dev, block, grid, (cudaStream_t)stream, goals_dev));
   return RMP_OK;
@@ -735,11 +736,13 @@ int batch_async_impl(rmp_ctx* c, uint32_t map_id, const double* states_dev,
 int rmp_combined_eval_batch_async(rmp_ctx* c, uint32_t map_id, const double* states_dev,
                                   const uint32_t* n_rays_dev, uint32_t n_states,
                                   uint32_t max_rays, const rmp_params_t* params,
-                                  const double* goals_dev, double alpha, double beta, void* ws,
-                                  size_t ws_bytes, rmp_stream_t stream, rmp_result_t* out_dev) {
-  if (!goals_dev) return RMP_ERR_INVALID_ARG;
+                                  const double* goals_dev, double alpha, double beta,
+                                  uint32_t metric_mean, void* ws, size_t ws_bytes,
+                                  rmp_stream_t stream, rmp_result_t* out_dev) {
+  if (!goals_dev || metric_mean > 1) return RMP_ERR_INVALID_ARG;
   return batch_async_impl(c, map_id, states_dev, n_rays_dev, n_states, max_rays, params, ws,
-                          ws_bytes, stream, out_dev, nullptr, nullptr, goals_dev, alpha, beta);
+                          ws_bytes, stream, out_dev, nullptr, nullptr, goals_dev, alpha, beta,
+                          (int)metric_mean);
 }
 
 int rmp_rollout(rmp_ctx* c, uint32_t map_id, const double* robots, uint32_t n,
@@ -748,7 +751,7 @@ int rmp_rollout(rmp_ctx* c, uint32_t map_id, const double* robots, uint32_t n,
   if (!c || !robots || !params || !rp || !out || n == 0 || n > kMaxBatchStates)
     return RMP_ERR_INVALID_ARG;
   if (!(rp->dt > 0.0 && std::isfinite(rp->dt)) || !(rp->goal_tol >= 0.0) || rp->max_steps == 0 ||
-      rp->n_rays == 0)
+      rp->n_rays == 0 || rp->metric_mean > 1)
     return RMP_ERR_INVALID_ARG;
   DevMap dm;
   {
@@ -804,7 +807,8 @@ int rmp_rollout(rmp_ctx* c, uint32_t map_id, const double* robots, uint32_t n,
     e = cudaMemsetAsync(d_cnt, 0, 4, s);
     for (uint32_t i = 0; i < kRound && step < rp->max_steps && e == cudaSuccess; ++i, ++step) {
       status = batch_async_impl(c, map_id, d_st, d_nr, n, rp->n_rays, params, buf + o_ws, wsb,
-                                stream, d_res, nullptr, nullptr, d_goal, rp->alpha, rp->beta);
+                                stream, d_res, nullptr, nullptr, d_goal, rp->alpha, rp->beta,
+                                (int)rp->metric_mean);
       if (status != RMP_OK) break;
       e = launch_rollout_step(dm, rc, d_res, d_st, d_goal, d_nr, d_rs, n,
                               i + 1 == kRound || step + 1 == rp->max_steps ? d_cnt : nullptr, s);

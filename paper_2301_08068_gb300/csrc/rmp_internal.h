@@ -76,6 +76,8 @@ struct EvalConsts {
   int w_mode, reduce_mode;
   double c64;                        // soft-normalisation c (FP64, attractor)
   double att_alpha, att_beta;        // attractor gain and damping (combined evaluations)
+  int att_mean;                      // combined: ray sums divided by the ray count first
+  int pad_;
 };
 
 // Closed-loop rollout of point robots (per robot, device-resident).

@@ -1500,9 +1500,13 @@ __device__ __forceinline__ void load_partial(const CtaPartial* p, double v[9], u
 }
 
 // Attractor policy (Sec. III-B, Eq. attractorPolicy) combined by Eq. (1): its metric I is
-// added to sum A and f_a = alpha s(goal - x) - beta xdot to sum A f, in FP64.
+// added to sum A and f_a = alpha s(goal - x) - beta xdot to sum A f, in FP64 -- after
+// dividing the ray sums by the ray count when the ray policies' mean is asked for.
 __device__ __forceinline__ void add_attractor(const EvalConsts& k, const double* st,
-                                              const double* goal, double tv[9]) {
+                                              const double* goal, uint32_t n_rays, double tv[9]) {
+  if (k.att_mean && n_rays > 0)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) tv[i] = tv[i] / (double)n_rays;
   const double v0 = goal[0] - st[0], v1 = goal[1] - st[1], v2 = goal[2] - st[2];
   const double z = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
   const double h = z + k.c64 * log1p(exp(-2.0 * k.c64 * z));
@@ -1751,7 +1755,8 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
           ta += a2;
         }
         warp_sum_partial(tv, th, ta);
-        if (goals && lane == 0) add_attractor(k, states + 6 * (size_t)b, goals + 3 * (size_t)b, tv);
+        if (goals && lane == 0)
+          add_attractor(k, states + 6 * (size_t)b, goals + 3 * (size_t)b, n_b, tv);
 #pragma unroll
         for (int i = 0; i < 9; ++i) tv[i] = __shfl_sync(0xffffffffu, tv[i], 0);
         rmp_result_t r;

@@ -70,7 +70,7 @@ class rmp_launch_info_t(C.Structure):
 class rmp_rollout_params_t(C.Structure):
     _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("dt", C.c_double),
                 ("goal_tol", C.c_double), ("max_steps", C.c_uint32), ("seg_steps", C.c_uint32),
-                ("n_rays", C.c_uint32), ("reserved", C.c_uint32)]
+                ("n_rays", C.c_uint32), ("metric_mean", C.c_uint32)]
 
 
 class rmp_rollout_result_t(C.Structure):
@@ -131,8 +131,8 @@ _SIGNATURES = {
     "rmp_raycast_eval_batch": [_P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(rmp_params_t), _P,
                                _P],
     "rmp_combined_eval_batch_async": [_P, C.c_uint32, _P, _P, C.c_uint32, C.c_uint32,
-                                      C.POINTER(rmp_params_t), _P, C.c_double, C.c_double, _P,
-                                      C.c_size_t, _P, _P],
+                                      C.POINTER(rmp_params_t), _P, C.c_double, C.c_double,
+                                      C.c_uint32, _P, C.c_size_t, _P, _P],
     "rmp_rollout": [_P, C.c_uint32, _P, C.c_uint32, C.POINTER(rmp_params_t),
                     C.POINTER(rmp_rollout_params_t), _P, _P],
     "rmp_raycast_eval_batch_static": [_P, C.c_uint32, _P, _P, C.c_uint32, C.c_uint32,
@@ -348,19 +348,23 @@ def rmp_raycast_eval_batch_static(ctx: int, map_id: int, states, n_rays, n_state
 
 def rmp_combined_eval_batch_async(ctx: int, map_id: int, states, n_rays, n_states: int,
                                   max_rays: int, params: rmp_params_t, goals, alpha: float,
-                                  beta: float, workspace, out, stream=None):
+                                  beta: float, workspace, out, stream=None,
+                                  metric_mean: bool = False):
     """Batched raycasting policy combined with per-state goal attractors (Eq. 1)."""
     _check(lib().rmp_combined_eval_batch_async(
         ctx, int(map_id), _dptr(states), _dptr(n_rays), int(n_states), int(max_rays),
-        C.byref(params), _dptr(goals), float(alpha), float(beta), _dptr(workspace),
+        C.byref(params), _dptr(goals), float(alpha), float(beta), int(bool(metric_mean)),
+        _dptr(workspace),
         workspace.numel() * workspace.element_size(), _stream(stream), _dptr(out)),
         "rmp_combined_eval_batch_async")
 
 
-def rollout_params(alpha, beta, dt, goal_tol, max_steps, seg_steps, n_rays) -> rmp_rollout_params_t:
+def rollout_params(alpha, beta, dt, goal_tol, max_steps, seg_steps, n_rays,
+                   metric_mean: bool = False) -> rmp_rollout_params_t:
     rp = rmp_rollout_params_t()
     rp.alpha, rp.beta, rp.dt, rp.goal_tol = float(alpha), float(beta), float(dt), float(goal_tol)
     rp.max_steps, rp.seg_steps, rp.n_rays = int(max_steps), int(seg_steps), int(n_rays)
+    rp.metric_mean = int(bool(metric_mean))
     return rp
 
 

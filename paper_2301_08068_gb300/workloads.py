@@ -410,6 +410,34 @@ def poisson_requests(n_maps: int, rate: float, duration: float, ray_lo: int, ray
     return t, maps, rays, vel
 
 
+@dataclasses.dataclass
+class RolloutTasks:
+    map: HashedMap
+    prims: List[Primitive]
+    starts: np.ndarray   # (n, 3)
+    goals: np.ndarray    # (n, 3)
+    max_range: float
+    params: dict
+
+
+def rollout_tasks(n_pairs: int, n_prims: int = 100, extent=(10.0, 10.0, 10.0), vs: float = 0.1,
+                  max_range: float = 10.0, size_range=(0.2, 2.0),
+                  seed_index: int = 9) -> RolloutTasks:
+    """Start/goal pairs across a random map shaped like the paper's planning maps (Sec. IV-A:
+    seeded spheres and boxes in a 10 m cube; radius / half-edge uniform in size_range):
+    starts uniform in the slab x in [0.5, 1.5] m, goals in x in [8.5, 9.5] m, y and z in
+    [0.5, 9.5] m, both at least 0.3 m from every obstacle (SDF > 0.3)."""
+    hm, prims = hashed_scene(tuple(extent), vs, n_prims, size_range=tuple(size_range),
+                             seed_index=seed_index)
+    rng = SplitMix64(SEED_BASE + seed_index + 0x2000)
+    e = np.asarray(extent, np.float64)
+    starts = free_points(rng, prims, [0.5, 0.5, 0.5], [1.5, e[1] - 0.5, e[2] - 0.5], n_pairs,
+                         TSDF_TRUNCATION)
+    goals = free_points(rng, prims, [e[0] - 1.5, 0.5, 0.5], [e[0] - 0.5, e[1] - 0.5, e[2] - 0.5],
+                        n_pairs, TSDF_TRUNCATION)
+    return RolloutTasks(hm, prims, starts, goals, max_range, dict(PARAMS_STATIC_MAP))
+
+
 def sphere_lattice_scan(n: int, radius: float) -> np.ndarray:
     """n float32 points of a spherical Fibonacci lattice of the given radius around the
     origin (z_k = 1 - (2k+1)/n, azimuth 2 pi k / golden ratio): an evenly spread view

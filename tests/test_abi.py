@@ -141,7 +141,7 @@ def test_null_arguments_rejected_without_gpu(rmp):
     assert L.rmp_server_wait(None, 1, 0, None, None) == 1
     assert L.rmp_server_stats(None, None) == 1
     assert L.rmp_rollout(None, 1, None, 1, None, None, None, None) == 1
-    assert L.rmp_combined_eval_batch_async(None, 1, None, None, 1, 1, None, None, 1.0, 1.0,
+    assert L.rmp_combined_eval_batch_async(None, 1, None, None, 1, 1, None, None, 1.0, 1.0, 0,
                                            None, 0, None, None) == 1
     cfg = rmp.rmp_server_config_default()
     assert (cfg.slots, cfg.max_batch_states, cfg.max_rays, cfg.mem_budget_bytes) == \

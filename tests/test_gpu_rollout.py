@@ -64,13 +64,15 @@ def test_combined_eval_matches_oracle(ctx):
         nr = torch.full((B,), n, dtype=torch.int32, device="cuda")
         ws = torch.empty(R.rmp_batch_workspace_bytes(B, n), dtype=torch.uint8, device="cuda")
         out = torch.empty((B, R.RESULT_BYTES), dtype=torch.uint8, device="cuda")
-        R.rmp_combined_eval_batch_async(ctx.handle, mid, st, nr, B, n, pg, gl, ALPHA, BETA, ws, out)
-        torch.cuda.synchronize()
-        for b, s in enumerate(wl.states):
-            g = R.result_from_bytes(out[b].cpu().numpy().tobytes())
-            ro = O.combined_eval(om, s.x, s.xdot, n, po, goals[b], ALPHA, BETA)
-            _, _, por = O.raycast_eval(om, s.x, s.xdot, n, po, want_hits=False)
-            assert_combined_close(g, ro, por)
+        for mean in (False, True):
+            R.rmp_combined_eval_batch_async(ctx.handle, mid, st, nr, B, n, pg, gl, ALPHA, BETA,
+                                            ws, out, metric_mean=mean)
+            torch.cuda.synchronize()
+            for b, s in enumerate(wl.states):
+                g = R.result_from_bytes(out[b].cpu().numpy().tobytes())
+                ro = O.combined_eval(om, s.x, s.xdot, n, po, goals[b], ALPHA, BETA, metric_mean=mean)
+                _, _, por = O.raycast_eval(om, s.x, s.xdot, n, po, want_hits=False)
+                assert_combined_close(g, ro, por / n if mean else por)
         R.rmp_map_release(ctx.handle, mid)
 
 
@@ -117,16 +119,18 @@ def test_short_rollouts_among_obstacles(ctx):
     starts = [s.x for s in wl.states]
     goals = [s.x + rng.uniform(-5, 5, 3) for s in wl.states]
     steps = 25
-    rp = R.rollout_params(ALPHA, BETA, 0.01, 0.05, steps, 5, 1024)
-    orp = O.rollout_params(ALPHA, BETA, 0.01, 0.05, steps, 5, 1024)
-    got = R.rmp_rollout(ctx.handle, mid, _robots(starts, goals), R.make_params(wl.params, wl.max_range), rp)
     po = O.make_params(wl.params, wl.max_range)
-    for g, s0, gl in zip(got, starts, goals):
-        o = O.rollout(om, po, orp, s0, np.zeros(3), gl)
-        assert g["status"] == o["status"] and g["steps"] == o["steps"]
-        tol = 1e-4 * o["path_length"] + 1e-9
-        assert np.linalg.norm(g["x"] - o["x"]) <= tol, (g["x"], o["x"])
-        assert g["path_length"] == pytest.approx(o["path_length"], rel=1e-4, abs=1e-9)
+    for mean in (False, True):
+        rp = R.rollout_params(ALPHA, BETA, 0.01, 0.05, steps, 5, 1024, metric_mean=mean)
+        orp = O.rollout_params(ALPHA, BETA, 0.01, 0.05, steps, 5, 1024, metric_mean=mean)
+        got = R.rmp_rollout(ctx.handle, mid, _robots(starts, goals),
+                            R.make_params(wl.params, wl.max_range), rp)
+        for g, s0, gl in zip(got, starts, goals):
+            o = O.rollout(om, po, orp, s0, np.zeros(3), gl)
+            assert g["status"] == o["status"] and g["steps"] == o["steps"]
+            tol = 1e-4 * o["path_length"] + 1e-9
+            assert np.linalg.norm(g["x"] - o["x"]) <= tol, (g["x"], o["x"])
+            assert g["path_length"] == pytest.approx(o["path_length"], rel=1e-4, abs=1e-9)
     R.rmp_map_release(ctx.handle, mid)
 
 

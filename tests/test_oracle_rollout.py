@@ -63,13 +63,15 @@ def test_combined_solves_the_normal_equations():
     wl = W.dense_box_workload(n_states=4, jitter=True)
     om = O.OracleMap(wl.map)
     p = O.make_params(wl.params, wl.max_range)
-    for s in wl.states:
+    for s, mean in zip(wl.states, (False, True, False, True)):
         g = s.x + np.array([2.0, -1.0, 0.5])
-        r = O.combined_eval(om, s.x, s.xdot, 1024, p, g, ALPHA, BETA)
+        r = O.combined_eval(om, s.x, s.xdot, 1024, p, g, ALPHA, BETA, metric_mean=mean)
         obs = O.raycast_eval(om, s.x, s.xdot, 1024, p, want_hits=False, want_per_ray=False)[0]
         fa = O.attractor(s.x, s.xdot, g, ALPHA, BETA, p.c)
-        assert np.allclose(r["sumA"], obs["sumA"] + np.array([1, 0, 0, 1, 0, 1]), rtol=1e-15)
-        assert np.allclose(r["sumAf"], obs["sumAf"] + fa, rtol=1e-15)
+        scale = 1.0 / 1024 if mean else 1.0                 # the ray policies' mean or sum
+        assert np.allclose(r["sumA"], scale * obs["sumA"] + np.array([1, 0, 0, 1, 0, 1]),
+                           rtol=1e-15)
+        assert np.allclose(r["sumAf"], scale * obs["sumAf"] + fa, rtol=1e-15)
         S = r["sumA"]
         M = np.array([[S[0], S[1], S[2]], [S[1], S[3], S[4]], [S[2], S[4], S[5]]])
         res = M @ r["f"] - r["sumAf"]
