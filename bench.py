@@ -285,6 +285,51 @@ def lidar_section(ctx, flush) -> dict:
             "floor_ms_one_point": ms1, "frac_of_floor": ms1 / ms}
 
 
+def lidar_stream_section(ctx) -> dict:
+    """OS-0 sizing (128 x 2048 = 262144 points per scan, the paper's 20 Hz sensor-rate
+    requirement): scans from pinned host memory through the copy/compute pipeline, each
+    result read back, against copying then evaluating one scan at a time."""
+    import torch
+    from paper_2301_08068_gb300 import rmp as R, workloads as W
+    sw = W.lidar_workload(beams=128, columns=2048, fov_deg=90.0)
+    p = R.make_params(sw.params, sw.max_range)
+    rng = np.random.default_rng(11)
+    scans = [(torch.from_numpy(sw.points.copy()).pin_memory(), rng.normal(size=3))
+             for _ in range(8)]
+    n_scans = 400
+    with R.ScanPipeline(ctx, 262144, slots=2) as pipe:
+        for i in range(8):
+            pipe.wait(pipe.submit(scans[i][0], sw.x, scans[i][1], p))
+        lat = []
+        t0 = time.perf_counter()
+        prev = None
+        for i in range(n_scans):
+            pts, v = scans[i % 8]
+            ts = time.perf_counter()
+            t = pipe.submit(pts, sw.x, v, p)
+            if prev is not None:
+                pipe.wait(prev[0])
+                lat.append(time.perf_counter() - prev[1])
+            prev = (t, ts)
+        pipe.wait(prev[0])
+        lat.append(time.perf_counter() - prev[1])
+        span = time.perf_counter() - t0
+    dev = torch.empty((262144, 3), dtype=torch.float32, device="cuda")
+    t1 = time.perf_counter()
+    for i in range(n_scans // 4):
+        pts, v = scans[i % 8]
+        dev.copy_(pts)
+        R.rmp_scan_eval(ctx.handle, dev, sw.x, v, p)
+    serial = (time.perf_counter() - t1) / (n_scans // 4)
+    return {"workload": "128 x 2048 scan (262144 points, 3 MiB) per step, pinned host points, "
+                        "2-slot pipeline; results read back",
+            "scans_per_s": n_scans / span, "ms_per_scan": 1e3 * span / n_scans,
+            "latency_p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "latency_p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "serial_copy_then_eval_ms": 1e3 * serial,
+            "budget_ms_at_20Hz": 50.0}
+
+
 def l2_probe(flush) -> float:
     """L2 bandwidth probe (GB/s): repeated device copies of a 24 MiB buffer pair, which
     stays resident in the 129 MB L2; bytes = read + write."""
@@ -561,6 +606,7 @@ def main():
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:
         extra["lidar"] = lidar_section(ctx, flush)
+        extra["lidar_stream_os0"] = lidar_stream_section(ctx)
         extra["batched"] = batch_section(ctx, mid, flush)
         extra["served"] = serve_section(ctx, args.serve_seconds)
         extra["rollout"] = rollout_section(ctx)

@@ -345,6 +345,24 @@ int rmp_rollout(rmp_ctx* ctx, uint32_t map_id, const double* robots, uint32_t n_
                 const rmp_params_t* params, const rmp_rollout_params_t* rollout,
                 rmp_stream_t stream, rmp_rollout_result_t* out);
 
+/* ------------------------------------------------------------------ streamed LiDAR scans
+ * A pipeline of `slots` (2..8) scan slots for a sensor stream (e.g. an OS-0 scan of
+ * 128 x 2048 = 262144 points at 20 Hz): submitting a scan copies its points from the
+ * caller's host memory (pinned, for the copy to be asynchronous; it must stay unchanged
+ * until the scan's result is waited for) on a copy stream and evaluates it
+ * (rmp_scan_eval semantics) on a compute stream, so the copy of one scan overlaps the
+ * evaluation of the previous one.  submit waits only when the slot it reuses still holds
+ * a scan in flight; wait blocks until that scan's result is in *out (host).  A ticket can
+ * be waited for until its slot is reused (`slots` submits later: RMP_ERR_BUSY). */
+typedef struct rmp_scan_pipeline rmp_scan_pipeline;
+int rmp_scan_pipeline_create(rmp_ctx* ctx, uint32_t max_points, uint32_t slots,
+                             rmp_scan_pipeline** out);
+int rmp_scan_pipeline_destroy(rmp_scan_pipeline* pipeline);
+int rmp_scan_pipeline_submit(rmp_scan_pipeline* pipeline, const float* points_host, uint32_t n,
+                             const double x[3], const double xdot[3], const rmp_params_t* params,
+                             uint64_t* ticket);
+int rmp_scan_pipeline_wait(rmp_scan_pipeline* pipeline, uint64_t ticket, rmp_result_t* out);
+
 /* ------------------------------------------------------------------ request server
  * Continuous batching of single-state requests (a serving layer over the batched
  * evaluation; the paper evaluates one state per control step and has no counterpart).

@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librmp.so")
-SOURCES = ["rmp_kernels.cu", "rmp_api.cu", "rmp_server.cu", "rmp_static.cu"]
+SOURCES = ["rmp_kernels.cu", "rmp_api.cu", "rmp_server.cu", "rmp_static.cu", "rmp_stream.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I" + INCLUDE, "-I" + CSRC]

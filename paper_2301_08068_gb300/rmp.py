@@ -137,6 +137,11 @@ _SIGNATURES = {
                     C.POINTER(rmp_rollout_params_t), _P, _P],
     "rmp_raycast_eval_batch_static": [_P, C.c_uint32, _P, _P, C.c_uint32, C.c_uint32,
                                       C.POINTER(rmp_params_t), _P, _P],
+    "rmp_scan_pipeline_create": [_P, C.c_uint32, C.c_uint32, C.POINTER(C.c_void_p)],
+    "rmp_scan_pipeline_destroy": [_P],
+    "rmp_scan_pipeline_submit": [_P, _P, C.c_uint32, _P, _P, C.POINTER(rmp_params_t),
+                                 C.POINTER(C.c_uint64)],
+    "rmp_scan_pipeline_wait": [_P, C.c_uint64, C.POINTER(rmp_result_t)],
     "rmp_server_config_default": [C.POINTER(rmp_server_config_t)],
     "rmp_server_create": [_P, C.POINTER(rmp_server_config_t), C.POINTER(C.c_void_p)],
     "rmp_server_destroy": [_P],
@@ -510,6 +515,47 @@ def rmp_server_stats(server: int) -> dict:
     st = rmp_server_stats_t()
     _check(lib().rmp_server_stats(server, C.byref(st)), "rmp_server_stats")
     return {n: int(getattr(st, n)) for n, _ in rmp_server_stats_t._fields_}
+
+
+class ScanPipeline:
+    """Owns one rmp_scan_pipeline: streamed LiDAR scans with copy/compute overlap.  Points
+    are host arrays (float32 (n, 3)); pass pinned torch tensors for asynchronous copies and
+    keep them unchanged until their result has been waited for."""
+
+    def __init__(self, ctx: "Context", max_points: int, slots: int = 2):
+        h = C.c_void_p()
+        _check(lib().rmp_scan_pipeline_create(ctx.handle, int(max_points), int(slots),
+                                              C.byref(h)), "rmp_scan_pipeline_create")
+        self.handle = h.value
+
+    def submit(self, points, x, xdot, params: rmp_params_t) -> int:
+        t = C.c_uint64()
+        if isinstance(points, np.ndarray):
+            assert points.dtype == np.float32 and points.flags.c_contiguous
+            ptr, n = points.ctypes.data, points.shape[0]
+        else:
+            ptr, n = points.data_ptr(), points.shape[0]
+        _check(lib().rmp_scan_pipeline_submit(self.handle, ptr, int(n), _vec3(x), _vec3(xdot),
+                                              C.byref(params), C.byref(t)),
+               "rmp_scan_pipeline_submit")
+        return int(t.value)
+
+    def wait(self, ticket: int) -> dict:
+        out = rmp_result_t()
+        _check(lib().rmp_scan_pipeline_wait(self.handle, int(ticket), C.byref(out)),
+               "rmp_scan_pipeline_wait")
+        return result_dict(out)
+
+    def close(self):
+        if self.handle:
+            _check(lib().rmp_scan_pipeline_destroy(self.handle), "rmp_scan_pipeline_destroy")
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Server:

@@ -366,14 +366,16 @@ def lidar_directions(beams: int = 64, columns: int = 1024,
 
 
 def lidar_workload(beams: int = 64, columns: int = 1024, max_return: float = 30.0,
-                   noise: float = 0.02, seed_index: int = 2) -> ScanWorkload:
+                   noise: float = 0.02, seed_index: int = 2,
+                   fov_deg: float = 45.0) -> ScanWorkload:
     """A 64 x 1024 scan of the hashed scene's primitives from a free sensor position,
-    analytic first-hit ranges (FP64) plus N(0, 0.02 m); no return within 30 m -> NaN."""
+    analytic first-hit ranges (FP64) plus N(0, 0.02 m); no return within 30 m -> NaN.
+    (OS-0 sizing: 128 beams x 2048 columns over a 90 degree vertical field of view.)"""
     hm, prims = hashed_scene()
     rng = SplitMix64(SEED_BASE + seed_index)
     sensor = free_points(rng, prims, np.zeros(3), np.array([40.0, 40.0, 10.0]), 1,
                          TSDF_TRUNCATION)[0]
-    u = lidar_directions(beams, columns)
+    u = lidar_directions(beams, columns, fov_deg)
     o = np.broadcast_to(sensor, u.shape)
     t = np.full(u.shape[0], np.inf)
     for pr in prims:
