@@ -424,11 +424,15 @@ int rmp_server_stats(rmp_server* server, rmp_server_stats_t* out);
  *                        march); 1: Halton index order
  *  RMP_TUNE_SPLIT_BUDGET block visits after which the pieces still running in a warp are
  *                        cut into sub-pieces marched by the warp's idle lanes (1..65536),
- *                        0 never, -1 (default) the library's choice (currently never) */
+ *                        0 never, -1 (default) the library's choice (currently never)
+ *  RMP_TUNE_CELL_SKIP    free boxes of voxels inside occupied blocks crossed in one step
+ *                        (grid layout maps): 1 always, 0 never, -1 (default) in batched
+ *                        evaluations only (measured faster there, slower for one state) */
 #define RMP_TUNE_BLOCK 1
 #define RMP_TUNE_LG_SEGMENTS 2
 #define RMP_TUNE_RAY_ORDER 3
 #define RMP_TUNE_SPLIT_BUDGET 4
+#define RMP_TUNE_CELL_SKIP 5
 int rmp_tune_set(rmp_ctx* ctx, int knob, int value);
 int rmp_tune_get(rmp_ctx* ctx, int knob, int* value);
 

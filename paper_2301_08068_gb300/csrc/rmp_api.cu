@@ -21,6 +21,7 @@ struct MapRec {
   void* bricks = nullptr;
   void* table = nullptr;
   void* radius = nullptr;
+  void* cells = nullptr;
   uint32_t n_bricks = 0;
   uint32_t cap = 0;
   uint64_t bytes = 0;
@@ -38,6 +39,7 @@ struct rmp_ctx {
   int tune_lg_segs = -1;     // log2 segments per ray (-1: chosen from the ray count)
   int tune_ray_order = 0;    // 0: coherent direction cells, 1: Halton index order
   int tune_split = -1;       // split budget (-1: default, 0: never split)
+  int tune_cells = -1;       // voxel-box skipping (-1: batches only, 0: off, 1: on)
   // scratch of the synchronous calls (serialised by mu)
   void* ws = nullptr;
   double* state_dev = nullptr;
@@ -198,7 +200,8 @@ void free_map(MapRec& r) {
   if (r.bricks) cudaFree(r.bricks);
   if (r.table) cudaFree(r.table);
   if (r.radius) cudaFree(r.radius);
-  r.bricks = r.table = r.radius = nullptr;
+  if (r.cells) cudaFree(r.cells);
+  r.bricks = r.table = r.radius = r.cells = nullptr;
 }
 
 // uint32 words of a 4-bit-per-brick radius field, in whole uint4s (TMA copy granularity)
@@ -218,6 +221,12 @@ int build_radius(MapRec& r, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&b, n);
   if (e == cudaSuccess)
     e = launch_grid_radius((const uint32_t*)r.bricks, r.dm, a, b, (uint32_t*)r.radius, s);
+  // 2^3-cell free distances for voxel-box skipping inside occupied blocks (optional)
+  if (e == cudaSuccess && n * 32 <= kMaxCellBytes) {
+    e = cudaMalloc(&r.cells, n * 32);
+    if (e == cudaSuccess) e = launch_cell_dist((const uint32_t*)r.bricks, r.dm, (uint32_t*)r.cells, s);
+    if (e == cudaSuccess) r.dm.cells = (const uint32_t*)r.cells;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (a) cudaFree(a);
   if (b) cudaFree(b);
@@ -367,7 +376,7 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
     if (e != cudaSuccess) return fail(cuda_status(e));
     const int rs = build_radius(r, s);
     if (rs != RMP_OK) return fail(rs);
-    r.bytes = nbr * 64 + (uint64_t)r.dm.radius_words * 4;
+    r.bytes = nbr * 64 + (uint64_t)r.dm.radius_words * 4 + (r.cells ? nbr * 32 : 0);
   } else if (d->kind == RMP_MAP_HASHED_TSDF) {
     const uint32_t n = d->n_blocks;
     if (n > (1u << 26)) return RMP_ERR_INVALID_ARG;
@@ -448,7 +457,7 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
       if (e != cudaSuccess) return fail(cuda_status(e));
       const int rs = build_radius(r, s);
       if (rs != RMP_OK) return fail(rs);
-      r.bytes = grid_bytes + (uint64_t)r.dm.radius_words * 4;
+      r.bytes = grid_bytes + (uint64_t)r.dm.radius_words * 4 + (r.cells ? gprod * 32 : 0);
     } else {
       r.dm.layout = kLayoutHash;
       r.bricks = compact;
@@ -514,6 +523,9 @@ int rmp_tune_set(rmp_ctx* c, int knob, int value) {
   } else if (knob == RMP_TUNE_SPLIT_BUDGET) {
     if (value < -1 || value > 65536) return RMP_ERR_INVALID_ARG;
     c->tune_split = value;
+  } else if (knob == RMP_TUNE_CELL_SKIP) {
+    if (value < -1 || value > 1) return RMP_ERR_INVALID_ARG;
+    c->tune_cells = value;
   } else {
     return RMP_ERR_INVALID_ARG;
   }
@@ -552,6 +564,7 @@ int rmp_tune_get(rmp_ctx* c, int knob, int* value) {
   else if (knob == RMP_TUNE_LG_SEGMENTS) *value = c->tune_lg_segs;
   else if (knob == RMP_TUNE_RAY_ORDER) *value = c->tune_ray_order;
   else if (knob == RMP_TUNE_SPLIT_BUDGET) *value = c->tune_split;
+  else if (knob == RMP_TUNE_CELL_SKIP) *value = c->tune_cells;
   else return RMP_ERR_INVALID_ARG;
   return RMP_OK;
 }
@@ -574,6 +587,7 @@ int rmp_raycast_eval_async(rmp_ctx* c, uint32_t map_id, const double* state_dev,
     auto it = c->maps.find(map_id);
     if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
     dm = it->second.dm;
+    if (c->tune_cells != 1) dm.cells = nullptr;   // single states: off unless asked for
   }
   EvalConsts k;
   int st = make_consts(params, dm.vs, n_rays, false, &k, tuning_of(c));
@@ -594,7 +608,8 @@ int rmp_raycast_eval(rmp_ctx* c, uint32_t map_id, const double x[3], const doubl
   std::lock_guard<std::mutex> lk(c->mu);      // held until the result is back
   auto it = c->maps.find(map_id);
   if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
-  const DevMap dm = it->second.dm;
+  DevMap dm = it->second.dm;
+  if (c->tune_cells != 1) dm.cells = nullptr;     // single states: off unless asked for
   EvalConsts k;
   int st = make_consts(params, dm.vs, n_rays, false, &k, tuning_of(c));
   if (st != RMP_OK) return st;
@@ -687,6 +702,7 @@ int batch_setup(rmp_ctx* c, uint32_t map_id, uint32_t n_states, uint32_t max_ray
     auto it = c->maps.find(map_id);
     if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
     *dm = it->second.dm;
+    if (c->tune_cells == 0) dm->cells = nullptr;  // batches: on unless switched off
     t = tuning_of(c);
     *block = c->tune_block;
   }

@@ -44,6 +44,8 @@ constexpr int kLayoutGrid = 0;
 constexpr int kLayoutHash = 1;
 constexpr uint32_t kMaxSmemRadiusBytes = 48 * 1024;   // staged in shared memory up to this
 constexpr int kMaxFreeRadius = 15;
+constexpr int kCellDistCap = 4;                       // cell free distances are capped here
+constexpr uint64_t kMaxCellBytes = 256ull << 20;      // cell distances kept up to this size
 constexpr uint64_t kMaxGridBricks = 1ull << 26;       // grid layout up to 4 GiB of bricks
 
 struct DevMap {
@@ -60,6 +62,8 @@ struct DevMap {
   int gdim[3];              // grid: bricks per axis
   const uint4* bricks;      // grid: brick (x + gdim0 (y + gdim1 z)); hash: by slot
   const uint32_t* radius;   // grid: 4-bit free radius of brick idx at bits 4 (idx & 7)
+  const uint32_t* cells;    // grid (optional): 8 words per brick, the 4-bit free distance of
+                            // each 2^3 cell c = cx + 4 cy + 16 cz at word c >> 3, bits 4 (c & 7)
   const HashEntry* table;   // hash layout only
 };
 
@@ -191,6 +195,9 @@ cudaError_t launch_dense_bricks(const uint8_t* occ, const int dims[3], const int
 // Free-radius field of a grid from its bricks (scratch: two byte arrays, one per brick).
 cudaError_t launch_grid_radius(const uint32_t* bricks, const DevMap& m, uint8_t* scratch_a,
                                uint8_t* scratch_b, uint32_t* radius, cudaStream_t stream);
+// Free distance of every 2^3 cell of the occupied bricks of a grid (see DevMap::cells).
+cudaError_t launch_cell_dist(const uint32_t* bricks, const DevMap& m, uint32_t* cells,
+                             cudaStream_t stream);
 cudaError_t launch_key_bbox(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,
                             int* bbox, cudaStream_t stream);
 cudaError_t launch_grid_scatter(const int32_t* keys, const uint32_t* bricks, uint32_t n_blocks,

@@ -158,7 +158,7 @@ __device__ __forceinline__ bool brick_bit(const Brick& b, int kx, int ky, int kz
 // box the radius is the distance to the box.  Hash layout: 1 for free blocks.
 template <int LAYOUT>
 __device__ __forceinline__ int block_radius(const DevMap& m, const uint32_t* rad, int bx, int by,
-                                            int bz, const uint4** src) {
+                                            int bz, const uint4** src, uint32_t* bidx = nullptr) {
   if (LAYOUT == kLayoutGrid) {
     const int x = bx - m.gmin[0], y = by - m.gmin[1], z = bz - m.gmin[2];
     if ((unsigned)x >= (unsigned)m.gdim[0] || (unsigned)y >= (unsigned)m.gdim[1] ||
@@ -171,6 +171,7 @@ __device__ __forceinline__ int block_radius(const DevMap& m, const uint32_t* rad
     const uint32_t idx = (uint32_t)x + (uint32_t)m.gdim[0] * ((uint32_t)y + (uint32_t)m.gdim[1] * (uint32_t)z);
     const int v = (int)((rad[idx >> 3] >> ((idx & 7) * 4)) & 15u);
     *src = m.bricks + 4 * (size_t)idx;
+    if (bidx) *bidx = idx;
     return v;
   } else {
     const int slot = hash_lookup(m, bx, by, bz);
@@ -213,8 +214,8 @@ __device__ __forceinline__ bool outside(const DevMap& m, const int k[3]) {
           (unsigned)k[2] >= (unsigned)m.dims[2]);
 }
 
-// The ray is in a free box: the blocks within Chebyshev distance R of its current block
-// (clipped to the dense grid).  Advance the DDA state to the first voxel beyond the box
+// The ray is in a free box: the blocks within Chebyshev distance R of its current block, or
+// the voxels within R of its current voxel (clipped to the dense grid).  Advance the DDA state to the first voxel beyond the box
 // exactly as single steps would: the box is left through the axis e whose face crossing
 // F_e/|D_e| comes first (ties: lowest axis); every other axis b crosses its interior
 // boundaries that come strictly before that time (or at the same time if b < e, the tie
@@ -227,13 +228,15 @@ __device__ __forceinline__ bool outside(const DevMap& m, const int k[3]) {
 template <int KIND>
 __device__ __forceinline__ bool skip_box(const DevMap& m, int k[3], const int s[3], uint32_t N[3],
                                          const uint32_t A[3], const float rA[3], const uint32_t L[3],
-                                         int R, uint32_t& steps, uint32_t& n_last,
+                                         int R, bool voxel_box, uint32_t& steps, uint32_t& n_last,
                                          uint32_t& a_last) {
   uint32_t c[3], F[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int b = k[a] >> 3;
-    int ca = s[a] > 0 ? 8 * (b + R) + 7 - k[a] : k[a] - 8 * (b - R);
+    // voxels left in the box along the step direction: a box of blocks within R blocks of
+    // the current block, or (voxel_box) the voxels within R of the current voxel
+    int ca = voxel_box ? R : (s[a] > 0 ? 8 * (b + R) + 7 - k[a] : k[a] - 8 * (b - R));
     if (KIND == RMP_MAP_DENSE_U8) {
       const int g = s[a] > 0 ? m.dims[a] - 1 - k[a] : k[a];
       ca = ca < g ? ca : g;
@@ -402,7 +405,7 @@ __device__ __forceinline__ void state_at(const RayFx& r, long long R_fx, uint32_
 // (skip_box) or enters an occupied block, whose brick is held in registers while the inner
 // loop steps voxel by voxel, the order of the next crossings kept in the exact differences
 // E_ab = N_a |D_b| - N_b |D_a|.
-template <int KIND, int LAYOUT>
+template <int KIND, int LAYOUT, bool CELLS>
 __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, MarchState& st,
                                          const RayFx& r, const uint32_t L[3], int at_limit,
                                          uint32_t budget) {
@@ -418,9 +421,23 @@ __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, Ma
   int status = budget < guard ? kBudgetOut : at_limit;
   for (uint32_t it = 0; it < iters; ++it) {
     const uint4* src = nullptr;
-    const int v = block_radius<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, &src);
-    if (v > 0) {
-      if (skip_box<KIND>(m, k, s, N, A, rA, L, v - 1, st.steps, st.n_last, st.a_last)) {
+    uint32_t bidx = 0;
+    const int v = block_radius<LAYOUT>(m, bm, k[0] >> 3, k[1] >> 3, k[2] >> 3, &src, &bidx);
+    // a free block is left through the box of free blocks around it; in an occupied block,
+    // a voxel whose 2^3 cell lies at Chebyshev distance dv >= 2 from every occupied voxel
+    // (grid layout's cell distances) is left through the free box of half-width dv - 1
+    // voxels around it -- both in one exact step
+    int R = v - 1;
+    bool vox = false;
+    if (CELLS && v == 0 && LAYOUT == kLayoutGrid && m.cells) {
+      const uint32_t ci = (uint32_t)(((k[0] & 7) >> 1) | (((k[1] & 7) >> 1) << 2) |
+                                     (((k[2] & 7) >> 1) << 4));
+      const int dv = (int)((__ldg(m.cells + 8 * (size_t)bidx + (ci >> 3)) >> (4 * (ci & 7))) & 15u);
+      R = dv - 1;
+      vox = true;
+    }
+    if (R >= (vox ? 1 : 0)) {
+      if (skip_box<KIND>(m, k, s, N, A, rA, L, R, vox, st.steps, st.n_last, st.a_last)) {
         status = at_limit;
         break;
       }
@@ -1123,7 +1140,7 @@ __device__ __forceinline__ bool bulk_load_wait(uint64_t* bar) {
 // the first final one (lowest index), else the last one.  Warp-synchronous: every lane of
 // the warp calls it (work = false for lanes without a segment).  Returns the ray's status;
 // mo is its final state (valid in every lane of the ray's segment group).
-template <int KIND, int LAYOUT>
+template <int KIND, int LAYOUT, bool CELLS>
 __device__ __forceinline__ int march_ray(const DevMap& m, const uint32_t* bm, const EvalConsts& k,
                                          const long long P[3], const Ray& ray, uint32_t seg,
                                          uint32_t lgS, bool work, MarchState& mo) {
@@ -1148,7 +1165,8 @@ __device__ __forceinline__ int march_ray(const DevMap& m, const uint32_t* bm, co
   int own_stat = kSegContinues;
   for (int phase = 0; phase < 2; ++phase) {
     if (work)
-      sstat = march_run<KIND, LAYOUT>(m, bm, so, r, L, lim, phase == 0 ? k.split_budget : 0xffffffffu);
+      sstat = march_run<KIND, LAYOUT, CELLS>(m, bm, so, r, L, lim,
+                                             phase == 0 ? k.split_budget : 0xffffffffu);
     if (phase == 1) break;
     const uint32_t unfinished = __ballot_sync(0xffffffffu, work && sstat == kBudgetOut);
     if (!unfinished) break;
@@ -1216,7 +1234,7 @@ __device__ __forceinline__ void ray_outputs(const DevMap& m, const EvalConsts& k
 // ray sit in adjacent lanes, and the ray's result is the first segment (lowest index) that
 // hit or left the map, else the last one -- found with a warp ballot and moved to the
 // ray's first lane by shuffles.  That lane evaluates the policy and writes the outputs.
-template <int KIND, int LAYOUT, int RED>
+template <int KIND, int LAYOUT, int RED, bool CELLS>
 __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k,
                                                           const double* __restrict__ state,
                                                           WsHeader* ws, CtaPartial* parts,
@@ -1273,7 +1291,7 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
     first = false;
     const long long P[3] = {cs.P[0], cs.P[1], cs.P[2]};
     MarchState mo;
-    const int mstat = march_ray<KIND, LAYOUT>(m, bm, k, P, ray, seg, lgS, active && !bad, mo);
+    const int mstat = march_ray<KIND, LAYOUT, CELLS>(m, bm, k, P, ray, seg, lgS, active && !bad, mo);
     if (!active || bad || seg != 0) continue;
     float vals[9];
     ray_outputs(m, k, P, ray, mo, mstat, cs.v, cs.vl, hits ? hits + ray_idx : nullptr,
@@ -1673,7 +1691,7 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
     const uint32_t ray_idx = ray_of_slot_p(active ? slot : 0, pM, pQ, n_b - pQ * pM);
     const Ray ray = make_ray(ray_idx + k.halton_offset);
     MarchState mo;
-    const int mstat = march_ray<KIND, LAYOUT>(m, bm, k, P, ray, seg, lgS, active, mo);
+    const int mstat = march_ray<KIND, LAYOUT, true>(m, bm, k, P, ray, seg, lgS, active, mo);
     float vals[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     unsigned nh = 0, na = 0;
     if (active && seg == 0) {
@@ -1912,6 +1930,59 @@ __global__ void radius_pack_kernel(const uint8_t* __restrict__ v, uint32_t n, ui
   }
 }
 
+// Occupancy of grid voxel (x, y, z) (grid-local voxel coordinates; outside the grid: free).
+__device__ __forceinline__ bool grid_voxel_bit(const uint32_t* bricks, const DevMap& m, int x,
+                                               int y, int z) {
+  if ((unsigned)x >= (unsigned)(8 * m.gdim[0]) || (unsigned)y >= (unsigned)(8 * m.gdim[1]) ||
+      (unsigned)z >= (unsigned)(8 * m.gdim[2]))
+    return false;
+  const size_t b = (size_t)(x >> 3) + (size_t)m.gdim[0] * ((size_t)(y >> 3) +
+                                                           (size_t)m.gdim[1] * (size_t)(z >> 3));
+  const uint32_t bit = (uint32_t)((x & 7) + 8 * (y & 7) + 64 * (z & 7));
+  return (__ldg(bricks + 16 * b + (bit >> 5)) >> (bit & 31)) & 1u;
+}
+
+// Free distance of each 2^3 cell of the occupied bricks: the Chebyshev distance in voxels
+// from the cell to the nearest occupied voxel, capped at kCellDistCap (a free cell at
+// distance dv holds no voxel closer than dv to an obstacle, so every voxel of it centres a
+// free box of half-width dv - 1).  One thread per brick word (8 cells); the cell's
+// neighbourhood within the cap is scanned directly.  Free bricks get 0 (never read).
+__global__ void cell_dist_kernel(const uint32_t* __restrict__ bricks, DevMap m, uint64_t n_bricks,
+                                 uint32_t* __restrict__ cells) {
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n_bricks * 8;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t b = t >> 3;
+    const uint32_t wi = (uint32_t)(t & 7);
+    uint32_t any = 0;
+    for (int q = 0; q < 16; ++q) any |= __ldg(bricks + 16 * b + q);
+    if (!any) {
+      cells[t] = 0;
+      continue;
+    }
+    const int bx = (int)(b % (uint64_t)m.gdim[0]);
+    const int by = (int)((b / (uint64_t)m.gdim[0]) % (uint64_t)m.gdim[1]);
+    const int bz = (int)(b / ((uint64_t)m.gdim[0] * (uint64_t)m.gdim[1]));
+    uint32_t word = 0;
+    for (int i = 0; i < 8; ++i) {
+      const int c = (int)(wi * 8 + i);
+      const int x0 = 8 * bx + 2 * (c & 3), y0 = 8 * by + 2 * ((c >> 2) & 3), z0 = 8 * bz + 2 * (c >> 4);
+      int d = kCellDistCap;
+      const int span = kCellDistCap - 1;          // voxels beyond the cell that can be nearer
+      for (int z = z0 - span; z <= z0 + 1 + span && d > 0; ++z)
+        for (int y = y0 - span; y <= y0 + 1 + span && d > 0; ++y)
+          for (int x = x0 - span; x <= x0 + 1 + span && d > 0; ++x) {
+            if (!grid_voxel_bit(bricks, m, x, y, z)) continue;
+            const int dx = max(max(x0 - x, x - (x0 + 1)), 0);
+            const int dy = max(max(y0 - y, y - (y0 + 1)), 0);
+            const int dz = max(max(z0 - z, z - (z0 + 1)), 0);
+            d = min(d, max(dx, max(dy, dz)));
+          }
+      word |= (uint32_t)d << (4 * i);
+    }
+    cells[t] = word;
+  }
+}
+
 // Bounding box (min xyz, max xyz) of the blocks whose brick holds an occupied voxel.
 __global__ void key_bbox_kernel(const int32_t* __restrict__ keys, const uint4* __restrict__ bricks,
                                 uint32_t n_blocks, int* bbox) {
@@ -2036,20 +2107,35 @@ static void prefer_shared() {
   __atomic_fetch_or(&done_mask, 1ull << dev, __ATOMIC_ACQ_REL);
 }
 
+template <int KIND, int LAYOUT, bool CELLS>
+static void launch_raycast_c(const DevMap& m, const EvalConsts& k, const double* state_dev,
+                             WsHeader* hdr, CtaPartial* parts, rmp_result_t* out_dev,
+                             rmp_ray_hit_t* hits, float* per_ray, int block, int grid,
+                             size_t smem, cudaStream_t stream) {
+  if (k.reduce_mode == RMP_REDUCE_FP64) {
+    prefer_shared<raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_FP64, CELLS>>();
+    raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_FP64, CELLS><<<grid, block, smem, stream>>>(
+        m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
+  } else {
+    prefer_shared<raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_KAHAN32, CELLS>>();
+    raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_KAHAN32, CELLS><<<grid, block, smem, stream>>>(
+        m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
+  }
+}
+
+// The voxel-box path is compiled in only where it is used (grid layouts with cell
+// distances): without it the single-state march keeps its shorter code.
 template <int KIND, int LAYOUT>
 static void launch_raycast_t(const DevMap& m, const EvalConsts& k, const double* state_dev,
                              WsHeader* hdr, CtaPartial* parts, rmp_result_t* out_dev,
                              rmp_ray_hit_t* hits, float* per_ray, int block, int grid,
                              size_t smem, cudaStream_t stream) {
-  if (k.reduce_mode == RMP_REDUCE_FP64) {
-    prefer_shared<raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_FP64>>();
-    raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_FP64><<<grid, block, smem, stream>>>(
-        m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
-  } else {
-    prefer_shared<raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_KAHAN32>>();
-    raycast_rmp_kernel<KIND, LAYOUT, RMP_REDUCE_KAHAN32><<<grid, block, smem, stream>>>(
-        m, k, state_dev, hdr, parts, out_dev, hits, per_ray);
-  }
+  if (LAYOUT == kLayoutGrid && m.cells)
+    launch_raycast_c<KIND, LAYOUT, LAYOUT == kLayoutGrid>(m, k, state_dev, hdr, parts, out_dev,
+                                                          hits, per_ray, block, grid, smem, stream);
+  else
+    launch_raycast_c<KIND, LAYOUT, false>(m, k, state_dev, hdr, parts, out_dev, hits, per_ray,
+                                          block, grid, smem, stream);
 }
 
 int raycast_occupancy(const DevMap& m, int reduce_mode, int block) {
@@ -2057,14 +2143,14 @@ int raycast_occupancy(const DevMap& m, int reduce_mode, int block) {
   const size_t smem = raycast_smem_bytes(m);
   cudaError_t e;
   if (m.kind == RMP_MAP_DENSE_U8)
-    e = reduce_mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_FP64>, block, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_KAHAN32>, block, smem);
+    e = reduce_mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_FP64, false>, block, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_KAHAN32, false>, block, smem);
   else if (m.layout == kLayoutGrid)
-    e = reduce_mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutGrid, RMP_REDUCE_FP64>, block, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutGrid, RMP_REDUCE_KAHAN32>, block, smem);
+    e = reduce_mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutGrid, RMP_REDUCE_FP64, false>, block, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutGrid, RMP_REDUCE_KAHAN32, false>, block, smem);
   else
-    e = reduce_mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutHash, RMP_REDUCE_FP64>, block, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutHash, RMP_REDUCE_KAHAN32>, block, smem);
+    e = reduce_mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutHash, RMP_REDUCE_FP64, false>, block, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, raycast_rmp_kernel<RMP_MAP_HASHED_TSDF, kLayoutHash, RMP_REDUCE_KAHAN32, false>, block, smem);
   return e == cudaSuccess ? n : -1;
 }
 
@@ -2225,6 +2311,13 @@ cudaError_t launch_grid_radius(const uint32_t* bricks, const DevMap& m, uint8_t*
   }
   radius_pack_kernel<<<grid_for(m.radius_words), 256, 0, stream>>>(a, (uint32_t)n, m.radius_words,
                                                                    radius);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_dist(const uint32_t* bricks, const DevMap& m, uint32_t* cells,
+                             cudaStream_t stream) {
+  const uint64_t n = (uint64_t)m.gdim[0] * m.gdim[1] * m.gdim[2];
+  cell_dist_kernel<<<grid_for(n * 8), 256, 0, stream>>>(bricks, m, n, cells);
   return cudaGetLastError();
 }
 

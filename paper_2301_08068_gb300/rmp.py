@@ -30,6 +30,7 @@ RMP_MAP_DENSE_U8, RMP_MAP_HASHED_TSDF = 0, 1
 RMP_PRESET_STATIC_MAP, RMP_PRESET_LIDAR = 0, 1
 RMP_REDUCE_KAHAN32, RMP_REDUCE_FP64 = 0, 1
 RMP_TUNE_BLOCK, RMP_TUNE_LG_SEGMENTS, RMP_TUNE_RAY_ORDER, RMP_TUNE_SPLIT_BUDGET = 1, 2, 3, 4
+RMP_TUNE_CELL_SKIP = 5
 
 
 class RmpError(RuntimeError):

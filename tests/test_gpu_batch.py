@@ -89,17 +89,19 @@ def test_batch_log_uniform_counts_fp64(ctx, hashed):
     check_batch(ctx, mid, om, wu.states, wu.n_rays, p, wl.max_range)
 
 
-@pytest.mark.parametrize("lgs,split", [(2, 0), (1, 3), (0, 1)])
-def test_batch_segments_and_split_dense(ctx, dense, lgs, split):
+@pytest.mark.parametrize("lgs,split,cells", [(2, 0, -1), (1, 3, 0), (0, 1, -1), (0, 0, 0)])
+def test_batch_segments_and_split_dense(ctx, dense, lgs, split, cells):
     wl, mid, om = dense
     R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, lgs)
     R.rmp_tune_set(ctx.handle, R.RMP_TUNE_SPLIT_BUDGET, split)
+    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_CELL_SKIP, cells)
     try:
         check_batch(ctx, mid, om, wl.states, [1024, 4097, 1, 300, 2048, 999], wl.params,
                     wl.max_range)
     finally:
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, -1)
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_SPLIT_BUDGET, -1)
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_CELL_SKIP, -1)
 
 
 def test_batch_matches_single_state_calls(ctx, hashed):

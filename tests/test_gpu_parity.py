@@ -336,6 +336,27 @@ def test_layouts_grid_and_hash_fallback(ctx, hashed):
     assert a[1].tobytes() == b[1].tobytes()
 
 
+@pytest.mark.parametrize("cells,lgs", [(1, 0), (1, 2), (0, 0)])
+def test_cell_skip_keeps_results(ctx, hashed, dense, cells, lgs):
+    """Voxel-box skipping inside occupied blocks on or off changes nothing: hit records
+    bit-identical to the oracle's, values within tolerance (single-state kernel)."""
+    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_CELL_SKIP, cells)
+    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, lgs)
+    try:
+        assert R.rmp_tune_get(ctx.handle, R.RMP_TUNE_CELL_SKIP) == cells
+        wl, mid, om = hashed
+        for s, n in ((wl.states[0], 65536), (wl.states[5], 3001)):
+            check_raycast(ctx, mid, om, s.x, s.xdot, n, wl.params, wl.max_range)
+        wl, mid, om = dense
+        for s, n in ((wl.states[1], 4096), (wl.states[7], 1000)):
+            check_raycast(ctx, mid, om, s.x, s.xdot, n, wl.params, wl.max_range)
+    finally:
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_CELL_SKIP, -1)
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, -1)
+    with pytest.raises(R.RmpError):
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_CELL_SKIP, 2)
+
+
 @pytest.mark.parametrize("order,budget,lgs", [(0, 1, 0), (0, 2, 2), (1, 3, 0), (1, 24, 1),
                                                (0, 0, 0), (1, -1, -1), (0, 7, 1)])
 def test_split_and_ray_order_keep_results(ctx, hashed, dense, order, budget, lgs):
