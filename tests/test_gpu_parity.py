@@ -402,3 +402,39 @@ def test_tuning_knobs_keep_results(ctx, hashed, block, lgs):
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, -1)
     with pytest.raises(R.RmpError):
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 100)
+
+
+def test_maximum_ray_count_sampled(ctx, dense):
+    """The largest evaluation the ABI allows (2^24 - 1 rays with Halton offset 1): the hit
+    counts add up over all rays, and 3000 sampled rays match the oracle ray by ray (hit
+    record bit-exact, per-ray policy within tolerance)."""
+    torch = torch_cuda()
+    wl, mid, om = dense
+    s = wl.states[3]
+    n = (1 << 24) - 1
+    pg = R.make_params(wl.params, wl.max_range)
+    po = O.make_params(wl.params, wl.max_range)
+    hits = torch.empty(n * 24, dtype=torch.uint8, device="cuda")
+    per = torch.empty(n * 9, dtype=torch.float32, device="cuda")
+    res = R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, n, pg, hits=hits, per_ray=per)
+    h = hits.cpu().numpy().view(R.HIT_DTYPE)
+    assert res["status"] == 0 and res["n_rays"] == n
+    assert res["n_hits"] == int(np.count_nonzero(h["status"] == R.RMP_RAY_HIT))
+    idx = np.random.default_rng(12).choice(n, 3000, replace=False)
+    P = O.quantize_pos(s.x, wl.map.origin, wl.map.voxel_size)
+    R_fx = O.range_fx(wl.max_range, wl.map.voxel_size)
+    dirs = np.concatenate([O.ray_dirs(1, int(j) + 1) for j in idx])
+    ho = O.dda(om, P, O.quantize_dirs(dirs), R_fx)
+    assert_hits_exact(h[idx], ho)
+    pv = per.view(n, 9)[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    por = np.zeros((len(idx), 9))
+    for i, (rec, d) in enumerate(zip(ho, dirs)):
+        if rec["status"] != R.RMP_RAY_HIT:
+            continue
+        r = -d.astype(np.float64)
+        f, A = O.ray_policy(po, r, float(rec["d"]), s.xdot, O.active32(s.xdot, d),
+                            float(rec["d"]) < po.r)
+        por[i, :3], por[i, 3:] = f, A
+    assert_per_ray_close(pv, por)
+    with pytest.raises(R.RmpError):
+        R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, n + 1, pg)
