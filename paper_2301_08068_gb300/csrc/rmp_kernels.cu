@@ -1021,22 +1021,27 @@ __device__ void grid_finish(const double part[9], unsigned hits, unsigned act, W
   if (stage == 0) return;
   __threadfence();
   sum_partials(parts + g0, gsz, tot, &tot_h, &tot_a);
-  if (threadIdx.x == 0) {
-    CtaPartial p;
+  if (n_groups > 1) {
+    if (threadIdx.x == 0) {
+      CtaPartial p;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) p.v[q] = tot[q];
-    p.n_hits = tot_h;
-    p.n_active = tot_a;
-    groups[gi] = p;
-    ws->group_ticket[gi] = 0;
+      for (int q = 0; q < 9; ++q) p.v[q] = tot[q];
+      p.n_hits = tot_h;
+      p.n_active = tot_a;
+      groups[gi] = p;
+      ws->group_ticket[gi] = 0;
+      __threadfence();
+      const unsigned t = atomicAdd(&ws->ticket, 1u);
+      stage = (t == (unsigned)n_groups - 1) ? 2 : 0;
+    }
+    __syncthreads();
+    if (stage != 2) return;
     __threadfence();
-    const unsigned t = atomicAdd(&ws->ticket, 1u);
-    stage = (t == (unsigned)n_groups - 1) ? 2 : 0;
+    sum_partials(groups, n_groups, tot, &tot_h, &tot_a);
+  } else if (threadIdx.x == 0) {
+    // a single group: its sum is the total (the same value the second level would give)
+    ws->group_ticket[gi] = 0;
   }
-  __syncthreads();
-  if (stage != 2) return;
-  __threadfence();
-  sum_partials(groups, n_groups, tot, &tot_h, &tot_a);
   __shared__ rmp_result_t r;
   if (threadIdx.x == 0) {
     for (int q = 0; q < 6; ++q) r.A[q] = tot[q];
