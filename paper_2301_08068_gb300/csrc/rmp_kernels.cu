@@ -926,36 +926,51 @@ __device__ void resolve_pinv(const double* S, const double* b, rmp_result_t& r) 
     den[i] = __shfl_sync(0xffffffffu, den_t, i);
   }
   if (t != 0) return;
-  int idx[3] = {0, 1, 2};
-  if (lam[idx[1]] < lam[idx[0]]) { int u = idx[0]; idx[0] = idx[1]; idx[1] = u; }
-  if (lam[idx[2]] < lam[idx[1]]) { int u = idx[1]; idx[1] = idx[2]; idx[2] = u; }
-  if (lam[idx[1]] < lam[idx[0]]) { int u = idx[0]; idx[0] = idx[1]; idx[1] = u; }
-  const double lmax = lam[idx[2]];
-  uint32_t rank = 0;
-  bool keep[3];
+  // ascending eigenpairs by a 3-element sorting network on registers (no indexed arrays)
+  double e0 = lam[0], e1 = lam[1], e2 = lam[2];
+  double d0 = den[0], d1 = den[1], d2 = den[2];
+  float c0[3] = {V[0][0], V[1][0], V[2][0]}, c1[3] = {V[0][1], V[1][1], V[2][1]},
+        c2[3] = {V[0][2], V[1][2], V[2][2]};
+  auto swap01 = [&]() {
+    const double te = e0, td = d0;
+    e0 = e1; d0 = d1; e1 = te; d1 = td;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    r.eig[i] = lam[idx[i]];
-    keep[i] = lmax > 1e-300 && lam[idx[i]] > 1e-12 * lmax;
-    rank += keep[i] ? 1u : 0u;
+    for (int i = 0; i < 3; ++i) { const float tc = c0[i]; c0[i] = c1[i]; c1[i] = tc; }
+  };
+  if (e1 < e0) swap01();
+  if (e2 < e1) {
+    const double te = e1, td = d1;
+    e1 = e2; d1 = d2; e2 = te; d2 = td;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { const float tc = c1[i]; c1[i] = c2[i]; c2[i] = tc; }
   }
-  r.rank = rank;
+  if (e1 < e0) swap01();
+  const double lmax = e2;
+  const bool k0 = lmax > 1e-300 && e0 > 1e-12 * lmax, k1 = lmax > 1e-300 && e1 > 1e-12 * lmax,
+             k2 = lmax > 1e-300 && e2 > 1e-12 * lmax;
+  r.eig[0] = e0;
+  r.eig[1] = e1;
+  r.eig[2] = e2;
+  r.rank = (k0 ? 1u : 0u) + (k1 ? 1u : 0u) + (k2 ? 1u : 0u);
   r.f[0] = r.f[1] = r.f[2] = 0.0;
-  if (rank == 3 && ok) {
+  if (r.rank == 3 && ok) {
     r.f[0] = fa0;
     r.f[1] = fa1;
     r.f[2] = fa2;
     return;
   }
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    if (!keep[i]) continue;
-    const int e = idx[i];
-    const double v0 = V[0][e], v1 = V[1][e], v2 = V[2][e];
-    const double proj = (v0 * b[0] + v1 * b[1] + v2 * b[2]) / (lam[e] * den[e]);
-    r.f[0] += proj * v0;
-    r.f[1] += proj * v1;
-    r.f[2] += proj * v2;
+  // a deficient rank projects b on the kept eigenvectors
+  if (k0) {
+    const double proj = (c0[0] * b[0] + c0[1] * b[1] + c0[2] * b[2]) / (e0 * d0);
+    r.f[0] += proj * c0[0]; r.f[1] += proj * c0[1]; r.f[2] += proj * c0[2];
+  }
+  if (k1) {
+    const double proj = (c1[0] * b[0] + c1[1] * b[1] + c1[2] * b[2]) / (e1 * d1);
+    r.f[0] += proj * c1[0]; r.f[1] += proj * c1[1]; r.f[2] += proj * c1[2];
+  }
+  if (k2) {
+    const double proj = (c2[0] * b[0] + c2[1] * b[1] + c2[2] * b[2]) / (e2 * d2);
+    r.f[0] += proj * c2[0]; r.f[1] += proj * c2[1]; r.f[2] += proj * c2[2];
   }
 }
 
