@@ -16,8 +16,9 @@ Printed JSON line (rank 0):
             timed region), wall clock per call;
   roofline  algorithmic bytes per launch / mean kernel time against the measured HBM copy
             bandwidth; traffic from the committed ncu capture when it matches this kernel;
-  cpu_baseline  the C oracle, single-threaded on this host, on a bounded sample.
---impl reference times the oracle instead (rank 0 only).
+  cpu_baseline  the C oracle on a bounded sample: one evaluation per host thread at once,
+            on every core of this host (and, beside it, on one core).
+--impl reference times the oracle instead (rank 0 only, every host core).
 """
 from __future__ import annotations
 
@@ -43,6 +44,13 @@ N_RAYS = 65536
 N_STATES = 64
 FLUSH_BYTES = 256 << 20
 PAPER_RATE = 65536 * 3000 / 1e9   # 65536 rays at up to 3 kHz (abstract), other hardware
+# integer operations of one step of the plain exact DDA: two cross-multiplied t comparisons
+# (two 32x32->64 products and a 64-bit compare each: 8), the range test (product, shift,
+# compare: 3), the step itself (voxel index, boundary numerator: 3), the voxel address
+# (block key, in-block offset: 4), the load's test and the loop branch (2)
+INT_OPS_PER_STEP = 20
+SM_COUNT = 152
+INT_LANES_PER_SM = 128
 
 
 def parse():
@@ -88,8 +96,41 @@ def whole_job_rate(world: int, rays_per_rank_step: int, ms_max: float) -> float:
     return world * rays_per_rank_step / (ms_max / 1e3) / 1e9
 
 
-def cpu_cores_used() -> int:
-    return 1
+def host_cores() -> int:
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_on_threads(om, p, states, n_rays: int, threads: int, evals: int):
+    """`evals` oracle evaluations of `n_rays` rays, state k % len(states) for evaluation k,
+    spread over `threads` host threads: the oracle is the unchanged single-threaded C code
+    (its evaluation keeps no global state and the ctypes call releases the GIL), run on
+    independent states at once.  Returns the wall time in seconds."""
+    import threading
+    import oracle as O
+    nxt = [0]
+    lock = threading.Lock()
+
+    def work():
+        while True:
+            with lock:
+                k = nxt[0]
+                nxt[0] += 1
+            if k >= evals:
+                return
+            s = states[k % len(states)]
+            O.raycast_eval(om, s.x, s.xdot, n_rays, p, want_hits=False, want_per_ray=False)
+
+    ts = [threading.Thread(target=work) for _ in range(threads)]
+    t0 = time.perf_counter()
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return time.perf_counter() - t0
 
 
 def time_oracle(wl, seconds: float, max_evals: int):
@@ -465,9 +506,9 @@ def serve_section(ctx, seconds: float) -> dict:
 
 
 def run_reference(args):
-    """The oracle on this host's cores (one thread).  Each step evaluates a bounded sample of
-    the workload -- the first m rays of a state -- with m sized so that warm-up plus timed
-    steps take about --ref-seconds in total."""
+    """The oracle on every core of this host, one evaluation per thread at once.  Each step
+    evaluates a bounded sample of the workload -- the first m rays of one state per thread --
+    with m sized so that warm-up plus timed steps take about --ref-seconds in total."""
     rank, local_rank, world = dist_env()
     if rank != 0:
         return
@@ -479,21 +520,20 @@ def run_reference(args):
     t = time.perf_counter()
     O.raycast_eval(om, s0.x, s0.xdot, 4096, p, want_hits=False, want_per_ray=False)
     per_ray = (time.perf_counter() - t) / 4096
-    budget = args.ref_seconds / max(1, args.steps + args.warmup)
+    cores = host_cores()
+    budget = args.ref_seconds / max(1, args.steps + args.warmup)   # wall seconds per step
     m = int(min(N_RAYS, max(256, budget / per_ray)) // 256 * 256)
     for i in range(args.warmup):
-        s = wl.states[i % N_STATES]
-        O.raycast_eval(om, s.x, s.xdot, m, p, want_hits=False, want_per_ray=False)
+        st = [wl.states[(i * cores + c) % N_STATES] for c in range(cores)]
+        oracle_on_threads(om, p, st, m, cores, cores)
     times = []
     for i in range(args.steps):
-        s = wl.states[i % N_STATES]
-        t = time.perf_counter()
-        O.raycast_eval(om, s.x, s.xdot, m, p, want_hits=False, want_per_ray=False)
-        times.append(time.perf_counter() - t)
+        st = [wl.states[(i * cores + c) % N_STATES] for c in range(cores)]
+        times.append(oracle_on_threads(om, p, st, m, cores, cores))
     ms = 1e3 * sum(times) / len(times)
-    value = m / (ms / 1e3) / 1e9
-    sample = ("each step: the first %d of the 65536 Halton rays of one state of the workload, "
-              "single-threaded C oracle" % m)
+    value = cores * m / (ms / 1e3) / 1e9
+    sample = ("each step: the first %d of the 65536 Halton rays of %d states of the workload, "
+              "the single-threaded C oracle on %d host threads at once" % (m, cores, cores))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -502,7 +542,7 @@ def run_reference(args):
         "config": {"workload": WORKLOAD, "n_rays": N_RAYS, "states": N_STATES,
                    "rays_per_step_sample": m},
         "evals_per_s": value * 1e9 / N_RAYS,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -538,12 +578,13 @@ def main():
 
     # algorithmic bytes per launch from the exact per-ray step and block counts
     hits = torch.empty(N_RAYS * 24, dtype=torch.uint8, device=dev)
-    alg = []
+    alg, steps_per_launch = [], []
     for i in range(N_STATES):
         R.rmp_raycast_eval_async(ctx.handle, mid, states[i], N_RAYS, params, ws, outs[i], hits=hits)
         h = hits.cpu().numpy().view(R.HIT_DTYPE)
         alg.append(float(((h["steps"].astype(np.int64) + 1) * 4).sum() +
                          16 * h["blocks"].astype(np.int64).sum()))
+        steps_per_launch.append(float(h["steps"].astype(np.int64).sum()))
     launch = R.rmp_eval_launch_info(ctx.handle, mid, N_RAYS, params)
     grid = launch["grid"]
     alg_bytes = float(np.mean(alg)) + grid * 80 + 48 + 144
@@ -598,10 +639,20 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, secs, _ = time_oracle(wl, args.cpu_seconds, 200)
-        cpu = {"value": n * N_RAYS / secs / 1e9, "unit": UNIT, "cores": cpu_cores_used(),
+        one = n * N_RAYS / secs / 1e9
+        import oracle as O
+        cores = host_cores()
+        # all cores: about cpu_seconds of CPU work in total, two evaluations per thread at least
+        evals = max(2 * cores, int(round(args.cpu_seconds / (secs / n))))
+        wall = oracle_on_threads(O.OracleMap(wl.map), O.make_params(wl.params, wl.max_range),
+                                 wl.states, N_RAYS, cores, evals)
+        cpu = {"value": evals * N_RAYS / wall / 1e9, "unit": UNIT, "cores": cores,
                "kind": "oracle",
-               "sample": "%d full evaluations (65536 rays each) of the workload's states, "
-                         "single-threaded C oracle, %.1f s" % (n, secs)}
+               "sample": "%d full evaluations (65536 rays each) of the workload's states, the "
+                         "single-threaded C oracle on %d host threads at once (independent "
+                         "states), %.2f s wall" % (evals, cores, wall),
+               "single_core": {"value": one, "unit": UNIT, "cores": 1,
+                               "sample": "%d full evaluations, one thread, %.1f s" % (n, secs)}}
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:
@@ -614,6 +665,10 @@ def main():
     src = kernel_source_hash()
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (ms / 1e3) / 1e9
+    # secondary ALU roofline: the plain DDA's integer work, INT_OPS_PER_STEP per voxel step,
+    # against every SM's integer lanes at the sampled SM clock
+    alu_ops = float(np.mean(steps_per_launch)) * INT_OPS_PER_STEP
+    alu_peak = SM_COUNT * INT_LANES_PER_SM * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e12
     traffic = committed_traffic(src)
     l2_gbs = l2_probe(flush) if rank == 0 else None
     if rank == 0:
@@ -640,6 +695,13 @@ def main():
                          "l2": {"achieved": achieved, "peak_probe": l2_gbs, "unit": "GB/s",
                                 "frac": achieved / l2_gbs if l2_gbs else None,
                                 "probe": "24 MiB device-to-device copies resident in L2"},
+                         "alu": {"achieved": alu_ops / (ms / 1e3) / 1e12, "peak": alu_peak,
+                                 "unit": "Tops/s",
+                                 "frac": alu_ops / (ms / 1e3) / 1e12 / alu_peak,
+                                 "voxel_steps_per_launch": float(np.mean(steps_per_launch)),
+                                 "ops_per_step": INT_OPS_PER_STEP,
+                                 "peak_source": "%d SMs x %d int32 lanes x SM clock" %
+                                                (SM_COUNT, INT_LANES_PER_SM)},
                          "kernel": "raycast_rmp_kernel<hashed TSDF, grid layout, "
                                    "compensated FP32 reduction>",
                          "kernel_source_sha256_16": src},

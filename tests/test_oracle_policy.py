@@ -174,6 +174,26 @@ def test_map_eval_sums_equal_exactly_rounded_sums(orc):
     assert np.linalg.eigvalsh(full(res["sumA"])).min() >= -1e-12 * np.abs(res["sumA"]).max()
 
 
+def test_concurrent_evaluations_equal_serial_ones(orc):
+    """The all-cores CPU baseline runs the oracle on several host threads at once; its
+    evaluation keeps no shared state, so each thread's result is the serial one bit for bit."""
+    from concurrent.futures import ThreadPoolExecutor
+    wl = W.hashed_workload(n_states=8)
+    om = orc.OracleMap(wl.map)
+    p = orc.make_params(wl.params, wl.max_range)
+
+    def run(s):
+        return orc.raycast_eval(om, s.x, s.xdot, 2048, p, want_hits=False, want_per_ray=False)[0]
+
+    serial = [run(s) for s in wl.states]
+    with ThreadPoolExecutor(4) as ex:
+        threaded = list(ex.map(run, wl.states))
+    for a, b in zip(serial, threaded):
+        for k in ("sumA", "sumAf", "f", "eig"):
+            assert np.array_equal(a[k], b[k]), k
+        assert (a["n_hits"], a["n_active"], a["rank"]) == (b["n_hits"], b["n_active"], b["rank"])
+
+
 def test_zero_velocity_gives_zero_policy(orc):
     wl = W.hashed_workload()
     om = orc.OracleMap(wl.map)
