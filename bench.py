@@ -57,7 +57,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10000)
-    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)
@@ -441,11 +441,7 @@ def serve_section(ctx, seconds: float) -> dict:
     continuous-batching server (256 MiB device-memory budget), and the same stream served
     by the plain kernel one request at a time (FIFO); latency = completion - arrival."""
     from paper_2301_08068_gb300 import rmp as R, workloads as W
-    wls = [W.dense_box_workload(n_states=64, dims=(128, 128, 128), vs=0.05, n_boxes=40,
-                                max_range=10.0, seed_index=6),
-           W.hashed_workload(n_states=64, state_seed_index=7),
-           W.hashed_workload(n_states=64, extent=(100.0, 100.0, 20.0), vs=0.2, n_prims=2500,
-                             seed_index=5, state_seed_index=8)]
+    wls = W.served_workloads(64)
     mids = [ctx.upload(w.map) for w in wls]
     params = [R.make_params(w.params, w.max_range) for w in wls]
     t_arr, maps, rays, vel = W.poisson_requests(3, 20000.0, seconds, 1024, 262144)
@@ -623,6 +619,26 @@ def main():
     res = [R.result_from_bytes(outs[i].cpu().numpy().tobytes()) for i in range(N_STATES)]
     assert all(r["status"] == 0 and np.all(np.isfinite(r["f"])) for r in res)
 
+    # the same evaluation with the per-ray outputs on (hit records 24 B and f, A 36 B per ray)
+    hits_on = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        per_ray = torch.empty(N_RAYS * 9, dtype=torch.float32, device=dev)
+        evo = []
+        for i in range(max(3, min(args.warmup, 50)) + 2000):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            R.rmp_raycast_eval_async(ctx.handle, mid, states[i % N_STATES], N_RAYS, params, ws,
+                                     outs[i % N_STATES], hits=hits, per_ray=per_ray)
+            b.record()
+            evo.append((a, b))
+        torch.cuda.synchronize()
+        t_on = [a.elapsed_time(b) for a, b in evo[-2000:]]
+        hits_on = {"outputs": "hit records and per-ray f, A (60 B per ray, 3.9 MB per launch)",
+                   "ms_per_step": float(np.mean(t_on)),
+                   "ms_per_step_p50": float(np.percentile(t_on, 50)),
+                   "Grays_per_s": N_RAYS / float(np.mean(t_on)) / 1e6, "steps": 2000}
+
     # end to end through the public synchronous call with host buffers
     n_e2e = max(1, min(args.steps, 2000))
     e2e_t = []
@@ -705,6 +721,7 @@ def main():
                          "kernel": "raycast_rmp_kernel<hashed TSDF, grid layout, "
                                    "compensated FP32 reduction>",
                          "kernel_source_sha256_16": src},
+            "per_ray_outputs_on": hits_on,
             "cpu_baseline": cpu,
             "gpu_launches": args.steps,
             **extra,

@@ -397,6 +397,17 @@ def sphere_shell_scan(n: int, radius: float, seed_index: int = 7) -> np.ndarray:
     return (g * radius).astype(np.float32)
 
 
+def served_workloads(n_states: int = 64):
+    """The three resident maps of the served stream, max range 10 m: dense 128^3 at 0.05 m
+    with 40 boxes; the hashed 40x40x10 m map at 0.1 m; hashed 100x100x20 m at 0.2 m with
+    2500 primitives (the 40x40x10 m density scaled by volume)."""
+    return [dense_box_workload(n_states=n_states, dims=(128, 128, 128), vs=0.05, n_boxes=40,
+                               max_range=10.0, seed_index=6),
+            hashed_workload(n_states=n_states, state_seed_index=7),
+            hashed_workload(n_states=n_states, extent=(100.0, 100.0, 20.0), vs=0.2,
+                            n_prims=2500, seed_index=5, state_seed_index=8)]
+
+
 def poisson_requests(n_maps: int, rate: float, duration: float, ray_lo: int, ray_hi: int,
                      seed_index: int = 4):
     """Poisson arrival times (s), map index (uniform) and log-uniform ray counts."""

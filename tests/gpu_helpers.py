@@ -69,13 +69,21 @@ def _full(a):
     return np.array([[a[0], a[1], a[2]], [a[1], a[3], a[4]], [a[2], a[4], a[5]]])
 
 
+def abs_Af(per):
+    """|A_i f_i| per ray (n x 3) from per-ray rows (f: 3, A: xx xy xz yy yz zz)."""
+    f, a = per[:, :3], per[:, 3:]
+    return np.abs(np.stack([a[:, 0] * f[:, 0] + a[:, 1] * f[:, 1] + a[:, 2] * f[:, 2],
+                            a[:, 1] * f[:, 0] + a[:, 3] * f[:, 1] + a[:, 4] * f[:, 2],
+                            a[:, 2] * f[:, 0] + a[:, 4] * f[:, 1] + a[:, 5] * f[:, 2]], axis=1))
+
+
 def assert_result_close(g, o, per_orc=None):
     assert g["status"] == 0
     assert g["n_rays"] == o["n_rays"] and g["n_hits"] == o["n_hits"]
     assert g["n_active"] == o["n_active"]
     if per_orc is not None:
         A = np.abs(per_orc[:, 3:]).sum(axis=0)
-        Af = np.stack([np.abs(_full(a) @ f) for a, f in zip(per_orc[:, 3:], per_orc[:, :3])]).sum(axis=0)
+        Af = abs_Af(per_orc).sum(axis=0)
     else:
         A = np.full(6, np.abs(o["sumA"]).max())
         Af = np.full(3, np.abs(o["sumAf"]).max())
