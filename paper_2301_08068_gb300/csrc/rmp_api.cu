@@ -40,12 +40,11 @@ struct rmp_ctx {
   int tune_ray_order = 0;    // 0: coherent direction cells, 1: Halton index order
   int tune_split = -1;       // split budget (-1: default, 0: never split)
   int tune_cells = -1;       // voxel-box skipping (-1: batches only, 0: off, 1: on)
-  // scratch of the synchronous calls (serialised by mu)
+  // scratch of the synchronous calls (serialised by mu): the state travels in the launch's
+  // constants; the kernel writes the result straight into mapped pinned host memory
   void* ws = nullptr;
-  double* state_dev = nullptr;
-  rmp_result_t* result_dev = nullptr;
-  double* state_host = nullptr;        // pinned
-  rmp_result_t* result_host = nullptr; // pinned
+  rmp_result_t* result_host = nullptr;  // pinned, mapped
+  rmp_result_t* result_map = nullptr;   // its device address
 };
 
 namespace {
@@ -98,18 +97,19 @@ float round_down_f32(double v) {
 // kernel's ray_of_slot).  Cells hold >= 32 rays so a warp spans at most two of them, about
 // n/48 cells, shaped close to square on the sphere (3^b ~ pi 2^a).
 void pick_ray_cells(uint32_t n, EvalConsts* k) {
+  // candidates M = 2^a 3^b with 32 M <= n, scored in log2 units with one logarithm per call:
+  // |log2 M - log2(n / 48)| + 0.5 |log2(3^b / (pi 2^a))|
+  const double L3 = 1.5849625007211562, LPI = 1.6514961294723187;   // log2 3, log2 pi
+  const double lt = std::log2(std::max(n / 48.0, 1.0));
   uint64_t best = 1;
   double best_score = 1e300;
-  const double target = n / 48.0;
   for (int a = 0; a <= 24; ++a) {
-    for (int b = 0; b <= 15; ++b) {
-      double m = std::ldexp(1.0, a) * std::pow(3.0, b);
-      if (m > n / 32.0) continue;
-      double score = std::fabs(std::log(m / std::max(target, 1.0))) +
-                     0.5 * std::fabs(std::log(std::pow(3.0, b) / (3.141592653589793 * std::ldexp(1.0, a))));
+    uint64_t m = 1ull << a;
+    for (int b = 0; b <= 15 && m * 32ull <= n; ++b, m *= 3ull) {
+      const double score = std::fabs(a + b * L3 - lt) + 0.5 * std::fabs(b * L3 - LPI - a);
       if (score < best_score) {
         best_score = score;
-        best = (uint64_t)m;
+        best = m;
       }
     }
   }
@@ -293,10 +293,9 @@ int rmp_ctx_create(rmp_ctx** out, int device) {
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaMalloc(&c->ws, workspace_bytes());
   if (e == cudaSuccess) e = cudaMemset(c->ws, 0, workspace_bytes());
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->state_dev, 6 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->result_dev, sizeof(rmp_result_t));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->state_host, 6 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->result_host, sizeof(rmp_result_t));
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void**)&c->result_host, sizeof(rmp_result_t), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->result_map, c->result_host, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     rmp_ctx_destroy(c);
@@ -314,9 +313,6 @@ int rmp_ctx_destroy(rmp_ctx* c) {
     for (auto& kv : c->maps) free_map(kv.second);
     c->maps.clear();
     if (c->ws) cudaFree(c->ws);
-    if (c->state_dev) cudaFree(c->state_dev);
-    if (c->result_dev) cudaFree(c->result_dev);
-    if (c->state_host) cudaFreeHost(c->state_host);
     if (c->result_host) cudaFreeHost(c->result_host);
   }
   delete c;
@@ -623,18 +619,14 @@ int rmp_raycast_eval(rmp_ctx* c, uint32_t map_id, const double x[3], const doubl
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  for (int a = 0; a < 3; ++a) {
-    c->state_host[a] = x[a];
-    c->state_host[3 + a] = xdot[a];
+  for (int a = 0; a < 3; ++a) {        // x, xdot go to the device inside the launch
+    k.x0[a] = x[a];
+    k.x0[3 + a] = xdot[a];
   }
   int block, grid;
   launch_shape(c, (uint64_t)n_rays << k.lg_segs, &block, &grid);
-  RMP_CUDA(cudaMemcpyAsync(c->state_dev, c->state_host, 6 * sizeof(double),
-                           cudaMemcpyHostToDevice, s));
-  RMP_CUDA(launch_raycast(dm, k, c->state_dev, c->ws, c->result_dev, hits_dev, per_ray_dev,
+  RMP_CUDA(launch_raycast(dm, k, nullptr, c->ws, c->result_map, hits_dev, per_ray_dev,
                           block, grid, s));
-  RMP_CUDA(cudaMemcpyAsync(c->result_host, c->result_dev, sizeof(rmp_result_t),
-                           cudaMemcpyDeviceToHost, s));
   RMP_CUDA(cudaStreamSynchronize(s));
   *out = *c->result_host;
   return RMP_OK;
@@ -670,18 +662,14 @@ int rmp_scan_eval(rmp_ctx* c, const float* points_dev, uint32_t n, const double 
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = (cudaStream_t)stream;
   for (int a = 0; a < 3; ++a) {
-    c->state_host[a] = x[a];
-    c->state_host[3 + a] = xdot[a];
+    k.x0[a] = x[a];
+    k.x0[3 + a] = xdot[a];
   }
   int block, grid;
   launch_shape(c, n, &block, &grid);
   scan_grid_cap(c, &grid);
-  RMP_CUDA(cudaMemcpyAsync(c->state_dev, c->state_host, 6 * sizeof(double),
-                           cudaMemcpyHostToDevice, s));
-  RMP_CUDA(launch_scan(points_dev, k, c->state_dev, c->ws, c->result_dev, per_ray_dev, block,
-                       grid, s));
-  RMP_CUDA(cudaMemcpyAsync(c->result_host, c->result_dev, sizeof(rmp_result_t),
-                           cudaMemcpyDeviceToHost, s));
+  RMP_CUDA(launch_scan(points_dev, k, nullptr, c->ws, c->result_map, per_ray_dev, block, grid,
+                       s));
   RMP_CUDA(cudaStreamSynchronize(s));
   *out = *c->result_host;
   return RMP_OK;

@@ -82,6 +82,8 @@ struct EvalConsts {
   double att_alpha, att_beta;        // attractor gain and damping (combined evaluations)
   int att_mean;                      // combined: ray sums divided by the ray count first
   int pad_;
+  double x0[6];                      // x, xdot carried in the launch itself, read when the
+                                     // kernel's state pointer is null (synchronous calls)
 };
 
 // Closed-loop rollout of point robots (per robot, device-resident).

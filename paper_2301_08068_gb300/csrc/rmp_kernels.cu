@@ -1085,8 +1085,17 @@ struct CtaState {
   int bad[3];
 };
 
-__device__ __forceinline__ void split_velocity(const double* state, CtaState& cs, int a) {
-  const double x = state[3 + a];
+// Component i of (x, xdot): from device memory, or, with a null pointer, from the copy the
+// launch carries in its constants (selected with constant offsets, no local-memory array).
+__device__ __forceinline__ double state_at(const double* state, const EvalConsts& k, int i) {
+  if (state) return state[i];
+  double v = k.x0[0];
+#pragma unroll
+  for (int j = 1; j < 6; ++j) v = i == j ? k.x0[j] : v;
+  return v;
+}
+
+__device__ __forceinline__ void split_velocity(double x, CtaState& cs, int a) {
   cs.v[a] = __double2float_rn(x);
   cs.vl[a] = __double2float_rn(__dsub_rn(x, (double)cs.v[a]));
 }
@@ -1275,13 +1284,13 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
     const int a = threadIdx.x;
     const double o = KIND != RMP_MAP_DENSE_U8 ? 0.0
                      : (a == 0 ? m.origin[0] : (a == 1 ? m.origin[1] : m.origin[2]));
-    const double q = __dmul_rn(__ddiv_rn(__dsub_rn(state[a], o), m.vs), 65536.0);
+    const double q = __dmul_rn(__ddiv_rn(__dsub_rn(state_at(state, k, a), o), m.vs), 65536.0);
     // |voxel| < 2^22 keeps block keys and fixed-point products in range; NaN fails too
     const int bad = !(fabs(q) < 274877906944.0);
     cs.bad[a] = bad;
     cs.P[a] = bad ? 0 : __double2ll_rn(q);
   } else if (threadIdx.x < 6) {
-    split_velocity(state, cs, threadIdx.x - 3);
+    split_velocity(state_at(state, k, threadIdx.x), cs, threadIdx.x - 3);
   }
   typename BlockReduce<RED>::Acc acc;
   BlockReduce<RED>::init(acc);
@@ -1827,9 +1836,9 @@ __global__ void __launch_bounds__(256) scan_rmp_kernel(const float* __restrict__
                                                        rmp_result_t* out, float* per_ray) {
   __shared__ CtaState cs;
   if (threadIdx.x < 3) {
-    cs.xf[threadIdx.x] = __double2float_rn(state[threadIdx.x]);
+    cs.xf[threadIdx.x] = __double2float_rn(state_at(state, k, threadIdx.x));
   } else if (threadIdx.x < 6) {
-    split_velocity(state, cs, threadIdx.x - 3);
+    split_velocity(state_at(state, k, threadIdx.x), cs, threadIdx.x - 3);
   }
   __syncthreads();
   typename BlockReduce<RED>::Acc acc;

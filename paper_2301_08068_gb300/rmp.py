@@ -195,13 +195,27 @@ def _check(status: int, what: str):
         raise RmpError(status, what)
 
 
+_torch = None
+
+
+def _current_stream() -> Optional[int]:
+    """Handle of torch's current CUDA stream (None without a usable torch CUDA)."""
+    global _torch
+    try:
+        if _torch is None:
+            import torch
+            _torch = torch
+        raw = getattr(_torch._C, "_cuda_getCurrentRawStream", None)
+        if raw is not None:                 # one call instead of building a Stream object
+            return raw(_torch.cuda.current_device())
+        return _torch.cuda.current_stream().cuda_stream
+    except Exception:
+        return None
+
+
 def _stream(stream) -> Optional[int]:
     if stream is None:
-        try:
-            import torch
-            return torch.cuda.current_stream().cuda_stream
-        except Exception:
-            return None
+        return _current_stream()
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
@@ -217,9 +231,13 @@ def _dptr(t) -> Optional[int]:
     return t.data_ptr()
 
 
+_D3 = C.c_double * 3
+
+
 def _vec3(v):
-    a = (C.c_double * 3)(*[float(x) for x in np.asarray(v, np.float64).reshape(3)])
-    return a
+    if not (isinstance(v, np.ndarray) and v.shape == (3,)):
+        v = np.asarray(v, np.float64).reshape(3)
+    return _D3(*v.tolist())
 
 
 def make_params(d: dict, max_range: float) -> rmp_params_t:
@@ -235,9 +253,9 @@ def make_params(d: dict, max_range: float) -> rmp_params_t:
 
 
 def result_dict(r: rmp_result_t) -> dict:
-    return dict(f=np.array(r.f[:]), sumA=np.array(r.A[:]), sumAf=np.array(r.Af[:]),
-                eig=np.array(r.eig[:]), n_rays=r.n_rays, n_hits=r.n_hits, n_active=r.n_active,
-                rank=r.rank, status=r.status)
+    v = np.frombuffer(r, np.float64, 15)    # f (3), sum A (6), sum A f (3), eig (3): views
+    return dict(f=v[0:3], sumA=v[3:9], sumAf=v[9:12], eig=v[12:15], n_rays=r.n_rays,
+                n_hits=r.n_hits, n_active=r.n_active, rank=r.rank, status=r.status)
 
 
 def result_from_bytes(b: bytes) -> dict:
