@@ -746,7 +746,24 @@ struct Acc64 {
   double s[9];
 };
 
-// Block-level reduction of the per-thread accumulators into 9 doubles (thread 0).
+// Sums of one CTA handed from the block reduction to grid_finish: the 9 terms and the hit
+// and active counts.  In shared memory, written by lanes 0-10 of warp 0 (lane q < 9: term q;
+// lanes 9, 10: the counts), which are the lanes that read them again.
+struct CtaSums {
+  double v[9];
+  unsigned u[2];
+};
+
+__device__ __forceinline__ void merge1(float& s, float& c, float s2, float c2) {
+  float t, e;
+  two_sum(s, s2, t, e);
+  s = t;
+  c = __fadd_rn(__fadd_rn(c, c2), e);
+}
+
+// Block-level reduction of the per-thread accumulators and counts: a shuffle tree per warp,
+// then lane q of warp 0 merges term q of the warps in warp order (all terms at once, not one
+// thread walking them).  Called by every thread.
 template <int RED>
 struct BlockReduce;
 
@@ -758,8 +775,9 @@ struct BlockReduce<RMP_REDUCE_KAHAN32> {
     for (int q = 0; q < 9; ++q) a.s[q] = a.c[q] = 0.0f;
   }
   __device__ static void add(Acc& a, const float v[9]) { acc_add(a, v); }
-  __device__ static void reduce(Acc& a, double out[9]) {
+  __device__ static void reduce(Acc& a, unsigned nh, unsigned na, CtaSums& out) {
     __shared__ float sh[32][18];
+    __shared__ unsigned shu[32][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -770,20 +788,28 @@ struct BlockReduce<RMP_REDUCE_KAHAN32> {
         acc_merge(a, s2, c2, q);
       }
     }
+    nh = __reduce_add_sync(0xffffffffu, nh);
+    na = __reduce_add_sync(0xffffffffu, na);
     if (lane == 0) {
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
         sh[warp][q] = a.s[q];
         sh[warp][9 + q] = a.c[q];
       }
+      shu[warp][0] = nh;
+      shu[warp][1] = na;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < nw; ++w)
-#pragma unroll
-        for (int q = 0; q < 9; ++q) acc_merge(a, sh[w][q], sh[w][9 + q], q);
-#pragma unroll
-      for (int q = 0; q < 9; ++q) out[q] = (double)a.s[q] + (double)a.c[q];
+    if (warp == 0) {
+      if (lane < 9) {
+        float s = sh[0][lane], c = sh[0][9 + lane];
+        for (int w = 1; w < nw; ++w) merge1(s, c, sh[w][lane], sh[w][9 + lane]);
+        out.v[lane] = (double)s + (double)c;
+      } else if (lane < 11) {
+        unsigned t = 0;
+        for (int w = 0; w < nw; ++w) t += shu[w][lane - 9];
+        out.u[lane - 9] = t;
+      }
     }
   }
 };
@@ -799,115 +825,116 @@ struct BlockReduce<RMP_REDUCE_FP64> {
 #pragma unroll
     for (int q = 0; q < 9; ++q) a.s[q] += (double)v[q];
   }
-  __device__ static void reduce(Acc& a, double out[9]) {
+  __device__ static void reduce(Acc& a, unsigned nh, unsigned na, CtaSums& out) {
     __shared__ double sh[32][9];
+    __shared__ unsigned shu[32][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
       for (int q = 0; q < 9; ++q) a.s[q] += __shfl_down_sync(0xffffffffu, a.s[q], off);
-    if (lane == 0)
+    nh = __reduce_add_sync(0xffffffffu, nh);
+    na = __reduce_add_sync(0xffffffffu, na);
+    if (lane == 0) {
 #pragma unroll
       for (int q = 0; q < 9; ++q) sh[warp][q] = a.s[q];
+      shu[warp][0] = nh;
+      shu[warp][1] = na;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < nw; ++w)
-#pragma unroll
-        for (int q = 0; q < 9; ++q) a.s[q] += sh[w][q];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) out[q] = a.s[q];
+    if (warp == 0) {
+      if (lane < 9) {
+        double s = sh[0][lane];
+        for (int w = 1; w < nw; ++w) s += sh[w][lane];
+        out.v[lane] = s;
+      } else if (lane < 11) {
+        unsigned t = 0;
+        for (int w = 0; w < nw; ++w) t += shu[w][lane - 9];
+        out.u[lane - 9] = t;
+      }
     }
   }
 };
 
-__device__ __forceinline__ unsigned block_sum_u32(unsigned v) {
-  __shared__ unsigned shu[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = __reduce_add_sync(0xffffffffu, v);
-  if (lane == 0) shu[warp] = v;
-  __syncthreads();
-  unsigned t = 0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < nw; ++w) t += shu[w];
-  __syncthreads();
-  return t;
-}
-
 // ------------------------------------------------------------------ FP64 resolve (Eq. 1)
 // f = (sum A)^+ (sum A f) with eigenvalues <= 1e-12 lambda_max treated as zero.  FP64
 // division and square root cost hundreds of cycles each on this GPU and FP64 issues at a
-// low rate, so the work is split over three lanes of one warp:
-//   lane 0: eigenvectors by cyclic Jacobi rotations in FP32 (matrix scaled by a power of
-//           two); lane 1, meanwhile: the FP64 adjugate solve adj(S) b / det(S);
+// low rate, so the work is split:
+//   eigenvectors by cyclic Jacobi rotations in FP32 (matrix scaled by a power of two), and,
+//   in another warp (or another lane of the same warp), the FP64 adjugate solve
+//   adj(S) b / det(S);
 //   lanes 0-2: each eigenvalue as the FP64 Rayleigh quotient v^T S v / v^T v of its FP32
-//           eigenvector (second-order accurate, ~1e-14 lambda_max), with
-//           1 / v^T v = 2 - v^T v to first order (v^T v = 1 + O(1e-7));
+//   eigenvector (second-order accurate, ~1e-14 lambda_max), with 1 / v^T v = 2 - v^T v to
+//   first order (v^T v = 1 + O(1e-7));
 //   lane 0: rank from the eigenvalues; full rank uses the adjugate solution, a deficient
-//           rank projects b on the kept eigenvectors, and writes f, eig, rank into r.
-// Called by all 32 lanes of one warp.
-__device__ void resolve_pinv(const double* S, const double* b, rmp_result_t& r) {
-  const int t = threadIdx.x & 31;
-  float W[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
-  double fa0 = 0.0, fa1 = 0.0, fa2 = 0.0;
-  int ok = 0;
-  if (t == 0) {
-    const double smax = fmax(fmax(fabs(S[0]), fabs(S[1])), fmax(fmax(fabs(S[2]), fabs(S[3])),
-                                                               fmax(fabs(S[4]), fabs(S[5]))));
-    const double scale = smax > 1e-300 ? ldexp(1.0, -ilogb(smax)) : 1.0;   // power of two
-    float a00 = (float)(S[0] * scale), a01 = (float)(S[1] * scale), a02 = (float)(S[2] * scale),
-          a11 = (float)(S[3] * scale), a12 = (float)(S[4] * scale), a22 = (float)(S[5] * scale);
-    for (int sweep = 0; sweep < 6; ++sweep) {
-      const float off = fabsf(a01) + fabsf(a02) + fabsf(a12);
-      const float dia = fabsf(a00) + fabsf(a11) + fabsf(a22);
-      if (!(off > 1e-6f * dia)) break;              // FP32 accuracy; FP64 refines below
+//   rank projects b on the kept eigenvectors, and writes f, eig, rank into r.
+
+// Eigenvectors (columns of W) of the symmetric S by FP32 Jacobi sweeps.  One thread.
+__device__ __forceinline__ void jacobi_f32(const double* S, float W[3][3]) {
+  const double smax = fmax(fmax(fabs(S[0]), fabs(S[1])), fmax(fmax(fabs(S[2]), fabs(S[3])),
+                                                           fmax(fabs(S[4]), fabs(S[5]))));
+  const double scale = smax > 1e-300 ? ldexp(1.0, -ilogb(smax)) : 1.0;   // power of two
+  float a00 = (float)(S[0] * scale), a01 = (float)(S[1] * scale), a02 = (float)(S[2] * scale),
+        a11 = (float)(S[3] * scale), a12 = (float)(S[4] * scale), a22 = (float)(S[5] * scale);
+  for (int sweep = 0; sweep < 6; ++sweep) {
+    const float off = fabsf(a01) + fabsf(a02) + fabsf(a12);
+    const float dia = fabsf(a00) + fabsf(a11) + fabsf(a22);
+    if (!(off > 1e-6f * dia)) break;              // FP32 accuracy; FP64 refines below
 #pragma unroll
-      for (int pq = 0; pq < 3; ++pq) {
-        float app, aqq, apq, apo, aqo;
-        if (pq == 0) { app = a00; aqq = a11; apq = a01; apo = a02; aqo = a12; }
-        else if (pq == 1) { app = a00; aqq = a22; apq = a02; apo = a01; aqo = a12; }
-        else { app = a11; aqq = a22; apq = a12; apo = a01; aqo = a02; }
-        if (apq == 0.0f) continue;
-        const float tau = __fdividef(aqq - app, 2.0f * apq);
-        const float at = fabsf(tau);
-        const float root = at < 1e18f ? (1.0f + at * at) * rsqrtf(1.0f + at * at) : at;
-        const float tt = copysignf(__fdividef(1.0f, at + root), tau);
-        const float c = rsqrtf(1.0f + tt * tt), sn = tt * c;
-        const float npp = app - tt * apq, nqq = aqq + tt * apq;
-        const float npo = c * apo - sn * aqo, nqo = sn * apo + c * aqo;
-        const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
-        if (pq == 0) { a00 = npp; a11 = nqq; a01 = 0.f; a02 = npo; a12 = nqo; }
-        else if (pq == 1) { a00 = npp; a22 = nqq; a02 = 0.f; a01 = npo; a12 = nqo; }
-        else { a11 = npp; a22 = nqq; a12 = 0.f; a01 = npo; a02 = nqo; }
+    for (int pq = 0; pq < 3; ++pq) {
+      float app, aqq, apq, apo, aqo;
+      if (pq == 0) { app = a00; aqq = a11; apq = a01; apo = a02; aqo = a12; }
+      else if (pq == 1) { app = a00; aqq = a22; apq = a02; apo = a01; aqo = a12; }
+      else { app = a11; aqq = a22; apq = a12; apo = a01; aqo = a02; }
+      if (apq == 0.0f) continue;
+      const float tau = __fdividef(aqq - app, 2.0f * apq);
+      const float at = fabsf(tau);
+      const float root = at < 1e18f ? (1.0f + at * at) * rsqrtf(1.0f + at * at) : at;
+      const float tt = copysignf(__fdividef(1.0f, at + root), tau);
+      const float c = rsqrtf(1.0f + tt * tt), sn = tt * c;
+      const float npp = app - tt * apq, nqq = aqq + tt * apq;
+      const float npo = c * apo - sn * aqo, nqo = sn * apo + c * aqo;
+      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      if (pq == 0) { a00 = npp; a11 = nqq; a01 = 0.f; a02 = npo; a12 = nqo; }
+      else if (pq == 1) { a00 = npp; a22 = nqq; a02 = 0.f; a01 = npo; a12 = nqo; }
+      else { a11 = npp; a22 = nqq; a12 = 0.f; a01 = npo; a02 = nqo; }
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const float vp = W[i][p], vq = W[i][q];
-          W[i][p] = c * vp - sn * vq;
-          W[i][q] = sn * vp + c * vq;
-        }
+      for (int i = 0; i < 3; ++i) {
+        const float vp = W[i][p], vq = W[i][q];
+        W[i][p] = c * vp - sn * vq;
+        W[i][q] = sn * vp + c * vq;
       }
     }
-  } else if (t == 1) {
-    const double c00 = S[3] * S[5] - S[4] * S[4], c01 = S[2] * S[4] - S[1] * S[5],
-                 c02 = S[1] * S[4] - S[2] * S[3], c11 = S[0] * S[5] - S[2] * S[2],
-                 c12 = S[1] * S[2] - S[0] * S[4], c22 = S[0] * S[3] - S[1] * S[1];
-    const double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
-    ok = det > 0.0;
-    if (det > 0.0) {
-      const double inv = 1.0 / det;
-      fa0 = (c00 * b[0] + c01 * b[1] + c02 * b[2]) * inv;
-      fa1 = (c01 * b[0] + c11 * b[1] + c12 * b[2]) * inv;
-      fa2 = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
-    }
   }
+}
+
+// FP64 solve adj(S) b / det(S); ok = det > 0.  One thread.
+__device__ __forceinline__ void adjugate_solve(const double* S, const double* b, double& fa0,
+                                               double& fa1, double& fa2, int& ok) {
+  const double c00 = S[3] * S[5] - S[4] * S[4], c01 = S[2] * S[4] - S[1] * S[5],
+               c02 = S[1] * S[4] - S[2] * S[3], c11 = S[0] * S[5] - S[2] * S[2],
+               c12 = S[1] * S[2] - S[0] * S[4], c22 = S[0] * S[3] - S[1] * S[1];
+  const double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
+  ok = det > 0.0;
+  if (det > 0.0) {
+    const double inv = 1.0 / det;
+    fa0 = (c00 * b[0] + c01 * b[1] + c02 * b[2]) * inv;
+    fa1 = (c01 * b[0] + c11 * b[1] + c12 * b[2]) * inv;
+    fa2 = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
+  }
+}
+
+// Rayleigh quotients, rank and f from the FP32 eigenvectors W (valid in lane 0) and the
+// adjugate solution (valid in every lane).  Called by all 32 lanes of one warp.
+__device__ __forceinline__ void resolve_finish(const double* S, const double* b,
+                                               const float (&W)[3][3], double fa0, double fa1,
+                                               double fa2, int ok, rmp_result_t& r) {
+  const int t = threadIdx.x & 31;
   float V[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) V[i][j] = __shfl_sync(0xffffffffu, W[i][j], 0);
-  fa0 = __shfl_sync(0xffffffffu, fa0, 1);
-  fa1 = __shfl_sync(0xffffffffu, fa1, 1);
-  fa2 = __shfl_sync(0xffffffffu, fa2, 1);
-  ok = __shfl_sync(0xffffffffu, ok, 1);
   double lam_t = 0.0, den_t = 0.0;
   if (t < 3) {
     const double v0 = t == 0 ? V[0][0] : (t == 1 ? V[0][1] : V[0][2]);
@@ -974,44 +1001,83 @@ __device__ void resolve_pinv(const double* S, const double* b, rmp_result_t& r) 
   }
 }
 
+
+// One warp: lane 0 runs the Jacobi sweeps, lane 1 the adjugate solve (the two branches
+// of one warp run one after the other).  Called by all 32 lanes of one warp.
+__device__ void resolve_pinv(const double* S, const double* b, rmp_result_t& r) {
+  const int t = threadIdx.x & 31;
+  float W[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+  double fa0 = 0.0, fa1 = 0.0, fa2 = 0.0;
+  int ok = 0;
+  if (t == 0) jacobi_f32(S, W);
+  else if (t == 1) adjugate_solve(S, b, fa0, fa1, fa2, ok);
+  fa0 = __shfl_sync(0xffffffffu, fa0, 1);
+  fa1 = __shfl_sync(0xffffffffu, fa1, 1);
+  fa2 = __shfl_sync(0xffffffffu, fa2, 1);
+  ok = __shfl_sync(0xffffffffu, ok, 1);
+  resolve_finish(S, b, W, fa0, fa1, fa2, ok, r);
+}
+
+// Two warps of a CTA (threads 0-63): warp 0 runs the Jacobi sweeps while warp 1 runs the
+// adjugate solve, so the two overlap; they meet at named barrier 1.  Called by threads
+// 0-63 of a CTA of at least 64 threads; S, b and r in shared memory.
+__device__ void resolve_pinv_cta(const double* S, const double* b, rmp_result_t& r) {
+  __shared__ double fa_sh[3];
+  __shared__ int ok_sh;
+  const int t = threadIdx.x;
+  float W[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+  if (t == 0) {
+    jacobi_f32(S, W);
+  } else if (t == 32) {
+    double fa0 = 0.0, fa1 = 0.0, fa2 = 0.0;
+    int ok = 0;
+    adjugate_solve(S, b, fa0, fa1, fa2, ok);
+    fa_sh[0] = fa0;
+    fa_sh[1] = fa1;
+    fa_sh[2] = fa2;
+    ok_sh = ok;
+  }
+  __syncwarp();
+  asm volatile("bar.sync 1, 64;" ::: "memory");
+  if (t >= 32) return;
+  resolve_finish(S, b, W, fa_sh[0], fa_sh[1], fa_sh[2], ok_sh, r);
+}
+
 // Sum `count` partials in a fixed order: thread (q, j) of the CTA (q < 11 terms, j < J =
-// blockDim / 16) adds partials j, j + J, ... of term q; then thread q adds its J sums in
-// order.  Result in tot / tot_h / tot_a.  Called by every thread.
+// blockDim / 16, a power of two) adds partials j, j + J, ... of term q; the J threads of a
+// term (adjacent lanes of one warp) then combine their sums by a shuffle tree.  Result in
+// tot / tot_h / tot_a.  Called by every thread.
 __device__ void sum_partials(const CtaPartial* p, int count, double* tot, unsigned* tot_h,
                              unsigned* tot_a) {
-  __shared__ double part_d[9][16];
-  __shared__ unsigned part_u[2][16];
   const int J = blockDim.x >> 4;
   const int q = threadIdx.x / J, j = threadIdx.x - q * J;
+  double s = 0.0;
+  unsigned u = 0;
   if (q < 9) {
-    double s = 0.0;
     for (int i = j; i < count; i += J) s += __ldcg(&p[i].v[q]);
-    part_d[q][j] = s;
   } else if (q < 11) {
-    unsigned s = 0;
-    for (int i = j; i < count; i += J) s += __ldcg(q == 9 ? &p[i].n_hits : &p[i].n_active);
-    part_u[q - 9][j] = s;
+    for (int i = j; i < count; i += J) u += __ldcg(q == 9 ? &p[i].n_hits : &p[i].n_active);
   }
-  __syncthreads();
-  if (threadIdx.x < 9) {
-    double s = 0.0;
-    for (int i = 0; i < J; ++i) s += part_d[threadIdx.x][i];
-    tot[threadIdx.x] = s;
-  } else if (threadIdx.x < 11) {
-    unsigned s = 0;
-    for (int i = 0; i < J; ++i) s += part_u[threadIdx.x - 9][i];
-    if (threadIdx.x == 9) *tot_h = s; else *tot_a = s;
+  for (int off = J >> 1; off > 0; off >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, off, J);
+    u += __shfl_down_sync(0xffffffffu, u, off, J);
+  }
+  if (j == 0) {
+    if (q < 9) tot[q] = s;
+    else if (q == 9) *tot_h = u;
+    else if (q == 10) *tot_a = u;
   }
   __syncthreads();
 }
 
-// Grid completion, deterministic and without one thread walking every CTA: each CTA stores
-// its partial; the last CTA of each group of kGroup CTAs (group ticket) sums the group's
-// partials in index order and stores a group partial; the last group to finish (grid
-// ticket) sums the group partials in index order in FP64 and resolves.  Tickets are reset
-// by the CTA that completes them.  Called by all threads of every CTA.
-__device__ void grid_finish(const double part[9], unsigned hits, unsigned act, WsHeader* ws,
-                            CtaPartial* parts, rmp_result_t* out, uint32_t n_rays, int status) {
+// Grid completion, deterministic and without one thread walking every CTA: lanes 0-10 of
+// warp 0 store the CTA's sums as its partial; the last CTA of each group of kGroup CTAs
+// (group ticket) sums the group's partials in index order and stores a group partial; the
+// last group to finish (grid ticket) sums the group partials in index order in FP64 and
+// resolves.  A grid of one CTA resolves its own sums.  Tickets are reset by the CTA that
+// completes them.  Called by all threads of every CTA after BlockReduce::reduce.
+__device__ void grid_finish(const CtaSums& cta, WsHeader* ws, CtaPartial* parts,
+                            rmp_result_t* out, uint32_t n_rays, int status) {
   __shared__ int stage;
   __shared__ double tot[9];
   __shared__ unsigned tot_h, tot_a;
@@ -1021,43 +1087,53 @@ __device__ void grid_finish(const double part[9], unsigned hits, unsigned act, W
   const int n_groups = (G + kGroup - 1) / kGroup;
   const int g0 = gi * kGroup;
   const int gsz = min(kGroup, G - g0);
-  if (threadIdx.x == 0) {
-    CtaPartial p;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) p.v[q] = part[q];
-    p.n_hits = hits;
-    p.n_active = act;
-    parts[blockIdx.x] = p;
-    __threadfence();
-    const unsigned t = atomicAdd(&ws->group_ticket[gi], 1u);
-    stage = (t == (unsigned)gsz - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  if (stage == 0) return;
-  __threadfence();
-  sum_partials(parts + g0, gsz, tot, &tot_h, &tot_a);
-  if (n_groups > 1) {
-    if (threadIdx.x == 0) {
-      CtaPartial p;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) p.v[q] = tot[q];
-      p.n_hits = tot_h;
-      p.n_active = tot_a;
-      groups[gi] = p;
-      ws->group_ticket[gi] = 0;
+  if (G == 1) {
+    if (threadIdx.x < 9) tot[threadIdx.x] = cta.v[threadIdx.x];
+    else if (threadIdx.x == 9) tot_h = cta.u[0];
+    else if (threadIdx.x == 10) tot_a = cta.u[1];
+  } else {
+    if (threadIdx.x < 11) {
+      CtaPartial* mine = parts + blockIdx.x;
+      if (threadIdx.x < 9) mine->v[threadIdx.x] = cta.v[threadIdx.x];
+      else if (threadIdx.x == 9) mine->n_hits = cta.u[0];
+      else mine->n_active = cta.u[1];
       __threadfence();
-      const unsigned t = atomicAdd(&ws->ticket, 1u);
-      stage = (t == (unsigned)n_groups - 1) ? 2 : 0;
+    }
+    if (threadIdx.x < 32) {
+      __syncwarp();
+      if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(&ws->group_ticket[gi], 1u);
+        stage = (t == (unsigned)gsz - 1) ? 1 : 0;
+      }
     }
     __syncthreads();
-    if (stage != 2) return;
+    if (stage == 0) return;
     __threadfence();
-    sum_partials(groups, n_groups, tot, &tot_h, &tot_a);
-  } else if (threadIdx.x == 0) {
-    // a single group: its sum is the total (the same value the second level would give)
-    ws->group_ticket[gi] = 0;
+    sum_partials(parts + g0, gsz, tot, &tot_h, &tot_a);
+    if (n_groups > 1) {
+      if (threadIdx.x == 0) {
+        CtaPartial p;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) p.v[q] = tot[q];
+        p.n_hits = tot_h;
+        p.n_active = tot_a;
+        groups[gi] = p;
+        ws->group_ticket[gi] = 0;
+        __threadfence();
+        const unsigned t = atomicAdd(&ws->ticket, 1u);
+        stage = (t == (unsigned)n_groups - 1) ? 2 : 0;
+      }
+      __syncthreads();
+      if (stage != 2) return;
+      __threadfence();
+      sum_partials(groups, n_groups, tot, &tot_h, &tot_a);
+    } else if (threadIdx.x == 0) {
+      // a single group: its sum is the total (the same value the second level would give)
+      ws->group_ticket[gi] = 0;
+    }
   }
   __shared__ rmp_result_t r;
+  __syncthreads();
   if (threadIdx.x == 0) {
     for (int q = 0; q < 6; ++q) r.A[q] = tot[q];
     for (int q = 0; q < 3; ++q) r.Af[q] = tot[6 + q];
@@ -1068,10 +1144,10 @@ __device__ void grid_finish(const double part[9], unsigned hits, unsigned act, W
     r.reserved = 0;
   }
   __syncthreads();
-  if (threadIdx.x < 32) resolve_pinv(r.A, r.Af, r);
+  if (threadIdx.x < 64) resolve_pinv_cta(r.A, r.Af, r);
   if (threadIdx.x == 0) {
     *out = r;
-    ws->ticket = 0;                   // ready for the next evaluation
+    if (G > 1) ws->ticket = 0;        // ready for the next evaluation
   }
 }
 
@@ -1328,13 +1404,11 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
     if (mstat == RMP_RAY_HIT) BlockReduce<RED>::add(acc, vals);
   }
   if (staged && bm_timeout) bulk_load_wait(&bm_bar);   // let a late copy land before exit
-  double part[9];
-  BlockReduce<RED>::reduce(acc, part);
-  const unsigned bh = block_sum_u32(n_hit);
-  const unsigned ba = block_sum_u32(n_act);
+  __shared__ CtaSums sums;
+  BlockReduce<RED>::reduce(acc, n_hit, n_act, sums);
   const int status = bm_timeout ? RMP_ERR_TIMEOUT
                      : ((cs.bad[0] | cs.bad[1] | cs.bad[2]) ? RMP_ERR_INVALID_ARG : RMP_OK);
-  grid_finish(part, bh, ba, ws, parts, out, k.n_rays, status);
+  grid_finish(sums, ws, parts, out, k.n_rays, status);
 }
 
 // ------------------------------------------------------------------ batched evaluation
@@ -1874,11 +1948,9 @@ __global__ void __launch_bounds__(256) scan_rmp_kernel(const float* __restrict__
       o[3] = A[0]; o[4] = A[1]; o[5] = A[2]; o[6] = A[3]; o[7] = A[4]; o[8] = A[5];
     }
   }
-  double part[9];
-  BlockReduce<RED>::reduce(acc, part);
-  const unsigned bh = block_sum_u32(n_hit);
-  const unsigned ba = block_sum_u32(n_act);
-  grid_finish(part, bh, ba, ws, parts, out, k.n_rays, RMP_OK);
+  __shared__ CtaSums sums;
+  BlockReduce<RED>::reduce(acc, n_hit, n_act, sums);
+  grid_finish(sums, ws, parts, out, k.n_rays, RMP_OK);
 }
 
 // ------------------------------------------------------------------ map build kernels
@@ -2186,6 +2258,9 @@ int raycast_occupancy(const DevMap& m, int reduce_mode, int block) {
 cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,
                            void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
                            float* per_ray, int block, int grid, cudaStream_t stream) {
+  // grid_finish needs whole warps 0 and 1 (the resolve's named barrier) and blockDim / 16
+  // a power of two (the partial sums' shuffle tree)
+  if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
   WsHeader* hdr = (WsHeader*)ws;
   CtaPartial* parts = (CtaPartial*)((char*)ws + kWsHeaderBytes);
   const size_t smem = raycast_smem_bytes(m);
@@ -2304,6 +2379,7 @@ cudaError_t launch_rollout_step(const DevMap& m, const RolloutConsts& rc, const 
 cudaError_t launch_scan(const float* pts, const EvalConsts& k, const double* state_dev,
                         void* ws, rmp_result_t* out_dev, float* per_ray, int block, int grid,
                         cudaStream_t stream) {
+  if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;  // as above
   WsHeader* hdr = (WsHeader*)ws;
   CtaPartial* parts = (CtaPartial*)((char*)ws + kWsHeaderBytes);
   if (k.reduce_mode == RMP_REDUCE_FP64)
