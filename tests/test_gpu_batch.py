@@ -242,7 +242,7 @@ def test_batch_autotuner(ctx, hashed):
         assert R.rmp_tune_get(ctx.handle, R.RMP_TUNE_LG_SEGMENTS) == (best // 2) % 3
         check_batch(ctx, mid, om, wl.states[:B], counts, wl.params, wl.max_range)
     finally:
-        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 128)
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 0)
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, -1)
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_SPLIT_BUDGET, -1)
 

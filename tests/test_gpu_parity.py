@@ -386,7 +386,7 @@ def test_split_and_ray_order_keep_results(ctx, hashed, dense, order, budget, lgs
             R.rmp_tune_set(ctx.handle, knob, bad)
 
 
-@pytest.mark.parametrize("block,lgs", [(64, 0), (128, 1), (256, 2), (128, -1)])
+@pytest.mark.parametrize("block,lgs", [(64, 0), (128, 1), (256, 2), (128, -1), (0, -1)])
 def test_tuning_knobs_keep_results(ctx, hashed, block, lgs):
     """Block size and ray segmentation change the launch shape only: hit records stay
     bit-identical to the oracle's, values within tolerance."""
@@ -398,10 +398,33 @@ def test_tuning_knobs_keep_results(ctx, hashed, block, lgs):
         for s, n in ((wl.states[1], 65536), (wl.states[2], 777)):
             check_raycast(ctx, mid, om, s.x, s.xdot, n, wl.params, wl.max_range)
     finally:
-        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 128)
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 0)
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, -1)
     with pytest.raises(R.RmpError):
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 100)
+
+
+def test_automatic_block_size(ctx, hashed):
+    """Threads per CTA by default: 256 while the launch fits in one wave of 256-thread CTAs
+    (occupancy x SMs), 128 beyond it; an explicit setting wins."""
+    wl, mid, om = hashed
+    p = R.make_params(wl.params, wl.max_range)
+    assert R.rmp_tune_get(ctx.handle, R.RMP_TUNE_BLOCK) == 0
+    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 256)
+    info = R.rmp_eval_launch_info(ctx.handle, mid, 65536, p)
+    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 0)
+    wave = info["sm_count"] * info["ctas_per_sm"] * 256
+    assert wave >= 65536                       # the headline evaluation fits in one wave
+    for n in (1, 1024, 65536, 262144, 1 << 20):
+        li = R.rmp_eval_launch_info(ctx.handle, mid, n, p)
+        threads = n << li["lg_segments"]
+        assert li["block"] == (256 if threads <= wave else 128), (n, li)
+        assert li["grid"] == min(4096, (threads + li["block"] - 1) // li["block"])
+    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 64)
+    try:
+        assert R.rmp_eval_launch_info(ctx.handle, mid, 65536, p)["block"] == 64
+    finally:
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 0)
 
 
 def test_maximum_ray_count_sampled(ctx, dense):
