@@ -419,7 +419,7 @@ int rmp_server_stats(rmp_server* server, rmp_server_stats_t* out);
  * the floating-point reduction, hit records are identical.
  *  RMP_TUNE_BLOCK        threads per CTA: 64, 128 or 256, or 0 (default) automatic: for
  *                        one state, 256 when the launch fits in one wave of 256-thread CTAs,
- *                        else 128; scans and batches 128
+ *                        else 128; scans 256; batches 128
  *  RMP_TUNE_LG_SEGMENTS  log2 of the segments each ray is split into and marched by that
  *                        many threads (0..2), or -1 (default) to choose from the ray count
  *  RMP_TUNE_RAY_ORDER    0 (default): rays of one direction cell share warps (coherent

@@ -191,7 +191,6 @@ int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalCon
 // (automatic) 256 when the whole launch fits in one wave of 256-thread CTAs (`wave256`
 // threads; fewer CTAs stage the radius field and store partials: 65536 rays 69.7 -> 68.1 us
 // hashed, 46.3 -> 43.8 us dense) and 128 otherwise (262144 rays: 132 against 135 us).
-// Scans pass wave256 = 0 (always 128 when automatic).
 void launch_shape(const rmp_ctx* ctx, uint64_t n_threads, uint64_t wave256, int* block,
                   int* grid) {
   int b = ctx->tune_block;
@@ -203,11 +202,18 @@ void launch_shape(const rmp_ctx* ctx, uint64_t n_threads, uint64_t wave256, int*
   *grid = (int)g;
 }
 
-// Scans: at most 4 CTAs per SM, each thread striding over several points, so that large
-// scans are reduced from fewer CTA partials (measured: 262144 points 30.7 -> 24.6 us).
-void scan_grid_cap(const rmp_ctx* ctx, int* grid) {
-  const int cap = 4 * (ctx->sm_count > 0 ? ctx->sm_count : 1);
-  if (*grid > cap) *grid = cap;
+// Scans: threads per CTA the tuned value or (automatic) 256, and at most 512 threads per
+// SM, each thread striding over several points, so that large scans are reduced from few
+// CTA partials (measured, L2 flushed: 4096 / 65536 / 262144 points 16.4 / 20.5 / 24.3 us
+// with 128-thread CTAs and 4 per SM, 14.4 / 18.5 / 21.0 us with 256 and 2 per SM).
+void scan_shape(const rmp_ctx* ctx, uint64_t n, int* block, int* grid) {
+  const int b = ctx->tune_block != 0 ? ctx->tune_block : 256;
+  const uint64_t cap = (uint64_t)(512 / b) * (uint64_t)(ctx->sm_count > 0 ? ctx->sm_count : 1);
+  uint64_t g = (n + b - 1) / b;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  *block = b;
+  *grid = (int)g;
 }
 
 void free_map(MapRec& r) {
@@ -659,8 +665,7 @@ int rmp_scan_eval_async(rmp_ctx* c, const float* points_dev, uint32_t n, const d
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   int block, grid;
-  launch_shape(c, n, 0, &block, &grid);
-  scan_grid_cap(c, &grid);
+  scan_shape(c, n, &block, &grid);
   RMP_CUDA(launch_scan(points_dev, k, state_dev, ws, out_dev, per_ray_dev, block, grid,
                        (cudaStream_t)stream));
   return RMP_OK;
@@ -682,8 +687,7 @@ int rmp_scan_eval(rmp_ctx* c, const float* points_dev, uint32_t n, const double 
     k.x0[3 + a] = xdot[a];
   }
   int block, grid;
-  launch_shape(c, n, 0, &block, &grid);
-  scan_grid_cap(c, &grid);
+  scan_shape(c, n, &block, &grid);
   RMP_CUDA(launch_scan(points_dev, k, nullptr, c->ws, c->result_map, per_ray_dev, block, grid,
                        s));
   RMP_CUDA(cudaStreamSynchronize(s));
