@@ -172,11 +172,24 @@ int rmp_map_release(rmp_ctx* ctx, uint32_t map_id);
 
 int rmp_map_info(rmp_ctx* ctx, uint32_t map_id, rmp_map_info_t* out);
 
+/* Free-space data of a grid-layout map, for diagnostics and tests (evaluation does not need
+ * it).  grid_min / grid_dim (3 int32 each, host) receive the block coordinates of the grid's
+ * first brick (x, y, z; dense maps: 0) and its bricks per axis.  cells (nullable, host,
+ * cells_words uint32 words, caller-owned) receives 8 words per brick in brick order
+ * (x + dim_x (y + dim_y z)): the Chebyshev distance in voxels from each 2^3 cell
+ * c = cx + 4 cy + 16 cz of the brick to the nearest occupied voxel, capped at 4, in bits
+ * 4 (c & 7) of word c >> 3; 0 for bricks without an occupied voxel.  Synchronous.
+ * RMP_ERR_INVALID_ARG for a hash-layout map, a map without cell distances (cells given),
+ * or cells_words below 8 x bricks. */
+int rmp_map_cell_distances(rmp_ctx* ctx, uint32_t map_id, int32_t grid_min[3],
+                           int32_t grid_dim[3], uint32_t* cells, uint64_t cells_words);
+
 /* ------------------------------------------------------------------ evaluation
  * Raycast RMP evaluation of one state (Sec. III-E, Eq. raytracing_policy, resolved by
- * Eq. 1), synchronous: copies x and xdot (3 doubles each, host) to the device, runs
- * one fused kernel on `stream` (Halton direction, exact DDA march, per-ray policy,
- * reduction, FP64 resolve) and copies the result back into *out (host).
+ * Eq. 1), synchronous: runs one fused kernel on `stream` (Halton direction, exact DDA
+ * march, per-ray policy, reduction, FP64 resolve) with x and xdot (3 doubles each, host)
+ * carried in the launch itself, waits for it and returns the result in *out (host; the
+ * kernel writes it into pinned host memory of the context).
  * n_rays in [1, 2^24 - halton_offset].  hits_dev (nullable) receives n_rays records;
  * per_ray_dev (nullable) receives n_rays x 9 floats: f_i (3) then A_i (6), zero for
  * rays that did not hit. */

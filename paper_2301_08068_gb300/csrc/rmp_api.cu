@@ -526,6 +526,27 @@ int rmp_map_info(rmp_ctx* c, uint32_t map_id, rmp_map_info_t* out) {
   return RMP_OK;
 }
 
+int rmp_map_cell_distances(rmp_ctx* c, uint32_t map_id, int32_t grid_min[3],
+                           int32_t grid_dim[3], uint32_t* cells, uint64_t cells_words) {
+  if (!c || !grid_min || !grid_dim) return RMP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->maps.find(map_id);
+  if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
+  const MapRec& r = it->second;
+  if (r.dm.layout != kLayoutGrid) return RMP_ERR_INVALID_ARG;
+  const uint64_t words = 8ull * (uint64_t)r.dm.gdim[0] * r.dm.gdim[1] * r.dm.gdim[2];
+  if (cells && (!r.cells || cells_words < words)) return RMP_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a) {
+    grid_min[a] = r.dm.gmin[a];
+    grid_dim[a] = r.dm.gdim[a];
+  }
+  if (!cells) return RMP_OK;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  RMP_CUDA(cudaMemcpy(cells, r.cells, words * 4, cudaMemcpyDeviceToHost));
+  return RMP_OK;
+}
+
 size_t rmp_workspace_bytes(void) { return workspace_bytes(); }
 
 int rmp_tune_set(rmp_ctx* c, int knob, int value) {

@@ -2031,56 +2031,88 @@ __global__ void radius_pack_kernel(const uint8_t* __restrict__ v, uint32_t n, ui
   }
 }
 
-// Occupancy of grid voxel (x, y, z) (grid-local voxel coordinates; outside the grid: free).
-__device__ __forceinline__ bool grid_voxel_bit(const uint32_t* bricks, const DevMap& m, int x,
-                                               int y, int z) {
-  if ((unsigned)x >= (unsigned)(8 * m.gdim[0]) || (unsigned)y >= (unsigned)(8 * m.gdim[1]) ||
-      (unsigned)z >= (unsigned)(8 * m.gdim[2]))
-    return false;
-  const size_t b = (size_t)(x >> 3) + (size_t)m.gdim[0] * ((size_t)(y >> 3) +
-                                                           (size_t)m.gdim[1] * (size_t)(z >> 3));
-  const uint32_t bit = (uint32_t)((x & 7) + 8 * (y & 7) + 64 * (z & 7));
-  return (__ldg(bricks + 16 * b + (bit >> 5)) >> (bit & 31)) & 1u;
-}
-
 // Free distance of each 2^3 cell of the occupied bricks: the Chebyshev distance in voxels
 // from the cell to the nearest occupied voxel, capped at kCellDistCap (a free cell at
 // distance dv holds no voxel closer than dv to an obstacle, so every voxel of it centres a
-// free box of half-width dv - 1).  One thread per brick word (8 cells); the cell's
-// neighbourhood within the cap is scanned directly.  Free bricks get 0 (never read).
-__global__ void cell_dist_kernel(const uint32_t* __restrict__ bricks, DevMap m, uint64_t n_bricks,
-                                 uint32_t* __restrict__ cells) {
-  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n_bricks * 8;
-       t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t b = t >> 3;
-    const uint32_t wi = (uint32_t)(t & 7);
-    uint32_t any = 0;
-    for (int q = 0; q < 16; ++q) any |= __ldg(bricks + 16 * b + q);
-    if (!any) {
-      cells[t] = 0;
+// free box of half-width dv - 1).  One CTA per brick: the 3^3 bricks around it are loaded
+// into shared memory as a 24^3 bit volume (rows of 24 x-bits), dilated by one voxel in the
+// Chebyshev metric kCellDistCap - 1 times (the 3^3 maximum, one pass per dilation); a cell's
+// distance is the first dilation that reaches one of its 8 voxels.  Only voxels within
+// kCellDistCap - 1 of the centre brick matter, and they lie inside the volume.  Free bricks
+// get 0 (never read).
+static_assert(kCellDistCap == 4, "the halo of one brick covers dilations up to 3 voxels");
+__global__ void __launch_bounds__(256) cell_dist_kernel(const uint32_t* __restrict__ bricks,
+                                                        DevMap m, uint64_t n_bricks,
+                                                        uint32_t* __restrict__ cells) {
+  __shared__ uint32_t vol[2][24][24];   // [z][y], bit x
+  __shared__ uint32_t words[8];
+  __shared__ int occupied;
+  const int t = threadIdx.x;
+  const int gx = m.gdim[0], gy = m.gdim[1], gz = m.gdim[2];
+  for (uint64_t b = blockIdx.x; b < n_bricks; b += gridDim.x) {
+    __syncthreads();                    // the previous brick's shared data is no longer read
+    if (t == 0) occupied = 0;
+    if (t < 8) words[t] = 0;
+    __syncthreads();
+    if (t < 16 && __ldg(bricks + 16 * b + t) != 0u) occupied = 1;
+    __syncthreads();
+    if (!occupied) {
+      if (t < 8) cells[8 * b + t] = 0u;
       continue;
     }
-    const int bx = (int)(b % (uint64_t)m.gdim[0]);
-    const int by = (int)((b / (uint64_t)m.gdim[0]) % (uint64_t)m.gdim[1]);
-    const int bz = (int)(b / ((uint64_t)m.gdim[0] * (uint64_t)m.gdim[1]));
-    uint32_t word = 0;
-    for (int i = 0; i < 8; ++i) {
-      const int c = (int)(wi * 8 + i);
-      const int x0 = 8 * bx + 2 * (c & 3), y0 = 8 * by + 2 * ((c >> 2) & 3), z0 = 8 * bz + 2 * (c >> 4);
-      int d = kCellDistCap;
-      const int span = kCellDistCap - 1;          // voxels beyond the cell that can be nearer
-      for (int z = z0 - span; z <= z0 + 1 + span && d > 0; ++z)
-        for (int y = y0 - span; y <= y0 + 1 + span && d > 0; ++y)
-          for (int x = x0 - span; x <= x0 + 1 + span && d > 0; ++x) {
-            if (!grid_voxel_bit(bricks, m, x, y, z)) continue;
-            const int dx = max(max(x0 - x, x - (x0 + 1)), 0);
-            const int dy = max(max(y0 - y, y - (y0 + 1)), 0);
-            const int dz = max(max(z0 - z, z - (z0 + 1)), 0);
-            d = min(d, max(dx, max(dy, dz)));
-          }
-      word |= (uint32_t)d << (4 * i);
+    const int bx = (int)(b % (uint64_t)gx);
+    const int by = (int)((b / (uint64_t)gx) % (uint64_t)gy);
+    const int bz = (int)(b / ((uint64_t)gx * (uint64_t)gy));
+    for (int r = t; r < 576; r += blockDim.x) {
+      const int zz = r / 24, yy = r - 24 * (r / 24);
+      const int nz = bz + zz / 8 - 1, ny = by + yy / 8 - 1;
+      const int lz = zz & 7, ly = yy & 7;
+      uint32_t row = 0u;
+      if ((unsigned)nz < (unsigned)gz && (unsigned)ny < (unsigned)gy) {
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const int nx = bx + dx - 1;
+          if ((unsigned)nx >= (unsigned)gx) continue;
+          const size_t nb = (size_t)nx + (size_t)gx * ((size_t)ny + (size_t)gy * (size_t)nz);
+          const uint32_t w = __ldg(bricks + 16 * nb + (ly >> 2) + 2 * lz);
+          row |= ((w >> (8 * (ly & 3))) & 0xffu) << (8 * dx);
+        }
+      }
+      vol[0][zz][yy] = row;
     }
-    cells[t] = word;
+    __syncthreads();
+    // thread c < 64: cell c of the centre brick (voxels 8 + 2 (c & 3) .. +1 in x, etc.)
+    const int cx = 8 + 2 * (t & 3), cy = 8 + 2 * ((t >> 2) & 3), cz = 8 + 2 * ((t >> 4) & 3);
+    const uint32_t cmask = 3u << cx;
+    int d = kCellDistCap;
+    auto touches = [&](int buf) {
+      return ((vol[buf][cz][cy] | vol[buf][cz][cy + 1] | vol[buf][cz + 1][cy] |
+               vol[buf][cz + 1][cy + 1]) & cmask) != 0u;
+    };
+    if (t < 64 && touches(0)) d = 0;
+    for (int k = 1; k < kCellDistCap; ++k) {
+      const int src = (k - 1) & 1, dst = k & 1;
+      for (int r = t; r < 576; r += blockDim.x) {
+        const int zz = r / 24, yy = r - 24 * (r / 24);
+        uint32_t acc = 0u;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy) {
+            const int z2 = zz + dz, y2 = yy + dy;
+            if ((unsigned)z2 < 24u && (unsigned)y2 < 24u) acc |= vol[src][z2][y2];
+          }
+        }
+        vol[dst][zz][yy] = (acc | (acc << 1) | (acc >> 1)) & 0xffffffu;
+      }
+      __syncthreads();
+      // the next dilation writes vol[src], whose reads ended at the barrier above, and only
+      // reads vol[dst]: no second barrier is needed
+      if (t < 64 && d == kCellDistCap && touches(dst)) d = k;
+    }
+    if (t < 64) atomicOr(&words[t >> 3], (uint32_t)d << (4 * (t & 7)));
+    __syncthreads();
+    if (t < 8) cells[8 * b + t] = words[t];
   }
 }
 
@@ -2422,7 +2454,8 @@ cudaError_t launch_grid_radius(const uint32_t* bricks, const DevMap& m, uint8_t*
 cudaError_t launch_cell_dist(const uint32_t* bricks, const DevMap& m, uint32_t* cells,
                              cudaStream_t stream) {
   const uint64_t n = (uint64_t)m.gdim[0] * m.gdim[1] * m.gdim[2];
-  cell_dist_kernel<<<grid_for(n * 8), 256, 0, stream>>>(bricks, m, n, cells);
+  const uint64_t g = n < 65536u ? n : 65536u;          // grid-stride beyond
+  cell_dist_kernel<<<(unsigned)(g > 0 ? g : 1), 256, 0, stream>>>(bricks, m, n, cells);
   return cudaGetLastError();
 }
 

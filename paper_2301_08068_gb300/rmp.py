@@ -114,6 +114,7 @@ _SIGNATURES = {
     "rmp_map_upload": [_P, C.POINTER(rmp_map_desc_t), _P, C.POINTER(C.c_uint32)],
     "rmp_map_release": [_P, C.c_uint32],
     "rmp_map_info": [_P, C.c_uint32, C.POINTER(rmp_map_info_t)],
+    "rmp_map_cell_distances": [_P, C.c_uint32, _P, _P, _P, C.c_uint64],
     "rmp_workspace_init": [_P, C.c_size_t, _P],
     "rmp_raycast_eval": [_P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(rmp_params_t), _P,
                          C.POINTER(rmp_result_t), _P, _P],
@@ -302,6 +303,20 @@ def rmp_map_info(ctx: int, map_id: int) -> dict:
     _check(lib().rmp_map_info(ctx, int(map_id), C.byref(info)), "rmp_map_info")
     return dict(kind=info.kind, n_bricks=info.n_bricks, hash_capacity=info.hash_capacity,
                 layout=info.layout, device_bytes=info.device_bytes)
+
+
+def rmp_map_cell_distances(ctx: int, map_id: int):
+    """(grid_min, grid_dim, cells): the grid's first block and bricks per axis (x, y, z),
+    and the 4-bit cell free distances, 8 uint32 words per brick in brick order."""
+    gmin = (C.c_int32 * 3)()
+    gdim = (C.c_int32 * 3)()
+    _check(lib().rmp_map_cell_distances(ctx, int(map_id), gmin, gdim, None, 0),
+           "rmp_map_cell_distances")
+    n = 8 * gdim[0] * gdim[1] * gdim[2]
+    cells = np.zeros(n, np.uint32)
+    _check(lib().rmp_map_cell_distances(ctx, int(map_id), gmin, gdim, cells.ctypes.data, n),
+           "rmp_map_cell_distances")
+    return np.array(gmin[:]), np.array(gdim[:]), cells
 
 
 def rmp_workspace_init(workspace, stream=None):

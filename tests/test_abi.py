@@ -147,6 +147,7 @@ def test_null_arguments_rejected_without_gpu(rmp):
     assert L.rmp_scan_pipeline_destroy(None) == 1
     assert L.rmp_scan_pipeline_submit(None, None, 1, None, None, None, None) == 1
     assert L.rmp_scan_pipeline_wait(None, 1, None) == 1
+    assert L.rmp_map_cell_distances(None, 1, None, None, None, 0) == 1
     cfg = rmp.rmp_server_config_default()
     assert (cfg.slots, cfg.max_batch_states, cfg.max_rays, cfg.mem_budget_bytes) == \
         (4, 256, 262144, 1 << 30)

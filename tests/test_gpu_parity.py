@@ -427,6 +427,63 @@ def test_automatic_block_size(ctx, hashed):
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 0)
 
 
+def _grid_occupancy(m, gmin, gdim):
+    """Occupancy [z, y, x] of the grid's voxels from the map description (outside: free)."""
+    V = np.zeros((8 * gdim[2], 8 * gdim[1], 8 * gdim[0]), bool)
+    if isinstance(m, W.DenseMap):
+        assert np.all(gmin == 0)
+        nz, ny, nx = m.occ.shape
+        V[:nz, :ny, :nx] = m.occ != 0
+        return V
+    for key, t in zip(m.keys, m.tsdf):
+        occ = (t <= 0).reshape(8, 8, 8)
+        b = key - gmin
+        if np.any(b < 0) or np.any(b >= gdim):
+            assert not occ.any()              # every occupied block lies inside the grid
+            continue
+        V[8 * b[2]:8 * b[2] + 8, 8 * b[1]:8 * b[1] + 8, 8 * b[0]:8 * b[0] + 8] = occ
+    return V
+
+
+def _dilate(D):
+    """One voxel of Chebyshev dilation (3^3 maximum), nothing beyond the volume."""
+    for ax in range(3):
+        E = D.copy()
+        hi = [slice(None)] * 3
+        lo = [slice(None)] * 3
+        hi[ax], lo[ax] = slice(1, None), slice(None, -1)
+        E[tuple(hi)] |= D[tuple(lo)]
+        E[tuple(lo)] |= D[tuple(hi)]
+        D = E
+    return D
+
+
+@pytest.mark.parametrize("which", ["dense", "hashed"])
+def test_cell_distances_brute_force(ctx, dense, hashed, which):
+    """The voxel-box data (4-bit Chebyshev distance of each 2^3 cell to the nearest occupied
+    voxel, capped at 4) equals a brute-force distance transform of the map's occupancy:
+    an overestimate would let the march skip an occupied voxel."""
+    wl, mid, _ = dense if which == "dense" else hashed
+    gmin, gdim, cells = R.rmp_map_cell_distances(ctx.handle, mid)
+    V = _grid_occupancy(wl.map, gmin, gdim)
+    dist = np.where(V, 0, 4).astype(np.uint8)
+    D = V
+    for k in range(1, 4):
+        D = _dilate(D)
+        dist[(dist == 4) & D] = k
+    gx, gy, gz = (int(v) for v in gdim)
+    cell = dist.reshape(4 * gz, 2, 4 * gy, 2, 4 * gx, 2).min(axis=(1, 3, 5))
+    per_brick = cell.reshape(gz, 4, gy, 4, gx, 4).transpose(0, 2, 4, 1, 3, 5).reshape(-1, 64)
+    occupied = V.reshape(gz, 8, gy, 8, gx, 8).any(axis=(1, 3, 5)).reshape(-1)
+    per_brick[~occupied] = 0
+    nib = per_brick.reshape(-1, 8, 8).astype(np.uint32) << (4 * np.arange(8, dtype=np.uint32))
+    expect = np.bitwise_or.reduce(nib, axis=2).reshape(-1)
+    assert cells.shape == expect.shape
+    assert occupied.sum() > 10 and np.any(per_brick[occupied] == 4) and np.any(per_brick == 1)
+    bad = np.nonzero(cells != expect)[0]
+    assert bad.size == 0, (bad[:8], cells[bad[:8]], expect[bad[:8]])
+
+
 def test_maximum_ray_count_sampled(ctx, dense):
     """The largest evaluation the ABI allows (2^24 - 1 rays with Halton offset 1): the hit
     counts add up over all rays, and 3000 sampled rays match the oracle ray by ray (hit
