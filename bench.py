@@ -96,6 +96,19 @@ def whole_job_rate(world: int, rays_per_rank_step: int, ms_max: float) -> float:
     return world * rays_per_rank_step / (ms_max / 1e3) / 1e9
 
 
+def host_cpu_model() -> str:
+    """The host CPU's model name (lscpu), or the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def host_cores() -> int:
     """Cores this process may run on."""
     try:
@@ -134,19 +147,29 @@ def oracle_on_threads(om, p, states, n_rays: int, threads: int, evals: int):
 
 
 def time_oracle(wl, seconds: float, max_evals: int):
-    """Single-threaded oracle evaluations of the workload's states until `seconds` pass."""
+    """Single-threaded oracle evaluations of the workload's states until `seconds` pass,
+    with this process pinned to one core meanwhile (where the OS allows it)."""
     import oracle as O
     om = O.OracleMap(wl.map)
     p = O.make_params(wl.params, wl.max_range)
-    t0 = time.perf_counter()
-    n = 0
-    times = []
-    while n < max_evals and (time.perf_counter() - t0 < seconds or n == 0):
-        s = wl.states[n % len(wl.states)]
-        t1 = time.perf_counter()
-        O.raycast_eval(om, s.x, s.xdot, N_RAYS, p, want_hits=False, want_per_ray=False)
-        times.append(time.perf_counter() - t1)
-        n += 1
+    try:
+        cpus = os.sched_getaffinity(0)
+        os.sched_setaffinity(0, {min(cpus)})
+    except (AttributeError, OSError):
+        cpus = None
+    try:
+        t0 = time.perf_counter()
+        n = 0
+        times = []
+        while n < max_evals and (time.perf_counter() - t0 < seconds or n == 0):
+            s = wl.states[n % len(wl.states)]
+            t1 = time.perf_counter()
+            O.raycast_eval(om, s.x, s.xdot, N_RAYS, p, want_hits=False, want_per_ray=False)
+            times.append(time.perf_counter() - t1)
+            n += 1
+    finally:
+        if cpus is not None:
+            os.sched_setaffinity(0, cpus)
     return n, sum(times), times
 
 
@@ -539,7 +562,8 @@ def run_reference(args):
                    "rays_per_step_sample": m},
         "evals_per_s": value * 1e9 / N_RAYS,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample,
+                         "host": {"cpu": host_cpu_model(), "nproc": os.cpu_count()}},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -668,7 +692,9 @@ def main():
                          "single-threaded C oracle on %d host threads at once (independent "
                          "states), %.2f s wall" % (evals, cores, wall),
                "single_core": {"value": one, "unit": UNIT, "cores": 1,
-                               "sample": "%d full evaluations, one thread, %.1f s" % (n, secs)}}
+                               "sample": "%d full evaluations, one thread pinned to one core, "
+                                         "%.1f s" % (n, secs)},
+               "host": {"cpu": host_cpu_model(), "nproc": os.cpu_count()}}
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:
