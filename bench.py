@@ -12,8 +12,9 @@ Printed JSON line (rank 0):
             per-step device time (CUDA events around each evaluation, inputs resident in HBM,
             L2 flushed by a 256 MiB write between timed steps, outside the events);
   e2e       the same metric through the public synchronous call rmp_raycast_eval with host
-            x/xdot and a host result (H2D of the state and D2H of the result inside the
-            timed region), wall clock per call;
+            x/xdot and a host result (the state goes to the device in the launch, the result
+            comes back into pinned host memory, both inside the timed region), wall clock
+            per call;
   roofline  algorithmic bytes per launch / mean kernel time against the measured HBM copy
             bandwidth; traffic from the committed ncu capture when it matches this kernel;
   cpu_baseline  the C oracle on a bounded sample: one evaluation per host thread at once,
@@ -729,7 +730,11 @@ def main():
             "timed_wall_s": wall,
             "e2e": {"value": whole_job_rate(world, N_RAYS, e2e_ms_max), "unit": UNIT,
                     "h2d_bytes_per_step": 48, "d2h_bytes_per_step": R.RESULT_BYTES,
-                    "ms_per_call": e2e_ms, "calls": n_e2e},
+                    "ms_per_call": e2e_ms, "calls": n_e2e,
+                    "path": "rmp_raycast_eval from Python, host x/xdot in and host result out: "
+                            "the 48-byte state travels in the kernel launch's parameter block, "
+                            "the kernel writes the 144-byte result into mapped pinned host "
+                            "memory, the call returns after a stream synchronisation"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,
