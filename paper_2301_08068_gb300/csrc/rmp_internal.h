@@ -44,6 +44,7 @@ constexpr int kLayoutGrid = 0;
 constexpr int kLayoutHash = 1;
 constexpr uint32_t kMaxSmemRadiusBytes = 48 * 1024;   // staged in shared memory up to this
 constexpr int kMaxFreeRadius = 15;
+constexpr int kSmemBrickBytes = 16 * 32 * 4;           // batch kernel: one warp's staged bricks
 constexpr int kCellDistCap = 4;                       // cell free distances are capped here
 constexpr uint64_t kMaxCellBytes = 256ull << 20;      // cell distances kept up to this size
 constexpr uint64_t kMaxGridBricks = 1ull << 26;       // grid layout up to 4 GiB of bricks
@@ -170,6 +171,7 @@ inline unsigned long long pack_key(int bx, int by, int bz) {
 
 // Launchers (rmp_kernels.cu).  All enqueue on `stream` and return cudaGetLastError().
 size_t raycast_smem_bytes(const DevMap& m);
+size_t batch_smem_bytes(const DevMap& m, int block);   // + the staged bricks, per warp
 int raycast_occupancy(const DevMap& m, int reduce_mode, int block);   // CTAs per SM
 cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,
                            void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,

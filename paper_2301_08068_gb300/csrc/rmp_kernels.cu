@@ -144,6 +144,21 @@ __device__ __forceinline__ void load_brick(const uint4* src, Brick& br) {
 
 // Occupancy of voxel k in the register brick: word (ly>>2) + 2 lz picked by a select
 // tree (no local memory), bit lx + 8 (ly & 3).
+// The same test on a brick staged in shared memory word-major: word q of the lane's brick
+// at sb[32 q] (sb = the warp's 16 x 32 words + lane), so a warp's lanes never share a bank.
+__device__ __forceinline__ bool smem_brick_bit(const uint32_t* sb, int kx, int ky, int kz) {
+  const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
+  return (sb[32 * ((ly >> 2) + 2 * lz)] >> (lx + 8 * (ly & 3))) & 1u;
+}
+
+__device__ __forceinline__ void store_smem_brick(const uint4* src, uint32_t* sb) {
+  const uint4 q0 = __ldg(src), q1 = __ldg(src + 1), q2 = __ldg(src + 2), q3 = __ldg(src + 3);
+  sb[0] = q0.x;   sb[32] = q0.y;  sb[64] = q0.z;  sb[96] = q0.w;
+  sb[128] = q1.x; sb[160] = q1.y; sb[192] = q1.z; sb[224] = q1.w;
+  sb[256] = q2.x; sb[288] = q2.y; sb[320] = q2.z; sb[352] = q2.w;
+  sb[384] = q3.x; sb[416] = q3.y; sb[448] = q3.z; sb[480] = q3.w;
+}
+
 __device__ __forceinline__ bool brick_bit(const Brick& b, int kx, int ky, int kz) {
   const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
   const int wi = (ly >> 2) + 2 * lz;
@@ -404,11 +419,13 @@ __device__ __forceinline__ void state_at(const RayFx& r, long long R_fx, uint32_
 // continues exactly).  Each visit of the outer loop either crosses a free box of blocks
 // (skip_box) or enters an occupied block, whose brick is held in registers while the inner
 // loop steps voxel by voxel, the order of the next crossings kept in the exact differences
-// E_ab = N_a |D_b| - N_b |D_a|.
-template <int KIND, int LAYOUT, bool CELLS>
+// E_ab = N_a |D_b| - N_b |D_a|.  SB: the brick is held in shared memory (`sb`, the lane's
+// column of its warp's 16 x 32 words) instead of 16 registers -- for the 64-register batch
+// kernel, where it trades register spills for one shared load per step.
+template <int KIND, int LAYOUT, bool CELLS, bool SB = false>
 __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, MarchState& st,
                                          const RayFx& r, const uint32_t L[3], int at_limit,
-                                         uint32_t budget) {
+                                         uint32_t budget, uint32_t* sb = nullptr) {
   if (outside<KIND>(m, st.k)) return RMP_RAY_MISS_EXIT;
   const uint32_t* A = r.A;
   const int* s = r.s;
@@ -451,8 +468,9 @@ __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, Ma
       continue;
     }
     Brick w;
-    load_brick(src, w);
-    if (brick_bit(w, k[0], k[1], k[2])) {
+    if (SB) store_smem_brick(src, sb);
+    else load_brick(src, w);
+    if (SB ? smem_brick_bit(sb, k[0], k[1], k[2]) : brick_bit(w, k[0], k[1], k[2])) {
       status = RMP_RAY_HIT;
       break;
     }
@@ -505,7 +523,7 @@ __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, Ma
         break;
       }
       if (crossed) break;
-      if (brick_bit(w, k[0], k[1], k[2])) {
+      if (SB ? smem_brick_bit(sb, k[0], k[1], k[2]) : brick_bit(w, k[0], k[1], k[2])) {
         fin = 3;
         break;
       }
@@ -1245,10 +1263,11 @@ __device__ __forceinline__ bool bulk_load_wait(uint64_t* bar) {
 // the first final one (lowest index), else the last one.  Warp-synchronous: every lane of
 // the warp calls it (work = false for lanes without a segment).  Returns the ray's status;
 // mo is its final state (valid in every lane of the ray's segment group).
-template <int KIND, int LAYOUT, bool CELLS>
+template <int KIND, int LAYOUT, bool CELLS, bool SB = false>
 __device__ __forceinline__ int march_ray(const DevMap& m, const uint32_t* bm, const EvalConsts& k,
                                          const long long P[3], const Ray& ray, uint32_t seg,
-                                         uint32_t lgS, bool work, MarchState& mo) {
+                                         uint32_t lgS, bool work, MarchState& mo,
+                                         uint32_t* sb = nullptr) {
   const uint32_t S = 1u << lgS;
   const uint32_t lane = threadIdx.x & 31;
   // this lane's piece: segment seg of the ray, grid points j_lo .. j_hi
@@ -1270,8 +1289,8 @@ __device__ __forceinline__ int march_ray(const DevMap& m, const uint32_t* bm, co
   int own_stat = kSegContinues;
   for (int phase = 0; phase < 2; ++phase) {
     if (work)
-      sstat = march_run<KIND, LAYOUT, CELLS>(m, bm, so, r, L, lim,
-                                             phase == 0 ? k.split_budget : 0xffffffffu);
+      sstat = march_run<KIND, LAYOUT, CELLS, SB>(m, bm, so, r, L, lim,
+                                                 phase == 0 ? k.split_budget : 0xffffffffu, sb);
     if (phase == 1) break;
     const uint32_t unfinished = __ballot_sync(0xffffffffu, work && sstat == kBudgetOut);
     if (!unfinished) break;
@@ -1759,6 +1778,10 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
   // a copy that did not land in time leaves the CTA on the global copy of the field
   const uint32_t* bm = (staged && !bm_timeout) ? reinterpret_cast<const uint32_t*>(smem_radius)
                                                : m.radius;
+  // this lane's brick column, after the radius field (batch_smem_bytes)
+  uint32_t* sbr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem_radius) +
+                                              (staged ? bm_bytes : 0u)) +
+                  (threadIdx.x >> 5) * (kSmemBrickBytes / 4) + (threadIdx.x & 31);
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t total = *(volatile const uint32_t*)&hdr->total_chunks;
   const uint32_t nst = *(volatile const uint32_t*)&hdr->n_states;
@@ -1794,7 +1817,8 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
     const uint32_t ray_idx = ray_of_slot_p(active ? slot : 0, pM, pQ, n_b - pQ * pM);
     const Ray ray = make_ray(ray_idx + k.halton_offset);
     MarchState mo;
-    const int mstat = march_ray<KIND, LAYOUT, true>(m, bm, k, P, ray, seg, lgS, active, mo);
+    const int mstat = march_ray<KIND, LAYOUT, true, true>(m, bm, k, P, ray, seg, lgS, active, mo,
+                                                          sbr);
     float vals[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     unsigned nh = 0, na = 0;
     if (active && seg == 0) {
@@ -2226,6 +2250,11 @@ size_t raycast_smem_bytes(const DevMap& m) {
   return 0;
 }
 
+// Batch kernel: the radius field (a multiple of 16 bytes), then 16 x 32 brick words per warp.
+size_t batch_smem_bytes(const DevMap& m, int block) {
+  return raycast_smem_bytes(m) + (size_t)(block / 32) * kSmemBrickBytes;
+}
+
 // The kernels keep up to 48 KB of the map's radius field in shared memory: ask for the
 // largest shared-memory carveout once per device so that register use, not the L1/shared
 // split, bounds the CTAs resident per SM (a whole evaluation should fit in one wave).
@@ -2237,6 +2266,10 @@ static void prefer_shared() {
   if (__atomic_load_n(&done_mask, __ATOMIC_ACQUIRE) & (1ull << dev)) return;
   cudaFuncSetAttribute(Fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                        (int)cudaSharedmemCarveoutMaxShared);
+  // the batch kernel's dynamic shared memory may exceed the default 48 KB: the radius field
+  // (up to kMaxSmemRadiusBytes) plus the staged bricks of up to 8 warps
+  cudaFuncSetAttribute(Fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(kMaxSmemRadiusBytes + 8 * kSmemBrickBytes));
   __atomic_fetch_or(&done_mask, 1ull << dev, __ATOMIC_ACQ_REL);
 }
 
@@ -2317,7 +2350,7 @@ static int batch_occupancy_t(int block, size_t smem) {
 }
 
 int batch_occupancy(const DevMap& m, int reduce_mode, int block) {
-  const size_t smem = raycast_smem_bytes(m);
+  const size_t smem = batch_smem_bytes(m, block);
   if (m.kind == RMP_MAP_DENSE_U8)
     return reduce_mode ? batch_occupancy_t<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_FP64>(block, smem)
                        : batch_occupancy_t<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_KAHAN32>(block, smem);
@@ -2372,7 +2405,7 @@ cudaError_t launch_batch(const DevMap& m, const EvalConsts& k, const double* sta
   CtaPartial* gparts = (CtaPartial*)(w + L.gparts);
   batch_prep_kernel<<<1, 1024, 0, stream>>>(states_dev, n_rays_dev, n_states, max_rays, m, k, hdr,
                                             bs, sticket, gticket, out_dev);
-  const size_t smem = raycast_smem_bytes(m);
+  const size_t smem = batch_smem_bytes(m, block);
   if (m.kind == RMP_MAP_DENSE_U8)
     launch_batch_r<RMP_MAP_DENSE_U8, kLayoutGrid>(m, k, hdr, bs, sticket, gticket, cparts, gparts,
                                                   out_dev, hits, per_ray, max_rays, block, grid,
