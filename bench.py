@@ -305,7 +305,7 @@ def batch_section(ctx, mid, flush) -> dict:
                          "evals_per_s": B / ms * 1e3, "tuned": tuned,
                          "autotune_ms": [round(t, 4) for t in times]}
         # the plain single-state kernel, one launch per state, same states and counts
-        R.rmp_tune_set(ctx.handle, 1, 128)
+        R.rmp_tune_set(ctx.handle, 1, 0)
         R.rmp_tune_set(ctx.handle, 2, -1)
         R.rmp_tune_set(ctx.handle, 4, -1)
         p = R.make_params(wl.params, wl.max_range)
