@@ -223,22 +223,29 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_source_hash() -> str:
+LAUNCH_KEYS = ("block", "grid", "lg_segments", "ray_cells", "smem_bytes")
+
+
+def kernel_source_hash(launch: dict) -> str:
+    """Identity of the measured launch: the device code (kernel source and its header) and
+    the launch shape the host chose for it.  The committed DRAM traffic is used only while
+    both are unchanged."""
     h = hashlib.sha256()
-    for f in ("rmp_kernels.cu", "rmp_internal.h", "rmp_api.cu"):
+    for f in ("rmp_kernels.cu", "rmp_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2301_08068_gb300", "csrc", f), "rb").read())
+    h.update(json.dumps([launch.get(k) for k in LAUNCH_KEYS]).encode())
     return h.hexdigest()[:16]
 
 
 def committed_traffic(src_hash: str):
     """Per-launch DRAM bytes of the raycast kernel from the committed ncu summary, if it
-    was taken on the current kernel source."""
+    was taken on the current kernel source and launch shape."""
     path = os.path.join(ROOT, "profiles", "raycast_hashed_65536_traffic.json")
     try:
         d = json.load(open(path))
     except Exception:
         return None
-    if d.get("kernel_source_sha256_16") != src_hash:
+    if d.get("kernel_launch_sha256_16") != src_hash:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -705,7 +712,7 @@ def main():
         extra["served"] = serve_section(ctx, args.serve_seconds)
         extra["rollout"] = rollout_section(ctx)
 
-    src = kernel_source_hash()
+    src = kernel_source_hash(launch)
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (ms / 1e3) / 1e9
     # secondary ALU roofline: the plain DDA's integer work, INT_OPS_PER_STEP per voxel step,
@@ -751,7 +758,7 @@ def main():
                                                 (SM_COUNT, INT_LANES_PER_SM)},
                          "kernel": "raycast_rmp_kernel<hashed TSDF, grid layout, "
                                    "compensated FP32 reduction>",
-                         "kernel_source_sha256_16": src},
+                         "kernel_launch_sha256_16": src},
             "per_ray_outputs_on": hits_on,
             "cpu_baseline": cpu,
             "gpu_launches": args.steps,

@@ -187,6 +187,19 @@ int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalCon
   return RMP_OK;
 }
 
+// Segments per ray of a single-state evaluation left to the library: as many (up to 4) as
+// keep the launch within one wave of 256-thread CTAs (`wave256` threads), since the
+// evaluation lasts as long as its longest ray's serial march and segments shorten it
+// while the extra threads still find free SMs (measured, hashed map: 16384 rays 54.3 us
+// with 2 segments, 47.1 with 4; 32768 rays 65.5 with 1, 57.2 with 2; 65536 rays best
+// with 1).  Without a wave size (0) the ray-count rule of make_consts stays.
+void auto_segments(const Tuning& t, uint32_t n, uint64_t wave256, EvalConsts* k) {
+  if (t.lg_segs >= 0 || wave256 == 0) return;
+  uint32_t lg = 2;
+  while (lg > 0 && ((uint64_t)n << lg) > wave256) --lg;
+  k->lg_segs = lg;
+}
+
 // n_threads: rays (or points) times segments per ray.  Threads per CTA: the tuned value, or
 // (automatic) 256 when the whole launch fits in one wave of 256-thread CTAs (`wave256`
 // threads; fewer CTAs stage the radius field and store partials: 65536 rays 69.7 -> 68.1 us
@@ -581,8 +594,10 @@ int rmp_eval_launch_info(rmp_ctx* c, uint32_t map_id, uint32_t n_rays, const rmp
   if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
   const DevMap dm = it->second.dm;
   EvalConsts k;
-  int st = make_consts(params, dm.vs, n_rays, false, &k, tuning_of(c));
+  const Tuning t = tuning_of(c);
+  int st = make_consts(params, dm.vs, n_rays, false, &k, t);
   if (st != RMP_OK) return st;
+  auto_segments(t, n_rays, it->second.wave256[k.reduce_mode], &k);
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   int block, grid;
@@ -635,8 +650,10 @@ int rmp_raycast_eval_async(rmp_ctx* c, uint32_t map_id, const double* state_dev,
     wave256[1] = it->second.wave256[1];
   }
   EvalConsts k;
-  int st = make_consts(params, dm.vs, n_rays, false, &k, tuning_of(c));
+  const Tuning t = tuning_of(c);
+  int st = make_consts(params, dm.vs, n_rays, false, &k, t);
   if (st != RMP_OK) return st;
+  auto_segments(t, n_rays, wave256[k.reduce_mode], &k);
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   int block, grid;
@@ -656,8 +673,10 @@ int rmp_raycast_eval(rmp_ctx* c, uint32_t map_id, const double x[3], const doubl
   DevMap dm = it->second.dm;
   if (c->tune_cells != 1) dm.cells = nullptr;     // single states: off unless asked for
   EvalConsts k;
-  int st = make_consts(params, dm.vs, n_rays, false, &k, tuning_of(c));
+  const Tuning t = tuning_of(c);
+  int st = make_consts(params, dm.vs, n_rays, false, &k, t);
   if (st != RMP_OK) return st;
+  auto_segments(t, n_rays, it->second.wave256[k.reduce_mode], &k);
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;

@@ -405,8 +405,9 @@ def test_tuning_knobs_keep_results(ctx, hashed, block, lgs):
 
 
 def test_automatic_block_size(ctx, hashed):
-    """Threads per CTA by default: 256 while the launch fits in one wave of 256-thread CTAs
-    (occupancy x SMs), 128 beyond it; an explicit setting wins."""
+    """Launch shape by default: as many segments per ray (up to 4) as keep the launch within
+    one wave of 256-thread CTAs (occupancy x SMs), 256 threads per CTA while it fits, 128
+    beyond it; an explicit setting wins."""
     wl, mid, om = hashed
     p = R.make_params(wl.params, wl.max_range)
     assert R.rmp_tune_get(ctx.handle, R.RMP_TUNE_BLOCK) == 0
@@ -415,8 +416,13 @@ def test_automatic_block_size(ctx, hashed):
     R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 0)
     wave = info["sm_count"] * info["ctas_per_sm"] * 256
     assert wave >= 65536                       # the headline evaluation fits in one wave
-    for n in (1, 1024, 65536, 262144, 1 << 20):
+    for n in (1, 1024, 4096, 16384, 19456, 19457, 32768, 38912, 38913, 65536, 262144, 1 << 20):
         li = R.rmp_eval_launch_info(ctx.handle, mid, n, p)
+        # segments per ray: the most (up to 4) that keep the launch within one wave
+        lg = 2
+        while lg > 0 and (n << lg) > wave:
+            lg -= 1
+        assert li["lg_segments"] == lg, (n, li)
         threads = n << li["lg_segments"]
         assert li["block"] == (256 if threads <= wave else 128), (n, li)
         assert li["grid"] == min(4096, (threads + li["block"] - 1) // li["block"])
