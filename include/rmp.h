@@ -436,7 +436,8 @@ int rmp_server_stats(rmp_server* server, rmp_server_stats_t* out);
  *  RMP_TUNE_LG_SEGMENTS  log2 of the segments each ray is split into and marched by that
  *                        many threads (0..2), or -1 (default) to choose: one state, the
  *                        most (up to 4) that keep the launch within one wave of 256-thread
- *                        CTAs; batches, 4 up to 4096 rays, 2 up to 16384, else 1
+ *                        CTAs; batches, per state the most (up to 4) whose threads the
+ *                        persistent launch holds at once
  *  RMP_TUNE_RAY_ORDER    0 (default): rays of one direction cell share warps (coherent
  *                        march); 1: Halton index order
  *  RMP_TUNE_SPLIT_BUDGET block visits after which the pieces still running in a warp are

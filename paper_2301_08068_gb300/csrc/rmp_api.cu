@@ -771,6 +771,7 @@ int batch_setup(rmp_ctx* c, uint32_t map_id, uint32_t n_states, uint32_t max_ray
   const int occ = batch_occupancy(*dm, k->reduce_mode, *block);
   if (occ <= 0) return RMP_ERR_CUDA;
   *grid = c->sm_count * occ;
+  k->seg_threads = (uint32_t)*grid * (uint32_t)*block;
   return RMP_OK;
 }
 

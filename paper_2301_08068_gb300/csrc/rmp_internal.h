@@ -82,7 +82,7 @@ struct EvalConsts {
   double c64;                        // soft-normalisation c (FP64, attractor)
   double att_alpha, att_beta;        // attractor gain and damping (combined evaluations)
   int att_mean;                      // combined: ray sums divided by the ray count first
-  int pad_;
+  uint32_t seg_threads;              // batches: threads of the persistent launch (segments)
   double x0[6];                      // x, xdot carried in the launch itself, read when the
                                      // kernel's state pointer is null (synchronous calls)
 };
