@@ -445,7 +445,8 @@ int rmp_server_stats(rmp_server* server, rmp_server_stats_t* out);
  *                        0 never, -1 (default) the library's choice (currently never)
  *  RMP_TUNE_CELL_SKIP    free boxes of voxels inside occupied blocks crossed in one step
  *                        (grid layout maps): 1 always, 0 never, -1 (default) in batched
- *                        evaluations only (measured faster there, slower for one state) */
+ *                        evaluations and in single-state ones marched as 4 segments per
+ *                        ray (measured faster there, slower for one segment per ray) */
 #define RMP_TUNE_BLOCK 1
 #define RMP_TUNE_LG_SEGMENTS 2
 #define RMP_TUNE_RAY_ORDER 3
