@@ -181,9 +181,12 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device: int):
+        import tempfile
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        # raw samples: RMP_BENCH_CLOCKS_DIR if set (to keep them), else a temporary folder
+        folder = os.environ.get("RMP_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, "clocks_bench_%d.csv" % os.getpid())
 
     def start(self):
         try:
