@@ -44,8 +44,9 @@ def run_batch(ctx, mid, states, counts, params, max_rays=None, want=True):
     nr = torch.tensor(counts.astype(np.int32), device="cuda")
     ws = torch.empty(R.rmp_batch_workspace_bytes(B, mr), dtype=torch.uint8, device="cuda")
     out = torch.empty((B, R.RESULT_BYTES), dtype=torch.uint8, device="cuda")
-    hits = torch.empty(B * mr * 24, dtype=torch.uint8, device="cuda") if want else None
-    per = torch.empty(B * mr * 9, dtype=torch.float32, device="cuda") if want else None
+    # zeroed: slots of invalid states and beyond a state's count are never written
+    hits = torch.zeros(B * mr * 24, dtype=torch.uint8, device="cuda") if want else None
+    per = torch.zeros(B * mr * 9, dtype=torch.float32, device="cuda") if want else None
     R.rmp_raycast_eval_batch_async(ctx.handle, mid, st, nr, B, mr, params, ws, out, hits=hits,
                                    per_ray=per)
     torch.cuda.synchronize()
