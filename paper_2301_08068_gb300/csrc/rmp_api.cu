@@ -121,14 +121,17 @@ void pick_ray_cells(uint32_t n, EvalConsts* k) {
 
 // Derive the per-evaluation constants; validates every parameter.
 struct Tuning {
-  int lg_segs = -1, ray_order = 0, split = -1;
+  int lg_segs = -1, ray_order = 0, split = -1, block = 0, cells = -1;
 };
 
+// Snapshot of the context's launch knobs; call with c->mu held (rmp_tune_set writes them).
 Tuning tuning_of(const rmp_ctx* c) {
   Tuning t;
   t.lg_segs = c->tune_lg_segs;
   t.ray_order = c->tune_ray_order;
   t.split = c->tune_split;
+  t.block = c->tune_block;
+  t.cells = c->tune_cells;
   return t;
 }
 
@@ -213,9 +216,9 @@ void single_state_cells(int tune_cells, const EvalConsts& k, DevMap* dm) {
 // (automatic) 256 when the whole launch fits in one wave of 256-thread CTAs (`wave256`
 // threads; fewer CTAs stage the radius field and store partials: 65536 rays 69.7 -> 68.1 us
 // hashed, 46.3 -> 43.8 us dense) and 128 otherwise (262144 rays: 132 against 135 us).
-void launch_shape(const rmp_ctx* ctx, uint64_t n_threads, uint64_t wave256, int* block,
+void launch_shape(const Tuning& t, uint64_t n_threads, uint64_t wave256, int* block,
                   int* grid) {
-  int b = ctx->tune_block;
+  int b = t.block;
   if (b == 0) b = (wave256 > 0 && n_threads <= wave256) ? 256 : 128;
   uint64_t g = (n_threads + b - 1) / b;
   if (g > (uint64_t)kMaxGrid) g = kMaxGrid;
@@ -228,9 +231,9 @@ void launch_shape(const rmp_ctx* ctx, uint64_t n_threads, uint64_t wave256, int*
 // SM, each thread striding over several points, so that large scans are reduced from few
 // CTA partials (measured, L2 flushed: 4096 / 65536 / 262144 points 16.4 / 20.5 / 24.3 us
 // with 128-thread CTAs and 4 per SM, 14.4 / 18.5 / 21.0 us with 256 and 2 per SM).
-void scan_shape(const rmp_ctx* ctx, uint64_t n, int* block, int* grid) {
-  const int b = ctx->tune_block != 0 ? ctx->tune_block : 256;
-  const uint64_t cap = (uint64_t)(512 / b) * (uint64_t)(ctx->sm_count > 0 ? ctx->sm_count : 1);
+void scan_shape(const Tuning& t, int sm_count, uint64_t n, int* block, int* grid) {
+  const int b = t.block != 0 ? t.block : 256;
+  const uint64_t cap = (uint64_t)(512 / b) * (uint64_t)(sm_count > 0 ? sm_count : 1);
   uint64_t g = (n + b - 1) / b;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
@@ -610,7 +613,7 @@ int rmp_eval_launch_info(rmp_ctx* c, uint32_t map_id, uint32_t n_rays, const rmp
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   int block, grid;
-  launch_shape(c, (uint64_t)n_rays << k.lg_segs, it->second.wave256[k.reduce_mode], &block,
+  launch_shape(t, (uint64_t)n_rays << k.lg_segs, it->second.wave256[k.reduce_mode], &block,
                &grid);
   std::memset(out, 0, sizeof(*out));
   out->block = block;
@@ -649,26 +652,25 @@ int rmp_raycast_eval_async(rmp_ctx* c, uint32_t map_id, const double* state_dev,
     return RMP_ERR_INVALID_ARG;
   DevMap dm;
   uint64_t wave256[2];
-  int cells;
+  Tuning t;
   {
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->maps.find(map_id);
     if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
     dm = it->second.dm;
-    cells = c->tune_cells;
+    t = tuning_of(c);
     wave256[0] = it->second.wave256[0];
     wave256[1] = it->second.wave256[1];
   }
   EvalConsts k;
-  const Tuning t = tuning_of(c);
   int st = make_consts(params, dm.vs, n_rays, false, &k, t);
   if (st != RMP_OK) return st;
   auto_segments(t, n_rays, wave256[k.reduce_mode], &k);
-  single_state_cells(cells, k, &dm);
+  single_state_cells(t.cells, k, &dm);
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   int block, grid;
-  launch_shape(c, (uint64_t)n_rays << k.lg_segs, wave256[k.reduce_mode], &block, &grid);
+  launch_shape(t, (uint64_t)n_rays << k.lg_segs, wave256[k.reduce_mode], &block, &grid);
   RMP_CUDA(launch_raycast(dm, k, state_dev, ws, out_dev, hits_dev, per_ray_dev, block, grid,
                           (cudaStream_t)stream));
   return RMP_OK;
@@ -687,7 +689,7 @@ int rmp_raycast_eval(rmp_ctx* c, uint32_t map_id, const double x[3], const doubl
   int st = make_consts(params, dm.vs, n_rays, false, &k, t);
   if (st != RMP_OK) return st;
   auto_segments(t, n_rays, it->second.wave256[k.reduce_mode], &k);
-  single_state_cells(c->tune_cells, k, &dm);
+  single_state_cells(t.cells, k, &dm);
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
@@ -696,7 +698,7 @@ int rmp_raycast_eval(rmp_ctx* c, uint32_t map_id, const double x[3], const doubl
     k.x0[3 + a] = xdot[a];
   }
   int block, grid;
-  launch_shape(c, (uint64_t)n_rays << k.lg_segs, it->second.wave256[k.reduce_mode], &block,
+  launch_shape(t, (uint64_t)n_rays << k.lg_segs, it->second.wave256[k.reduce_mode], &block,
                &grid);
   RMP_CUDA(launch_raycast(dm, k, nullptr, c->ws, c->result_map, hits_dev, per_ray_dev,
                           block, grid, s));
@@ -713,10 +715,15 @@ int rmp_scan_eval_async(rmp_ctx* c, const float* points_dev, uint32_t n, const d
   EvalConsts k;
   int st = make_consts(params, 1.0, n, true, &k);
   if (st != RMP_OK) return st;
+  Tuning t;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    t = tuning_of(c);
+  }
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   int block, grid;
-  scan_shape(c, n, &block, &grid);
+  scan_shape(t, c->sm_count, n, &block, &grid);
   RMP_CUDA(launch_scan(points_dev, k, state_dev, ws, out_dev, per_ray_dev, block, grid,
                        (cudaStream_t)stream));
   return RMP_OK;
@@ -738,7 +745,7 @@ int rmp_scan_eval(rmp_ctx* c, const float* points_dev, uint32_t n, const double 
     k.x0[3 + a] = xdot[a];
   }
   int block, grid;
-  scan_shape(c, n, &block, &grid);
+  scan_shape(tuning_of(c), c->sm_count, n, &block, &grid);
   RMP_CUDA(launch_scan(points_dev, k, nullptr, c->ws, c->result_map, per_ray_dev, block, grid,
                        s));
   RMP_CUDA(cudaStreamSynchronize(s));
@@ -770,9 +777,9 @@ int batch_setup(rmp_ctx* c, uint32_t map_id, uint32_t n_states, uint32_t max_ray
     auto it = c->maps.find(map_id);
     if (it == c->maps.end()) return RMP_ERR_UNKNOWN_MAP;
     *dm = it->second.dm;
-    if (c->tune_cells == 0) dm->cells = nullptr;  // batches: on unless switched off
     t = tuning_of(c);
-    *block = c->tune_block != 0 ? c->tune_block : 128;
+    if (t.cells == 0) dm->cells = nullptr;        // batches: on unless switched off
+    *block = t.block != 0 ? t.block : 128;
   }
   int st = make_consts(params, dm->vs, max_rays, false, k, t);
   if (st != RMP_OK) return st;
