@@ -156,6 +156,27 @@ def test_batch_results_independent_of_order_and_company(ctx, hashed):
             assert np.array_equal(alone[key], base[b][key]), (b, key)
 
 
+def test_batch_segment_thresholds(ctx, hashed):
+    """Ray counts on both sides of the default per-state segment thresholds (4 segments
+    while 4 n fits in the persistent launch's threads, 2 while 2 n does, else 1; 155648
+    threads on a 152-SM part): every state matches the oracle, and its result is bitwise
+    the same alone as in the mixed batch."""
+    wl, mid, om = hashed
+    pg = R.make_params(wl.params, wl.max_range)
+    po = O.make_params(wl.params, wl.max_range)
+    counts = np.array([38912, 38913, 77824, 77825], np.uint32)
+    states = np.stack([np.concatenate([s.x, s.xdot]) for s in wl.states[:4]])
+    mixed, h, p, _ = run_batch(ctx, mid, states, counts, pg)
+    for b, n in enumerate(counts):
+        s = wl.states[b]
+        ro, ho, por = O.raycast_eval(om, s.x, s.xdot, int(n), po)
+        assert_hits_exact(h[b, :n], ho)
+        assert_result_close(mixed[b], ro, por)
+        alone = run_batch(ctx, mid, states[b:b + 1], counts[b:b + 1], pg, want=False)[0][0]
+        for key in ("f", "sumA", "sumAf", "eig"):
+            assert np.array_equal(alone[key], mixed[b][key]), (n, key)
+
+
 def test_batch_invalid_states_are_isolated(ctx, hashed):
     wl, mid, om = hashed
     pg = R.make_params(wl.params, wl.max_range)
