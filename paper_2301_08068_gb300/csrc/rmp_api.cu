@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "rmp_internal.h"
+#include "rmp_policy.h"
 
 using namespace rmp;
 
@@ -94,36 +95,6 @@ float round_down_f32(double v) {
   return f;
 }
 
-// Coherent ray order: residue classes modulo M = 2^a 3^b are direction cells (see the
-// kernel's ray_of_slot).  Cells hold >= 32 rays so a warp spans at most two of them, about
-// n/48 cells, shaped close to square on the sphere (3^b ~ pi 2^a).
-void pick_ray_cells(uint32_t n, EvalConsts* k) {
-  // candidates M = 2^a 3^b with 32 M <= n, scored in log2 units with one logarithm per call:
-  // |log2 M - log2(n / 48)| + 0.5 |log2(3^b / (pi 2^a))|
-  const double L3 = 1.5849625007211562, LPI = 1.6514961294723187;   // log2 3, log2 pi
-  const double lt = std::log2(std::max(n / 48.0, 1.0));
-  uint64_t best = 1;
-  double best_score = 1e300;
-  for (int a = 0; a <= 24; ++a) {
-    uint64_t m = 1ull << a;
-    for (int b = 0; b <= 15 && m * 32ull <= n; ++b, m *= 3ull) {
-      const double score = std::fabs(a + b * L3 - lt) + 0.5 * std::fabs(b * L3 - LPI - a);
-      if (score < best_score) {
-        best_score = score;
-        best = m;
-      }
-    }
-  }
-  k->perm_M = (uint32_t)best;
-  k->perm_Q = n / k->perm_M;
-  k->perm_R = n % k->perm_M;
-}
-
-// Derive the per-evaluation constants; validates every parameter.
-struct Tuning {
-  int lg_segs = -1, ray_order = 0, split = -1, block = 0, cells = -1;
-};
-
 // Snapshot of the context's launch knobs; call with c->mu held (rmp_tune_set writes them).
 Tuning tuning_of(const rmp_ctx* c) {
   Tuning t;
@@ -135,6 +106,7 @@ Tuning tuning_of(const rmp_ctx* c) {
   return t;
 }
 
+// Derive the per-evaluation constants; validates every parameter.
 int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalConsts* k,
                 const Tuning& tune = Tuning()) {
   if (!p) return RMP_ERR_INVALID_ARG;
@@ -188,57 +160,6 @@ int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalCon
     k->perm_R = 0;
   }
   return RMP_OK;
-}
-
-// Segments per ray of a single-state evaluation left to the library: as many (up to 4) as
-// keep the launch within one wave of 256-thread CTAs (`wave256` threads), since the
-// evaluation lasts as long as its longest ray's serial march and segments shorten it
-// while the extra threads still find free SMs (measured, hashed map: 16384 rays 54.3 us
-// with 2 segments, 47.1 with 4; 32768 rays 65.5 with 1, 57.2 with 2; 65536 rays best
-// with 1).  Without a wave size (0) the ray-count rule of make_consts stays.
-void auto_segments(const Tuning& t, uint32_t n, uint64_t wave256, EvalConsts* k) {
-  if (t.lg_segs >= 0 || wave256 == 0) return;
-  uint32_t lg = 2;
-  while (lg > 0 && ((uint64_t)n << lg) > wave256) --lg;
-  k->lg_segs = lg;
-}
-
-// Voxel boxes in a single-state evaluation: as tuned, or (default) only with 4 segments per
-// ray, where they pay (measured, 16384 rays: hashed 47.1 -> 44.6 us, dense 37.5 -> 36.6 us)
-// -- with one segment per ray their extra dependent load lengthens the slowest warps
-// (65536 rays: hashed 68.0 -> 71.2 us, dense 43.9 -> 49.4 us).
-void single_state_cells(int tune_cells, const EvalConsts& k, DevMap* dm) {
-  if (tune_cells == 1) return;
-  if (tune_cells == 0 || k.lg_segs < 2) dm->cells = nullptr;
-}
-
-// n_threads: rays (or points) times segments per ray.  Threads per CTA: the tuned value, or
-// (automatic) 256 when the whole launch fits in one wave of 256-thread CTAs (`wave256`
-// threads; fewer CTAs stage the radius field and store partials: 65536 rays 69.7 -> 68.1 us
-// hashed, 46.3 -> 43.8 us dense) and 128 otherwise (262144 rays: 132 against 135 us).
-void launch_shape(const Tuning& t, uint64_t n_threads, uint64_t wave256, int* block,
-                  int* grid) {
-  int b = t.block;
-  if (b == 0) b = (wave256 > 0 && n_threads <= wave256) ? 256 : 128;
-  uint64_t g = (n_threads + b - 1) / b;
-  if (g > (uint64_t)kMaxGrid) g = kMaxGrid;
-  if (g < 1) g = 1;
-  *block = b;
-  *grid = (int)g;
-}
-
-// Scans: threads per CTA the tuned value or (automatic) 256, and at most 512 threads per
-// SM, each thread striding over several points, so that large scans are reduced from few
-// CTA partials (measured, L2 flushed: 4096 / 65536 / 262144 points 16.4 / 20.5 / 24.3 us
-// with 128-thread CTAs and 4 per SM, 14.4 / 18.5 / 21.0 us with 256 and 2 per SM).
-void scan_shape(const Tuning& t, int sm_count, uint64_t n, int* block, int* grid) {
-  const int b = t.block != 0 ? t.block : 256;
-  const uint64_t cap = (uint64_t)(512 / b) * (uint64_t)(sm_count > 0 ? sm_count : 1);
-  uint64_t g = (n + b - 1) / b;
-  if (g > cap) g = cap;
-  if (g < 1) g = 1;
-  *block = b;
-  *grid = (int)g;
 }
 
 void free_map(MapRec& r) {
