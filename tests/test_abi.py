@@ -82,6 +82,38 @@ int main(void) {
     assert got["rmp_result_t"] == 144 and got["rmp_ray_hit_t"] == 24
 
 
+def test_c_program_links_and_calls_host_functions(rmp, tmp_path):
+    """The library is usable from plain C: a program compiled against include/rmp.h and
+    linked with librmp.so calls the host-only entry points (no GPU needed)."""
+    src = tmp_path / "use.c"
+    src.write_text("""
+#include <stdio.h>
+#include <string.h>
+#include "rmp.h"
+int main(void) {
+  rmp_params_t p;
+  memset(&p, 0, sizeof(p));
+  if (rmp_params_preset(RMP_PRESET_STATIC_MAP, &p) != RMP_OK) return 1;
+  if (rmp_params_preset(7, &p) != RMP_ERR_INVALID_ARG) return 2;
+  if (rmp_ctx_create(NULL, 0) != RMP_ERR_INVALID_ARG) return 3;
+  if (strcmp(rmp_status_string(RMP_OK), "ok") != 0) return 4;
+  printf("%.17g %.17g %zu %zu\\n", p.eta_rep, p.r, rmp_workspace_bytes(),
+         rmp_batch_workspace_bytes(3, 1000));
+  return 0;
+}
+""")
+    exe = tmp_path / "use"
+    lib = rmp.lib_path()
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe),
+                           "-L", os.path.dirname(lib), "-lrmp",
+                           "-Wl,-rpath," + os.path.dirname(lib)])
+    out = subprocess.check_output([str(exe)], text=True).split()
+    p = rmp.rmp_params_preset(rmp.RMP_PRESET_STATIC_MAP)
+    assert float(out[0]) == p.eta_rep and float(out[1]) == p.r
+    assert int(out[2]) == rmp.rmp_workspace_bytes()
+    assert int(out[3]) == rmp.rmp_batch_workspace_bytes(3, 1000)
+
+
 def test_presets_equal_table_one(rmp):
     gold = json.load(open(os.path.join(ROOT, "tests", "golden", "table1_params.json")))
     for preset, col in ((rmp.RMP_PRESET_STATIC_MAP, "static_map"), (rmp.RMP_PRESET_LIDAR, "lidar")):
