@@ -118,33 +118,30 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_on_threads(om, p, states, n_rays: int, threads: int, evals: int):
+def oracle_on_threads(om, p, states, n_rays: int, threads: int, evals: int, pool=None):
     """`evals` oracle evaluations of `n_rays` rays, state k % len(states) for evaluation k,
     spread over `threads` host threads: the oracle is the unchanged single-threaded C code
     (its evaluation keeps no global state and the ctypes call releases the GIL), run on
-    independent states at once.  Returns the wall time in seconds."""
-    import threading
+    independent states at once.  `pool` (a ThreadPoolExecutor of `threads` workers) is
+    reused across calls when given.  Returns the wall time in seconds."""
+    from concurrent.futures import ThreadPoolExecutor
     import oracle as O
-    nxt = [0]
-    lock = threading.Lock()
 
-    def work():
-        while True:
-            with lock:
-                k = nxt[0]
-                nxt[0] += 1
-            if k >= evals:
-                return
-            s = states[k % len(states)]
-            O.raycast_eval(om, s.x, s.xdot, n_rays, p, want_hits=False, want_per_ray=False)
+    def work(k):
+        s = states[k % len(states)]
+        O.raycast_eval(om, s.x, s.xdot, n_rays, p, want_hits=False, want_per_ray=False)
 
-    ts = [threading.Thread(target=work) for _ in range(threads)]
-    t0 = time.perf_counter()
-    for t in ts:
-        t.start()
-    for t in ts:
-        t.join()
-    return time.perf_counter() - t0
+    own = pool is None
+    if own:
+        pool = ThreadPoolExecutor(threads)
+    try:
+        t0 = time.perf_counter()
+        for f in [pool.submit(work, k) for k in range(evals)]:
+            f.result()
+        return time.perf_counter() - t0
+    finally:
+        if own:
+            pool.shutdown()
 
 
 def time_oracle(wl, seconds: float, max_evals: int):
@@ -553,13 +550,16 @@ def run_reference(args):
     cores = host_cores()
     budget = args.ref_seconds / max(1, args.steps + args.warmup)   # wall seconds per step
     m = int(min(N_RAYS, max(256, budget / per_ray)) // 256 * 256)
+    from concurrent.futures import ThreadPoolExecutor
+    pool = ThreadPoolExecutor(cores)              # one pool for every step
     for i in range(args.warmup):
         st = [wl.states[(i * cores + c) % N_STATES] for c in range(cores)]
-        oracle_on_threads(om, p, st, m, cores, cores)
+        oracle_on_threads(om, p, st, m, cores, cores, pool)
     times = []
     for i in range(args.steps):
         st = [wl.states[(i * cores + c) % N_STATES] for c in range(cores)]
-        times.append(oracle_on_threads(om, p, st, m, cores, cores))
+        times.append(oracle_on_threads(om, p, st, m, cores, cores, pool))
+    pool.shutdown()
     ms = 1e3 * sum(times) / len(times)
     value = cores * m / (ms / 1e3) / 1e9
     sample = ("each step: the first %d of the 65536 Halton rays of %d states of the workload, "
