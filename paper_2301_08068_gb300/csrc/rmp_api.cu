@@ -51,19 +51,24 @@ struct rmp_ctx {
 
 namespace {
 
+// Makes `dev` current for a scope and restores the caller's device; no driver call when
+// it already is current (the common case, on the synchronous path of every evaluation).
 class DeviceGuard {
  public:
   explicit DeviceGuard(int dev) {
-    ok_ = cudaGetDevice(&prev_) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess;
+    ok_ = cudaGetDevice(&prev_) == cudaSuccess;
+    switched_ = ok_ && prev_ != dev;
+    if (switched_) ok_ = cudaSetDevice(dev) == cudaSuccess;
   }
   ~DeviceGuard() {
-    if (ok_) cudaSetDevice(prev_);
+    if (ok_ && switched_) cudaSetDevice(prev_);
   }
   bool ok() const { return ok_; }
 
  private:
   int prev_ = 0;
   bool ok_ = false;
+  bool switched_ = false;
 };
 
 int cuda_status(cudaError_t e) {
