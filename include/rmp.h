@@ -170,6 +170,8 @@ int rmp_map_upload(rmp_ctx* ctx, const rmp_map_desc_t* desc, rmp_stream_t stream
 /* Free a map.  No evaluation using it may still be running. */
 int rmp_map_release(rmp_ctx* ctx, uint32_t map_id);
 
+/* Kind, layout, bricks held, hash capacity and device bytes of a map (*out: host).
+ * RMP_ERR_UNKNOWN_MAP for an id not registered in this context. */
 int rmp_map_info(rmp_ctx* ctx, uint32_t map_id, rmp_map_info_t* out);
 
 /* Free-space data of a grid-layout map, for diagnostics and tests (evaluation does not need
@@ -368,12 +370,21 @@ int rmp_rollout(rmp_ctx* ctx, uint32_t map_id, const double* robots, uint32_t n_
  * a scan in flight; wait blocks until that scan's result is in *out (host).  A ticket can
  * be waited for until its slot is reused (`slots` submits later: RMP_ERR_BUSY). */
 typedef struct rmp_scan_pipeline rmp_scan_pipeline;
+/* max_points (>= 1) per scan, slots in 2..8: allocates per-slot device buffers, pinned
+ * staging and two streams on the context's device; *out receives the pipeline, which must
+ * not outlive the context.  RMP_ERR_INVALID_ARG, RMP_ERR_NO_MEMORY. */
 int rmp_scan_pipeline_create(rmp_ctx* ctx, uint32_t max_points, uint32_t slots,
                              rmp_scan_pipeline** out);
+/* Waits for the scans in flight, then frees everything the pipeline holds. */
 int rmp_scan_pipeline_destroy(rmp_scan_pipeline* pipeline);
+/* points_host: n x 3 floats (x, y, z in the frame of x), n in [1, max_points]; x, xdot: host,
+ * 3 doubles each.  *ticket identifies the scan.  RMP_ERR_INVALID_ARG for bad arguments or
+ * parameters (as rmp_scan_eval), RMP_ERR_CUDA if a copy or launch fails. */
 int rmp_scan_pipeline_submit(rmp_scan_pipeline* pipeline, const float* points_host, uint32_t n,
                              const double x[3], const double xdot[3], const rmp_params_t* params,
                              uint64_t* ticket);
+/* Blocks until the ticket's scan is evaluated and writes its result to *out (host).
+ * RMP_ERR_INVALID_ARG for a ticket never issued, RMP_ERR_BUSY once its slot was reused. */
 int rmp_scan_pipeline_wait(rmp_scan_pipeline* pipeline, uint64_t ticket, rmp_result_t* out);
 
 /* ------------------------------------------------------------------ request server
@@ -424,6 +435,7 @@ int rmp_server_poll(rmp_server* server, uint64_t ticket, rmp_result_t* out, doub
 /* Like poll, but waits up to timeout_ms; RMP_ERR_TIMEOUT if the result is not there then. */
 int rmp_server_wait(rmp_server* server, uint64_t ticket, uint32_t timeout_ms, rmp_result_t* out,
                     double* latency_s);
+/* Counters since the server started (*out: host). */
 int rmp_server_stats(rmp_server* server, rmp_server_stats_t* out);
 
 /* ------------------------------------------------------------------ launch tuning
@@ -452,6 +464,8 @@ int rmp_server_stats(rmp_server* server, rmp_server_stats_t* out);
 #define RMP_TUNE_RAY_ORDER 3
 #define RMP_TUNE_SPLIT_BUDGET 4
 #define RMP_TUNE_CELL_SKIP 5
+/* Set / read one knob of the context.  RMP_ERR_INVALID_ARG for an unknown knob or a value
+ * outside its range; *value receives 0 or -1 where the library chooses. */
 int rmp_tune_set(rmp_ctx* ctx, int knob, int value);
 int rmp_tune_get(rmp_ctx* ctx, int knob, int* value);
 
