@@ -183,3 +183,31 @@ def test_null_arguments_rejected_without_gpu(rmp):
     cfg = rmp.rmp_server_config_default()
     assert (cfg.slots, cfg.max_batch_states, cfg.max_rays, cfg.mem_budget_bytes) == \
         (4, 256, 262144, 1 << 30)
+
+
+def test_missing_library_fails_loudly(rmp, monkeypatch):
+    """No fallback: when librmp.so is missing or stale and cannot be built, every use of the
+    binding raises instead of computing anything some other way."""
+    import paper_2301_08068_gb300.rmp as R
+    saved = R._lib
+    monkeypatch.setattr(R, "_lib", None)
+    monkeypatch.setattr(R._build, "up_to_date", lambda: False)
+
+    def no_toolchain():
+        raise OSError("nvcc not found")
+    monkeypatch.setattr(R._build, "build", no_toolchain)
+    with pytest.raises(RuntimeError, match="could not be built"):
+        R.lib()
+    with pytest.raises(RuntimeError):
+        R.rmp_params_preset(R.RMP_PRESET_STATIC_MAP)
+    monkeypatch.setattr(R, "_lib", saved)
+
+
+def test_context_without_gpu_is_an_error(rmp):
+    """On a machine without a usable GPU the context cannot be created (status, no
+    fallback)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(rmp.RmpError):
+        rmp.Context(0)
