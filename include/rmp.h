@@ -430,9 +430,11 @@ int rmp_server_submit(rmp_server* server, uint32_t map_id, const double x[3],
                       const double xdot[3], uint32_t n_rays, const rmp_params_t* params,
                       uint64_t* ticket);
 /* RMP_OK and the result (and its submit-to-completion latency in seconds, nullable) if
- * done; RMP_ERR_NOT_READY if not yet; RMP_ERR_INVALID_ARG for a ticket never issued. */
+ * done, which collects it; RMP_ERR_NOT_READY if not yet; RMP_ERR_INVALID_ARG for a ticket
+ * never issued or already collected. */
 int rmp_server_poll(rmp_server* server, uint64_t ticket, rmp_result_t* out, double* latency_s);
-/* Like poll, but waits up to timeout_ms; RMP_ERR_TIMEOUT if the result is not there then. */
+/* Like poll, but waits up to timeout_ms; RMP_ERR_TIMEOUT if the result is not there then;
+ * RMP_ERR_INVALID_ARG for a ticket never issued or collected (also while waiting). */
 int rmp_server_wait(rmp_server* server, uint64_t ticket, uint32_t timeout_ms, rmp_result_t* out,
                     double* latency_s);
 /* Counters since the server started (*out: host). */

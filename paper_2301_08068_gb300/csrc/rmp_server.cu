@@ -18,6 +18,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "rmp_arena.h"
@@ -97,6 +98,7 @@ struct rmp_server {
   std::condition_variable cv_work, cv_done;
   std::deque<Request> pending;
   std::unordered_map<uint64_t, Finished> finished;
+  std::unordered_set<uint64_t> outstanding;      // issued tickets not yet collected
   std::vector<Slot> slots;
   std::thread worker;
   bool stop = false;
@@ -371,6 +373,7 @@ int rmp_server_submit(rmp_server* s, uint32_t map_id, const double x[3], const d
     if (s->stop) return RMP_ERR_BUSY;
     r.id = s->next_id++;
     s->pending.push_back(r);
+    s->outstanding.insert(r.id);
     s->stats.submitted += 1;
   }
   s->cv_work.notify_one();
@@ -381,12 +384,13 @@ int rmp_server_submit(rmp_server* s, uint32_t map_id, const double x[3], const d
 int rmp_server_poll(rmp_server* s, uint64_t ticket, rmp_result_t* out, double* latency_s) {
   if (!s || !out) return RMP_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
+  if (!s->outstanding.count(ticket)) return RMP_ERR_INVALID_ARG;   // never issued or collected
   auto it = s->finished.find(ticket);
-  if (it == s->finished.end()) return ticket == 0 || ticket >= s->next_id ? RMP_ERR_INVALID_ARG
-                                                                          : RMP_ERR_NOT_READY;
+  if (it == s->finished.end()) return RMP_ERR_NOT_READY;
   *out = it->second.result;
   if (latency_s) *latency_s = it->second.latency;
   s->finished.erase(it);
+  s->outstanding.erase(ticket);
   return RMP_OK;
 }
 
@@ -394,14 +398,16 @@ int rmp_server_wait(rmp_server* s, uint64_t ticket, uint32_t timeout_ms, rmp_res
                     double* latency_s) {
   if (!s || !out) return RMP_ERR_INVALID_ARG;
   std::unique_lock<std::mutex> lk(s->mu);
-  if (ticket == 0 || ticket >= s->next_id) return RMP_ERR_INVALID_ARG;
   const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
   for (;;) {
+    // never issued, or collected (also by another thread while this one waited)
+    if (!s->outstanding.count(ticket)) return RMP_ERR_INVALID_ARG;
     auto it = s->finished.find(ticket);
     if (it != s->finished.end()) {
       *out = it->second.result;
       if (latency_s) *latency_s = it->second.latency;
       s->finished.erase(it);
+      s->outstanding.erase(ticket);
       return RMP_OK;
     }
     if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout &&

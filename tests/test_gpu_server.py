@@ -133,6 +133,11 @@ def test_server_errors(env):
         ok = srv.submit(mid, wl.states[1].x, wl.states[1].xdot, 1000, p)
         res, _ = srv.wait(ok)
         assert res["status"] == 0
+        # a collected ticket is no longer valid: poll and wait fail at once, not NOT_READY
+        with pytest.raises(R.RmpError):
+            srv.poll(ok)
+        with pytest.raises(R.RmpError):
+            srv.wait(ok, 60000)
 
 
 def test_server_concurrent_submitters(env):
