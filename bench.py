@@ -226,13 +226,38 @@ class ClockSampler:
 LAUNCH_KEYS = ("block", "grid", "lg_segments", "ray_cells", "smem_bytes")
 
 
+def code_only(text: str) -> str:
+    """C++/CUDA source without comments, whitespace collapsed (string literals kept)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash(launch: dict) -> str:
-    """Identity of the measured launch: the device code (kernel source and its header) and
-    the launch shape the host chose for it.  The committed DRAM traffic is used only while
-    both are unchanged."""
+    """Identity of the measured launch: the device code (kernel source and its header,
+    comments and layout aside) and the launch shape the host chose for it.  The committed
+    DRAM traffic is used only while both are unchanged."""
     h = hashlib.sha256()
     for f in ("rmp_kernels.cu", "rmp_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_2301_08068_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2301_08068_gb300", "csrc", f)).read()
+        h.update(code_only(src).encode())
     h.update(json.dumps([launch.get(k) for k in LAUNCH_KEYS]).encode())
     return h.hexdigest()[:16]
 

@@ -3,12 +3,14 @@
 //
 // One evaluation is ONE launch: each thread generates its ray's Halton direction in
 // registers (Sec. III-E, Eq. halton), marches it with an exact fixed-point DDA through
-// the occupancy bricks (Sec. III-F; the current 8^3 brick of each ray is staged in shared
-// memory, so steps inside a brick touch no global memory), evaluates the obstacle policy
-// (Sec. III-C), and the block reduces the 9 unique terms of sum A_i and sum A_i f_i
-// (Fig. 3's block reduce) with a compensated FP32 tree (or FP64).  The last CTA to
-// finish sums the per-CTA partials in a fixed order in FP64 and resolves Eq. (1) with an
-// FP64 Jacobi pseudo-inverse, so the result is deterministic.
+// the occupancy bricks (Sec. III-F; free blocks are crossed box by box through the free
+// radius field staged in shared memory, and the 8^3 brick of an occupied block is held
+// in registers -- in the batch kernel in shared memory -- so steps inside it touch no
+// global memory), evaluates the obstacle policy (Sec. III-C), and the block reduces the
+// 9 unique terms of sum A_i and sum A_i f_i (Fig. 3's block reduce) with a compensated
+// FP32 tree (or FP64).  The last CTA to finish sums the per-CTA partials in a fixed order
+// in FP64 and resolves Eq. (1) (FP32 Jacobi eigenvectors refined by FP64 Rayleigh
+// quotients, FP64 adjugate solve at full rank), so the result is deterministic.
 //
 // Bit-exact steps (Halton direction, DDA, hit distance, the FP32 decisions that gate a
 // ray) use explicitly rounded intrinsics (__fmul_rn, __fmaf_rn, ...) so that no

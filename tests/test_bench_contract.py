@@ -52,3 +52,11 @@ def test_traffic_only_for_the_captured_launch():
     # occupancy and SM count are not part of the identity
     assert bench.kernel_source_hash(launch) == bench.kernel_source_hash(
         dict(launch, ctas_per_sm=2, sm_count=152))
+
+
+def test_launch_identity_ignores_comments_and_layout():
+    a = 'int a = 1;  // note\n/* block\n comment */ const char* s = "x // y /* z */";\n'
+    b = 'int a = 1;\nconst char* s = "x // y /* z */";'
+    assert bench.code_only(a) == bench.code_only(b)
+    assert bench.code_only('int a = 1;') != bench.code_only('int a = 2;')
+    assert '"x // y /* z */"' in bench.code_only(a)          # string literals are code
