@@ -59,6 +59,22 @@ def test_weight_flat_at_the_radius(orc):
             assert abs(w(h) - w(0.0)) < 1e-7
 
 
+@pytest.mark.parametrize("w_mode", [0, 1])
+def test_weight_relative_accuracy_near_the_radius(orc, w_mode):
+    """w_r(d) keeps its relative accuracy as d -> r: against the exact rational value of the
+    printed quadratic (or the cubic) at the FP64 d and r, for 1 - d/r from 1e-1 to 1e-9.
+    (c -> 0 and a head-on velocity make trace(A) = w_r(d) to ~1e-18.)"""
+    from fractions import Fraction as Fr
+    p = params(orc, c=1e-15, w_mode=w_mode)
+    xdot = -5.0 * R_UNIT
+    for k in range(1, 10):
+        d = p.r * (1.0 - 10.0 ** -k)
+        x = Fr(d) / Fr(p.r)
+        exact = x * x - 2 * x + 1 if w_mode == 0 else 1 - 3 * x * x + 2 * x * x * x
+        tr = np.trace(full(orc.ray_policy(p, R_UNIT, d, xdot, True, True)[1]))
+        assert abs(Fr(tr) - exact) <= Fr(1, 10 ** 12) * exact, (k, tr, float(exact))
+
+
 def test_metric_rank_one_along_obstacle_direction(orc):
     p = params(orc)
     rng = np.random.default_rng(3)
