@@ -649,14 +649,16 @@ def main():
         R.rmp_raycast_eval_async(ctx.handle, mid, states[i % N_STATES], N_RAYS, params, ws,
                                  outs[i % N_STATES])
 
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    # the clock sampler starts (and settles) before the warm-up, so the warm-up steps, with
+    # the same L2 flush between them as the timed ones, run right before the timed loop
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
+    for i in range(args.warmup):
+        flush.fill_(i & 0xFF)
+        step(i)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()

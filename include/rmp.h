@@ -294,6 +294,8 @@ int rmp_batch_autotune(rmp_ctx* ctx, uint32_t map_id, const double* states_dev,
  * states of 65536).  Nothing in the array has to start at zero: each call's set-up kernel clears
  * what it uses.  The first call on a device looks up the array's address with that device
  * current (which can load module data), so make one call before any stream capture.
+ * The address is kept for the life of the process: do not use this entry point after a
+ * cudaDeviceReset of its device (the kept address would then be stale).
  * All calls on a device share the one array: calls that may overlap in time (different
  * streams without ordering, other threads) race on it and give wrong results; order them
  * on one stream or synchronise between them. */
@@ -460,12 +462,20 @@ int rmp_server_stats(rmp_server* server, rmp_server_stats_t* out);
  *  RMP_TUNE_CELL_SKIP    free boxes of voxels inside occupied blocks crossed in one step
  *                        (grid layout maps): 1 always, 0 never, -1 (default) in batched
  *                        evaluations and in single-state ones marched as 4 segments per
- *                        ray (measured faster there, slower for one segment per ray) */
+ *                        ray (measured faster there, slower for one segment per ray)
+ *  RMP_TUNE_PERSISTENT   single-state evaluations by the persistent kernel, whose lanes
+ *                        take rays from a counter as they finish (one segment per ray,
+ *                        256-thread CTAs, every CTA the device holds at once): 1 on (up to
+ *                        2^19 rays), 0 or -1 (default) off
+ *  RMP_TUNE_ROUND_VISITS block visits each lane of the persistent kernel marches between
+ *                        fetches of new rays (1..64), or 0 (default, 4) */
 #define RMP_TUNE_BLOCK 1
 #define RMP_TUNE_LG_SEGMENTS 2
 #define RMP_TUNE_RAY_ORDER 3
 #define RMP_TUNE_SPLIT_BUDGET 4
 #define RMP_TUNE_CELL_SKIP 5
+#define RMP_TUNE_PERSISTENT 6
+#define RMP_TUNE_ROUND_VISITS 7
 /* Set / read one knob of the context.  RMP_ERR_INVALID_ARG for an unknown knob or a value
  * outside its range; *value receives 0 or -1 where the library chooses. */
 int rmp_tune_set(rmp_ctx* ctx, int knob, int value);
@@ -473,10 +483,11 @@ int rmp_tune_get(rmp_ctx* ctx, int knob, int* value);
 
 /* Launch shape rmp_raycast_eval[_async] would use for this map, ray count and parameters:
  * threads per CTA, CTAs, log2 segments per ray, resident CTAs per SM (occupancy), SMs,
- * dynamic shared memory per CTA (the staged free-radius field) and the number of
- * direction cells of the ray order.  Host-side only; launches nothing. */
+ * dynamic shared memory per CTA (the staged free-radius field), the number of
+ * direction cells of the ray order, and 1 if the persistent kernel runs it (0 for the
+ * one-wave kernel).  Host-side only; launches nothing. */
 typedef struct {
-  int32_t block, grid, lg_segments, ctas_per_sm, sm_count, smem_bytes, ray_cells, reserved;
+  int32_t block, grid, lg_segments, ctas_per_sm, sm_count, smem_bytes, ray_cells, persistent;
 } rmp_launch_info_t;
 int rmp_eval_launch_info(rmp_ctx* ctx, uint32_t map_id, uint32_t n_rays,
                          const rmp_params_t* params, rmp_launch_info_t* out);

@@ -11,6 +11,9 @@
 // and completes its requests, which frees room for the requests that arrived meanwhile.
 // A request whose batch alone would exceed the budget is completed with
 // RMP_ERR_NO_MEMORY; a CUDA error completes the batch's requests with RMP_ERR_CUDA.
+// The worker sleeps while batches are in flight: a host function enqueued after each
+// batch marks its slot done and wakes the worker (no polling of the GPU from the host).
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -49,6 +52,8 @@ struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   bool busy = false;
+  std::atomic<bool> finished{false};   // set by the batch's host function
+  rmp_server* owner = nullptr;
   std::vector<uint64_t> ids;
   std::vector<double> t_submit;
   size_t off = 0, bytes = 0;
@@ -90,6 +95,7 @@ using namespace rmp;
 
 struct rmp_server {
   rmp_ctx* ctx = nullptr;
+  std::atomic<uint32_t> completions{0};   // host functions run since the worker last looked
   int device = 0;
   rmp_server_config_t cfg;
   char* arena_dev = nullptr;
@@ -133,6 +139,19 @@ void complete_now(rmp_server* s, const Request& r, int status) {
   s->stats.completed += 1;
   s->stats.rejected += 1;
   s->cv_done.notify_all();
+}
+
+// Host function enqueued after a batch's result copy: marks the slot finished and wakes the
+// worker.  It takes the server lock only to order the flag with the worker's wait (the
+// worker never waits on a stream while holding the lock after a host function has been
+// enqueued on it), and calls no CUDA function.
+void CUDART_CB batch_done(void* arg) {
+  Slot* sl = static_cast<Slot*>(arg);
+  rmp_server* s = sl->owner;
+  sl->finished.store(true, std::memory_order_release);
+  s->completions.fetch_add(1, std::memory_order_release);
+  { std::lock_guard<std::mutex> lk(s->mu); }
+  s->cv_work.notify_all();
 }
 
 // Form and launch one batch on free slot `sl` from the pending queue.  Returns false if
@@ -209,6 +228,9 @@ bool launch_batch_on(rmp_server* s, Slot& sl) {
                       sl.stream) != cudaSuccess)
     st = RMP_ERR_CUDA;
   if (st == RMP_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = RMP_ERR_CUDA;
+  sl.finished.store(false, std::memory_order_relaxed);
+  if (st == RMP_OK && cudaLaunchHostFunc(sl.stream, batch_done, &sl) != cudaSuccess)
+    st = RMP_ERR_CUDA;
   if (st != RMP_OK) {
     // nothing usable was enqueued after the failure: wait for what was, then fail the batch
     cudaStreamSynchronize(sl.stream);
@@ -229,13 +251,16 @@ void worker_main(rmp_server* s) {
   for (;;) {
     bool progress = false;
     bool busy = false;
+    s->completions.store(0, std::memory_order_relaxed);
     for (Slot& sl : s->slots) {
       if (!sl.busy) continue;
-      const cudaError_t q = cudaEventQuery(sl.done);
-      if (q == cudaErrorNotReady) {
+      if (!sl.finished.load(std::memory_order_acquire)) {
         busy = true;
         continue;
       }
+      // the host function ran after the batch's last operation: the event has completed,
+      // and its status carries any error of the batch
+      const cudaError_t q = cudaEventQuery(sl.done);
       reap(s, sl, q == cudaSuccess ? RMP_OK : RMP_ERR_CUDA);
       progress = true;
     }
@@ -253,13 +278,16 @@ void worker_main(rmp_server* s) {
     for (const Slot& sl : s->slots) busy = busy || sl.busy;
     if (s->stop && s->pending.empty() && !busy) break;
     if (progress) continue;
-    if (busy) {
-      // batches in flight: poll their events without holding the lock
-      lk.unlock();
-      std::this_thread::yield();
-      lk.lock();
-    } else {
-      s->cv_work.wait(lk, [s] { return s->stop || !s->pending.empty(); });
+    // sleep until a request arrives or a batch's host function runs; the timed wait is a
+    // backstop only (a host function that never ran would otherwise stall the server)
+    s->cv_work.wait_for(lk, std::chrono::milliseconds(50), [s] {
+      return s->stop || s->completions.load(std::memory_order_acquire) != 0 ||
+             !s->pending.empty();
+    });
+    if (s->completions.load(std::memory_order_acquire) == 0 && s->pending.empty() && !s->stop) {
+      for (Slot& sl : s->slots)                    // backstop: look at the events directly
+        if (sl.busy && cudaEventQuery(sl.done) == cudaSuccess)
+          sl.finished.store(true, std::memory_order_release);
     }
   }
 }
@@ -294,8 +322,9 @@ int rmp_server_create(rmp_ctx* ctx, const rmp_server_config_t* cfg, rmp_server**
   if (cudaSetDevice(s->device) != cudaSuccess) st = RMP_ERR_CUDA;
   if (st == RMP_OK && cudaMalloc((void**)&s->arena_dev, cfg->mem_budget_bytes) != cudaSuccess)
     st = RMP_ERR_NO_MEMORY;
-  s->slots.resize(cfg->slots);
+  s->slots = std::vector<Slot>(cfg->slots);
   for (Slot& sl : s->slots) {
+    sl.owner = s;
     if (st != RMP_OK) break;
     const size_t n = cfg->max_batch_states;
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||

@@ -14,7 +14,10 @@ constexpr size_t kStaticScratchBytes = 4u << 20;   // 4 MiB per device
 static __device__ __align__(256) unsigned char g_batch_scratch[kStaticScratchBytes];
 
 std::mutex g_mu;
-void* g_scratch[64];          // device address of g_batch_scratch, per device id
+// Device address of g_batch_scratch, per device id, looked up once per process: it stays
+// valid for the life of the device's primary context (a cudaDeviceReset ends it, and this
+// entry point must not be used after one).
+void* g_scratch[64];
 bool g_have[64];
 
 }  // namespace
@@ -42,8 +45,8 @@ extern "C" int rmp_raycast_eval_batch_static(rmp_ctx* ctx, uint32_t map_id,
       if (cudaSetDevice(dev) != cudaSuccess) return RMP_ERR_CUDA;
       void* p = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&p, g_batch_scratch);
-      cudaSetDevice(prev);
-      if (e != cudaSuccess || !p) return RMP_ERR_CUDA;
+      const cudaError_t e_restore = cudaSetDevice(prev);
+      if (e != cudaSuccess || !p || e_restore != cudaSuccess) return RMP_ERR_CUDA;
       g_scratch[dev] = p;
       g_have[dev] = true;
     }

@@ -8,7 +8,8 @@ import oracle as O
 from paper_2301_08068_gb300 import rmp as R
 from paper_2301_08068_gb300 import workloads as W
 
-from gpu_helpers import assert_per_ray_close, assert_result_close, gpu_scan, torch_cuda
+from gpu_helpers import (assert_per_ray_close, assert_result_close, gpu_scan, scan_abs_term,
+                         torch_cuda)
 
 pytestmark = pytest.mark.gpu
 
@@ -32,8 +33,9 @@ def test_os0_scan_matches_oracle(ctx, os0):
     assert os0.points.shape == (262144, 3)
     rg, pgr = gpu_scan(ctx, os0.points, os0.x, os0.xdot, pg)
     ro, por = O.scan_eval(os0.points, os0.x, os0.xdot, po)
-    assert_per_ray_close(pgr, por)
-    assert_result_close(rg, ro, por)
+    at = scan_abs_term(os0.points, os0.x, os0.xdot, os0.params)
+    assert_per_ray_close(pgr, por, at)
+    assert_result_close(rg, ro, por, at)
 
 
 def test_pipeline_matches_direct_scans(ctx, os0):
@@ -68,5 +70,6 @@ def test_pipeline_matches_direct_scans(ctx, os0):
             pipe.wait(tickets[0])
         with pytest.raises(R.RmpError):
             pipe.wait(999)
-    ro, por = O.scan_eval(scans[2][0].numpy(), os0.x, scans[2][1], O.make_params(os0.params, os0.max_range))
-    assert_result_close(direct[2], ro, por)
+    pts2 = scans[2][0].numpy()
+    ro, por = O.scan_eval(pts2, os0.x, scans[2][1], O.make_params(os0.params, os0.max_range))
+    assert_result_close(direct[2], ro, por, scan_abs_term(pts2, os0.x, scans[2][1], os0.params))

@@ -1,21 +1,24 @@
 """The batched evaluation with the library's static device scratch
 (rmp_raycast_eval_batch_static, through the C ABI) against the caller-workspace entry
-point rmp_raycast_eval_batch_async on the same inputs, for two calls in a row, and its
-rejection of batches larger than the static scratch.  Collected last on purpose: it must
-pass after every other test has run in the same process, and alone."""
+point rmp_raycast_eval_batch_async on the same inputs -- bit for bit, since both run the
+same kernels with the same fixed summation order -- for two calls in a row; one state
+against the CPU oracle; no change of the device's free memory across a warm call; and the
+size limit at its boundary (the largest accepted one-state batch, and one ray more).
+Collected last on purpose: it must pass after every other test has run in the same process,
+and alone."""
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2301_08068_gb300 import rmp as R
 from paper_2301_08068_gb300 import workloads as W
 
-from gpu_helpers import torch_cuda
+from gpu_helpers import assert_result_close, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
-
-def _results(out, B):
-    return [R.result_from_bytes(out[b].cpu().numpy().tobytes()) for b in range(B)]
+STATIC_BYTES = 4 << 20        # the library's static scratch per device
+ONE_STATE_MAX = 406016        # largest max_rays of a one-state batch that fits it
 
 
 def test_static_scratch_batch_matches_workspace_batch():
@@ -34,22 +37,38 @@ def test_static_scratch_batch_matches_workspace_batch():
         ref_out = torch.empty((B, R.RESULT_BYTES), dtype=torch.uint8, device="cuda")
         R.rmp_raycast_eval_batch_async(ctx.handle, mid, states, nr, B, mr, pg, ws, ref_out)
         torch.cuda.synchronize()
-        ref = _results(ref_out, B)
+        ref = ref_out.cpu().numpy().copy()
+        out = torch.zeros((B, R.RESULT_BYTES), dtype=torch.uint8, device="cuda")
         for call in range(2):                       # two calls in a row
-            out = torch.zeros((B, R.RESULT_BYTES), dtype=torch.uint8, device="cuda")
+            out.zero_()
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
             R.rmp_raycast_eval_batch_static(ctx.handle, mid, states, nr, B, mr, pg, out)
             torch.cuda.synchronize()
-            got = _results(out, B)
-            for g, r in zip(got, ref):
-                assert g["status"] == r["status"] == 0
-                assert g["n_rays"] == r["n_rays"] and g["n_hits"] == r["n_hits"]
-                assert g["n_active"] == r["n_active"] and g["rank"] == r["rank"]
-                scale = max(np.abs(r["sumA"]).max(), 1e-30)
-                assert np.all(np.abs(g["sumA"] - r["sumA"]) <= 1e-9 * scale)
-                assert np.all(np.abs(g["sumAf"] - r["sumAf"]) <=
-                              1e-9 * max(np.abs(r["sumAf"]).max(), 1e-30))
-                nf = np.linalg.norm(r["f"])
-                assert np.linalg.norm(g["f"] - r["f"]) <= 1e-9 * max(nf, 1e-30)
+            if call == 1:                           # warm: the call allocates nothing
+                assert torch.cuda.mem_get_info()[0] == free0
+            got = out.cpu().numpy()
+            for b in range(B):
+                assert R.result_from_bytes(got[b].tobytes())["status"] == 0
+                assert got[b].tobytes() == ref[b].tobytes(), (call, b)
+        # one state against the oracle (4096 rays)
+        s = wl.states[1]
+        ro, _, por = O.raycast_eval(O.OracleMap(wl.map), s.x, s.xdot, 4096,
+                                    O.make_params(wl.params, wl.max_range), want_hits=False)
+        assert_result_close(R.result_from_bytes(got[1].tobytes()), ro, por)
+        # the limit at its boundary: one state of up to ONE_STATE_MAX rays fits, one more
+        # does not (the call checks max_rays, the size its workspace is laid out for)
+        assert R.rmp_batch_workspace_bytes(1, ONE_STATE_MAX) <= STATIC_BYTES
+        assert R.rmp_batch_workspace_bytes(1, ONE_STATE_MAX + 1) > STATIC_BYTES
+        n1 = torch.tensor([1000], dtype=torch.int32, device="cuda")
+        out1 = torch.zeros((1, R.RESULT_BYTES), dtype=torch.uint8, device="cuda")
+        R.rmp_raycast_eval_batch_static(ctx.handle, mid, states[:1], n1, 1, ONE_STATE_MAX, pg, out1)
+        torch.cuda.synchronize()
+        assert R.result_from_bytes(out1[0].cpu().numpy().tobytes())["n_rays"] == 1000
+        with pytest.raises(R.RmpError) as e:
+            R.rmp_raycast_eval_batch_static(ctx.handle, mid, states[:1], n1, 1,
+                                            ONE_STATE_MAX + 1, pg, out1)
+        assert e.value.status == R.STATUS_CODES["RMP_ERR_NO_MEMORY"]
         # a batch whose workspace exceeds the static scratch is refused, not truncated
         big = torch.full((7,), 65536, dtype=torch.int32, device="cuda")
         st7 = torch.cat([states, states[:1]])
