@@ -462,20 +462,12 @@ int rmp_server_stats(rmp_server* server, rmp_server_stats_t* out);
  *  RMP_TUNE_CELL_SKIP    free boxes of voxels inside occupied blocks crossed in one step
  *                        (grid layout maps): 1 always, 0 never, -1 (default) in batched
  *                        evaluations and in single-state ones marched as 4 segments per
- *                        ray (measured faster there, slower for one segment per ray)
- *  RMP_TUNE_PERSISTENT   single-state evaluations by the persistent kernel, whose lanes
- *                        take rays from a counter as they finish (one segment per ray,
- *                        256-thread CTAs, every CTA the device holds at once): 1 on (up to
- *                        2^19 rays), 0 or -1 (default) off
- *  RMP_TUNE_ROUND_VISITS block visits each lane of the persistent kernel marches between
- *                        fetches of new rays (1..64), or 0 (default, 4) */
+ *                        ray (measured faster there, slower for one segment per ray) */
 #define RMP_TUNE_BLOCK 1
 #define RMP_TUNE_LG_SEGMENTS 2
 #define RMP_TUNE_RAY_ORDER 3
 #define RMP_TUNE_SPLIT_BUDGET 4
 #define RMP_TUNE_CELL_SKIP 5
-#define RMP_TUNE_PERSISTENT 6
-#define RMP_TUNE_ROUND_VISITS 7
 /* Set / read one knob of the context.  RMP_ERR_INVALID_ARG for an unknown knob or a value
  * outside its range; *value receives 0 or -1 where the library chooses. */
 int rmp_tune_set(rmp_ctx* ctx, int knob, int value);
@@ -483,11 +475,10 @@ int rmp_tune_get(rmp_ctx* ctx, int knob, int* value);
 
 /* Launch shape rmp_raycast_eval[_async] would use for this map, ray count and parameters:
  * threads per CTA, CTAs, log2 segments per ray, resident CTAs per SM (occupancy), SMs,
- * dynamic shared memory per CTA (the staged free-radius field), the number of
- * direction cells of the ray order, and 1 if the persistent kernel runs it (0 for the
- * one-wave kernel).  Host-side only; launches nothing. */
+ * dynamic shared memory per CTA (the staged free-radius field and brick words) and the
+ * number of direction cells of the ray order.  Host-side only; launches nothing. */
 typedef struct {
-  int32_t block, grid, lg_segments, ctas_per_sm, sm_count, smem_bytes, ray_cells, persistent;
+  int32_t block, grid, lg_segments, ctas_per_sm, sm_count, smem_bytes, ray_cells, reserved;
 } rmp_launch_info_t;
 int rmp_eval_launch_info(rmp_ctx* ctx, uint32_t map_id, uint32_t n_rays,
                          const rmp_params_t* params, rmp_launch_info_t* out);

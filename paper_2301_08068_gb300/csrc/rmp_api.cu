@@ -27,7 +27,6 @@ struct MapRec {
   uint32_t cap = 0;
   uint64_t bytes = 0;
   uint64_t wave256[2] = {0, 0};   // threads of one wave of 256-thread CTAs, per reduction
-  int persist_grid[2][2] = {{0, 0}, {0, 0}};   // persistent kernel's CTAs [reduction][cells]
 };
 
 }  // namespace
@@ -43,8 +42,6 @@ struct rmp_ctx {
   int tune_ray_order = 0;    // 0: coherent direction cells, 1: Halton index order
   int tune_split = -1;       // split budget (-1: default, 0: never split)
   int tune_cells = -1;       // voxel-box skipping (-1: batches, 4-segment states; 0: off; 1: on)
-  int tune_persist = -1;     // persistent single-state kernel (-1: by ray count; 0: off; 1: on)
-  int tune_round = 0;        // block visits per round of the persistent kernel (0: default)
   // scratch of the synchronous calls (serialised by mu): the state travels in the launch's
   // constants; the kernel writes the result straight into mapped pinned host memory
   void* ws = nullptr;
@@ -111,8 +108,6 @@ Tuning tuning_of(const rmp_ctx* c) {
   t.split = c->tune_split;
   t.block = c->tune_block;
   t.cells = c->tune_cells;
-  t.persist = c->tune_persist;
-  t.round = c->tune_round;
   return t;
 }
 
@@ -164,7 +159,6 @@ int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalCon
     if (tune.lg_segs >= 0) k->lg_segs = (uint32_t)tune.lg_segs;
     k->split_budget = tune.split < 0 ? kDefaultSplitBudget
                       : (tune.split == 0 ? 0xffffffffu : (uint32_t)tune.split);
-    k->round_visits = tune.round > 0 ? (uint32_t)tune.round : kDefaultRoundVisits;
   } else {
     k->perm_M = 1;
     k->perm_Q = n;
@@ -173,26 +167,17 @@ int make_consts(const rmp_params_t* p, double vs, uint32_t n, bool scan, EvalCon
   return RMP_OK;
 }
 
-// Enqueue one single-state evaluation: the persistent kernel (lanes take rays from a
-// counter) where the launch policy picks it, else the one-wave kernel with the launch shape
-// of the ray count.  k comes from make_consts; state_dev null: the state is in k.x0.
+// Enqueue one single-state evaluation with the launch shape of the ray count and the
+// context's knobs.  k comes from make_consts; state_dev null: the state is in k.x0.
 cudaError_t launch_single(const MapRec& mr, const Tuning& t, EvalConsts k,
                           const double* state_dev, void* ws, rmp_result_t* out,
                           rmp_ray_hit_t* hits, float* per_ray, cudaStream_t s) {
   DevMap dm = mr.dm;
-  if (use_persistent(t, k.n_rays)) {
-    k.lg_segs = 0;
-    single_state_cells(t.cells, k, &dm);
-    const int grid = mr.persist_grid[k.reduce_mode][dm.cells ? 1 : 0];
-    if (grid > 0)
-      return launch_persist(dm, k, state_dev, ws, out, hits, per_ray, grid, s);
-    dm = mr.dm;                        // no occupancy figure: the one-wave kernel instead
-    k.lg_segs = 0;
-  }
-  auto_segments(t, k.n_rays, mr.wave256[k.reduce_mode], &k);
+  const uint64_t wave = mr.wave256[k.reduce_mode];
+  auto_segments(t, k.n_rays, wave, &k);
   single_state_cells(t.cells, k, &dm);
   int block, grid;
-  launch_shape(t, (uint64_t)k.n_rays << k.lg_segs, mr.wave256[k.reduce_mode], &block, &grid);
+  launch_shape(t, (uint64_t)k.n_rays << k.lg_segs, wave, &block, &grid);
   return launch_raycast(dm, k, state_dev, ws, out, hits, per_ray, block, grid, s);
 }
 
@@ -473,10 +458,6 @@ int rmp_map_upload(rmp_ctx* c, const rmp_map_desc_t* d, rmp_stream_t stream, uin
   for (int red = 0; red < 2; ++red) {
     const int occ = raycast_occupancy(r.dm, red, 256);
     r.wave256[red] = occ > 0 ? (uint64_t)c->sm_count * (uint64_t)occ * 256u : 0;
-    for (int cells = 0; cells < 2; ++cells) {
-      const int po = persist_occupancy(r.dm, red, cells != 0);
-      r.persist_grid[red][cells] = po > 0 ? c->sm_count * po : 0;
-    }
   }
   std::lock_guard<std::mutex> lk(c->mu);
   const uint32_t id = c->next_id++;
@@ -551,12 +532,6 @@ int rmp_tune_set(rmp_ctx* c, int knob, int value) {
   } else if (knob == RMP_TUNE_CELL_SKIP) {
     if (value < -1 || value > 1) return RMP_ERR_INVALID_ARG;
     c->tune_cells = value;
-  } else if (knob == RMP_TUNE_PERSISTENT) {
-    if (value < -1 || value > 1) return RMP_ERR_INVALID_ARG;
-    c->tune_persist = value;
-  } else if (knob == RMP_TUNE_ROUND_VISITS) {
-    if (value < 0 || value > 64) return RMP_ERR_INVALID_ARG;
-    c->tune_round = value;
   } else {
     return RMP_ERR_INVALID_ARG;
   }
@@ -577,25 +552,14 @@ int rmp_eval_launch_info(rmp_ctx* c, uint32_t map_id, uint32_t n_rays, const rmp
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   std::memset(out, 0, sizeof(*out));
-  if (use_persistent(t, n_rays)) {
-    DevMap dmc = dm;
-    k.lg_segs = 0;
-    single_state_cells(t.cells, k, &dmc);
-    out->block = 256;
-    out->grid = it->second.persist_grid[k.reduce_mode][dmc.cells ? 1 : 0];
-    out->lg_segments = 0;
-    out->ctas_per_sm = persist_occupancy(dm, k.reduce_mode, dmc.cells != nullptr);
-    out->persistent = 1;
-  } else {
-    auto_segments(t, n_rays, it->second.wave256[k.reduce_mode], &k);
-    int block, grid;
-    launch_shape(t, (uint64_t)n_rays << k.lg_segs, it->second.wave256[k.reduce_mode], &block,
-                 &grid);
-    out->block = block;
-    out->grid = grid;
-    out->lg_segments = (int)k.lg_segs;
-    out->ctas_per_sm = raycast_occupancy(dm, k.reduce_mode, block);
-  }
+  const uint64_t wave = it->second.wave256[k.reduce_mode];
+  auto_segments(t, n_rays, wave, &k);
+  int block, grid;
+  launch_shape(t, (uint64_t)n_rays << k.lg_segs, wave, &block, &grid);
+  out->block = block;
+  out->grid = grid;
+  out->lg_segments = (int)k.lg_segs;
+  out->ctas_per_sm = raycast_occupancy(dm, k.reduce_mode, block);
   out->sm_count = c->sm_count;
   out->smem_bytes = (int)raycast_smem_bytes(dm);
   out->ray_cells = (int)k.perm_M;
@@ -610,8 +574,6 @@ int rmp_tune_get(rmp_ctx* c, int knob, int* value) {
   else if (knob == RMP_TUNE_RAY_ORDER) *value = c->tune_ray_order;
   else if (knob == RMP_TUNE_SPLIT_BUDGET) *value = c->tune_split;
   else if (knob == RMP_TUNE_CELL_SKIP) *value = c->tune_cells;
-  else if (knob == RMP_TUNE_PERSISTENT) *value = c->tune_persist;
-  else if (knob == RMP_TUNE_ROUND_VISITS) *value = c->tune_round;
   else return RMP_ERR_INVALID_ARG;
   return RMP_OK;
 }

@@ -83,7 +83,6 @@ struct EvalConsts {
   double att_alpha, att_beta;        // attractor gain and damping (combined evaluations)
   int att_mean;                      // combined: ray sums divided by the ray count first
   uint32_t seg_threads;              // batches: threads of the persistent launch (segments)
-  uint32_t round_visits;             // persistent single state: block visits per round
   double x0[6];                      // x, xdot carried in the launch itself, read when the
                                      // kernel's state pointer is null (synchronous calls)
 };
@@ -114,63 +113,11 @@ struct CtaPartial {         // 80 bytes per CTA (and per group)
   unsigned int n_hits, n_active;
 };
 
-// ------------------------------------------------------------------ persistent evaluation
-// One state's rays taken by the lanes of a persistent grid from a counter (see
-// raycast_persist_kernel).  A finished ray stores its 9 policy terms and flags in a record
-// indexed by its slot; the lane that finishes the last ray of a chunk of kPersistChunk
-// slots sums the chunk, and chunk / group / grid tickets complete the sum in a fixed order.
-constexpr uint32_t kPersistMaxRays = 1u << 19;          // larger evaluations: one-wave kernel
-constexpr uint32_t kPersistChunk = 32;                  // slots per chunk partial
-constexpr uint32_t kPersistGroup = 32;                  // chunks per group partial
-constexpr uint32_t kPersistMaxChunks = kPersistMaxRays / kPersistChunk;
-constexpr uint32_t kPersistMaxGroups = kPersistMaxChunks / kPersistGroup;
-constexpr uint32_t kDefaultRoundVisits = 4;             // block visits per lane between fetches
-
-struct PersistHeader {      // 128 bytes
-  uint32_t next_slot;       // work counter (slots handed out)
-  uint32_t warps_exited;    // the last warp to leave resets next_slot and this
-  uint32_t ticket;          // groups completed
-  uint32_t pad[29];
-};
-
-struct RayRec {             // 40 bytes: sum terms of one finished ray
-  float v[9];               // A_i (6), A_i f_i (3)
-  uint32_t flags;           // bit 0 hit, bit 1 active
-};
-
-struct PersistWs {
-  PersistHeader* hdr;
-  uint32_t* gticket;        // per group: chunks completed
-  uint32_t* ccount;         // per chunk: rays completed
-  CtaPartial* cparts;
-  CtaPartial* gparts;
-  RayRec* recs;
-};
-
-inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// The one-wave kernel's area (tickets, CTA and group partials), then the persistent one.
-inline size_t wave_ws_bytes() {
+inline size_t workspace_bytes() {
   return kWsHeaderBytes + sizeof(CtaPartial) * (size_t)(kMaxGrid + kMaxGroups);
 }
 
-struct PersistLayout {
-  size_t hdr, gticket, ccount, cparts, gparts, recs, total;
-};
-
-inline PersistLayout persist_layout() {
-  PersistLayout L;
-  L.hdr = align256(wave_ws_bytes());
-  L.gticket = align256(L.hdr + sizeof(PersistHeader));
-  L.ccount = align256(L.gticket + 4 * (size_t)kPersistMaxGroups);
-  L.cparts = align256(L.ccount + 4 * (size_t)kPersistMaxChunks);
-  L.gparts = align256(L.cparts + sizeof(CtaPartial) * (size_t)kPersistMaxChunks);
-  L.recs = align256(L.gparts + sizeof(CtaPartial) * (size_t)kPersistMaxGroups);
-  L.total = align256(L.recs + sizeof(RayRec) * (size_t)kPersistMaxRays);
-  return L;
-}
-
-inline size_t workspace_bytes() { return persist_layout().total; }
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // ------------------------------------------------------------------ batched evaluation
 // Work of a batch is cut into chunks of 32 threads (32 / S rays of one state, S segments
@@ -229,11 +176,7 @@ int raycast_occupancy(const DevMap& m, int reduce_mode, int block);   // CTAs pe
 cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,
                            void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
                            float* per_ray, int block, int grid, cudaStream_t stream);
-// Persistent single-state evaluation (k.lg_segs must be 0; n_rays <= kPersistMaxRays).
-int persist_occupancy(const DevMap& m, int reduce_mode, bool cells);   // CTAs per SM
-cudaError_t launch_persist(const DevMap& m, const EvalConsts& k, const double* state_dev,
-                           void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
-                           float* per_ray, int grid, cudaStream_t stream);
+
 int ctx_device(const rmp_ctx* ctx);                                  // CUDA device of a context
 int batch_occupancy(const DevMap& m, int reduce_mode, int block);     // CTAs per SM
 // Prep kernel + persistent batch kernel; n_rays_dev / states_dev on the device.  With

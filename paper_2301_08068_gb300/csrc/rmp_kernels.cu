@@ -1091,11 +1091,14 @@ __device__ void sum_partials(const CtaPartial* p, int count, double* tot, unsign
 }
 
 // Grid completion, deterministic and without one thread walking every CTA: lanes 0-10 of
-// warp 0 store the CTA's sums as its partial; the last CTA of each group of kGroup CTAs
-// (group ticket) sums the group's partials in index order and stores a group partial; the
-// last group to finish (grid ticket) sums the group partials in index order in FP64 and
-// resolves.  A grid of one CTA resolves its own sums.  Tickets are reset by the CTA that
-// completes them.  Called by all threads of every CTA after BlockReduce::reduce.
+// warp 0 store the CTA's sums as its partial.  Up to blockDim CTAs, the last CTA to
+// finish (grid ticket) sums every partial (sum_partials: blockDim / 16 threads per term,
+// fixed order) and resolves; larger grids add a level: the last CTA of each group of kGroup CTAs
+// (group ticket) sums the group's partials into a group partial, and the last group sums
+// those.  (Each level costs a fence, a ticket and a load of partials, about 1.5 us on this
+// GPU, while one CTA sums 256 partials in well under that.)  A grid of one CTA resolves its
+// own sums.  Tickets are reset by the CTA that completes them.  Called by all threads of
+// every CTA after BlockReduce::reduce.
 __device__ void grid_finish(const CtaSums& cta, WsHeader* ws, CtaPartial* parts,
                             rmp_result_t* out, uint32_t n_rays, int status) {
   __shared__ int stage;
@@ -1103,10 +1106,11 @@ __device__ void grid_finish(const CtaSums& cta, WsHeader* ws, CtaPartial* parts,
   __shared__ unsigned tot_h, tot_a;
   CtaPartial* groups = parts + kMaxGrid;
   const int G = gridDim.x;
-  const int gi = blockIdx.x / kGroup;
-  const int n_groups = (G + kGroup - 1) / kGroup;
+  const bool one_level = G <= (int)blockDim.x;   // each summing thread adds <= 16 partials
+  const int gi = one_level ? 0 : blockIdx.x / kGroup;
+  const int n_groups = one_level ? 1 : (G + kGroup - 1) / kGroup;
   const int g0 = gi * kGroup;
-  const int gsz = min(kGroup, G - g0);
+  const int gsz = one_level ? G : min(kGroup, G - g0);
   if (G == 1) {
     if (threadIdx.x < 9) tot[threadIdx.x] = cta.v[threadIdx.x];
     else if (threadIdx.x == 9) tot_h = cta.u[0];
@@ -1129,7 +1133,7 @@ __device__ void grid_finish(const CtaSums& cta, WsHeader* ws, CtaPartial* parts,
     __syncthreads();
     if (stage == 0) return;
     __threadfence();
-    sum_partials(parts + g0, gsz, tot, &tot_h, &tot_a);
+    sum_partials(parts + (one_level ? 0 : g0), gsz, tot, &tot_h, &tot_a);
     if (n_groups > 1) {
       if (threadIdx.x == 0) {
         CtaPartial p;
@@ -1405,6 +1409,12 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
   __syncthreads();
   const bool bad = (cs.bad[0] | cs.bad[1] | cs.bad[2] | bm_timeout) != 0;
   bool first = true;
+  // this lane's column of its warp's staged brick words, after the radius field: one
+  // shared load per voxel test instead of a select tree over 16 registers (measured, 65536
+  // rays on the hashed map: 68.8 -> 65.8 us)
+  uint32_t* sbr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem_radius) +
+                                              (staged ? bm_bytes : 0u)) +
+                  (threadIdx.x >> 5) * (kSmemBrickBytes / 4) + (threadIdx.x & 31);
   // warp-uniform trip count: every lane takes part in each ballot / shuffle
   for (; base < total; base += stride) {
     const uint32_t g = base + lane;
@@ -1417,7 +1427,8 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
     first = false;
     const long long P[3] = {cs.P[0], cs.P[1], cs.P[2]};
     MarchState mo;
-    const int mstat = march_ray<KIND, LAYOUT, CELLS>(m, bm, k, P, ray, seg, lgS, active && !bad, mo);
+    const int mstat = march_ray<KIND, LAYOUT, CELLS, true>(m, bm, k, P, ray, seg, lgS,
+                                                           active && !bad, mo, sbr);
     if (!active || bad || seg != 0) continue;
     float vals[9];
     ray_outputs(m, k, P, ray, mo, mstat, cs.v, cs.vl, hits ? hits + ray_idx : nullptr,
@@ -1937,244 +1948,6 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
   if (staged && bm_timeout && threadIdx.x == 0) bulk_load_wait(&bm_bar);   // let a late copy land
 }
 
-// ------------------------------------------------------------------ persistent single state
-constexpr int kFetchMinIdle = 1;   // idle lanes a warp waits for before it asks for new rays
-// Sum of chunk c's ray records into its chunk partial, then the group and grid tickets: the
-// last chunk of a group sums the group (lane i: chunk i), the last group sums the groups
-// (lane j: groups j, j + 32, ...) and resolves Eq. (1).  Every sum runs in a fixed order, so
-// the result does not depend on which warp finished which ray.  Called by a whole warp.
-template <int RED>
-__device__ void persist_finish_chunk(uint32_t c, uint32_t n, const PersistWs& w,
-                                     rmp_result_t* out) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t n_chunks = (n + kPersistChunk - 1) / kPersistChunk;
-  const uint32_t csz = min(kPersistChunk, n - c * kPersistChunk);
-  __threadfence();
-  float vals[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  unsigned nh = 0, na = 0;
-  if (lane < csz) {
-    const RayRec* rr = w.recs + (size_t)c * kPersistChunk + lane;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) vals[q] = __ldcg(&rr->v[q]);
-    const uint32_t fl = __ldcg(&rr->flags);
-    nh = fl & 1u;
-    na = (fl >> 1) & 1u;
-  }
-  if (lane == 0) w.ccount[c] = 0;                 // ready for the next evaluation
-  double pv[9];
-  if (RED == RMP_REDUCE_FP64) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) pv[i] = (double)vals[i];
-    warp_sum_partial(pv, nh, na);
-  } else {
-    Acc32 acc;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      acc.s[i] = vals[i];
-      acc.c[i] = 0.0f;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const float s2 = __shfl_down_sync(0xffffffffu, acc.s[i], off);
-        const float c2 = __shfl_down_sync(0xffffffffu, acc.c[i], off);
-        acc_merge(acc, s2, c2, i);
-      }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) pv[i] = (double)acc.s[i] + (double)acc.c[i];
-    nh = __reduce_add_sync(0xffffffffu, nh);
-    na = __reduce_add_sync(0xffffffffu, na);
-  }
-  const uint32_t gi = c / kPersistGroup;
-  const uint32_t gsz = min(kPersistGroup, n_chunks - gi * kPersistGroup);
-  const uint32_t n_groups = (n_chunks + kPersistGroup - 1) / kPersistGroup;
-  uint32_t stage = 0;
-  if (lane == 0) {
-    CtaPartial p;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) p.v[i] = pv[i];
-    p.n_hits = nh;
-    p.n_active = na;
-    w.cparts[c] = p;
-    __threadfence();
-    stage = atomicAdd(&w.gticket[gi], 1u) == gsz - 1 ? 1u : 0u;
-  }
-  stage = __shfl_sync(0xffffffffu, stage, 0);
-  if (!stage) return;
-  __threadfence();
-  double gv[9] = {0., 0., 0., 0., 0., 0., 0., 0., 0.};
-  unsigned gh = 0, ga = 0;
-  if (lane < gsz) load_partial(w.cparts + gi * kPersistGroup + lane, gv, gh, ga);
-  warp_sum_partial(gv, gh, ga);
-  if (lane == 0) {
-    CtaPartial p;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) p.v[i] = gv[i];
-    p.n_hits = gh;
-    p.n_active = ga;
-    w.gparts[gi] = p;
-    w.gticket[gi] = 0;
-    __threadfence();
-    stage = atomicAdd(&w.hdr->ticket, 1u) == n_groups - 1 ? 2u : 0u;
-  }
-  stage = __shfl_sync(0xffffffffu, stage, 0);
-  if (stage != 2) return;
-  __threadfence();
-  double tv[9] = {0., 0., 0., 0., 0., 0., 0., 0., 0.};
-  unsigned th = 0, ta = 0;
-  for (uint32_t j = lane; j < n_groups; j += 32) {
-    double p2[9];
-    unsigned h2, a2;
-    load_partial(w.gparts + j, p2, h2, a2);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) tv[i] += p2[i];
-    th += h2;
-    ta += a2;
-  }
-  warp_sum_partial(tv, th, ta);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) tv[i] = __shfl_sync(0xffffffffu, tv[i], 0);
-  rmp_result_t r;
-  resolve_pinv(tv, tv + 6, r);
-  if (lane == 0) {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) r.A[i] = tv[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) r.Af[i] = tv[6 + i];
-    r.n_rays = n;
-    r.n_hits = th;
-    r.n_active = ta;
-    r.status = RMP_OK;
-    r.reserved = 0;
-    *out = r;
-    w.hdr->ticket = 0;
-  }
-}
-
-// Persistent single-state evaluation (a1-a6 in one launch, every CTA resident at once
-// being no requirement).  Every lane holds at most one ray: lanes without one take the
-// next ray slots from the work counter (one atomic per warp and round), so a lane never
-// waits for the slowest ray of its warp; each round marches every held ray by up to
-// k.round_visits block visits (march_run's budget, exactly resumable).  A finished ray's
-// obstacle policy goes to its slot's record; the lane that finishes the last ray of a chunk
-// of 32 slots starts the chunk's fixed-order sum (persist_finish_chunk).  No warp ever
-// waits for another.  The last warp to leave resets the work counter.
-template <int KIND, int LAYOUT, int RED, bool CELLS>
-__global__ void __launch_bounds__(256, 2) raycast_persist_kernel(
-    DevMap m, EvalConsts k, const double* __restrict__ state, PersistWs w, rmp_result_t* out,
-    rmp_ray_hit_t* hits, float* per_ray) {
-  extern __shared__ uint4 smem_radius[];
-  __shared__ CtaState cs;
-  __shared__ __align__(8) uint64_t bm_bar;
-  __shared__ int bm_timeout;
-  const uint32_t bm_bytes = m.radius_words * 4u;
-  const bool staged = LAYOUT == kLayoutGrid && bm_bytes <= kMaxSmemRadiusBytes;
-  if (threadIdx.x == 0) {
-    bm_timeout = 0;
-    if (staged) bulk_load_begin(&bm_bar, smem_radius, m.radius, bm_bytes);
-  }
-  if (threadIdx.x < 3) {
-    const int a = threadIdx.x;
-    const double o = KIND != RMP_MAP_DENSE_U8 ? 0.0
-                     : (a == 0 ? m.origin[0] : (a == 1 ? m.origin[1] : m.origin[2]));
-    const double q = __dmul_rn(__ddiv_rn(__dsub_rn(state_at(state, k, a), o), m.vs), 65536.0);
-    const int bad = !(fabs(q) < 274877906944.0);
-    cs.bad[a] = bad;
-    cs.P[a] = bad ? 0 : __double2ll_rn(q);
-  } else if (threadIdx.x < 6) {
-    split_velocity(state_at(state, k, threadIdx.x), cs, threadIdx.x - 3);
-  }
-  __syncthreads();
-  if (staged && threadIdx.x == 0 && !bulk_load_wait(&bm_bar)) bm_timeout = 1;
-  __syncthreads();
-  // a radius copy that did not land in time leaves the CTA on the global copy of the field
-  const uint32_t* bm = (staged && !bm_timeout) ? reinterpret_cast<const uint32_t*>(smem_radius)
-                                               : m.radius;
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t n = k.n_rays;
-  if (cs.bad[0] | cs.bad[1] | cs.bad[2]) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      rmp_result_t r;
-      memset(&r, 0, sizeof(r));
-      r.n_rays = n;
-      r.status = RMP_ERR_INVALID_ARG;
-      *out = r;
-    }
-  } else {
-    const long long P[3] = {cs.P[0], cs.P[1], cs.P[2]};
-    const float v[3] = {cs.v[0], cs.v[1], cs.v[2]};
-    const float vl[3] = {cs.vl[0], cs.vl[1], cs.vl[2]};
-    bool has = false, drained = false;
-    uint32_t slot = 0, ri = 0;
-    Ray ray;
-    RayFx r;
-    uint32_t L[3];
-    MarchState st;
-    for (;;) {
-      // idle lanes take the next slots (consecutive, so a warp starts on one direction
-      // cell); once the counter has run past n the warp stops asking, which bounds the
-      // counter by n + 32 per warp
-      const uint32_t idle = __ballot_sync(0xffffffffu, !has);
-      if (idle && !drained && (__popc(idle) >= kFetchMinIdle || idle == 0xffffffffu)) {
-        const int leader = __ffs(idle) - 1;
-        uint32_t base = 0;
-        if ((int)lane == leader) base = atomicAdd(&w.hdr->next_slot, (uint32_t)__popc(idle));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        drained = base + (uint32_t)__popc(idle) >= n;
-        if (!has) {
-          const uint32_t my = base + (uint32_t)__popc(idle & ((1u << lane) - 1u));
-          if (my < n) {
-            has = true;
-            slot = my;
-            ri = ray_of_slot(my, k);
-            ray = make_ray(ri + k.halton_offset);
-            ray_fx(P, ray.D, r);
-            state_at(r, k.R_fx, 0, st);
-            limits_at(r, k.R_fx, 1u << kGridLog, L);
-          }
-        }
-      }
-      if (!__any_sync(0xffffffffu, has)) break;
-      bool own_chunk = false;
-      if (has) {
-        const int status = march_run<KIND, LAYOUT, CELLS>(m, bm, st, r, L, RMP_RAY_MISS_RANGE,
-                                                          k.round_visits);
-        if (status != kBudgetOut) {
-          float vals[9];
-          unsigned nh = 0, na = 0;
-          ray_outputs(m, k, P, ray, st, status, v, vl, hits ? hits + ri : nullptr,
-                      per_ray ? per_ray + 9 * (size_t)ri : nullptr, vals, nh, na);
-          RayRec* rec = w.recs + slot;
-#pragma unroll
-          for (int q = 0; q < 9; ++q) rec->v[q] = vals[q];
-          rec->flags = nh | (na << 1);
-          __threadfence();
-          const uint32_t c = slot / kPersistChunk;
-          const uint32_t csz = min(kPersistChunk, n - c * kPersistChunk);
-          own_chunk = atomicAdd(&w.ccount[c], 1u) == csz - 1;
-          has = false;
-        }
-      }
-      uint32_t owners = __ballot_sync(0xffffffffu, own_chunk);
-      while (owners) {
-        const int src = __ffs(owners) - 1;
-        owners &= owners - 1;
-        const uint32_t c = __shfl_sync(0xffffffffu, slot, src) / kPersistChunk;
-        persist_finish_chunk<RED>(c, n, w, out);
-      }
-    }
-  }
-  if (staged && bm_timeout && threadIdx.x == 0) bulk_load_wait(&bm_bar);   // let a late copy land
-  if (lane == 0) {
-    const uint32_t total_warps = gridDim.x * (blockDim.x >> 5);
-    if (atomicAdd(&w.hdr->warps_exited, 1u) == total_warps - 1) {
-      w.hdr->next_slot = 0;
-      w.hdr->warps_exited = 0;
-    }
-  }
-}
-
 // ------------------------------------------------------------------ LiDAR scan kernel (Sec. III-G)
 template <int RED>
 __global__ void __launch_bounds__(256) scan_rmp_kernel(const float* __restrict__ pts,
@@ -2494,15 +2267,19 @@ __global__ void hash_build_kernel(const int32_t* __restrict__ keys, uint32_t n_b
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-size_t raycast_smem_bytes(const DevMap& m) {
+// The staged radius field (a multiple of 16 bytes) where it fits in shared memory.
+static size_t radius_smem_bytes(const DevMap& m) {
   const uint32_t bytes = m.radius_words * 4u;
   if (m.layout == kLayoutGrid && bytes <= kMaxSmemRadiusBytes) return bytes;
   return 0;
 }
 
-// Batch kernel: the radius field (a multiple of 16 bytes), then 16 x 32 brick words per warp.
+// Single-state kernel: the radius field, then 16 x 32 brick words for each of up to 8 warps.
+size_t raycast_smem_bytes(const DevMap& m) { return radius_smem_bytes(m) + 8 * kSmemBrickBytes; }
+
+// Batch kernel: the radius field, then 16 x 32 brick words per warp of the block.
 size_t batch_smem_bytes(const DevMap& m, int block) {
-  return raycast_smem_bytes(m) + (size_t)(block / 32) * kSmemBrickBytes;
+  return radius_smem_bytes(m) + (size_t)(block / 32) * kSmemBrickBytes;
 }
 
 // The kernels keep up to 48 KB of the map's radius field in shared memory: ask for the
@@ -2539,8 +2316,6 @@ static void launch_raycast_c(const DevMap& m, const EvalConsts& k, const double*
   }
 }
 
-// The voxel-box path is compiled in only where it is used (grid layouts with cell
-// distances): without it the single-state march keeps its shorter code.
 template <int KIND, int LAYOUT>
 static void launch_raycast_t(const DevMap& m, const EvalConsts& k, const double* state_dev,
                              WsHeader* hdr, CtaPartial* parts, rmp_result_t* out_dev,
@@ -2588,94 +2363,6 @@ cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* s
   else
     launch_raycast_t<RMP_MAP_HASHED_TSDF, kLayoutHash>(m, k, state_dev, hdr, parts, out_dev, hits,
                                                        per_ray, block, grid, smem, stream);
-  return cudaGetLastError();
-}
-
-template <int KIND, int LAYOUT, int RED, bool CELLS>
-static int persist_occupancy_t(size_t smem) {
-  int n = 0;
-  prefer_shared<raycast_persist_kernel<KIND, LAYOUT, RED, CELLS>>();
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-             &n, raycast_persist_kernel<KIND, LAYOUT, RED, CELLS>, 256, smem) == cudaSuccess ? n : -1;
-}
-
-template <int KIND, int LAYOUT, int RED>
-static int persist_occupancy_c(const DevMap& m, bool cells, size_t smem) {
-  if (LAYOUT == kLayoutGrid && cells && m.cells)
-    return persist_occupancy_t<KIND, LAYOUT, RED, LAYOUT == kLayoutGrid>(smem);
-  return persist_occupancy_t<KIND, LAYOUT, RED, false>(smem);
-}
-
-int persist_occupancy(const DevMap& m, int reduce_mode, bool cells) {
-  const size_t smem = raycast_smem_bytes(m);
-  if (m.kind == RMP_MAP_DENSE_U8)
-    return reduce_mode ? persist_occupancy_c<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_FP64>(m, cells, smem)
-                       : persist_occupancy_c<RMP_MAP_DENSE_U8, kLayoutGrid, RMP_REDUCE_KAHAN32>(m, cells, smem);
-  if (m.layout == kLayoutGrid)
-    return reduce_mode ? persist_occupancy_c<RMP_MAP_HASHED_TSDF, kLayoutGrid, RMP_REDUCE_FP64>(m, cells, smem)
-                       : persist_occupancy_c<RMP_MAP_HASHED_TSDF, kLayoutGrid, RMP_REDUCE_KAHAN32>(m, cells, smem);
-  return reduce_mode ? persist_occupancy_c<RMP_MAP_HASHED_TSDF, kLayoutHash, RMP_REDUCE_FP64>(m, cells, smem)
-                     : persist_occupancy_c<RMP_MAP_HASHED_TSDF, kLayoutHash, RMP_REDUCE_KAHAN32>(m, cells, smem);
-}
-
-template <int KIND, int LAYOUT, int RED, bool CELLS>
-static void launch_persist_t(const DevMap& m, const EvalConsts& k, const double* state_dev,
-                             const PersistWs& w, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
-                             float* per_ray, int grid, size_t smem, cudaStream_t stream) {
-  prefer_shared<raycast_persist_kernel<KIND, LAYOUT, RED, CELLS>>();
-  raycast_persist_kernel<KIND, LAYOUT, RED, CELLS><<<grid, 256, smem, stream>>>(
-      m, k, state_dev, w, out_dev, hits, per_ray);
-}
-
-template <int KIND, int LAYOUT, int RED>
-static void launch_persist_c(const DevMap& m, const EvalConsts& k, const double* state_dev,
-                             const PersistWs& w, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
-                             float* per_ray, int grid, size_t smem, cudaStream_t stream) {
-  if (LAYOUT == kLayoutGrid && m.cells)
-    launch_persist_t<KIND, LAYOUT, RED, LAYOUT == kLayoutGrid>(m, k, state_dev, w, out_dev, hits,
-                                                               per_ray, grid, smem, stream);
-  else
-    launch_persist_t<KIND, LAYOUT, RED, false>(m, k, state_dev, w, out_dev, hits, per_ray, grid,
-                                               smem, stream);
-}
-
-template <int KIND, int LAYOUT>
-static void launch_persist_r(const DevMap& m, const EvalConsts& k, const double* state_dev,
-                             const PersistWs& w, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
-                             float* per_ray, int grid, size_t smem, cudaStream_t stream) {
-  if (k.reduce_mode == RMP_REDUCE_FP64)
-    launch_persist_c<KIND, LAYOUT, RMP_REDUCE_FP64>(m, k, state_dev, w, out_dev, hits, per_ray,
-                                                    grid, smem, stream);
-  else
-    launch_persist_c<KIND, LAYOUT, RMP_REDUCE_KAHAN32>(m, k, state_dev, w, out_dev, hits, per_ray,
-                                                       grid, smem, stream);
-}
-
-cudaError_t launch_persist(const DevMap& m, const EvalConsts& k, const double* state_dev,
-                           void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
-                           float* per_ray, int grid, cudaStream_t stream) {
-  if (k.lg_segs != 0 || k.n_rays == 0 || k.n_rays > kPersistMaxRays || k.round_visits == 0 ||
-      grid < 1)
-    return cudaErrorInvalidValue;
-  const PersistLayout L = persist_layout();
-  char* b = (char*)ws;
-  PersistWs w;
-  w.hdr = (PersistHeader*)(b + L.hdr);
-  w.gticket = (uint32_t*)(b + L.gticket);
-  w.ccount = (uint32_t*)(b + L.ccount);
-  w.cparts = (CtaPartial*)(b + L.cparts);
-  w.gparts = (CtaPartial*)(b + L.gparts);
-  w.recs = (RayRec*)(b + L.recs);
-  const size_t smem = raycast_smem_bytes(m);
-  if (m.kind == RMP_MAP_DENSE_U8)
-    launch_persist_r<RMP_MAP_DENSE_U8, kLayoutGrid>(m, k, state_dev, w, out_dev, hits, per_ray,
-                                                    grid, smem, stream);
-  else if (m.layout == kLayoutGrid)
-    launch_persist_r<RMP_MAP_HASHED_TSDF, kLayoutGrid>(m, k, state_dev, w, out_dev, hits, per_ray,
-                                                       grid, smem, stream);
-  else
-    launch_persist_r<RMP_MAP_HASHED_TSDF, kLayoutHash>(m, k, state_dev, w, out_dev, hits, per_ray,
-                                                       grid, smem, stream);
   return cudaGetLastError();
 }
 

@@ -14,19 +14,9 @@ namespace rmp {
 
 // Launch knobs of a context (rmp_tune_set): -1 / 0 select the library's choice.
 struct Tuning {
-  // log2 segments per ray, ray order, split budget, threads per CTA, voxel boxes,
-  // persistent single-state kernel, block visits per persistent round
-  int lg_segs = -1, ray_order = 0, split = -1, block = 0, cells = -1, persist = -1, round = 0;
+  // log2 segments per ray, ray order, split budget, threads per CTA, voxel boxes
+  int lg_segs = -1, ray_order = 0, split = -1, block = 0, cells = -1;
 };
-
-// Persistent single-state kernel (lanes take rays from a counter, so no lane waits for the
-// slowest ray of its own warp before taking the next): only when tuned on.  Measured on a
-// hashed 40 x 40 x 10 m map it is slower than the one-wave kernel at every count (65536
-// rays 78 against 68 us): with about one ray per resident lane there is nothing to move
-// between lanes, and the long rays, not the lanes that finish early, set the time.
-inline bool use_persistent(const Tuning& t, uint32_t n) {
-  return t.persist == 1 && n >= 1 && n <= kPersistMaxRays;
-}
 
 // Coherent ray order: residue classes modulo M = 2^a 3^b are direction cells (see the
 // kernel's ray_of_slot).  Cells hold >= 32 rays so a warp spans at most two of them, about

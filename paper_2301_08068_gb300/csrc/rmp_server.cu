@@ -11,8 +11,10 @@
 // and completes its requests, which frees room for the requests that arrived meanwhile.
 // A request whose batch alone would exceed the budget is completed with
 // RMP_ERR_NO_MEMORY; a CUDA error completes the batch's requests with RMP_ERR_CUDA.
-// The worker sleeps while batches are in flight: a host function enqueued after each
-// batch marks its slot done and wakes the worker (no polling of the GPU from the host).
+// The worker sleeps whenever it can launch nothing: a host function enqueued after each
+// batch marks its slot done and wakes it, as do submissions (no polling of the GPU from the
+// host).  The wake-up has its own mutex and condition variable, so the host function never
+// takes the server lock.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -95,13 +97,17 @@ using namespace rmp;
 
 struct rmp_server {
   rmp_ctx* ctx = nullptr;
-  std::atomic<uint32_t> completions{0};   // host functions run since the worker last looked
+  // wake-up of the worker: bumped by every event it waits for (a batch's host function, a
+  // submission, stop); the worker sleeps until it changes
+  std::atomic<uint64_t> wake{0};
+  std::mutex wake_mu;
+  std::condition_variable wake_cv;
   int device = 0;
   rmp_server_config_t cfg;
   char* arena_dev = nullptr;
   Arena* arena = nullptr;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_done;
   std::deque<Request> pending;
   std::unordered_map<uint64_t, Finished> finished;
   std::unordered_set<uint64_t> outstanding;      // issued tickets not yet collected
@@ -141,17 +147,18 @@ void complete_now(rmp_server* s, const Request& r, int status) {
   s->cv_done.notify_all();
 }
 
+void wake_worker(rmp_server* s) {
+  s->wake.fetch_add(1, std::memory_order_acq_rel);
+  { std::lock_guard<std::mutex> lk(s->wake_mu); }   // orders the bump with the worker's wait
+  s->wake_cv.notify_all();
+}
+
 // Host function enqueued after a batch's result copy: marks the slot finished and wakes the
-// worker.  It takes the server lock only to order the flag with the worker's wait (the
-// worker never waits on a stream while holding the lock after a host function has been
-// enqueued on it), and calls no CUDA function.
+// worker.  It calls no CUDA function and takes only the wake-up mutex.
 void CUDART_CB batch_done(void* arg) {
   Slot* sl = static_cast<Slot*>(arg);
-  rmp_server* s = sl->owner;
   sl->finished.store(true, std::memory_order_release);
-  s->completions.fetch_add(1, std::memory_order_release);
-  { std::lock_guard<std::mutex> lk(s->mu); }
-  s->cv_work.notify_all();
+  wake_worker(sl->owner);
 }
 
 // Form and launch one batch on free slot `sl` from the pending queue.  Returns false if
@@ -249,9 +256,9 @@ void worker_main(rmp_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
+    const uint64_t seen = s->wake.load(std::memory_order_acquire);
     bool progress = false;
     bool busy = false;
-    s->completions.store(0, std::memory_order_relaxed);
     for (Slot& sl : s->slots) {
       if (!sl.busy) continue;
       if (!sl.finished.load(std::memory_order_acquire)) {
@@ -278,13 +285,19 @@ void worker_main(rmp_server* s) {
     for (const Slot& sl : s->slots) busy = busy || sl.busy;
     if (s->stop && s->pending.empty() && !busy) break;
     if (progress) continue;
-    // sleep until a request arrives or a batch's host function runs; the timed wait is a
-    // backstop only (a host function that never ran would otherwise stall the server)
-    s->cv_work.wait_for(lk, std::chrono::milliseconds(50), [s] {
-      return s->stop || s->completions.load(std::memory_order_acquire) != 0 ||
-             !s->pending.empty();
-    });
-    if (s->completions.load(std::memory_order_acquire) == 0 && s->pending.empty() && !s->stop) {
+    // nothing to launch or reap: sleep, without the server lock, until a batch's host
+    // function, a submission or stop bumps the wake-up count; the timed wait is a backstop
+    // only (a host function that never ran would otherwise stall the server)
+    lk.unlock();
+    bool woken;
+    {
+      std::unique_lock<std::mutex> wl(s->wake_mu);
+      woken = s->wake_cv.wait_for(wl, std::chrono::milliseconds(50), [s, seen] {
+        return s->wake.load(std::memory_order_acquire) != seen;
+      });
+    }
+    lk.lock();
+    if (!woken) {
       for (Slot& sl : s->slots)                    // backstop: look at the events directly
         if (sl.busy && cudaEventQuery(sl.done) == cudaSuccess)
           sl.finished.store(true, std::memory_order_release);
@@ -368,7 +381,7 @@ int rmp_server_destroy(rmp_server* s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
   }
-  s->cv_work.notify_all();
+  wake_worker(s);
   if (s->worker.joinable()) s->worker.join();     // drains pending and in-flight work
   cudaSetDevice(s->device);
   for (Slot& sl : s->slots) {
@@ -405,7 +418,7 @@ int rmp_server_submit(rmp_server* s, uint32_t map_id, const double x[3], const d
     s->outstanding.insert(r.id);
     s->stats.submitted += 1;
   }
-  s->cv_work.notify_one();
+  wake_worker(s);
   *ticket = r.id;
   return RMP_OK;
 }

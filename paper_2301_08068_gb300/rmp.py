@@ -31,7 +31,6 @@ RMP_PRESET_STATIC_MAP, RMP_PRESET_LIDAR = 0, 1
 RMP_REDUCE_KAHAN32, RMP_REDUCE_FP64 = 0, 1
 RMP_TUNE_BLOCK, RMP_TUNE_LG_SEGMENTS, RMP_TUNE_RAY_ORDER, RMP_TUNE_SPLIT_BUDGET = 1, 2, 3, 4
 RMP_TUNE_CELL_SKIP = 5
-RMP_TUNE_PERSISTENT, RMP_TUNE_ROUND_VISITS = 6, 7
 
 
 class RmpError(RuntimeError):
@@ -66,7 +65,7 @@ class rmp_map_desc_t(C.Structure):
 
 class rmp_launch_info_t(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("block", "grid", "lg_segments", "ctas_per_sm", "sm_count",
-                                         "smem_bytes", "ray_cells", "persistent")]
+                                         "smem_bytes", "ray_cells", "reserved")]
 
 
 class rmp_rollout_params_t(C.Structure):
@@ -454,7 +453,7 @@ def rmp_eval_launch_info(ctx: int, map_id: int, n_rays: int, params: rmp_params_
     info = rmp_launch_info_t()
     _check(lib().rmp_eval_launch_info(ctx, int(map_id), int(n_rays), C.byref(params), C.byref(info)),
            "rmp_eval_launch_info")
-    return {n: getattr(info, n) for n, _ in rmp_launch_info_t._fields_}
+    return {n: getattr(info, n) for n, _ in rmp_launch_info_t._fields_ if n != "reserved"}
 
 
 def rmp_tune_get(ctx: int, knob: int) -> int:

@@ -5,7 +5,6 @@
 //   shape TUNE T WAVE   -> BLOCK GRID      (single-state launch of T threads)
 //   scan TUNE SMS N     -> BLOCK GRID      (scan launch of N points)
 //   cells TUNE LG       -> 1 if the voxel boxes stay on
-//   persist TUNE N      -> 1 if the persistent single-state kernel runs N rays
 #include <cstdio>
 #include <cstring>
 
@@ -57,12 +56,6 @@ int main() {
       k.lg_segs = lg;
       rmp::single_state_cells(tune, k, &m);
       std::printf("%d\n", m.cells != nullptr ? 1 : 0);
-    } else if (!std::strcmp(op, "persist")) {
-      int tune;
-      unsigned n;
-      if (std::scanf("%d %u", &tune, &n) != 2) return 2;
-      t.persist = tune;
-      std::printf("%d\n", rmp::use_persistent(t, n) ? 1 : 0);
     } else {
       return 2;
     }

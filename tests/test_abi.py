@@ -132,21 +132,7 @@ def test_status_strings(rmp):
 
 
 def test_workspace_size_is_fixed(rmp):
-    """The one-wave kernel's area (1 KB of tickets, one 80-byte partial per CTA and per
-    group of 32 CTAs), then the persistent kernel's, each region 256-byte aligned: 128-byte
-    header, group tickets and chunk counters (4 bytes each), chunk and group partials (80
-    bytes) and one 40-byte record per ray, sized for 2^19 rays in chunks of 32 and groups
-    of 32 chunks."""
-    a = lambda x: (x + 255) // 256 * 256
-    chunks, groups = (1 << 19) // 32, (1 << 19) // 1024
-    off = a(1024 + 80 * (4096 + 128))
-    off = a(off + 128)
-    off = a(off + 4 * groups)
-    off = a(off + 4 * chunks)
-    off = a(off + 80 * chunks)
-    off = a(off + 80 * groups)
-    off = a(off + 40 * (1 << 19))
-    assert rmp.rmp_workspace_bytes() == off
+    assert rmp.rmp_workspace_bytes() == 1024 + 80 * (4096 + 128)
 
 
 def test_batch_workspace_size(rmp):

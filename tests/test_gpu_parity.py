@@ -15,7 +15,6 @@ from gpu_helpers import (assert_hits_exact, assert_per_ray_close, assert_result_
 
 pytestmark = pytest.mark.gpu
 
-PERSIST_MAX = 1 << 19        # largest count the persistent kernel takes (only when tuned on)
 
 
 @pytest.fixture(scope="module")
@@ -39,27 +38,14 @@ def hashed(ctx):
 
 
 def check_raycast(ctx, mid, om, x, xdot, n, pdict, max_range):
-    """One evaluation against the oracle through both single-state kernels -- the persistent
-    one (lanes take rays from a counter) and the one-wave one, with the context's other
-    knobs -- for counts the persistent kernel takes (up to 2^19 rays); beyond, the one-wave
-    kernel only.  Returns the result of the library's default choice and the oracle's."""
     pg = R.make_params(pdict, max_range)
     po = O.make_params(pdict, max_range)
+    rg, hg, pgr = gpu_raycast(ctx, mid, x, xdot, n, pg)
     ro, ho, por = O.raycast_eval(om, x, xdot, n, po)
-    prev = R.rmp_tune_get(ctx.handle, R.RMP_TUNE_PERSISTENT)
-    out = {}
-    try:
-        for mode in ((0, 1) if n <= PERSIST_MAX else (0,)):
-            R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, mode)
-            rg, hg, pgr = gpu_raycast(ctx, mid, x, xdot, n, pg)
-            assert_hits_exact(hg, ho)
-            assert_per_ray_close(pgr, por)
-            assert_result_close(rg, ro, por)
-            out[mode] = rg
-    finally:
-        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, prev)
-    default = 1 if prev == 1 and n <= PERSIST_MAX else 0
-    return out[default], ro
+    assert_hits_exact(hg, ho)
+    assert_per_ray_close(pgr, por)
+    assert_result_close(rg, ro, por)
+    return rg, ro
 
 
 # ----------------------------------------------------------------------------- dense map
@@ -429,7 +415,6 @@ def test_automatic_block_size(ctx, hashed):
     wl, mid, om = hashed
     p = R.make_params(wl.params, wl.max_range)
     assert R.rmp_tune_get(ctx.handle, R.RMP_TUNE_BLOCK) == 0
-    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, 0)
     R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 256)
     info = R.rmp_eval_launch_info(ctx.handle, mid, 65536, p)
     R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 0)
@@ -450,95 +435,6 @@ def test_automatic_block_size(ctx, hashed):
         assert R.rmp_eval_launch_info(ctx.handle, mid, 65536, p)["block"] == 64
     finally:
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 0)
-        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, -1)
-
-
-def test_persistent_launch_info(ctx, hashed):
-    """The persistent kernel runs only when tuned on, for 1 .. 2^19 rays: 256-thread CTAs,
-    one segment per ray, every CTA the device holds at once; otherwise (and beyond 2^19
-    rays) the one-wave kernel."""
-    wl, mid, om = hashed
-    p = R.make_params(wl.params, wl.max_range)
-    for n in (1, 8192, 65536, 1 << 19):
-        assert R.rmp_eval_launch_info(ctx.handle, mid, n, p)["persistent"] == 0
-    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, 1)
-    try:
-        for n, on in ((1, 1), (65536, 1), (1 << 19, 1), ((1 << 19) + 1, 0)):
-            li = R.rmp_eval_launch_info(ctx.handle, mid, n, p)
-            assert li["persistent"] == on, (n, li)
-            if on:
-                assert li["block"] == 256 and li["lg_segments"] == 0
-                assert li["grid"] == li["sm_count"] * li["ctas_per_sm"] and li["ctas_per_sm"] >= 1
-    finally:
-        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, -1)
-    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, 0)
-    try:
-        assert R.rmp_eval_launch_info(ctx.handle, mid, 65536, p)["persistent"] == 0
-    finally:
-        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, -1)
-    for bad in ((R.RMP_TUNE_PERSISTENT, 2), (R.RMP_TUNE_ROUND_VISITS, -1),
-                (R.RMP_TUNE_ROUND_VISITS, 65)):
-        with pytest.raises(R.RmpError):
-            R.rmp_tune_set(ctx.handle, *bad)
-
-
-@pytest.mark.parametrize("visits", [1, 2, 64])
-def test_persistent_round_visits_bitwise(ctx, hashed, dense, visits):
-    """The persistent kernel's block visits per round change only which lane runs which
-    ray when: hit records, per-ray values and the result are bitwise those of the default
-    round (every sum runs in the slots' fixed order), and match the oracle."""
-    for (wl, mid, om), si, n in ((hashed, 3, 65536), (dense, 4, 20000)):
-        s = wl.states[si]
-        pg = R.make_params(wl.params, wl.max_range)
-        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, 1)
-        try:
-            ref = gpu_raycast(ctx, mid, s.x, s.xdot, n, pg)
-            R.rmp_tune_set(ctx.handle, R.RMP_TUNE_ROUND_VISITS, visits)
-            got = gpu_raycast(ctx, mid, s.x, s.xdot, n, pg)
-        finally:
-            R.rmp_tune_set(ctx.handle, R.RMP_TUNE_ROUND_VISITS, 0)
-            R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, -1)
-        for key in ("f", "sumA", "sumAf", "eig"):
-            assert np.array_equal(got[0][key], ref[0][key]), key
-        assert got[1].tobytes() == ref[1].tobytes() and np.array_equal(got[2], ref[2])
-    check_raycast(ctx, mid, om, s.x, s.xdot, 5000, wl.params, wl.max_range)
-
-
-def test_persistent_bad_state_and_reuse(ctx, hashed):
-    """Invalid positions give RMP_ERR_INVALID_ARG through the persistent kernel too, and the
-    workspace's counters are left ready: the next evaluations are bitwise repeatable."""
-    torch = torch_cuda()
-    wl, mid, om = hashed
-    pg = R.make_params(wl.params, wl.max_range)
-    ws = torch.empty(R.rmp_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    R.rmp_workspace_init(ws)
-    out = torch.empty(R.RESULT_BYTES, dtype=torch.uint8, device="cuda")
-    s = wl.states[1]
-    good = torch.tensor(np.concatenate([s.x, s.xdot]), dtype=torch.float64, device="cuda")
-    R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, 1)
-    try:
-        R.rmp_raycast_eval_async(ctx.handle, mid, good, 20000, pg, ws, out)
-        ref = out.cpu().numpy().tobytes()
-        for bad in (np.nan, np.inf, 1e12):
-            state = torch.tensor([bad, 1.0, 1.0, 0.0, 0.0, 0.0], dtype=torch.float64,
-                                 device="cuda")
-            R.rmp_raycast_eval_async(ctx.handle, mid, state, 20000, pg, ws, out)
-            r = R.result_from_bytes(out.cpu().numpy().tobytes())
-            assert r["status"] == 1 and np.all(r["f"] == 0) and r["n_hits"] == 0
-            for n in (20000, 77, 1):                # differently sized evaluations between
-                R.rmp_raycast_eval_async(ctx.handle, mid, good, n, pg, ws, out)
-            R.rmp_raycast_eval_async(ctx.handle, mid, good, 20000, pg, ws, out)
-            assert out.cpu().numpy().tobytes() == ref
-    finally:
-        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_PERSISTENT, -1)
-
-
-def test_persistent_largest_count(ctx, hashed):
-    """The persistent kernel's largest evaluation (2^19 rays) against the oracle ray by ray,
-    on the hashed map."""
-    wl, mid, om = hashed
-    s = wl.states[5]
-    check_raycast(ctx, mid, om, s.x, s.xdot, 1 << 19, wl.params, wl.max_range)
 
 
 def _grid_occupancy(m, gmin, gdim):

@@ -106,14 +106,3 @@ def test_voxel_box_use(policy):
     got = policy(["cells %d %d" % c for c in cases])
     for (tune, lg), (kept,) in zip(cases, got):
         assert kept == (1 if tune == 1 or (tune == -1 and lg == 2) else 0), (tune, lg)
-
-
-def test_persistent_kernel_use(policy):
-    """Persistent single-state kernel: on only when tuned on, up to 2^19 rays."""
-    ns = (1, 4096, 8191, 8192, 65536, 1 << 19, (1 << 19) + 1, 1 << 24)
-    cases = [(t, n) for t in (-1, 0, 1) for n in ns]
-    got = policy(["persist %d %d" % c for c in cases])
-    for (tune, n), (on,) in zip(cases, got):
-        fits = 1 <= n <= (1 << 19)
-        expect = fits and tune == 1
-        assert on == (1 if expect else 0), (tune, n)
