@@ -93,6 +93,10 @@ def lib():
                 "orc_combined_eval": (C.c_int, [P, P, P, C.c_uint32, P, P, C.c_double,
                                                 C.c_double, C.c_int, P]),
                 "orc_rollout_step": (None, [P, P, P, P, P]),
+                "orc_esdf_query": (C.c_int, [P, C.c_uint32, P, P, P]),
+                "orc_esdf_eval": (None, [P, C.c_uint32, P, P, P, P, C.c_double, C.c_double,
+                                         P, P]),
+                "orc_esdf_rollout_step": (None, [P, P, C.c_uint32, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -306,6 +310,66 @@ def rollout(omap: "OracleMap", params: Params, rp: RolloutParams, x0, xdot0, goa
                smoothness=float(st.smooth_sum / st.smooth_n) if st.smooth_n else 1.0,
                smooth_n=int(st.smooth_n))
     return (out, np.array(path)) if want_path else out
+
+
+# ----------------------------------------------------------------------------- ESDF policy
+PRIM_DTYPE = np.dtype([("kind", "<u4"), ("reserved", "<u4"), ("center", "<f8", (3,)),
+                       ("size", "<f8", (3,))])
+PRIM_SPHERE, PRIM_BOX = 0, 1
+
+
+def prims_array(prims) -> np.ndarray:
+    """Primitives (objects with .kind "sphere"/"box", .center, .size) as the oracle's records
+    (sphere: size[0] = radius; box: half-extents)."""
+    a = np.zeros(len(prims), PRIM_DTYPE)
+    for i, pr in enumerate(prims):
+        a[i]["kind"] = PRIM_SPHERE if pr.kind == "sphere" else PRIM_BOX
+        a[i]["center"] = pr.center
+        sz = np.asarray(pr.size, np.float64)
+        a[i]["size"] = np.repeat(sz, 3) if sz.size == 1 else sz
+    return a
+
+
+def esdf_query(prims: np.ndarray, x):
+    """(d, gradient, index of the minimising primitive) of the exact ESDF of prims at x."""
+    xx = np.ascontiguousarray(x, np.float64)
+    d = C.c_double(0.0)
+    g = np.zeros(3)
+    i = lib().orc_esdf_query(_ptr(prims) if len(prims) else None, len(prims), _ptr(xx),
+                             C.byref(d), _ptr(g))
+    return float(d.value), g, int(i)
+
+
+def esdf_eval(prims: np.ndarray, x, xdot, params: Params, goal=None, alpha: float = 0.0,
+              beta: float = 0.0):
+    """The ESDF policy (Sec. III-D), with the attractor by Eq. (1) when a goal is given;
+    returns the result dict and the query (d, gradient) as 4 doubles."""
+    xx = np.ascontiguousarray(x, np.float64)
+    xd = np.ascontiguousarray(xdot, np.float64)
+    g = None if goal is None else np.ascontiguousarray(goal, np.float64)
+    res = Result()
+    q = np.zeros(4)
+    lib().orc_esdf_eval(_ptr(prims) if len(prims) else None, len(prims), _ptr(xx), _ptr(xd),
+                        C.byref(params), None if g is None else _ptr(g), float(alpha),
+                        float(beta), C.byref(res), _ptr(q))
+    return _result(res), q
+
+
+def esdf_rollout(omap: "OracleMap", prims: np.ndarray, params: Params, rp: RolloutParams, x0,
+                 xdot0, goal, steps: Optional[int] = None):
+    """Closed-loop rollout with the ESDF policy (collisions from the voxel map)."""
+    st = rollout_state(x0, xdot0)
+    g = np.ascontiguousarray(goal, np.float64)
+    n = rp.max_steps if steps is None else steps
+    for _ in range(n):
+        if st.status != ROLL_RUNNING:
+            break
+        lib().orc_esdf_rollout_step(omap.ref, _ptr(prims) if len(prims) else None, len(prims),
+                                    C.byref(params), C.byref(rp), _ptr(g), C.byref(st))
+    return dict(x=np.array(st.x[:]), xdot=np.array(st.xdot[:]), status=int(st.status),
+                steps=int(st.steps), path_length=float(st.path_length),
+                smoothness=float(st.smooth_sum / st.smooth_n) if st.smooth_n else 1.0,
+                smooth_n=int(st.smooth_n))
 
 
 def _result(res: Result) -> dict:

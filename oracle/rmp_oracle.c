@@ -595,15 +595,14 @@ int orc_combined_eval(const orc_map_t* m, const double x[3], const double xdot[3
 
 /* ------------------------------------------------------------------ closed loop (Sec. IV-A)
  * A point robot integrates the combined policy's acceleration. */
-void orc_rollout_step(const orc_map_t* m, const orc_params_t* p, const orc_rollout_params_t* rp,
-                      const double goal[3], orc_rollout_t* st) {
-  if (st->status != ORC_ROLL_RUNNING) return;
-  orc_result_t r;
-  orc_combined_eval(m, st->x, st->xdot, rp->n_rays, p, goal, rp->alpha, rp->beta,
-                    (int)rp->metric_mean, &r);
+/* Semi-implicit Euler with acceleration f, path and smoothness statistics, then the
+ * stopping checks (see orc_rollout_step). */
+static void rollout_advance(const orc_map_t* m, const orc_rollout_params_t* rp,
+                            const double goal[3], const double f_in[3], orc_rollout_t* st) {
+  const double f[3] = {f_in[0], f_in[1], f_in[2]};
   double xn[3], dl = 0.0;
   for (int a = 0; a < 3; ++a) {
-    st->xdot[a] = st->xdot[a] + r.f[a] * rp->dt;
+    st->xdot[a] = st->xdot[a] + f[a] * rp->dt;
     xn[a] = st->x[a] + st->xdot[a] * rp->dt;
     dl += (xn[a] - st->x[a]) * (xn[a] - st->x[a]);
     st->x[a] = xn[a];
@@ -642,6 +641,126 @@ void orc_rollout_step(const orc_map_t* m, const orc_params_t* p, const orc_rollo
   else if (occupied(m, k)) st->status = ORC_ROLL_COLLIDED;
   else if (sqrt(dg) < rp->goal_tol) st->status = ORC_ROLL_REACHED;
   else if (st->steps >= rp->max_steps) st->status = ORC_ROLL_TIMEOUT;
+}
+
+void orc_rollout_step(const orc_map_t* m, const orc_params_t* p, const orc_rollout_params_t* rp,
+                      const double goal[3], orc_rollout_t* st) {
+  if (st->status != ORC_ROLL_RUNNING) return;
+  orc_result_t r;
+  orc_combined_eval(m, st->x, st->xdot, rp->n_rays, p, goal, rp->alpha, rp->beta,
+                    (int)rp->metric_mean, &r);
+  rollout_advance(m, rp, goal, r.f, st);
+}
+
+/* ------------------------------------------------------------------ ESDF policy (Sec. III-D) */
+static double sign_of(double v) { return v < 0.0 ? -1.0 : 1.0; }
+
+static double prim_sdf(const orc_prim_t* pr, const double x[3]) {
+  double q[3];
+  for (int a = 0; a < 3; ++a) q[a] = x[a] - pr->center[a];
+  if (pr->kind == ORC_PRIM_SPHERE)
+    return sqrt((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) - pr->size[0];
+  double ai[3], o[3];
+  for (int a = 0; a < 3; ++a) {
+    ai[a] = fabs(q[a]) - pr->size[a];
+    o[a] = ai[a] > 0.0 ? ai[a] : 0.0;
+  }
+  const double out = sqrt((o[0] * o[0] + o[1] * o[1]) + o[2] * o[2]);
+  double in = ai[0] > ai[1] ? ai[0] : ai[1];
+  in = in > ai[2] ? in : ai[2];
+  in = in < 0.0 ? in : 0.0;
+  return out + in;
+}
+
+static void prim_grad(const orc_prim_t* pr, const double x[3], double g[3]) {
+  double q[3];
+  for (int a = 0; a < 3; ++a) q[a] = x[a] - pr->center[a];
+  if (pr->kind == ORC_PRIM_SPHERE) {
+    const double L = sqrt((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]);
+    for (int a = 0; a < 3; ++a) g[a] = L > 0.0 ? q[a] / L : 0.0;
+    return;
+  }
+  double ai[3], o[3];
+  for (int a = 0; a < 3; ++a) {
+    ai[a] = fabs(q[a]) - pr->size[a];
+    o[a] = ai[a] > 0.0 ? ai[a] : 0.0;
+  }
+  const double out = sqrt((o[0] * o[0] + o[1] * o[1]) + o[2] * o[2]);
+  if (out > 0.0) {
+    for (int a = 0; a < 3; ++a) g[a] = sign_of(q[a]) * o[a] / out;
+    return;
+  }
+  const int k = (ai[0] >= ai[1] && ai[0] >= ai[2]) ? 0 : (ai[1] >= ai[2] ? 1 : 2);
+  for (int a = 0; a < 3; ++a) g[a] = a == k ? sign_of(q[a]) : 0.0;
+}
+
+int orc_esdf_query(const orc_prim_t* prims, uint32_t n, const double x[3], double* d,
+                   double grad[3]) {
+  int best = -1;
+  double bv = INFINITY;
+  for (uint32_t i = 0; i < n; ++i) {
+    const double v = prim_sdf(&prims[i], x);
+    if (v < bv) {
+      bv = v;
+      best = (int)i;
+    }
+  }
+  grad[0] = grad[1] = grad[2] = 0.0;
+  if (best < 0) {
+    *d = INFINITY;
+    return -1;
+  }
+  *d = bv > 0.0 ? bv : 0.0;
+  prim_grad(&prims[best], x, grad);
+  return best;
+}
+
+void orc_esdf_eval(const orc_prim_t* prims, uint32_t n, const double x[3], const double xdot[3],
+                   const orc_params_t* p, const double* goal, double alpha, double beta,
+                   orc_result_t* out, double* query) {
+  memset(out, 0, sizeof(*out));
+  double d, r[3];
+  const int idx = orc_esdf_query(prims, n, x, &d, r);
+  if (query) {
+    query[0] = d;
+    for (int a = 0; a < 3; ++a) query[1 + a] = r[a];
+  }
+  double S[6] = {0, 0, 0, 0, 0, 0}, b[3] = {0, 0, 0};
+  out->n_rays = 1;
+  if (idx >= 0) {
+    const double xr = (xdot[0] * r[0] + xdot[1] * r[1]) + xdot[2] * r[2];
+    const int active = xr < 0.0, in_radius = d < p->r;
+    double f[3], A[6];
+    orc_ray_policy(p, r, d, xdot, active, in_radius, f, A);
+    for (int k = 0; k < 6; ++k) S[k] = A[k];
+    sym_mul(A, f, b);
+    out->n_hits = 1;
+    out->n_active = (uint32_t)(active && in_radius);
+  }
+  if (goal) {
+    double fa[3];
+    orc_attractor(x, xdot, goal, alpha, beta, p->c, fa);
+    S[0] += 1.0;
+    S[3] += 1.0;
+    S[5] += 1.0;
+    for (int a = 0; a < 3; ++a) b[a] += fa[a];
+  }
+  for (int k = 0; k < 6; ++k) out->sumA[k] = S[k];
+  for (int k = 0; k < 3; ++k) out->sumAf[k] = b[k];
+  double P[6];
+  orc_pinv3(S, P, out->eig, &out->rank);
+  out->f[0] = P[0] * b[0] + P[1] * b[1] + P[2] * b[2];
+  out->f[1] = P[1] * b[0] + P[3] * b[1] + P[4] * b[2];
+  out->f[2] = P[2] * b[0] + P[4] * b[1] + P[5] * b[2];
+}
+
+void orc_esdf_rollout_step(const orc_map_t* m, const orc_prim_t* prims, uint32_t n,
+                           const orc_params_t* p, const orc_rollout_params_t* rp,
+                           const double goal[3], orc_rollout_t* st) {
+  if (st->status != ORC_ROLL_RUNNING) return;
+  orc_result_t r;
+  orc_esdf_eval(prims, n, st->x, st->xdot, p, goal, rp->alpha, rp->beta, &r, NULL);
+  rollout_advance(m, rp, goal, r.f, st);
 }
 
 /* ------------------------------------------------------------------ batch helpers (tests) */

@@ -123,6 +123,50 @@ typedef struct {
 void orc_rollout_step(const orc_map_t* m, const orc_params_t* p, const orc_rollout_params_t* rp,
                       const double goal[3], orc_rollout_t* st);
 
+/* ------------------------------------------------------------------ ESDF policy (Sec. III-D)
+ * The single-query baseline: the distance to the closest obstacle d_obs(x) and its gradient
+ * stand in for a ray's d and r in the obstacle policy of Sec. III-C.  The ESDF is the exact
+ * Euclidean signed distance of a union of primitives (spheres, boxes): the minimum over
+ * primitives, the first minimum on ties; d = max(sdf, 0) (inside an obstacle the distance
+ * to the closest obstacle is 0); the gradient is that of the minimising primitive's
+ * distance (a unit vector pointing away from it).  Evaluation order (FP64, one rounding
+ * per operation, no fused operations) is part of the definition, since the GPU side
+ * reproduces d and the gradient bit for bit:
+ *   sphere (centre c, radius rho): q = x - c, L = sqrt((q0 q0 + q1 q1) + q2 q2),
+ *     sdf = L - rho, gradient q_a / L (0 if L = 0);
+ *   box (centre c, half-extents h): q = x - c, a_i = |q_i| - h_i, o_i = max(a_i, 0),
+ *     out = sqrt((o0 o0 + o1 o1) + o2 o2), in = min(max(max(a0, a1), a2), 0),
+ *     sdf = out + in; gradient: out > 0: sign(q_i) o_i / out; else sign(q_k) e_k for
+ *     k = argmax a_i (lowest index on ties); sign(0) = +1. */
+enum { ORC_PRIM_SPHERE = 0, ORC_PRIM_BOX = 1 };
+
+typedef struct {
+  uint32_t kind, reserved;
+  double center[3];
+  double size[3];           /* sphere: size[0] = radius; box: half-extents */
+} orc_prim_t;
+
+/* d (+inf with no primitives) and the gradient at x; returns the minimising primitive's
+ * index, -1 with none. */
+int orc_esdf_query(const orc_prim_t* prims, uint32_t n, const double x[3], double* d,
+                   double grad[3]);
+
+/* The ESDF policy at (x, xdot): the obstacle policy with d = d_obs(x), r = its gradient,
+ * active iff xdot . r < 0 and in radius iff d < r_w (both FP64); with a goal (non-null) the
+ * attractor is combined by Eq. (1): f = (A_obs + I)^+ (A_obs f_obs + f_a), else
+ * f = A_obs^+ A_obs f_obs.  out->sumA / sumAf hold the metric and the metric-weighted force
+ * that are resolved; n_rays = 1, n_hits = 1 if there is a primitive, n_active = 1 if the
+ * policy is active and in radius.  query (nullable): d and the gradient (4 doubles). */
+void orc_esdf_eval(const orc_prim_t* prims, uint32_t n, const double x[3], const double xdot[3],
+                   const orc_params_t* p, const double* goal, double alpha, double beta,
+                   orc_result_t* out, double* query);
+
+/* One closed-loop step as orc_rollout_step, with the ESDF policy combined with the
+ * attractor in place of the raycasting policy (the voxel map m still decides collisions). */
+void orc_esdf_rollout_step(const orc_map_t* m, const orc_prim_t* prims, uint32_t n,
+                           const orc_params_t* p, const orc_rollout_params_t* rp,
+                           const double goal[3], orc_rollout_t* st);
+
 /* batch helpers used by the tests */
 void orc_halton_batch(uint32_t n, uint32_t offset, float* u, float* v, uint32_t* num3);
 void orc_sincos_batch(uint32_t n, const float* v, float* c, float* s);
