@@ -262,17 +262,18 @@ def kernel_source_hash(launch: dict) -> str:
     return h.hexdigest()[:16]
 
 
-def committed_traffic(src_hash: str):
-    """Per-launch DRAM bytes of the raycast kernel from the committed ncu summary, if it
-    was taken on the current kernel source and launch shape."""
+def committed_counters(src_hash: str) -> dict:
+    """Per-launch counters of the raycast kernel from the committed ncu capture (DRAM bytes,
+    L2 bytes, warp instructions), if it was taken on the current kernel source and launch
+    shape; empty otherwise."""
     path = os.path.join(ROOT, "profiles", "raycast_hashed_65536_traffic.json")
     try:
         d = json.load(open(path))
     except Exception:
-        return None
+        return {}
     if d.get("kernel_launch_sha256_16") != src_hash:
-        return None
-    return d.get("dram_bytes_per_launch")
+        return {}
+    return d
 
 
 def measured_peak_hbm():
@@ -300,11 +301,47 @@ def timed_device(fn, flush, reps: int):
     return float(np.median([a.elapsed_time(b) for a, b in ev]))
 
 
-def batch_section(ctx, mid, flush) -> dict:
+def config1_section(ctx, flush) -> dict:
+    """Config 1: dense uint8 grid 64^3 at 0.1 m with 20 boxes, 1024 Halton rays, max range
+    5 m, one state per call (device-resident state and result, L2 flushed between calls),
+    against the same kernel's floor: a one-ray evaluation."""
+    import torch
+    from paper_2301_08068_gb300 import rmp as R, workloads as W
+    wl = W.dense_box_workload(n_states=16, jitter=True)
+    mid = ctx.upload(wl.map)
+    p = R.make_params(wl.params, wl.max_range)
+    st = torch.tensor(np.stack([np.concatenate([s.x, s.xdot]) for s in wl.states]),
+                      dtype=torch.float64, device="cuda")
+    ws = torch.empty(R.rmp_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    R.rmp_workspace_init(ws)
+    out = torch.empty((16, R.RESULT_BYTES), dtype=torch.uint8, device="cuda")
+    n = wl.n_rays
+    ev = []
+    for i in range(400):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        R.rmp_raycast_eval_async(ctx.handle, mid, st[i % 16], n, p, ws, out[i % 16])
+        b.record()
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    t = [x.elapsed_time(y) for x, y in ev[20:]]      # the first 20 calls warm up
+    ms = float(np.mean(t))
+    ms1 = timed_device(lambda: R.rmp_raycast_eval_async(ctx.handle, mid, st[0], 1, p, ws, out[0]),
+                       flush, 200)
+    R.rmp_map_release(ctx.handle, mid)
+    return {"workload": "dense 64^3 at 0.1 m, 20 boxes, 1024 rays, max range 5 m",
+            "us_per_eval": 1e3 * ms, "us_per_eval_p50": 1e3 * float(np.percentile(t, 50)),
+            "Grays_per_s": n / ms / 1e6, "evals_per_s": 1e3 / ms,
+            "floor_us_one_ray": 1e3 * ms1, "frac_of_floor": ms1 / ms}
+
+
+def batch_section(ctx, mid, flush, per_state: bool = False) -> dict:
     """Batched evaluation: 256 states over the same hashed map with ray counts drawn
     log-uniform in [4096, 65536]; autotuned launch, captured once in a CUDA graph and
     replayed; against the plain single-state kernel called once per state; both
-    reductions (compensated FP32, FP64)."""
+    reductions (compensated FP32, FP64).  per_state: also the per-state results of both
+    reductions (for the precision report against the oracle)."""
     import torch
     from paper_2301_08068_gb300 import rmp as R, workloads as W
     wl = W.hashed_workload(n_states=256, uneven_rays=(4096, 65536))
@@ -336,6 +373,10 @@ def batch_section(ctx, mid, flush) -> dict:
             res[name] = {"ms_per_batch": ms, "Grays_per_s": float(counts.sum()) / ms / 1e6,
                          "evals_per_s": B / ms * 1e3, "tuned": tuned,
                          "autotune_ms": [round(t, 4) for t in times]}
+            if per_state:
+                o = out.cpu().numpy()
+                res.setdefault("_results", {})[name] = [R.result_from_bytes(o[b].tobytes())
+                                                        for b in range(B)]
         # the plain single-state kernel, one launch per state, same states and counts
         R.rmp_tune_set(ctx.handle, 1, 0)
         R.rmp_tune_set(ctx.handle, 2, -1)
@@ -427,25 +468,30 @@ def lidar_stream_section(ctx) -> dict:
             "budget_ms_at_20Hz": 50.0}
 
 
-def l2_probe(flush) -> float:
-    """L2 bandwidth probe (GB/s): repeated device copies of a 24 MiB buffer pair, which
-    stays resident in the 129 MB L2; bytes = read + write."""
+def l2_probe(ctx) -> dict:
+    """L2 read bandwidth: the library's probe kernel reads a 32 MiB buffer (resident in the
+    129 MB L2) 200 times with 16-byte loads that bypass L1, on every SM; best of 5 launches
+    by CUDA events.  GB/s = bytes read / time."""
     import torch
-    a = torch.empty(24 << 20, dtype=torch.uint8, device="cuda")
-    b = torch.empty_like(a)
-    a.fill_(1)
+    from paper_2301_08068_gb300 import rmp as R
+    buf = torch.ones(32 << 20, dtype=torch.uint8, device="cuda")
+    chk = torch.zeros(4096, dtype=torch.int64, device="cuda")
+    passes = 200
+    for _ in range(2):
+        R.rmp_probe_l2_read(ctx.handle, buf, passes, chk)
+    torch.cuda.synchronize()
+    best = None
     for _ in range(5):
-        b.copy_(a)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    reps = 200
-    e0.record()
-    for _ in range(reps):
-        b.copy_(a)
-    e1.record()
-    torch.cuda.synchronize()
-    return 2.0 * a.numel() * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        R.rmp_probe_l2_read(ctx.handle, buf, passes, chk)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return {"GBps": buf.numel() * passes / (best / 1e3) / 1e9, "bytes": buf.numel(),
+            "passes": passes,
+            "probe": "rmp_probe_l2_read: 32 MiB read 200 times (ld.global.cg, 16 B per load)"}
 
 
 def rollout_section(ctx) -> dict:
@@ -464,6 +510,24 @@ def rollout_section(ctx) -> dict:
         mid = ctx.upload(t.map)
         p = R.make_params(t.params, t.max_range)
         robots = np.concatenate([t.starts, np.zeros_like(t.starts), t.goals], axis=1)
+        # the ESDF single-query policy (Sec. III-D) on the same start/goal pairs
+        eid = R.rmp_esdf_upload(ctx.handle, t.prims)
+        rp = R.rollout_params(10.0, 15.0, 0.01, 0.2, 6000, 10, 1)
+        t0 = time.perf_counter()
+        res = R.rmp_rollout_esdf(ctx.handle, mid, eid, robots, p, rp)
+        wall = time.perf_counter() - t0
+        R.rmp_esdf_release(ctx.handle, eid)
+        st = np.array([r["status"] for r in res])
+        steps = np.array([r["steps"] for r in res])
+        ok = st == R.RMP_ROLLOUT_REACHED
+        out["%d_prims_%g-%gm_esdf" % (n_prims, size[0], size[1])] = {
+            "policy": "ESDF single query (exact distance and gradient of the primitives)",
+            "success": float(ok.mean()), "collided": float((st == R.RMP_ROLLOUT_COLLIDED).mean()),
+            "timeout": float((st == R.RMP_ROLLOUT_TIMEOUT).mean()),
+            "smoothness_success_mean": float(np.mean([r["smoothness"] for r, o in zip(res, ok)
+                                                      if o])) if ok.any() else None,
+            "steps_max": int(steps.max()), "wall_s": wall,
+            "ms_per_control_step": 1e3 * wall / max(1, int(steps.max()))}
         for mean in (True, False):
             rows = []
             for side in (4, 8, 16, 32, 64):
@@ -522,6 +586,9 @@ def serve_section(ctx, seconds: float) -> dict:
         for m in range(3):
             srv.wait(srv.submit(mids[m], wls[m].states[0].x, wls[m].states[0].xdot, 4096,
                                 params[m]))
+        import threading
+        me = threading.get_native_id()
+        cpu0 = thread_cpu_seconds(me)
         tickets = []
         t0 = time.perf_counter()
         for i, (m, x, v, r) in enumerate(reqs):
@@ -534,10 +601,12 @@ def serve_section(ctx, seconds: float) -> dict:
             assert res["status"] == 0
             lat.append(l)
         span = time.perf_counter() - t0
+        cpu = thread_cpu_seconds(me) - cpu0
         st = srv.stats()
     out["served"] = dict(pct(lat), Grays_per_s=total_rays / span / 1e9, makespan_s=span,
                          batches=st["batches"], mean_batch=st["batched_states"] / max(1, st["batches"]),
-                         max_inflight=st["max_inflight"], mem_high_water=st["mem_high_water"])
+                         max_inflight=st["max_inflight"], mem_high_water=st["mem_high_water"],
+                         library_threads_cpu_per_s=cpu / span)
     # the plain kernel, one request at a time in arrival order
     for m in range(3):
         R.rmp_raycast_eval(ctx.handle, mids[m], wls[m].states[0].x, wls[m].states[0].xdot, 4096,
@@ -552,8 +621,162 @@ def serve_section(ctx, seconds: float) -> dict:
     span = time.perf_counter() - t0
     out["plain_per_request"] = dict(pct(lat), Grays_per_s=total_rays / span / 1e9,
                                     makespan_s=span)
+    out["load_sweep"] = load_sweep(ctx, mids, params, wls)
+    ok = [r["rate_req_s"] for r in out["load_sweep"] if r["server"]["p99_ms"] < 1.0]
+    out["max_rate_p99_under_1ms"] = max(ok) if ok else None
     for m in mids:
         R.rmp_map_release(ctx.handle, m)
+    return out
+
+
+def thread_cpu_seconds(exclude_tid: int) -> float:
+    """CPU time (user + system) of this process's threads other than exclude_tid, from
+    /proc (0 where /proc is unavailable)."""
+    tot = 0.0
+    tick = os.sysconf("SC_CLK_TCK") if hasattr(os, "sysconf") else 100
+    try:
+        for tid in os.listdir("/proc/self/task"):
+            if int(tid) == exclude_tid:
+                continue
+            with open("/proc/self/task/%s/stat" % tid) as f:
+                fields = f.read().rsplit(")", 1)[1].split()
+            tot += (int(fields[11]) + int(fields[12])) / tick
+    except (OSError, ValueError, IndexError):
+        return 0.0
+    return tot
+
+
+def load_sweep(ctx, mids, params, wls, seconds: float = 0.25) -> list:
+    """The served stream at several offered loads (Poisson, 5k..80k requests/s for
+    `seconds` each, same maps and ray-count law): server against the plain kernel one
+    request at a time (FIFO), p50/p99 latency, achieved Grays/s, mean batch size, and the
+    CPU time the library's threads (server worker, CUDA callbacks) used per second."""
+    import threading
+    from paper_2301_08068_gb300 import rmp as R, workloads as W
+    rows = []
+    me = threading.get_native_id()
+    for rate in (5000.0, 10000.0, 20000.0, 40000.0, 80000.0):
+        t_arr, maps, rays, vel = W.poisson_requests(3, rate, seconds, 1024, 262144,
+                                                    seed_index=40 + int(rate) // 1000)
+        reqs = [(int(maps[i]), wls[maps[i]].states[i % len(wls[maps[i]].states)].x, vel[i],
+                 int(rays[i])) for i in range(len(t_arr))]
+        total = float(np.sum(rays))
+        row = {"rate_req_s": rate, "requests": len(reqs), "offered_Grays_per_s": total / seconds / 1e9}
+        with R.Server(ctx, slots=4, max_batch_states=256, max_rays=262144,
+                      mem_budget_bytes=256 << 20) as srv:
+            srv.wait(srv.submit(mids[1], wls[1].states[0].x, wls[1].states[0].xdot, 4096, params[1]))
+            cpu0 = thread_cpu_seconds(me)
+            t0 = time.perf_counter()
+            tickets = []
+            for i, (m, x, v, r) in enumerate(reqs):
+                while time.perf_counter() - t0 < t_arr[i]:
+                    pass
+                tickets.append(srv.submit(mids[m], x, v, r, params[m]))
+            lat = []
+            for tk in tickets:
+                res, l = srv.wait(tk, 60000)
+                lat.append(l)
+            span = time.perf_counter() - t0
+            cpu = thread_cpu_seconds(me) - cpu0
+            st = srv.stats()
+        row["server"] = {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                         "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                         "Grays_per_s": total / span / 1e9,
+                         "mean_batch": st["batched_states"] / max(1, st["batches"]),
+                         "library_threads_cpu_per_s": cpu / span}
+        lat = []
+        t0 = time.perf_counter()
+        for i, (m, x, v, r) in enumerate(reqs):
+            while time.perf_counter() - t0 < t_arr[i]:
+                pass
+            R.rmp_raycast_eval(ctx.handle, mids[m], x, v, r, params[m])
+            lat.append(time.perf_counter() - t0 - t_arr[i])
+        span = time.perf_counter() - t0
+        row["plain"] = {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                        "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                        "Grays_per_s": total / span / 1e9}
+        rows.append(row)
+    return rows
+
+
+def oracle_configs(cores: int, gpu_batch: dict) -> dict:
+    """The oracle (unchanged single-threaded C) on configs 1, 3, 4 and 5, on one core and on
+    every host core (one evaluation per thread at once), in rays (points) per second; and
+    config 4's precision: each of the 256 states of the batch against the FP64 oracle, for
+    both GPU reductions (gpu_batch: batch_section's per-state results)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle as O
+    from paper_2301_08068_gb300 import workloads as W
+    out = {}
+    pool = ThreadPoolExecutor(cores)
+
+    def rate(fn, items, rays_of, sample: str):
+        t0 = time.perf_counter()
+        fn(items[0])
+        one = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        res = list(pool.map(fn, items))
+        wall = time.perf_counter() - t0
+        n_all = float(sum(rays_of(i) for i in items))
+        return {"single_thread_rays_per_s": rays_of(items[0]) / one,
+                "all_cores_rays_per_s": n_all / wall, "cores": cores, "sample": sample}, res
+
+    # config 1: dense 64^3, 1024 rays
+    w1 = W.dense_box_workload(n_states=2 * cores, jitter=True)
+    om1 = O.OracleMap(w1.map)
+    p1 = O.make_params(w1.params, w1.max_range)
+    out["config1"], _ = rate(lambda s: O.raycast_eval(om1, s.x, s.xdot, w1.n_rays, p1,
+                                                      want_hits=False, want_per_ray=False),
+                             w1.states, lambda s: w1.n_rays,
+                             "%d states x 1024 rays" % len(w1.states))
+    # config 3: 64 x 1024 scan
+    sw = W.lidar_workload()
+    p3 = O.make_params(sw.params, sw.max_range)
+    out["config3"], _ = rate(lambda k: O.scan_eval(sw.points, sw.x, sw.xdot, p3,
+                                                   want_per_ray=False),
+                             list(range(cores)), lambda k: len(sw.points),
+                             "%d scans of 65536 points" % cores)
+    # config 4: all 256 states of the batch (5.26 M rays), and the precision per state
+    w4 = W.hashed_workload(n_states=256, uneven_rays=(4096, 65536))
+    om4 = O.OracleMap(w4.map)
+    p4 = O.make_params(w4.params, w4.max_range)
+    idx = list(range(256))
+    out["config4"], orc = rate(lambda b: O.raycast_eval(om4, w4.states[b].x, w4.states[b].xdot,
+                                                        int(w4.n_rays[b]), p4, want_hits=False,
+                                                        want_per_ray=False)[0],
+                               idx, lambda b: int(w4.n_rays[b]),
+                               "the 256 states of the batch, %d rays" % int(np.sum(w4.n_rays)))
+    if gpu_batch:
+        prec = {}
+        for name, res in gpu_batch.items():
+            eA, ef, cond = [], [], []
+            for g, o in zip(res, orc):
+                eA.append(float(np.abs(g["sumA"] - o["sumA"]).max() /
+                                max(np.abs(o["sumA"]).max(), 1e-300)))
+                ef.append(float(np.linalg.norm(g["f"] - o["f"]) /
+                                max(np.linalg.norm(o["f"]), 1e-300)))
+                lam = o["eig"]
+                cond.append(float(lam.max() / lam.min()) if lam.min() > 0 else float("inf"))
+            worst = int(np.argmax(ef))
+            prec[name] = {"sumA_rel_max": max(eA), "sumA_rel_median": float(np.median(eA)),
+                          "f_rel_max": max(ef), "f_rel_median": float(np.median(ef)),
+                          "f_rel_max_state": worst, "cond_of_worst_state": cond[worst],
+                          "states": len(ef),
+                          "f_rel_per_state": [float("%.3g" % e) for e in ef]}
+        out["config4_precision"] = prec
+    # config 5: a sample of the served stream's requests over the three maps
+    wls = W.served_workloads(64)
+    oms = [O.OracleMap(w.map) for w in wls]
+    ps = [O.make_params(w.params, w.max_range) for w in wls]
+    t_arr, maps, rays, vel = W.poisson_requests(3, 20000.0, 2.0, 1024, 262144)
+    pick = list(range(0, len(maps), max(1, len(maps) // (4 * cores))))[:4 * cores]
+    out["config5"], _ = rate(lambda i: O.raycast_eval(oms[maps[i]],
+                                                      wls[maps[i]].states[i % 64].x, vel[i],
+                                                      int(rays[i]), ps[maps[i]], want_hits=False,
+                                                      want_per_ray=False),
+                             pick, lambda i: int(rays[i]),
+                             "%d requests of the served stream" % len(pick))
+    pool.shutdown()
     return out
 
 
@@ -736,23 +959,62 @@ def main():
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:
+        extra["config1_dense"] = config1_section(ctx, flush)
         extra["lidar"] = lidar_section(ctx, flush)
         extra["lidar_stream_os0"] = lidar_stream_section(ctx)
-        extra["batched"] = batch_section(ctx, mid, flush)
+        extra["batched"] = batch_section(ctx, mid, flush, per_state=cpu is not None)
         extra["served"] = serve_section(ctx, args.serve_seconds)
         extra["rollout"] = rollout_section(ctx)
+    if cpu is not None:
+        gb = extra.get("batched", {}).pop("_results", None)
+        cpu["configs"] = oracle_configs(host_cores(), gb)
 
     src = kernel_source_hash(launch)
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (ms / 1e3) / 1e9
-    # secondary ALU roofline: the plain DDA's integer work, INT_OPS_PER_STEP per voxel step,
+    # the kernel's bound: the serial integer DDA chain (INT_OPS_PER_STEP per voxel step)
     # against every SM's integer lanes at the sampled SM clock
+    sm_mhz = clk.get("sm_mhz") or 2070.0
     alu_ops = float(np.mean(steps_per_launch)) * INT_OPS_PER_STEP
-    alu_peak = SM_COUNT * INT_LANES_PER_SM * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e12
-    traffic = committed_traffic(src)
-    l2_gbs = l2_probe(flush) if rank == 0 else None
+    alu_peak = SM_COUNT * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    alu_achieved = alu_ops / (ms / 1e3) / 1e12
+    counters = committed_counters(src)
+    traffic = counters.get("dram_bytes_per_launch")
+    l2 = l2_probe(ctx) if rank == 0 else None
+    l2_bytes = counters.get("lts_bytes_per_launch")
+    insts = counters.get("warp_inst_per_launch")
     if rank == 0:
         value = whole_job_rate(world, N_RAYS, ms_max)
+        # compact scalars of the other configs (kept beside the workload description)
+        summary = {"ms_per_step_p50": float(np.percentile(per, 50))}
+        try:
+            if "config1_dense" in extra:
+                summary["c1_dense_1024_us_per_eval"] = extra["config1_dense"]["us_per_eval"]
+            if "lidar" in extra:
+                summary["c3_lidar_64x1024_us_per_scan"] = 1e3 * extra["lidar"]["ms_per_scan"]
+            if "batched" in extra:
+                b = extra["batched"]
+                summary["c4_batch256_Grays_per_s"] = b["kahan_fp32"]["Grays_per_s"]
+                summary["c4_batch256_ms"] = b["kahan_fp32"]["ms_per_batch"]
+                summary["c4_batch256_fp64_Grays_per_s"] = b["fp64"]["Grays_per_s"]
+            if cpu is not None and "config4_precision" in cpu.get("configs", {}):
+                pr = cpu["configs"]["config4_precision"]
+                summary["c4_f_rel_err_max_kahan32"] = pr["kahan_fp32"]["f_rel_max"]
+                summary["c4_f_rel_err_median_kahan32"] = pr["kahan_fp32"]["f_rel_median"]
+                summary["c4_sumA_rel_err_max_kahan32"] = pr["kahan_fp32"]["sumA_rel_max"]
+            if "served" in extra:
+                sv = extra["served"]
+                summary["c5_served_p50_ms"] = sv["served"]["p50_ms"]
+                summary["c5_served_p99_ms"] = sv["served"]["p99_ms"]
+                summary["c5_served_Grays_per_s"] = sv["served"]["Grays_per_s"]
+                summary["c5_plain_p50_ms"] = sv["plain_per_request"]["p50_ms"]
+                summary["c5_max_rate_p99_under_1ms"] = sv.get("max_rate_p99_under_1ms")
+            if "rollout" in extra:
+                ro = extra["rollout"]
+                summary["rollout_ray1024_success"] = ro["200_prims_0.2-0.6m_mean"][3]["success"]
+                summary["rollout_esdf_success"] = ro["200_prims_0.2-0.6m_esdf"]["success"]
+        except (KeyError, IndexError, TypeError):
+            pass
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
@@ -760,7 +1022,7 @@ def main():
             "config": {"workload": WORKLOAD, "n_rays": N_RAYS, "states": N_STATES,
                        "map_blocks": wl.map.n_blocks, "parallelism": "replicas x%d" % world,
                        "l2": "flushed between timed steps (256 MiB write outside the events)",
-                       "launch": launch},
+                       "launch": launch, **summary},
             "evals_per_s": world * 1e3 / ms_max,
             "ms_per_step_p50": float(np.percentile(per, 50)),
             "ms_per_step_p99": float(np.percentile(per, 99)),
@@ -772,20 +1034,32 @@ def main():
                             "the 48-byte state travels in the kernel launch's parameter block, "
                             "the kernel writes the 144-byte result into mapped pinned host "
                             "memory, the call returns after a stream synchronisation"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,
-                         "algorithmic_bytes_per_launch": alg_bytes,
-                         "l2": {"achieved": achieved, "peak_probe": l2_gbs, "unit": "GB/s",
-                                "frac": achieved / l2_gbs if l2_gbs else None,
-                                "probe": "24 MiB device-to-device copies resident in L2"},
-                         "alu": {"achieved": alu_ops / (ms / 1e3) / 1e12, "peak": alu_peak,
-                                 "unit": "Tops/s",
-                                 "frac": alu_ops / (ms / 1e3) / 1e12 / alu_peak,
-                                 "voxel_steps_per_launch": float(np.mean(steps_per_launch)),
-                                 "ops_per_step": INT_OPS_PER_STEP,
-                                 "peak_source": "%d SMs x %d int32 lanes x SM clock" %
-                                                (SM_COUNT, INT_LANES_PER_SM)},
+            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                         "unit": "Tops/s", "frac": alu_achieved / alu_peak, "traffic": traffic,
+                         "peak_source": "%d SMs x %d int32 lanes x sampled SM clock %.0f MHz "
+                                        "(derived)" % (SM_COUNT, INT_LANES_PER_SM, sm_mhz),
+                         "algorithmic": "%d integer operations per voxel step of the plain "
+                                        "exact DDA x %.0f voxel steps per launch (from the "
+                                        "kernel's hit records)" %
+                                        (INT_OPS_PER_STEP, float(np.mean(steps_per_launch))),
+                         "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                                 "frac": achieved / peak,
+                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,
+                                 "algorithmic_bytes_per_launch": alg_bytes,
+                                 "dram_bytes_per_launch": traffic},
+                         "l2": {"achieved": (l2_bytes / (ms / 1e3) / 1e9) if l2_bytes else None,
+                                "peak": l2["GBps"] if l2 else None, "unit": "GB/s",
+                                "frac": (l2_bytes / (ms / 1e3) / 1e9 / l2["GBps"])
+                                        if (l2_bytes and l2) else None,
+                                "bytes_per_launch": l2_bytes,
+                                "bytes_source": "ncu lts__t_bytes.sum of the committed capture",
+                                "probe": l2},
+                         "issue": {"frac": (insts / (4 * SM_COUNT * sm_mhz * 1e6 * ms / 1e3))
+                                           if insts else None,
+                                   "warp_instructions_per_launch": insts,
+                                   "schedulers": 4 * SM_COUNT,
+                                   "what": "warp instructions (committed ncu capture) / "
+                                           "(schedulers x cycles of the measured mean time)"},
                          "kernel": "raycast_rmp_kernel<hashed TSDF, grid layout, "
                                    "compensated FP32 reduction>",
                          "kernel_launch_sha256_16": src},

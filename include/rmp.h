@@ -442,6 +442,68 @@ int rmp_server_wait(rmp_server* server, uint64_t ticket, uint32_t timeout_ms, rm
 /* Counters since the server started (*out: host). */
 int rmp_server_stats(rmp_server* server, rmp_server_stats_t* out);
 
+/* ------------------------------------------------------------------ ESDF policy (Sec. III-D)
+ * The paper's single-query baseline: an ESDF gives the distance d_obs(x) to the closest
+ * obstacle and its gradient, which stand in for one ray's d and r in the obstacle policy
+ * of Sec. III-C; combined with the goal attractor by Eq. (1) it is a simple local planner,
+ * the comparison for the raycasting policy.  The ESDF here is the exact Euclidean signed
+ * distance of a union of primitives (spheres, boxes -- the seeded scenes the maps are built
+ * from), kept on the device: d = max(0, min over primitives of their signed distance), the
+ * first minimum on ties; the gradient is that of the minimising primitive's distance (a
+ * unit vector pointing away from it; inside a box, the normal of its nearest face, the
+ * lowest axis on ties).  Everything is FP64; d and the gradient are reproduced bit for bit
+ * by a fixed operation order: sphere (centre c, radius rho): q = x - c,
+ * L = sqrt((q0 q0 + q1 q1) + q2 q2), sdf = L - rho, gradient q / L (0 at the centre); box
+ * (centre c, half-extents h): a_i = |x_i - c_i| - h_i, o_i = max(a_i, 0),
+ * out = sqrt((o0 o0 + o1 o1) + o2 o2), sdf = out + min(max(max(a0, a1), a2), 0),
+ * gradient sign(x_i - c_i) o_i / out when out > 0 (sign(0) = +1). */
+typedef struct {
+  uint32_t kind;            /* RMP_PRIM_SPHERE or RMP_PRIM_BOX */
+  uint32_t reserved;        /* 0 */
+  double center[3];
+  double size[3];           /* sphere: size[0] = radius (others ignored); box: half-extents */
+} rmp_primitive_t;
+#define RMP_PRIM_SPHERE 0
+#define RMP_PRIM_BOX 1
+
+/* Copy n primitives (host; n in [0, 2^20], finite, sizes > 0) to the device as an ESDF;
+ * *esdf_id names it (ids are shared with maps, never equal to a map's).  Synchronous. */
+int rmp_esdf_upload(rmp_ctx* ctx, const rmp_primitive_t* prims, uint32_t n, uint32_t* esdf_id);
+int rmp_esdf_release(rmp_ctx* ctx, uint32_t esdf_id);
+
+/* The ESDF policy for n_states states (states_dev: x then xdot, 6 doubles each).  Per state:
+ * d, r from the ESDF; active iff xdot . r < 0 and in radius iff d < params->r (both FP64);
+ * f_obs, A_obs as for one ray (Sec. III-C, FP64); with goals_dev (3 doubles per state,
+ * nullable) the attractor f_a = alpha s(goal - x) - beta xdot (metric I) is combined by
+ * Eq. (1): out.f = (A_obs + I)^+ (A_obs f_obs + f_a), out.A / out.Af the combined sums;
+ * without goals out.f = A_obs^+ A_obs f_obs.  out.n_rays = 1, n_hits = 1 if the ESDF has a
+ * primitive, n_active = 1 if the policy is active and in radius; a state with a non-finite
+ * component gets RMP_ERR_INVALID_ARG in its status.  query_dev (nullable): d and the
+ * gradient per state (4 doubles; d = +inf with no primitive).  One warp per state, one
+ * kernel on `stream`, no allocation; the result is written to out_dev[n_states]. */
+int rmp_esdf_eval_async(rmp_ctx* ctx, uint32_t esdf_id, const double* states_dev,
+                        const double* goals_dev, uint32_t n_states, const rmp_params_t* params,
+                        double alpha, double beta, rmp_stream_t stream, rmp_result_t* out_dev,
+                        double* query_dev);
+
+/* Closed loop with the ESDF policy in place of the raycasting policy: as rmp_rollout (same
+ * robots layout, integrator, stopping rules and statistics; collisions from the voxel map
+ * map_id), each control step evaluating the ESDF policy combined with the attractor
+ * (rp->alpha, rp->beta; rp->n_rays and rp->metric_mean are not used). */
+int rmp_rollout_esdf(rmp_ctx* ctx, uint32_t map_id, uint32_t esdf_id, const double* robots,
+                     uint32_t n_robots, const rmp_params_t* params,
+                     const rmp_rollout_params_t* rp, rmp_stream_t stream,
+                     rmp_rollout_result_t* out);
+
+/* ------------------------------------------------------------------ diagnostics
+ * L2 read bandwidth probe (measurement support, no counterpart in the paper): reads the
+ * `bytes` at buf_dev (a multiple of 16, 16-byte aligned; sized to stay resident in L2,
+ * e.g. 32 MiB) `passes` times with 16-byte loads that bypass L1, on every SM, and XORs
+ * them into checksum_dev[0..(grid - 1)] (uint64, grid = SMs x 4 entries; keeps the loads
+ * live).  Enqueues one kernel on `stream`; the caller times it (bytes x passes / time). */
+int rmp_probe_l2_read(rmp_ctx* ctx, const void* buf_dev, size_t bytes, uint32_t passes,
+                      rmp_stream_t stream, uint64_t* checksum_dev);
+
 /* ------------------------------------------------------------------ launch tuning
  * Knobs of the evaluation kernels (per context; picked by the batch autotuner, settable by
  * hand).  They change the launch shape only: results are identical up to the order of

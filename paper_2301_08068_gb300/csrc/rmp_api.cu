@@ -31,11 +31,18 @@ struct MapRec {
 
 }  // namespace
 
+// An ESDF of primitives on the device (rmp_esdf_upload).
+struct EsdfRec {
+  rmp_primitive_t* prims = nullptr;
+  uint32_t n = 0;
+};
+
 struct rmp_ctx {
   int device = 0;
   int sm_count = 0;
   std::mutex mu;
   std::map<uint32_t, MapRec> maps;
+  std::map<uint32_t, EsdfRec> esdfs;
   uint32_t next_id = 1;
   int tune_block = 0;        // threads per CTA of the evaluation kernels (0: automatic)
   int tune_lg_segs = -1;     // log2 segments per ray (-1: chosen from the ray count)
@@ -290,6 +297,9 @@ int rmp_ctx_destroy(rmp_ctx* c) {
     std::lock_guard<std::mutex> lk(c->mu);
     for (auto& kv : c->maps) free_map(kv.second);
     c->maps.clear();
+    for (auto& kv : c->esdfs)
+      if (kv.second.prims) cudaFree(kv.second.prims);
+    c->esdfs.clear();
     if (c->ws) cudaFree(c->ws);
     if (c->result_host) cudaFreeHost(c->result_host);
   }
@@ -764,14 +774,45 @@ int rmp_combined_eval_batch_async(rmp_ctx* c, uint32_t map_id, const double* sta
                           (int)metric_mean);
 }
 
-int rmp_rollout(rmp_ctx* c, uint32_t map_id, const double* robots, uint32_t n,
-                const rmp_params_t* params, const rmp_rollout_params_t* rp, rmp_stream_t stream,
-                rmp_rollout_result_t* out) {
+}  // extern "C"
+
+namespace {
+
+// Constants of the ESDF policy from rmp_params_t (validated as for the ray policy).
+int make_esdf_consts(const rmp_params_t* p, double alpha, double beta, EsdfConsts* k) {
+  EvalConsts e;
+  const int st = make_consts(p, 1.0, 1, true, &e);
+  if (st != RMP_OK) return st;
+  if (!(std::isfinite(alpha) && alpha >= 0.0 && std::isfinite(beta) && beta >= 0.0))
+    return RMP_ERR_INVALID_ARG;
+  std::memset(k, 0, sizeof(*k));
+  k->eta_rep = p->eta_rep;
+  k->nu_rep = p->nu_rep;
+  k->eta_damp = p->eta_damp;
+  k->nu_damp = p->nu_damp;
+  k->r = p->r;
+  k->c = p->c;
+  k->eps = p->eps;
+  k->alpha = alpha;
+  k->beta = beta;
+  k->w_mode = (int)p->w_mode;
+  return RMP_OK;
+}
+
+// Closed loop of rmp_rollout (esdf null: the raycasting policy) and rmp_rollout_esdf.
+int rollout_impl(rmp_ctx* c, uint32_t map_id, const EsdfRec* esdf, const double* robots,
+                 uint32_t n, const rmp_params_t* params, const rmp_rollout_params_t* rp,
+                 rmp_stream_t stream, rmp_rollout_result_t* out) {
   if (!c || !robots || !params || !rp || !out || n == 0 || n > kMaxBatchStates)
     return RMP_ERR_INVALID_ARG;
   if (!(rp->dt > 0.0 && std::isfinite(rp->dt)) || !(rp->goal_tol >= 0.0) || rp->max_steps == 0 ||
-      rp->n_rays == 0 || rp->metric_mean > 1)
+      (!esdf && (rp->n_rays == 0 || rp->metric_mean > 1)))
     return RMP_ERR_INVALID_ARG;
+  EsdfConsts ek;
+  if (esdf) {
+    const int st = make_esdf_consts(params, rp->alpha, rp->beta, &ek);
+    if (st != RMP_OK) return st;
+  }
   DevMap dm;
   {
     std::lock_guard<std::mutex> lk(c->mu);
@@ -782,7 +823,7 @@ int rmp_rollout(rmp_ctx* c, uint32_t map_id, const double* robots, uint32_t n,
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t wsb = batch_layout(n, rp->n_rays).total;
+  const size_t wsb = esdf ? 0 : batch_layout(n, rp->n_rays).total;
   const size_t o_st = 0, o_goal = align256(48 * (size_t)n), o_nr = o_goal + align256(24 * (size_t)n),
                o_res = o_nr + align256(4 * (size_t)n),
                o_rs = o_res + align256(sizeof(rmp_result_t) * n),
@@ -825,10 +866,15 @@ int rmp_rollout(rmp_ctx* c, uint32_t map_id, const double* robots, uint32_t n,
                           step < rp->max_steps;) {
     e = cudaMemsetAsync(d_cnt, 0, 4, s);
     for (uint32_t i = 0; i < kRound && step < rp->max_steps && e == cudaSuccess; ++i, ++step) {
-      status = batch_async_impl(c, map_id, d_st, d_nr, n, rp->n_rays, params, buf + o_ws, wsb,
-                                stream, d_res, nullptr, nullptr, d_goal, rp->alpha, rp->beta,
-                                (int)rp->metric_mean);
-      if (status != RMP_OK) break;
+      if (esdf) {
+        e = launch_esdf_eval(esdf->prims, esdf->n, ek, d_st, d_goal, n, d_res, nullptr, s);
+        if (e != cudaSuccess) break;
+      } else {
+        status = batch_async_impl(c, map_id, d_st, d_nr, n, rp->n_rays, params, buf + o_ws, wsb,
+                                  stream, d_res, nullptr, nullptr, d_goal, rp->alpha, rp->beta,
+                                  (int)rp->metric_mean);
+        if (status != RMP_OK) break;
+      }
       e = launch_rollout_step(dm, rc, d_res, d_st, d_goal, d_nr, d_rs, n,
                               i + 1 == kRound || step + 1 == rp->max_steps ? d_cnt : nullptr, s);
     }
@@ -860,6 +906,106 @@ int rmp_rollout(rmp_ctx* c, uint32_t map_id, const double* robots, uint32_t n,
     r.smooth_segments = rs[b].smooth_n;
   }
   return RMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rmp_rollout(rmp_ctx* c, uint32_t map_id, const double* robots, uint32_t n,
+                const rmp_params_t* params, const rmp_rollout_params_t* rp, rmp_stream_t stream,
+                rmp_rollout_result_t* out) {
+  return rollout_impl(c, map_id, nullptr, robots, n, params, rp, stream, out);
+}
+
+int rmp_probe_l2_read(rmp_ctx* c, const void* buf_dev, size_t bytes, uint32_t passes,
+                      rmp_stream_t stream, uint64_t* checksum_dev) {
+  if (!c || !buf_dev || !checksum_dev || bytes == 0 || bytes % 16 != 0 ||
+      ((uintptr_t)buf_dev & 15u) != 0 || passes == 0)
+    return RMP_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  RMP_CUDA(launch_probe_l2((const uint4*)buf_dev, bytes / 16, passes, c->sm_count * 4,
+                           checksum_dev, (cudaStream_t)stream));
+  return RMP_OK;
+}
+
+int rmp_esdf_upload(rmp_ctx* c, const rmp_primitive_t* prims, uint32_t n, uint32_t* esdf_id) {
+  if (!c || !esdf_id || (n > 0 && !prims) || n > (1u << 20)) return RMP_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < n; ++i) {
+    const rmp_primitive_t& p = prims[i];
+    if (p.kind > RMP_PRIM_BOX || p.reserved != 0) return RMP_ERR_INVALID_ARG;
+    const int ns = p.kind == RMP_PRIM_SPHERE ? 1 : 3;
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(p.center[a])) return RMP_ERR_INVALID_ARG;
+    for (int a = 0; a < ns; ++a)
+      if (!finite_pos(p.size[a])) return RMP_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  EsdfRec r;
+  r.n = n;
+  if (n > 0) {
+    RMP_CUDA(cudaMalloc((void**)&r.prims, sizeof(rmp_primitive_t) * n));
+    const cudaError_t e = cudaMemcpy(r.prims, prims, sizeof(rmp_primitive_t) * n,
+                                     cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(r.prims);
+      return cuda_status(e);
+    }
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  const uint32_t id = c->next_id++;
+  c->esdfs[id] = r;
+  *esdf_id = id;
+  return RMP_OK;
+}
+
+int rmp_esdf_release(rmp_ctx* c, uint32_t esdf_id) {
+  if (!c) return RMP_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->esdfs.find(esdf_id);
+  if (it == c->esdfs.end()) return RMP_ERR_UNKNOWN_MAP;
+  if (it->second.prims) cudaFree(it->second.prims);
+  c->esdfs.erase(it);
+  return RMP_OK;
+}
+
+int rmp_esdf_eval_async(rmp_ctx* c, uint32_t esdf_id, const double* states_dev,
+                        const double* goals_dev, uint32_t n_states, const rmp_params_t* params,
+                        double alpha, double beta, rmp_stream_t stream, rmp_result_t* out_dev,
+                        double* query_dev) {
+  if (!c || !states_dev || !out_dev || n_states == 0) return RMP_ERR_INVALID_ARG;
+  EsdfConsts k;
+  const int st = make_esdf_consts(params, alpha, beta, &k);
+  if (st != RMP_OK) return st;
+  EsdfRec r;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->esdfs.find(esdf_id);
+    if (it == c->esdfs.end()) return RMP_ERR_UNKNOWN_MAP;
+    r = it->second;
+  }
+  DeviceGuard g(c->device);
+  if (!g.ok()) return RMP_ERR_CUDA;
+  RMP_CUDA(launch_esdf_eval(r.prims, r.n, k, states_dev, goals_dev, n_states, out_dev, query_dev,
+                            (cudaStream_t)stream));
+  return RMP_OK;
+}
+
+int rmp_rollout_esdf(rmp_ctx* c, uint32_t map_id, uint32_t esdf_id, const double* robots,
+                     uint32_t n, const rmp_params_t* params, const rmp_rollout_params_t* rp,
+                     rmp_stream_t stream, rmp_rollout_result_t* out) {
+  if (!c) return RMP_ERR_INVALID_ARG;
+  EsdfRec r;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->esdfs.find(esdf_id);
+    if (it == c->esdfs.end()) return RMP_ERR_UNKNOWN_MAP;
+    r = it->second;
+  }
+  return rollout_impl(c, map_id, &r, robots, n, params, rp, stream, out);
 }
 
 int rmp_raycast_eval_batch_async(rmp_ctx* c, uint32_t map_id, const double* states_dev,

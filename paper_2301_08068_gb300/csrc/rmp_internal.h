@@ -169,6 +169,14 @@ inline unsigned long long pack_key(int bx, int by, int bz) {
          ((unsigned long long)(uint32_t)(bz + kKeyBias) << 42);
 }
 
+// ESDF policy constants (FP64) of one evaluation.
+struct EsdfConsts {
+  double eta_rep, nu_rep, eta_damp, nu_damp, r, c, eps;
+  double alpha, beta;       // attractor (with goals)
+  int w_mode;
+  int pad;
+};
+
 // Launchers (rmp_kernels.cu).  All enqueue on `stream` and return cudaGetLastError().
 size_t raycast_smem_bytes(const DevMap& m);
 size_t batch_smem_bytes(const DevMap& m, int block);   // + the staged bricks, per warp
@@ -188,6 +196,13 @@ cudaError_t launch_batch(const DevMap& m, const EvalConsts& k, const double* sta
                          const double* goals_dev = nullptr);
 // One control step of every robot (see rollout_step_kernel); counts running robots into
 // *running (which the caller zeroes) when running is not null.
+// L2 read-bandwidth probe (see rmp_probe_l2_read): grid CTAs of 512 threads.
+cudaError_t launch_probe_l2(const uint4* buf, size_t n16, uint32_t passes, int grid,
+                            uint64_t* checksum, cudaStream_t stream);
+// The ESDF policy for n states, one warp each (see rmp_esdf_eval_async).
+cudaError_t launch_esdf_eval(const rmp_primitive_t* prims, uint32_t n_prims, const EsdfConsts& k,
+                             const double* states, const double* goals, uint32_t n_states,
+                             rmp_result_t* out, double* query, cudaStream_t stream);
 cudaError_t launch_rollout_step(const DevMap& m, const RolloutConsts& rc, const rmp_result_t* res,
                                 double* states, const double* goals, uint32_t* n_rays,
                                 RolloutDev* rs, uint32_t n, uint32_t* running,

@@ -1948,6 +1948,202 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
   if (staged && bm_timeout && threadIdx.x == 0) bulk_load_wait(&bm_bar);   // let a late copy land
 }
 
+// ------------------------------------------------------------------ L2 bandwidth probe
+// Reads n16 uint4 words `passes` times, grid-stride, 16-byte loads cached in L2 only
+// (ld.global.cg), four independent loads in flight per thread; XOR of everything read per
+// CTA into checksum[blockIdx.x].
+__global__ void __launch_bounds__(512) probe_l2_kernel(const uint4* __restrict__ buf, size_t n16,
+                                                       uint32_t passes, uint64_t* checksum) {
+  uint32_t acc = 0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (uint32_t p = 0; p < passes; ++p) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n16; i += 4 * stride) {
+      const uint4 a = __ldcg(buf + i), b = __ldcg(buf + i + stride),
+                  c = __ldcg(buf + i + 2 * stride), d = __ldcg(buf + i + 3 * stride);
+      acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^
+             d.z ^ d.w;
+    }
+    for (; i < n16; i += stride) {
+      const uint4 a = __ldcg(buf + i);
+      acc ^= a.x ^ a.y ^ a.z ^ a.w;
+    }
+  }
+  acc = __reduce_xor_sync(0xffffffffu, acc);
+  __shared__ uint32_t warp_acc[16];
+  if ((threadIdx.x & 31) == 0) warp_acc[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) t ^= warp_acc[w];
+    checksum[blockIdx.x] = t;
+  }
+}
+
+// ------------------------------------------------------------------ ESDF policy (Sec. III-D)
+// Signed distance of one primitive at x, in the fixed FP64 order of the ABI's definition
+// (explicitly rounded operations: no contraction may change the distance or the argmin).
+__device__ __forceinline__ double esdf_prim_sdf(const rmp_primitive_t& p, const double x[3]) {
+  const double q0 = __dsub_rn(x[0], p.center[0]), q1 = __dsub_rn(x[1], p.center[1]),
+               q2 = __dsub_rn(x[2], p.center[2]);
+  if (p.kind == RMP_PRIM_SPHERE)
+    return __dsub_rn(__dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)),
+                                          __dmul_rn(q2, q2))),
+                     p.size[0]);
+  const double a0 = __dsub_rn(fabs(q0), p.size[0]), a1 = __dsub_rn(fabs(q1), p.size[1]),
+               a2 = __dsub_rn(fabs(q2), p.size[2]);
+  const double o0 = a0 > 0.0 ? a0 : 0.0, o1 = a1 > 0.0 ? a1 : 0.0, o2 = a2 > 0.0 ? a2 : 0.0;
+  const double out = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(o0, o0), __dmul_rn(o1, o1)),
+                                          __dmul_rn(o2, o2)));
+  double in = a0 > a1 ? a0 : a1;
+  in = in > a2 ? in : a2;
+  in = in < 0.0 ? in : 0.0;
+  return __dadd_rn(out, in);
+}
+
+// Gradient of one primitive's distance at x (unit, pointing away from the primitive).
+__device__ __forceinline__ void esdf_prim_grad(const rmp_primitive_t& p, const double x[3],
+                                               double g[3]) {
+  const double q[3] = {__dsub_rn(x[0], p.center[0]), __dsub_rn(x[1], p.center[1]),
+                       __dsub_rn(x[2], p.center[2])};
+  if (p.kind == RMP_PRIM_SPHERE) {
+    const double L = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(q[0], q[0]), __dmul_rn(q[1], q[1])),
+                                          __dmul_rn(q[2], q[2])));
+    for (int a = 0; a < 3; ++a) g[a] = L > 0.0 ? __ddiv_rn(q[a], L) : 0.0;
+    return;
+  }
+  double ai[3], o[3];
+  for (int a = 0; a < 3; ++a) {
+    ai[a] = __dsub_rn(fabs(q[a]), p.size[a]);
+    o[a] = ai[a] > 0.0 ? ai[a] : 0.0;
+  }
+  const double out = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(o[0], o[0]), __dmul_rn(o[1], o[1])),
+                                          __dmul_rn(o[2], o[2])));
+  if (out > 0.0) {
+    for (int a = 0; a < 3; ++a) g[a] = __ddiv_rn(q[a] < 0.0 ? -o[a] : o[a], out);
+    return;
+  }
+  const int k = (ai[0] >= ai[1] && ai[0] >= ai[2]) ? 0 : (ai[1] >= ai[2] ? 1 : 2);
+  for (int a = 0; a < 3; ++a) g[a] = a == k ? (q[a] < 0.0 ? -1.0 : 1.0) : 0.0;
+}
+
+// One warp per state: the lanes scan the primitives (lane i: i, i + 32, ...), the warp keeps
+// the smallest distance (lowest index on ties: the first minimum of a sequential scan);
+// lane 0 evaluates the obstacle policy of Sec. III-C on (d, gradient) in FP64 and adds the
+// attractor; the warp resolves Eq. (1).
+__global__ void __launch_bounds__(256) esdf_eval_kernel(const rmp_primitive_t* __restrict__ prims,
+                                                        uint32_t n_prims, EsdfConsts k,
+                                                        const double* __restrict__ states,
+                                                        const double* __restrict__ goals,
+                                                        uint32_t n_states, rmp_result_t* out,
+                                                        double* query) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < n_states;
+       b += n_warps) {
+    const double* st = states + 6 * (size_t)b;
+    const double x[3] = {st[0], st[1], st[2]};
+    const double v[3] = {st[3], st[4], st[5]};
+    bool bad = false;
+    for (int a = 0; a < 6; ++a) bad = bad || !isfinite(st[a]);
+    double best = INFINITY;
+    uint32_t bi = 0xffffffffu;
+    if (!bad)
+      for (uint32_t i = lane; i < n_prims; i += 32) {
+        const double sd = esdf_prim_sdf(prims[i], x);
+        if (sd < best) {                  // strict: a lane's earlier primitive wins ties
+          best = sd;
+          bi = i;
+        }
+      }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double b2 = __shfl_down_sync(0xffffffffu, best, off);
+      const uint32_t i2 = __shfl_down_sync(0xffffffffu, bi, off);
+      if (b2 < best || (b2 == best && i2 < bi)) {
+        best = b2;
+        bi = i2;
+      }
+    }
+    double tv[9] = {0., 0., 0., 0., 0., 0., 0., 0., 0.};
+    double d = INFINITY, g[3] = {0.0, 0.0, 0.0};
+    unsigned hit = 0, act = 0;
+    if (lane == 0 && !bad) {
+      if (bi != 0xffffffffu) {
+        d = best > 0.0 ? best : 0.0;
+        esdf_prim_grad(prims[bi], x, g);
+        hit = 1;
+        // obstacle policy (Sec. III-C) on the single pair (d, r = g), FP64
+        const double xr = __dadd_rn(__dadd_rn(__dmul_rn(v[0], g[0]), __dmul_rn(v[1], g[1])),
+                                    __dmul_rn(v[2], g[2]));
+        const bool active = xr < 0.0, in_r = d < k.r;
+        act = (active && in_r) ? 1u : 0u;
+        const double frep = k.eta_rep * exp(-d / k.nu_rep);
+        const double m = active ? xr * xr : 0.0;
+        const double kd = k.eta_damp / (d / k.nu_damp + k.eps);
+        const double z = kd * m;                          // |f_damp|
+        double w = 0.0;
+        if (in_r) {
+          const double y = (k.r - d) / k.r;               // 1 - d / r, exact difference
+          w = k.w_mode == 0 ? y * y : y * y * (1.0 + 2.0 * (d / k.r));
+        }
+        const double h = z + k.c * log1p(exp(-2.0 * k.c * z));
+        const double sc = h > 0.0 ? z / h : 0.0;
+        const double alpha_m = w * sc * sc;               // A = alpha_m r r^T
+        const double fr = frep + z;                       // f = fr r
+        tv[0] = alpha_m * g[0] * g[0];
+        tv[1] = alpha_m * g[0] * g[1];
+        tv[2] = alpha_m * g[0] * g[2];
+        tv[3] = alpha_m * g[1] * g[1];
+        tv[4] = alpha_m * g[1] * g[2];
+        tv[5] = alpha_m * g[2] * g[2];
+        const double rf = fr * ((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);
+        for (int a = 0; a < 3; ++a) tv[6 + a] = alpha_m * rf * g[a];
+      }
+      if (goals) {                                         // attractor, metric I (Eq. 1)
+        const double* gl = goals + 3 * (size_t)b;
+        const double e0 = gl[0] - x[0], e1 = gl[1] - x[1], e2 = gl[2] - x[2];
+        const double zz = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+        const double hh = zz + k.c * log1p(exp(-2.0 * k.c * zz));
+        tv[0] += 1.0;
+        tv[3] += 1.0;
+        tv[5] += 1.0;
+        tv[6] += k.alpha * (e0 / hh) - k.beta * v[0];
+        tv[7] += k.alpha * (e1 / hh) - k.beta * v[1];
+        tv[8] += k.alpha * (e2 / hh) - k.beta * v[2];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) tv[i] = __shfl_sync(0xffffffffu, tv[i], 0);
+    rmp_result_t r;
+    resolve_pinv(tv, tv + 6, r);
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) r.A[i] = tv[i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) r.Af[i] = tv[6 + i];
+      r.n_rays = 1;
+      r.n_hits = hit;
+      r.n_active = act;
+      r.status = bad ? RMP_ERR_INVALID_ARG : RMP_OK;
+      r.reserved = 0;
+      if (bad) {
+        r.f[0] = r.f[1] = r.f[2] = 0.0;
+        r.eig[0] = r.eig[1] = r.eig[2] = 0.0;
+        r.rank = 0;
+      }
+      out[b] = r;
+      if (query) {
+        double* qd = query + 4 * (size_t)b;
+        qd[0] = d;
+        qd[1] = g[0];
+        qd[2] = g[1];
+        qd[3] = g[2];
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ LiDAR scan kernel (Sec. III-G)
 template <int RED>
 __global__ void __launch_bounds__(256) scan_rmp_kernel(const float* __restrict__ pts,
@@ -2463,6 +2659,24 @@ cudaError_t launch_rollout_step(const DevMap& m, const RolloutConsts& rc, const 
   else
     rollout_step_kernel<RMP_MAP_HASHED_TSDF, kLayoutHash><<<grid, block, 0, stream>>>(
         m, rc, res, states, goals, n_rays, rs, n, running);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_l2(const uint4* buf, size_t n16, uint32_t passes, int grid,
+                            uint64_t* checksum, cudaStream_t stream) {
+  probe_l2_kernel<<<grid, 512, 0, stream>>>(buf, n16, passes, checksum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_esdf_eval(const rmp_primitive_t* prims, uint32_t n_prims, const EsdfConsts& k,
+                             const double* states, const double* goals, uint32_t n_states,
+                             rmp_result_t* out, double* query, cudaStream_t stream) {
+  if (n_states == 0) return cudaSuccess;
+  const uint32_t warps = 8;                         // states per 256-thread CTA
+  uint32_t grid = (n_states + warps - 1) / warps;
+  if (grid > 65535) grid = 65535;                   // warp-stride beyond
+  esdf_eval_kernel<<<grid, 32 * warps, 0, stream>>>(prims, n_prims, k, states, goals, n_states,
+                                                     out, query);
   return cudaGetLastError();
 }
 

@@ -95,6 +95,14 @@ class rmp_server_stats_t(C.Structure):
                                           "mem_high_water")]
 
 
+class rmp_primitive_t(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("reserved", C.c_uint32), ("center", C.c_double * 3),
+                ("size", C.c_double * 3)]
+
+
+RMP_PRIM_SPHERE, RMP_PRIM_BOX = 0, 1
+
+
 class rmp_map_info_t(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_bricks", C.c_uint32), ("hash_capacity", C.c_uint32),
                 ("layout", C.c_uint32), ("device_bytes", C.c_uint64)]
@@ -154,6 +162,13 @@ _SIGNATURES = {
     "rmp_server_stats": [_P, C.POINTER(rmp_server_stats_t)],
     "rmp_batch_autotune": [_P, C.c_uint32, _P, _P, C.c_uint32, C.c_uint32, C.POINTER(rmp_params_t),
                            _P, C.c_size_t, _P, _P, C.c_int, _P, C.c_int],
+    "rmp_probe_l2_read": [_P, _P, C.c_size_t, C.c_uint32, _P, _P],
+    "rmp_esdf_upload": [_P, _P, C.c_uint32, C.POINTER(C.c_uint32)],
+    "rmp_esdf_release": [_P, C.c_uint32],
+    "rmp_esdf_eval_async": [_P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(rmp_params_t), C.c_double,
+                            C.c_double, _P, _P, _P],
+    "rmp_rollout_esdf": [_P, C.c_uint32, C.c_uint32, _P, C.c_uint32, C.POINTER(rmp_params_t),
+                         C.POINTER(rmp_rollout_params_t), _P, _P],
 }
 # Symbols every build must export (checked by the not-gpu ABI test against include/rmp.h).
 EXPORTS = sorted(list(_SIGNATURES) + ["rmp_status_string", "rmp_workspace_bytes",
@@ -414,6 +429,64 @@ def rmp_rollout(ctx: int, map_id: int, robots, params: rmp_params_t, rp: rmp_rol
     out = (rmp_rollout_result_t * rb.shape[0])()
     _check(lib().rmp_rollout(ctx, int(map_id), rb.ctypes.data, int(rb.shape[0]), C.byref(params),
                              C.byref(rp), _stream(stream), out), "rmp_rollout")
+    return [dict(x=np.array(r.x[:]), xdot=np.array(r.xdot[:]), path_length=r.path_length,
+                 smoothness=r.smoothness, status=int(r.status), steps=int(r.steps),
+                 smooth_n=int(r.smooth_segments)) for r in out]
+
+
+def primitives(prims) -> "C.Array":
+    """rmp_primitive_t records from objects with .kind ("sphere" / "box"), .center and .size
+    (sphere: radius; box: half-extents)."""
+    arr = (rmp_primitive_t * max(1, len(prims)))()
+    for i, pr in enumerate(prims):
+        arr[i].kind = RMP_PRIM_SPHERE if pr.kind == "sphere" else RMP_PRIM_BOX
+        sz = np.asarray(pr.size, np.float64).reshape(-1)
+        for a in range(3):
+            arr[i].center[a] = float(pr.center[a])
+            arr[i].size[a] = float(sz[a] if sz.size == 3 else sz[0])
+    return arr
+
+
+def rmp_probe_l2_read(ctx: int, buf, passes: int, checksum, stream=None):
+    """L2 read-bandwidth probe over the device tensor buf (contiguous, bytes % 16 == 0);
+    checksum: device uint64 tensor with at least SMs x 4 entries."""
+    _check(lib().rmp_probe_l2_read(ctx, _dptr(buf), buf.numel() * buf.element_size(),
+                                   int(passes), _stream(stream), _dptr(checksum)),
+           "rmp_probe_l2_read")
+
+
+def rmp_esdf_upload(ctx: int, prims) -> int:
+    """Upload an ESDF of primitives (see primitives()); returns its id."""
+    arr = primitives(prims)
+    out = C.c_uint32(0)
+    _check(lib().rmp_esdf_upload(ctx, C.cast(arr, C.c_void_p), len(prims), C.byref(out)),
+           "rmp_esdf_upload")
+    return out.value
+
+
+def rmp_esdf_release(ctx: int, esdf_id: int):
+    _check(lib().rmp_esdf_release(ctx, int(esdf_id)), "rmp_esdf_release")
+
+
+def rmp_esdf_eval_async(ctx: int, esdf_id: int, states, goals, n_states: int,
+                        params: rmp_params_t, alpha: float, beta: float, out, query=None,
+                        stream=None):
+    """ESDF policy (Sec. III-D) for n_states device states (n x 6 float64), with the attractor
+    when goals (n x 3 float64, device) is given; out: n x RESULT_BYTES device bytes."""
+    _check(lib().rmp_esdf_eval_async(ctx, int(esdf_id), _dptr(states), _dptr(goals),
+                                     int(n_states), C.byref(params), float(alpha), float(beta),
+                                     _stream(stream), _dptr(out), _dptr(query)),
+           "rmp_esdf_eval_async")
+
+
+def rmp_rollout_esdf(ctx: int, map_id: int, esdf_id: int, robots, params: rmp_params_t,
+                     rp: rmp_rollout_params_t, stream=None) -> list:
+    """As rmp_rollout with the ESDF policy (collisions from the voxel map)."""
+    rb = np.ascontiguousarray(robots, np.float64).reshape(-1, 9)
+    out = (rmp_rollout_result_t * rb.shape[0])()
+    _check(lib().rmp_rollout_esdf(ctx, int(map_id), int(esdf_id), rb.ctypes.data,
+                                  int(rb.shape[0]), C.byref(params), C.byref(rp),
+                                  _stream(stream), out), "rmp_rollout_esdf")
     return [dict(x=np.array(r.x[:]), xdot=np.array(r.xdot[:]), path_length=r.path_length,
                  smoothness=r.smoothness, status=int(r.status), steps=int(r.steps),
                  smooth_n=int(r.smooth_segments)) for r in out]

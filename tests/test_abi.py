@@ -64,6 +64,8 @@ int main(void) {
          sizeof(rmp_rollout_params_t), sizeof(rmp_rollout_result_t));
   O(rmp_rollout_params_t, max_steps); O(rmp_rollout_result_t, status);
   O(rmp_rollout_result_t, smooth_segments);
+  printf("\\"rmp_primitive_t\\": %zu,\\n", sizeof(rmp_primitive_t));
+  O(rmp_primitive_t, center); O(rmp_primitive_t, size);
   printf("\\"end\\": 0}\\n");
   return 0;
 }
@@ -73,13 +75,14 @@ int main(void) {
     got = json.loads(subprocess.check_output([str(exe)]))
     for T in ("rmp_params_t", "rmp_result_t", "rmp_ray_hit_t", "rmp_map_desc_t", "rmp_map_info_t",
               "rmp_launch_info_t", "rmp_server_config_t", "rmp_server_stats_t",
-              "rmp_rollout_params_t", "rmp_rollout_result_t"):
+              "rmp_rollout_params_t", "rmp_rollout_result_t", "rmp_primitive_t"):
         assert C.sizeof(getattr(rmp, T)) == got[T], T
     for key, off in got.items():
         if "." in key:
             T, f = key.split(".")
             assert getattr(getattr(rmp, T), f).offset == off, key
     assert got["rmp_result_t"] == 144 and got["rmp_ray_hit_t"] == 24
+    assert got["rmp_primitive_t"] == 56
 
 
 def test_c_program_links_and_calls_host_functions(rmp, tmp_path):

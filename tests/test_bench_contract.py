@@ -43,8 +43,9 @@ def test_whole_job_rate():
 
 def test_traffic_only_for_the_captured_launch():
     d = json.load(open(os.path.join(ROOT, "profiles", "raycast_hashed_65536_traffic.json")))
-    assert bench.committed_traffic(d["kernel_launch_sha256_16"]) == d["dram_bytes_per_launch"]
-    assert bench.committed_traffic("0" * 16) is None
+    got = bench.committed_counters(d["kernel_launch_sha256_16"])
+    assert got["dram_bytes_per_launch"] == d["dram_bytes_per_launch"]
+    assert bench.committed_counters("0" * 16) == {}
     launch = {"block": 256, "grid": 256, "lg_segments": 0, "ray_cells": 1296, "smem_bytes": 16256}
     other = dict(launch, block=128, grid=512)
     assert bench.kernel_source_hash(launch) == bench.kernel_source_hash(dict(launch))
