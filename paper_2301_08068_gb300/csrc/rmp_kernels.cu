@@ -145,12 +145,12 @@ __device__ __forceinline__ void load_brick(const uint4* src, Brick& br) {
 }
 
 // Occupancy of voxel k in the register brick: word (ly>>2) + 2 lz picked by a select
-// tree (no local memory), bit lx + 8 (ly & 3).
-// The same test on a brick staged in shared memory word-major: word q of the lane's brick
-// at sb[32 q] (sb = the warp's 16 x 32 words + lane), so a warp's lanes never share a bank.
-__device__ __forceinline__ bool smem_brick_bit(const uint32_t* sb, int kx, int ky, int kz) {
-  const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
-  return (sb[32 * ((ly >> 2) + 2 * lz)] >> (lx + 8 * (ly & 3))) & 1u;
+// tree (no local memory), bit lx + 8 (ly & 3) -- bit p = lx + 8 ly + 64 lz of the brick.
+// The same test on a brick staged in shared memory word-major, by bit index p: word q of
+// the lane's brick at sb[32 q] (sb = the warp's 16 x 32 words + lane), so a warp's lanes
+// never share a bank.
+__device__ __forceinline__ bool smem_brick_bit(const uint32_t* sb, uint32_t p) {
+  return (sb[32 * (p >> 5)] >> (p & 31u)) & 1u;
 }
 
 __device__ __forceinline__ void store_smem_brick(const uint4* src, uint32_t* sb) {
@@ -416,18 +416,33 @@ __device__ __forceinline__ void state_at(const RayFx& r, long long R_fx, uint32_
   st.a_last = any ? ba : 1;
 }
 
+// Crossings of every axis still within the limits L from state st: per axis the count of
+// boundaries N_a + 2^16 m (m >= 0) with N_a + 2^16 m <= L_a (none where |D_a| = 0: then
+// N_a = 1 > L_a = 0).  The march takes crossings in time order and a crossing is within the
+// limit exactly when its time is at most the piece's end, so the piece reaches its limit
+// exactly when st.steps has grown by this count.
+__device__ __forceinline__ uint32_t crossings_within(const uint32_t N[3], const uint32_t L[3]) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) c += N[a] <= L[a] ? ((L[a] - N[a]) >> 16) + 1u : 0u;
+  return c;
+}
+
 // March a piece from state st until a hit, a map exit, the limits L (returns `at_limit`) or
 // `budget` block visits (returns kBudgetOut; st is then a state from which march_run
 // continues exactly).  Each visit of the outer loop either crosses a free box of blocks
-// (skip_box) or enters an occupied block, whose brick is held in registers while the inner
-// loop steps voxel by voxel, the order of the next crossings kept in the exact differences
-// E_ab = N_a |D_b| - N_b |D_a|.  SB: the brick is held in shared memory (`sb`, the lane's
-// column of its warp's 16 x 32 words) instead of 16 registers -- for the 64-register batch
-// kernel, where it trades register spills for one shared load per step.
-template <int KIND, int LAYOUT, bool CELLS, bool SB = false>
+// (skip_box) or enters an occupied block, whose brick is staged in the lane's column of
+// shared memory (`sb`: word q at sb[32 q], so a warp's lanes never share a bank) while the
+// inner loop steps voxel by voxel, the order of the next crossings kept in the exact
+// differences E_ab = N_a |D_b| - N_b |D_a|.  Per step the inner loop keeps only what the
+// next step needs: the voxel, its brick bit index p = lx + 8 ly + 64 lz (brick word p / 32,
+// bit p % 32), the crossing numerators and the number of crossings left before the limit;
+// the step count and the entry crossing of the current voxel are brought up to date when
+// the walk leaves the block.
+template <int KIND, int LAYOUT, bool CELLS>
 __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, MarchState& st,
                                          const RayFx& r, const uint32_t L[3], int at_limit,
-                                         uint32_t budget, uint32_t* sb = nullptr) {
+                                         uint32_t budget, uint32_t* sb) {
   if (outside<KIND>(m, st.k)) return RMP_RAY_MISS_EXIT;
   const uint32_t* A = r.A;
   const int* s = r.s;
@@ -435,6 +450,9 @@ __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, Ma
   uint32_t* N = st.N;
   const float rA[3] = {__frcp_rn(__uint2float_rn(A[0])), __frcp_rn(__uint2float_rn(A[1])),
                        __frcp_rn(__uint2float_rn(A[2]))};
+  const uint32_t lim_steps = st.steps + crossings_within(N, L);
+  // brick-index change of one step along each axis
+  const int d0 = s[0], d1 = 8 * s[1], d2 = 64 * s[2];
   const uint32_t guard = 8u * (kMaxRangeVoxels + 2);
   const uint32_t iters = budget < guard ? budget : guard;
   int status = budget < guard ? kBudgetOut : at_limit;
@@ -469,10 +487,9 @@ __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, Ma
       }
       continue;
     }
-    Brick w;
-    if (SB) store_smem_brick(src, sb);
-    else load_brick(src, w);
-    if (SB ? smem_brick_bit(sb, k[0], k[1], k[2]) : brick_bit(w, k[0], k[1], k[2])) {
+    store_smem_brick(src, sb);
+    uint32_t p = (uint32_t)((k[0] & 7) | ((k[1] & 7) << 3) | ((k[2] & 7) << 6));
+    if (smem_brick_bit(sb, p)) {
       status = RMP_RAY_HIT;
       break;
     }
@@ -482,27 +499,28 @@ __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, Ma
     long long eyz = (long long)N[1] * A[2] - (long long)N[2] * A[1];
     const long long u0 = (long long)A[0] << 16, u1 = (long long)A[1] << 16,
                     u2 = (long long)A[2] << 16;
+    const uint32_t rem0 = lim_steps - st.steps;   // crossings left within the limit
+    uint32_t rem = rem0;
+    int axl = 0;                                  // axis of the walk's latest step
     int fin = 0;
     // at most 21 interior steps and one exit step inside an 8^3 block
     for (int j = 0; j < 24; ++j) {
-      const bool ylx = exy > 0;
-      const bool zlw = ylx ? (eyz > 0) : (exz > 0);
-      const int ax = zlw ? 2 : (ylx ? 1 : 0);
-      const uint32_t na = sel3(N, ax), aa = sel3(A, ax), la = sel3(L, ax);
-      if (na > la) {                                   // next crossing beyond the limit
+      if (rem == 0u) {                                 // next crossing beyond the limit
         fin = 1;
         break;
       }
-      st.n_last = na;
-      st.a_last = aa;
-      st.ax_last = ax;
-      st.steps += 1;
+      const bool ylx = exy > 0;
+      const bool zlw = ylx ? (eyz > 0) : (exz > 0);
+      const int ax = zlw ? 2 : (ylx ? 1 : 0);
+      --rem;
+      axl = ax;
       bool crossed = false;
       if (ax == 0) {
         const int kn = k[0] + s[0];
         crossed = ((kn ^ k[0]) & ~7) != 0;
         k[0] = kn;
         N[0] += 65536u;
+        p += d0;
         exy += u1;
         exz += u2;
       } else if (ax == 1) {
@@ -510,6 +528,7 @@ __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, Ma
         crossed = ((kn ^ k[1]) & ~7) != 0;
         k[1] = kn;
         N[1] += 65536u;
+        p += d1;
         exy -= u0;
         eyz += u2;
       } else {
@@ -517,6 +536,7 @@ __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, Ma
         crossed = ((kn ^ k[2]) & ~7) != 0;
         k[2] = kn;
         N[2] += 65536u;
+        p += d2;
         exz -= u0;
         eyz -= u1;
       }
@@ -525,10 +545,16 @@ __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, Ma
         break;
       }
       if (crossed) break;
-      if (SB ? smem_brick_bit(sb, k[0], k[1], k[2]) : brick_bit(w, k[0], k[1], k[2])) {
+      if (smem_brick_bit(sb, p)) {
         fin = 3;
         break;
       }
+    }
+    if (rem != rem0) {                                 // the walk took steps
+      st.steps += rem0 - rem;
+      st.ax_last = axl;
+      st.n_last = sel3(N, axl) - 65536u;
+      st.a_last = sel3(A, axl);
     }
     if (fin) {
       status = fin == 1 ? at_limit : (fin == 2 ? RMP_RAY_MISS_EXIT : RMP_RAY_HIT);
@@ -766,11 +792,13 @@ struct Acc64 {
   double s[9];
 };
 
-// Sums of one CTA handed from the block reduction to grid_finish: the 9 terms and the hit
-// and active counts.  In shared memory, written by lanes 0-10 of warp 0 (lane q < 9: term q;
-// lanes 9, 10: the counts), which are the lanes that read them again.
+// Sums of one CTA handed from the block reduction to grid_finish: the 9 terms (FP64 value
+// v, and for the compensated reduction also the unevaluated FP32 pair s + c it came from)
+// and the hit and active counts.  In shared memory, written by lanes 0-10 of warp 0 (lane
+// q < 9: term q; lanes 9, 10: the counts), which are the lanes that read them again.
 struct CtaSums {
   double v[9];
+  float s[9], c[9];
   unsigned u[2];
 };
 
@@ -824,6 +852,8 @@ struct BlockReduce<RMP_REDUCE_KAHAN32> {
       if (lane < 9) {
         float s = sh[0][lane], c = sh[0][9 + lane];
         for (int w = 1; w < nw; ++w) merge1(s, c, sh[w][lane], sh[w][9 + lane]);
+        out.s[lane] = s;
+        out.c[lane] = c;
         out.v[lane] = (double)s + (double)c;
       } else if (lane < 11) {
         unsigned t = 0;
@@ -1063,107 +1093,174 @@ __device__ void resolve_pinv_cta(const double* S, const double* b, rmp_result_t&
   resolve_finish(S, b, W, fa_sh[0], fa_sh[1], fa_sh[2], ok_sh, r);
 }
 
-// Sum `count` partials in a fixed order: thread (q, j) of the CTA (q < 11 terms, j < J =
-// blockDim / 16, a power of two) adds partials j, j + J, ... of term q; the J threads of a
-// term (adjacent lanes of one warp) then combine their sums by a shuffle tree.  Result in
-// tot / tot_h / tot_a.  Called by every thread.
-__device__ void sum_partials(const CtaPartial* p, int count, double* tot, unsigned* tot_h,
-                             unsigned* tot_a) {
-  const int J = blockDim.x >> 4;
-  const int q = threadIdx.x / J, j = threadIdx.x - q * J;
-  double s = 0.0;
-  unsigned u = 0;
-  if (q < 9) {
-    for (int i = j; i < count; i += J) s += __ldcg(&p[i].v[q]);
-  } else if (q < 11) {
-    for (int i = j; i < count; i += J) u += __ldcg(q == 9 ? &p[i].n_hits : &p[i].n_active);
+// A partial in the workspace (80 bytes, one per CTA and one per group): the compensated
+// reduction stores each term as its FP32 pair (s, c), the FP64 reduction as a double
+// (CtaPartial).  Both are read back as five 16-byte words.
+struct CtaPartial32 {
+  float s[9], c[9];
+  unsigned n_hits, n_active;
+};
+static_assert(sizeof(CtaPartial32) == sizeof(CtaPartial) && sizeof(CtaPartial) == 80,
+              "partials are five 16-byte words");
+
+__device__ __forceinline__ void load_partial_words(const CtaPartial* p, uint32_t w[20]) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+  uint4 v[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) v[i] = __ldcg(q + i);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    w[4 * i] = v[i].x;
+    w[4 * i + 1] = v[i].y;
+    w[4 * i + 2] = v[i].z;
+    w[4 * i + 3] = v[i].w;
   }
-  for (int off = J >> 1; off > 0; off >>= 1) {
-    s += __shfl_down_sync(0xffffffffu, s, off, J);
-    u += __shfl_down_sync(0xffffffffu, u, off, J);
+}
+
+// Storing a CTA's (or a group's) sums as a partial, lanes 0-10 of warp 0 one field each,
+// and starting a thread's accumulator from the words of a partial / merging one into it.
+template <int RED>
+struct PartialIO;
+
+template <>
+struct PartialIO<RMP_REDUCE_KAHAN32> {
+  __device__ static void store(CtaPartial* slot, const CtaSums& cs, int t) {
+    CtaPartial32* p = reinterpret_cast<CtaPartial32*>(slot);
+    if (t < 9) {
+      p->s[t] = cs.s[t];
+      p->c[t] = cs.c[t];
+    } else if (t == 9) {
+      p->n_hits = cs.u[0];
+    } else if (t == 10) {
+      p->n_active = cs.u[1];
+    }
   }
-  if (j == 0) {
-    if (q < 9) tot[q] = s;
-    else if (q == 9) *tot_h = u;
-    else if (q == 10) *tot_a = u;
+  __device__ static void set(Acc32& a, const uint32_t w[20]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      a.s[q] = __uint_as_float(w[q]);
+      a.c[q] = __uint_as_float(w[9 + q]);
+    }
   }
+  __device__ static void merge(Acc32& a, const uint32_t w[20]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) merge1(a.s[q], a.c[q], __uint_as_float(w[q]), __uint_as_float(w[9 + q]));
+  }
+};
+
+template <>
+struct PartialIO<RMP_REDUCE_FP64> {
+  __device__ static void store(CtaPartial* slot, const CtaSums& cs, int t) {
+    if (t < 9) slot->v[t] = cs.v[t];
+    else if (t == 9) slot->n_hits = cs.u[0];
+    else if (t == 10) slot->n_active = cs.u[1];
+  }
+  __device__ static double word_pair(const uint32_t w[20], int q) {
+    return __hiloint2double((int)w[2 * q + 1], (int)w[2 * q]);
+  }
+  __device__ static void set(Acc64& a, const uint32_t w[20]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) a.s[q] = word_pair(w, q);
+  }
+  __device__ static void merge(Acc64& a, const uint32_t w[20]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) a.s[q] += word_pair(w, q);
+  }
+};
+
+// Grid ticket: add one, acquire-release at GPU scope (the partials this CTA's warp stored
+// before are visible to whichever CTA draws the last ticket, and that CTA sees all of
+// them), returning the previous count.
+__device__ __forceinline__ unsigned ticket_add(unsigned* p) {
+  unsigned t;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(t) : "l"(p) : "memory");
+  return t;
+}
+
+// Sum `count` <= 2 blockDim partials in a fixed order: thread t loads partials t and
+// t + blockDim (all loads in flight at once: one L2 round trip instead of one per
+// partial), then the block reduction combines the threads.  Result in out (as
+// BlockReduce::reduce leaves it).  Called by every thread.
+template <int RED>
+__device__ void sum_partials(const CtaPartial* p, int count, CtaSums& out) {
+  const int t = threadIdx.x, B = blockDim.x;
+  uint32_t w0[20], w1[20];
+  const bool h0 = t < count, h1 = t + B < count;
+  if (h0) load_partial_words(p + t, w0);
+  if (h1) load_partial_words(p + t + B, w1);
+  typename BlockReduce<RED>::Acc acc;
+  BlockReduce<RED>::init(acc);
+  unsigned nh = 0, na = 0;
+  if (h0) {
+    PartialIO<RED>::set(acc, w0);
+    nh = w0[18];
+    na = w0[19];
+  }
+  if (h1) {
+    PartialIO<RED>::merge(acc, w1);
+    nh += w1[18];
+    na += w1[19];
+  }
+  BlockReduce<RED>::reduce(acc, nh, na, out);
   __syncthreads();
 }
 
 // Grid completion, deterministic and without one thread walking every CTA: lanes 0-10 of
-// warp 0 store the CTA's sums as its partial.  Up to blockDim CTAs, the last CTA to
-// finish (grid ticket) sums every partial (sum_partials: blockDim / 16 threads per term,
-// fixed order) and resolves; larger grids add a level: the last CTA of each group of kGroup CTAs
-// (group ticket) sums the group's partials into a group partial, and the last group sums
-// those.  (Each level costs a fence, a ticket and a load of partials, about 1.5 us on this
-// GPU, while one CTA sums 256 partials in well under that.)  A grid of one CTA resolves its
-// own sums.  Tickets are reset by the CTA that completes them.  Called by all threads of
-// every CTA after BlockReduce::reduce.
+// warp 0 store the CTA's sums as its partial and lane 0 draws a ticket.  Up to blockDim
+// CTAs, the last CTA to finish sums every partial (sum_partials) and resolves; larger
+// grids add a level: the last CTA of each group of kGroup CTAs (group ticket) sums the
+// group's partials into a group partial, and the last group sums those.  (Each level costs
+// a ticket and an L2 round trip of partials, about 1.5 us on this GPU.)  A grid of one CTA
+// resolves its own sums.  Tickets are reset by the CTA that completes them.  Called by all
+// threads of every CTA after BlockReduce::reduce.
+template <int RED>
 __device__ void grid_finish(const CtaSums& cta, WsHeader* ws, CtaPartial* parts,
                             rmp_result_t* out, uint32_t n_rays, int status) {
   __shared__ int stage;
-  __shared__ double tot[9];
-  __shared__ unsigned tot_h, tot_a;
+  __shared__ CtaSums gsum;
   CtaPartial* groups = parts + kMaxGrid;
   const int G = gridDim.x;
-  const bool one_level = G <= (int)blockDim.x;   // each summing thread adds <= 16 partials
+  const bool one_level = G <= (int)blockDim.x;
   const int gi = one_level ? 0 : blockIdx.x / kGroup;
   const int n_groups = one_level ? 1 : (G + kGroup - 1) / kGroup;
   const int g0 = gi * kGroup;
   const int gsz = one_level ? G : min(kGroup, G - g0);
-  if (G == 1) {
-    if (threadIdx.x < 9) tot[threadIdx.x] = cta.v[threadIdx.x];
-    else if (threadIdx.x == 9) tot_h = cta.u[0];
-    else if (threadIdx.x == 10) tot_a = cta.u[1];
-  } else {
-    if (threadIdx.x < 11) {
-      CtaPartial* mine = parts + blockIdx.x;
-      if (threadIdx.x < 9) mine->v[threadIdx.x] = cta.v[threadIdx.x];
-      else if (threadIdx.x == 9) mine->n_hits = cta.u[0];
-      else mine->n_active = cta.u[1];
-      __threadfence();
-    }
+  const CtaSums* tot = &cta;
+  if (G > 1) {
     if (threadIdx.x < 32) {
+      PartialIO<RED>::store(parts + blockIdx.x, cta, threadIdx.x);
       __syncwarp();
-      if (threadIdx.x == 0) {
-        const unsigned t = atomicAdd(&ws->group_ticket[gi], 1u);
-        stage = (t == (unsigned)gsz - 1) ? 1 : 0;
-      }
+      if (threadIdx.x == 0) stage = ticket_add(&ws->group_ticket[gi]) == (unsigned)gsz - 1 ? 1 : 0;
     }
     __syncthreads();
     if (stage == 0) return;
-    __threadfence();
-    sum_partials(parts + (one_level ? 0 : g0), gsz, tot, &tot_h, &tot_a);
+    sum_partials<RED>(parts + (one_level ? 0 : g0), gsz, gsum);
     if (n_groups > 1) {
-      if (threadIdx.x == 0) {
-        CtaPartial p;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) p.v[q] = tot[q];
-        p.n_hits = tot_h;
-        p.n_active = tot_a;
-        groups[gi] = p;
-        ws->group_ticket[gi] = 0;
-        __threadfence();
-        const unsigned t = atomicAdd(&ws->ticket, 1u);
-        stage = (t == (unsigned)n_groups - 1) ? 2 : 0;
+      if (threadIdx.x < 32) {
+        PartialIO<RED>::store(groups + gi, gsum, threadIdx.x);
+        __syncwarp();
+        if (threadIdx.x == 0) {
+          ws->group_ticket[gi] = 0;
+          stage = ticket_add(&ws->ticket) == (unsigned)n_groups - 1 ? 2 : 0;
+        }
       }
       __syncthreads();
       if (stage != 2) return;
-      __threadfence();
-      sum_partials(groups, n_groups, tot, &tot_h, &tot_a);
+      sum_partials<RED>(groups, n_groups, gsum);
     } else if (threadIdx.x == 0) {
       // a single group: its sum is the total (the same value the second level would give)
       ws->group_ticket[gi] = 0;
     }
+    tot = &gsum;
   }
   __shared__ rmp_result_t r;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int q = 0; q < 6; ++q) r.A[q] = tot[q];
-    for (int q = 0; q < 3; ++q) r.Af[q] = tot[6 + q];
+    for (int q = 0; q < 6; ++q) r.A[q] = tot->v[q];
+    for (int q = 0; q < 3; ++q) r.Af[q] = tot->v[6 + q];
     r.n_rays = n_rays;
-    r.n_hits = tot_h;
-    r.n_active = tot_a;
+    r.n_hits = tot->u[0];
+    r.n_active = tot->u[1];
     r.status = status;
     r.reserved = 0;
   }
@@ -1268,12 +1365,12 @@ __device__ __forceinline__ bool bulk_load_wait(uint64_t* bar) {
 // warp and finished, phase 1), then combine the ray's S segments -- adjacent lanes -- into
 // the first final one (lowest index), else the last one.  Warp-synchronous: every lane of
 // the warp calls it (work = false for lanes without a segment).  Returns the ray's status;
-// mo is its final state (valid in every lane of the ray's segment group).
-template <int KIND, int LAYOUT, bool CELLS, bool SB = false>
+// mo is its final state (valid in every lane of the ray's segment group).  sb: the lane's
+// shared-memory brick column.
+template <int KIND, int LAYOUT, bool CELLS>
 __device__ __forceinline__ int march_ray(const DevMap& m, const uint32_t* bm, const EvalConsts& k,
                                          const long long P[3], const Ray& ray, uint32_t seg,
-                                         uint32_t lgS, bool work, MarchState& mo,
-                                         uint32_t* sb = nullptr) {
+                                         uint32_t lgS, bool work, MarchState& mo, uint32_t* sb) {
   const uint32_t S = 1u << lgS;
   const uint32_t lane = threadIdx.x & 31;
   // this lane's piece: segment seg of the ray, grid points j_lo .. j_hi
@@ -1295,7 +1392,7 @@ __device__ __forceinline__ int march_ray(const DevMap& m, const uint32_t* bm, co
   int own_stat = kSegContinues;
   for (int phase = 0; phase < 2; ++phase) {
     if (work)
-      sstat = march_run<KIND, LAYOUT, CELLS, SB>(m, bm, so, r, L, lim,
+      sstat = march_run<KIND, LAYOUT, CELLS>(m, bm, so, r, L, lim,
                                                  phase == 0 ? k.split_budget : 0xffffffffu, sb);
     if (phase == 1) break;
     const uint32_t unfinished = __ballot_sync(0xffffffffu, work && sstat == kBudgetOut);
@@ -1427,7 +1524,7 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
     first = false;
     const long long P[3] = {cs.P[0], cs.P[1], cs.P[2]};
     MarchState mo;
-    const int mstat = march_ray<KIND, LAYOUT, CELLS, true>(m, bm, k, P, ray, seg, lgS,
+    const int mstat = march_ray<KIND, LAYOUT, CELLS>(m, bm, k, P, ray, seg, lgS,
                                                            active && !bad, mo, sbr);
     if (!active || bad || seg != 0) continue;
     float vals[9];
@@ -1440,7 +1537,7 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
   BlockReduce<RED>::reduce(acc, n_hit, n_act, sums);
   const int status = bm_timeout ? RMP_ERR_TIMEOUT
                      : ((cs.bad[0] | cs.bad[1] | cs.bad[2]) ? RMP_ERR_INVALID_ARG : RMP_OK);
-  grid_finish(sums, ws, parts, out, k.n_rays, status);
+  grid_finish<RED>(sums, ws, parts, out, k.n_rays, status);
 }
 
 // ------------------------------------------------------------------ batched evaluation
@@ -1840,7 +1937,7 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
     const uint32_t ray_idx = ray_of_slot_p(active ? slot : 0, pM, pQ, n_b - pQ * pM);
     const Ray ray = make_ray(ray_idx + k.halton_offset);
     MarchState mo;
-    const int mstat = march_ray<KIND, LAYOUT, true, true>(m, bm, k, P, ray, seg, lgS, active, mo,
+    const int mstat = march_ray<KIND, LAYOUT, true>(m, bm, k, P, ray, seg, lgS, active, mo,
                                                           sbr);
     float vals[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     unsigned nh = 0, na = 0;
@@ -2193,7 +2290,7 @@ __global__ void __launch_bounds__(256) scan_rmp_kernel(const float* __restrict__
   }
   __shared__ CtaSums sums;
   BlockReduce<RED>::reduce(acc, n_hit, n_act, sums);
-  grid_finish(sums, ws, parts, out, k.n_rays, RMP_OK);
+  grid_finish<RED>(sums, ws, parts, out, k.n_rays, RMP_OK);
 }
 
 // ------------------------------------------------------------------ map build kernels
@@ -2544,8 +2641,8 @@ int raycast_occupancy(const DevMap& m, int reduce_mode, int block) {
 cudaError_t launch_raycast(const DevMap& m, const EvalConsts& k, const double* state_dev,
                            void* ws, rmp_result_t* out_dev, rmp_ray_hit_t* hits,
                            float* per_ray, int block, int grid, cudaStream_t stream) {
-  // grid_finish needs whole warps 0 and 1 (the resolve's named barrier) and blockDim / 16
-  // a power of two (the partial sums' shuffle tree)
+  // grid_finish needs whole warps 0 and 1 (the resolve's named barrier) and at least 64
+  // threads (each summing thread takes at most two of the up to 128 group partials)
   if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
   WsHeader* hdr = (WsHeader*)ws;
   CtaPartial* parts = (CtaPartial*)((char*)ws + kWsHeaderBytes);
