@@ -262,6 +262,17 @@ def kernel_source_hash(launch: dict) -> str:
     return h.hexdigest()[:16]
 
 
+def stratified_order(costs) -> list:
+    """Indices of `costs` (a power-of-two count) such that every prefix samples the sorted
+    costs evenly: position p holds the state of cost rank bitreverse(p)."""
+    n = len(costs)
+    bits = max(1, (n - 1).bit_length())
+    assert n == 1 << bits
+    ranked = list(np.argsort(np.asarray(costs), kind="stable"))
+    rev = [int(format(p, "0%db" % bits)[::-1], 2) for p in range(n)]
+    return [int(ranked[r]) for r in rev]
+
+
 def committed_counters(src_hash: str) -> dict:
     """Per-launch counters of the raycast kernel from the committed ncu capture (DRAM bytes,
     L2 bytes, warp instructions), if it was taken on the current kernel source and launch
@@ -360,8 +371,7 @@ def batch_section(ctx, mid, flush, per_state: bool = False) -> dict:
             p = R.make_params(dict(wl.params, reduce_mode=mode), wl.max_range)
             times = R.rmp_batch_autotune(ctx.handle, mid, st, nr, B, mr, p, ws, out, reps=3)
             tuned = {"block": R.rmp_tune_get(ctx.handle, 1),
-                     "lg_segments": R.rmp_tune_get(ctx.handle, 2),
-                     "split_budget": R.rmp_tune_get(ctx.handle, 4)}
+                     "lg_segments": R.rmp_tune_get(ctx.handle, 2)}
             s = torch.cuda.Stream()
             with torch.cuda.stream(s):
                 R.rmp_raycast_eval_batch_async(ctx.handle, mid, st, nr, B, mr, p, ws, out)
@@ -868,9 +878,15 @@ def main():
     grid = launch["grid"]
     alg_bytes = float(np.mean(alg)) + grid * 80 + 48 + 144
 
+    # the states in an order stratified by their voxel-step counts (their cost): rank r of
+    # the sorted counts goes to position bitreverse(r), so every prefix of the timed steps
+    # (20 of the 64 states, say) spans the workload's range of costs evenly, and a short
+    # run measures the same mix as a long one
+    order = stratified_order(steps_per_launch)
+
     def step(i):
-        R.rmp_raycast_eval_async(ctx.handle, mid, states[i % N_STATES], N_RAYS, params, ws,
-                                 outs[i % N_STATES])
+        j = order[i % N_STATES]
+        R.rmp_raycast_eval_async(ctx.handle, mid, states[j], N_RAYS, params, ws, outs[j])
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -913,8 +929,9 @@ def main():
             flush.fill_(i & 0xFF)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            R.rmp_raycast_eval_async(ctx.handle, mid, states[i % N_STATES], N_RAYS, params, ws,
-                                     outs[i % N_STATES], hits=hits, per_ray=per_ray)
+            j = order[i % N_STATES]
+            R.rmp_raycast_eval_async(ctx.handle, mid, states[j], N_RAYS, params, ws,
+                                     outs[j], hits=hits, per_ray=per_ray)
             b.record()
             evo.append((a, b))
         torch.cuda.synchronize()
@@ -930,7 +947,7 @@ def main():
     for i in range(n_e2e):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
-        s = wl.states[i % N_STATES]
+        s = wl.states[order[i % N_STATES]]
         t = time.perf_counter()
         R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, N_RAYS, params)
         e2e_t.append(time.perf_counter() - t)
@@ -1022,6 +1039,8 @@ def main():
             "config": {"workload": WORKLOAD, "n_rays": N_RAYS, "states": N_STATES,
                        "map_blocks": wl.map.n_blocks, "parallelism": "replicas x%d" % world,
                        "l2": "flushed between timed steps (256 MiB write outside the events)",
+                       "state_order": "stratified by voxel-step count (every prefix of the "
+                                      "timed steps spans the states' cost range)",
                        "launch": launch, **summary},
             "evals_per_s": world * 1e3 / ms_max,
             "ms_per_step_p50": float(np.percentile(per, 50)),

@@ -271,12 +271,11 @@ int rmp_raycast_eval_batch(rmp_ctx* ctx, uint32_t map_id, const double* states,
                            const rmp_params_t* params, rmp_stream_t stream, rmp_result_t* out);
 
 /* Autotuner of the batch launch: times every combination of threads per CTA {64, 128,
- * 256}, segments per ray 2^{0,1,2} (rays per thread 1, 1/2, 1/4) and warp split of long
- * pieces {never, after 8 block visits} on this batch (one untimed launch, then the
- * median of `reps` timed launches, CUDA events on `stream`; synchronises), and leaves
- * the fastest in the context's knobs.  times_ms (nullable, n_times entries) receives
- * the medians in the order block-major, then segments, then split.  The workspace must
- * be sized for the batch (rmp_batch_workspace_bytes). */
+ * 256} and segments per ray 2^{0,1,2} (rays per thread 1, 1/2, 1/4) on this batch (one
+ * untimed launch, then the median of `reps` timed launches, CUDA events on `stream`;
+ * synchronises), and leaves the fastest in the context's knobs.  times_ms (nullable,
+ * n_times entries) receives the 9 medians in the order block-major, then segments.  The
+ * workspace must be sized for the batch (rmp_batch_workspace_bytes). */
 int rmp_batch_autotune(rmp_ctx* ctx, uint32_t map_id, const double* states_dev,
                        const uint32_t* n_rays_dev, uint32_t n_states, uint32_t max_rays,
                        const rmp_params_t* params, void* workspace_dev, size_t workspace_bytes,
@@ -518,9 +517,10 @@ int rmp_probe_l2_read(rmp_ctx* ctx, const void* buf_dev, size_t bytes, uint32_t 
  *                        persistent launch holds at once
  *  RMP_TUNE_RAY_ORDER    0 (default): rays of one direction cell share warps (coherent
  *                        march); 1: Halton index order
- *  RMP_TUNE_SPLIT_BUDGET block visits after which the pieces still running in a warp are
- *                        cut into sub-pieces marched by the warp's idle lanes (1..65536),
- *                        0 never, -1 (default) the library's choice (currently never)
+ *  RMP_TUNE_SPLIT_BUDGET single-state evaluations: block visits after which the pieces
+ *                        still running in a warp are cut into sub-pieces marched by the
+ *                        warp's idle lanes (1..65536), 0 never, -1 (default) the library's
+ *                        choice (currently never); batches never split
  *  RMP_TUNE_CELL_SKIP    free boxes of voxels inside occupied blocks crossed in one step
  *                        (grid layout maps): 1 always, 0 never, -1 (default) in batched
  *                        evaluations and in single-state ones marched as 4 segments per

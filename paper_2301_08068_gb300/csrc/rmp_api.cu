@@ -1058,7 +1058,6 @@ int rmp_batch_autotune(rmp_ctx* c, uint32_t map_id, const double* states_dev,
                        rmp_result_t* out_dev, int reps, float* times_ms, int n_times) {
   if (!c || reps < 1 || reps > 1000) return RMP_ERR_INVALID_ARG;
   static const int kBlocks[3] = {64, 128, 256};
-  static const int kSplits[2] = {0, 8};
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard g(c->device);
   if (!g.ok()) return RMP_ERR_CUDA;
@@ -1069,15 +1068,13 @@ int rmp_batch_autotune(rmp_ctx* c, uint32_t map_id, const double* states_dev,
     return RMP_ERR_CUDA;
   }
   float best = 3.0e38f;
-  int best_b = 128, best_l = 0, best_s = 0, idx = 0, st = RMP_OK;
+  int best_b = 128, best_l = 0, idx = 0, st = RMP_OK;
   for (int bi = 0; bi < 3 && st == RMP_OK; ++bi)
-    for (int l = 0; l <= 2 && st == RMP_OK; ++l)
-      for (int si = 0; si < 2 && st == RMP_OK; ++si, ++idx) {
+    for (int l = 0; l <= 2 && st == RMP_OK; ++l, ++idx) {
         {
           std::lock_guard<std::mutex> lk(c->mu);
           c->tune_block = kBlocks[bi];
           c->tune_lg_segs = l;
-          c->tune_split = kSplits[si];
         }
         // one untimed launch, then the median of `reps` timed ones
         st = rmp_raycast_eval_batch_async(c, map_id, states_dev, n_rays_dev, n_states, max_rays,
@@ -1102,15 +1099,13 @@ int rmp_batch_autotune(rmp_ctx* c, uint32_t map_id, const double* states_dev,
           best = med;
           best_b = kBlocks[bi];
           best_l = l;
-          best_s = kSplits[si];
         }
-      }
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   std::lock_guard<std::mutex> lk(c->mu);
   c->tune_block = best_b;
   c->tune_lg_segs = best_l;
-  c->tune_split = best_s;
   return st;
 }
 

@@ -1366,8 +1366,8 @@ __device__ __forceinline__ bool bulk_load_wait(uint64_t* bar) {
 // the first final one (lowest index), else the last one.  Warp-synchronous: every lane of
 // the warp calls it (work = false for lanes without a segment).  Returns the ray's status;
 // mo is its final state (valid in every lane of the ray's segment group).  sb: the lane's
-// shared-memory brick column.
-template <int KIND, int LAYOUT, bool CELLS>
+// shared-memory brick column.  NOSPLIT: no phase 1 (the split budget is ignored).
+template <int KIND, int LAYOUT, bool CELLS, bool NOSPLIT = false>
 __device__ __forceinline__ int march_ray(const DevMap& m, const uint32_t* bm, const EvalConsts& k,
                                          const long long P[3], const Ray& ray, uint32_t seg,
                                          uint32_t lgS, bool work, MarchState& mo, uint32_t* sb) {
@@ -1390,10 +1390,11 @@ __device__ __forceinline__ int march_ray(const DevMap& m, const uint32_t* bm, co
   bool split = false;
   MarchState own;
   int own_stat = kSegContinues;
-  for (int phase = 0; phase < 2; ++phase) {
+  for (int phase = 0; phase < (NOSPLIT ? 1 : 2); ++phase) {
     if (work)
       sstat = march_run<KIND, LAYOUT, CELLS>(m, bm, so, r, L, lim,
-                                                 phase == 0 ? k.split_budget : 0xffffffffu, sb);
+                                                 (phase == 0 && !NOSPLIT) ? k.split_budget : 0xffffffffu, sb);
+    if (NOSPLIT) break;
     if (phase == 1) break;
     const uint32_t unfinished = __ballot_sync(0xffffffffu, work && sstat == kBudgetOut);
     if (!unfinished) break;
@@ -1876,7 +1877,11 @@ __global__ void rollout_step_kernel(DevMap m, RolloutConsts rc, const rmp_result
 // depend on which warp ran which chunk.
 // Register budget 64 (launch bounds 256 x 4): 32 warps per SM instead of 16; the few
 // spills cost less than the latency the extra warps hide (measured: 3.42 against 2.77
-// Grays/s on 256 states; 80 registers 3.20, 51 registers 3.21).
+// Grays/s on 256 states; 80 registers 3.20, 51 registers 3.21; again with the current
+// march, 256 states: 64 registers 1.357 ms, 80: 1.516, 128: 1.734).  The in-warp split
+// of long pieces is compiled out (its saved piece state made most of the spills: 208 ->
+// 48 bytes; it never paid in the autotuner), and the per-state values used only after
+// the march are read after it.
 template <int KIND, int LAYOUT, int RED>
 __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
     DevMap m, EvalConsts k, BatchHeader* hdr, const BatchState* __restrict__ bs,
@@ -1924,10 +1929,7 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
     const uint32_t b = lo;
     const BatchState* sp = bs + b;
     const long long P[3] = {__ldg(&sp->P[0]), __ldg(&sp->P[1]), __ldg(&sp->P[2])};
-    const float v[3] = {__ldg(&sp->v[0]), __ldg(&sp->v[1]), __ldg(&sp->v[2])};
-    const float vl[3] = {__ldg(&sp->vl[0]), __ldg(&sp->vl[1]), __ldg(&sp->vl[2])};
     const uint32_t n_b = __ldg(&sp->n_rays), chunk0 = __ldg(&sp->chunk0);
-    const uint32_t n_chunks = __ldg(&sp->n_chunks), group0 = __ldg(&sp->group0);
     const uint32_t q = c - chunk0;
     const uint32_t lgS = __ldg(&sp->lg_segs), S = 1u << lgS;
     const uint32_t g = q * 32 + lane;
@@ -1937,8 +1939,12 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
     const uint32_t ray_idx = ray_of_slot_p(active ? slot : 0, pM, pQ, n_b - pQ * pM);
     const Ray ray = make_ray(ray_idx + k.halton_offset);
     MarchState mo;
-    const int mstat = march_ray<KIND, LAYOUT, true>(m, bm, k, P, ray, seg, lgS, active, mo,
+    const int mstat = march_ray<KIND, LAYOUT, true, true>(m, bm, k, P, ray, seg, lgS, active, mo,
                                                           sbr);
+    // read after the march, so that they are not held in registers across it
+    const float v[3] = {__ldg(&sp->v[0]), __ldg(&sp->v[1]), __ldg(&sp->v[2])};
+    const float vl[3] = {__ldg(&sp->vl[0]), __ldg(&sp->vl[1]), __ldg(&sp->vl[2])};
+    const uint32_t n_chunks = __ldg(&sp->n_chunks), group0 = __ldg(&sp->group0);
     float vals[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     unsigned nh = 0, na = 0;
     if (active && seg == 0) {

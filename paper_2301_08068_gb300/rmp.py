@@ -508,13 +508,13 @@ def rmp_raycast_eval_batch(ctx: int, map_id: int, states, n_rays, params: rmp_pa
 
 def rmp_batch_autotune(ctx: int, map_id: int, states, n_rays, n_states: int, max_rays: int,
                        params: rmp_params_t, workspace, out, reps: int = 5, stream=None) -> list:
-    """Runs the autotuner (leaves the fastest knobs in the context); returns the 18 median
-    times in ms (block-major, then segments, then split)."""
-    times = (C.c_float * 18)()
+    """Runs the autotuner (leaves the fastest knobs in the context); returns the 9 median
+    times in ms (block-major, then segments)."""
+    times = (C.c_float * 9)()
     _check(lib().rmp_batch_autotune(
         ctx, int(map_id), _dptr(states), _dptr(n_rays), int(n_states), int(max_rays),
         C.byref(params), _dptr(workspace), workspace.numel() * workspace.element_size(),
-        _stream(stream), _dptr(out), int(reps), times, 18), "rmp_batch_autotune")
+        _stream(stream), _dptr(out), int(reps), times, 9), "rmp_batch_autotune")
     return [float(t) for t in times]
 
 
