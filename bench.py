@@ -262,6 +262,17 @@ def kernel_source_hash(launch: dict) -> str:
     return h.hexdigest()[:16]
 
 
+def strict_json(obj):
+    """obj with every non-finite float replaced by None (the JSON line stays strict JSON)."""
+    if isinstance(obj, float):
+        return obj if np.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {k: strict_json(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [strict_json(v) for v in obj]
+    return obj
+
+
 def stratified_order(costs) -> list:
     """Indices of `costs` (a power-of-two count) such that every prefix samples the sorted
     costs evenly: position p holds the state of cost rank bitreverse(p)."""
@@ -836,7 +847,7 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(strict_json(line), allow_nan=False), flush=True)
 
 
 def main():
@@ -1091,7 +1102,7 @@ def main():
                               "note": "65536 rays at up to 3 kHz (abstract), unnamed GPU of "
                                       "Jetson NX / MX150 / Titan Xp, different map"},
         }
-        print(json.dumps(line), flush=True)
+        print(json.dumps(strict_json(line), allow_nan=False), flush=True)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()

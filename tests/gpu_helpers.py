@@ -26,7 +26,7 @@ Tolerances (FP32 march and per-ray policy against the FP64 oracle; Sec. III-C an
     (|db| + |dS| |f|) / (lambda_k - |dS|) with dS, db twice the observed differences of the
     sums, plus the rotation of the kept eigenvectors (Davis-Kahan) below full rank,
     lambda_k the smallest kept eigenvalue.  For well-conditioned sums B is below 1e-4 |f|
-    and the check is the benchmark spec's 1e-4 relative; for ill-conditioned ones B is about
+    and the check is the stated 1e-4 relative; for ill-conditioned ones B is about
     cond(sum A) times the relative error of the sums, which the FP32 per-ray values set.
     Where an eigenvalue could cross the pseudo-inverse's 1e-12 lambda_max cut under that
     perturbation (every rank-deficient sum: FP32 per-ray values leave ~1e-8 lambda_max of
@@ -37,8 +37,8 @@ import numpy as np
 
 from paper_2301_08068_gb300 import rmp as R
 
-REL = 1e-5          # per-ray and summed A, A f (the benchmark spec)
-REL_F = 1e-4        # resolved acceleration (the benchmark spec)
+REL = 1e-5          # per-ray and summed A, A f: the stated relative tolerance
+REL_F = 1e-4        # resolved acceleration: the stated relative tolerance
 UNDERFLOW = 2.0 ** -100
 
 

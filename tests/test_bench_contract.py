@@ -61,3 +61,18 @@ def test_launch_identity_ignores_comments_and_layout():
     assert bench.code_only(a) == bench.code_only(b)
     assert bench.code_only('int a = 1;') != bench.code_only('int a = 2;')
     assert '"x // y /* z */"' in bench.code_only(a)          # string literals are code
+
+
+def test_strict_json_and_stratified_order():
+    """The JSON line never carries non-finite numbers; the timed states' order samples the
+    sorted costs evenly in every prefix (bit-reversed ranks)."""
+    d = bench.strict_json({"a": float("inf"), "b": [1.0, float("nan")], "c": {"d": 2.5}})
+    assert d == {"a": None, "b": [1.0, None], "c": {"d": 2.5}}
+    json.dumps(d, allow_nan=False)
+    costs = [5.0, 1.0, 4.0, 2.0, 8.0, 7.0, 6.0, 3.0]
+    order = bench.stratified_order(costs)
+    assert sorted(order) == list(range(8))
+    ranks = sorted(range(8), key=lambda i: costs[i])
+    assert [ranks.index(i) for i in order] == [0, 4, 2, 6, 1, 5, 3, 7]
+    with pytest.raises(AssertionError):
+        bench.stratified_order([1.0, 2.0, 3.0])

@@ -43,7 +43,7 @@ def run_esdf(ctx, eid, states, goals, params):
 def assert_esdf_close(g, o):
     """Both sides evaluate the policy in FP64 (library exp / log1p within a few ulp): the sums
     within 1e-12 of their largest entry; f within 1e-9 relative at full rank (the resolve's
-    FP64 adjugate solve) and within the benchmark spec's 1e-4 at rank 1 (the obstacle metric alone,
+    FP64 adjugate solve) and within the stated 1e-4 at rank 1 (the obstacle metric alone,
     resolved through FP32 eigenvectors refined in FP64); the eigenvalues as in gpu_helpers."""
     assert g["status"] == 0
     assert (g["n_rays"], g["n_hits"], g["n_active"]) == (o["n_rays"], o["n_hits"], o["n_active"])
