@@ -43,6 +43,7 @@ WORKLOAD = ("hashed TSDF 40x40x10 m at 0.1 m (8^3 blocks, 200 boxes/spheres, tru
             "65536 Halton rays, max range 10 m, one state per call")
 N_RAYS = 65536
 N_STATES = 64
+PREWARM_S = 0.3   # untimed evaluations while the clock sampler starts
 FLUSH_BYTES = 256 << 20
 PAPER_RATE = 65536 * 3000 / 1e9   # 65536 rays at up to 3 kHz (abstract), other hardware
 # integer operations of one step of the plain exact DDA: two cross-multiplied t comparisons
@@ -902,10 +903,21 @@ def main():
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     # the clock sampler starts (and settles) before the warm-up, so the warm-up steps, with
-    # the same L2 flush between them as the timed ones, run right before the timed loop
+    # the same L2 flush between them as the timed ones, run right before the timed loop;
+    # while it starts, untimed evaluations keep the GPU busy (an idle GPU needs more than a
+    # few steps to come back to speed: 5 warm-up steps after 0.3 s idle measured 62.3 us,
+    # 50 steps 59.2 us)
     clocks = ClockSampler(local_rank)
     clocks.start()
-    time.sleep(0.3)
+    t_end = time.perf_counter() + PREWARM_S
+    n_pre = 0
+    while time.perf_counter() < t_end:
+        flush.fill_(n_pre & 0xFF)
+        step(n_pre)
+        n_pre += 1
+        if n_pre % 32 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
     for i in range(args.warmup):
         flush.fill_(i & 0xFF)
         step(i)
@@ -952,8 +964,14 @@ def main():
                    "ms_per_step_p50": float(np.percentile(t_on, 50)),
                    "Grays_per_s": N_RAYS / float(np.mean(t_on)) / 1e6, "steps": 2000}
 
-    # end to end through the public synchronous call with host buffers
+    # end to end through the public synchronous call with host buffers (after as many
+    # untimed calls as there are warm-up steps, at least 20, so the host path is warm too)
     n_e2e = max(1, min(args.steps, 2000))
+    for i in range(max(args.warmup, 20)):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        s = wl.states[order[i % N_STATES]]
+        R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, N_RAYS, params)
     e2e_t = []
     for i in range(n_e2e):
         flush.fill_(i & 0xFF)
@@ -1052,6 +1070,9 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write outside the events)",
                        "state_order": "stratified by voxel-step count (every prefix of the "
                                       "timed steps spans the states' cost range)",
+                       "prewarm": "untimed evaluations for %.1f s (%d) while the clock sampler "
+                                  "starts, then the %d warm-up steps" % (PREWARM_S, n_pre,
+                                                                          args.warmup),
                        "launch": launch, **summary},
             "evals_per_s": world * 1e3 / ms_max,
             "ms_per_step_p50": float(np.percentile(per, 50)),
