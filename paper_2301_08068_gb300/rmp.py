@@ -9,7 +9,9 @@ CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import importlib
 import os
+import struct
 import threading
 from typing import Optional
 
@@ -19,6 +21,7 @@ from . import build as _build
 
 _lock = threading.Lock()
 _lib = None
+_fast = None        # CPython marshalling of the synchronous calls (None: ctypes only)
 
 RMP_OK, RMP_ERR_INVALID_ARG = 0, 1
 STATUS_NAMES = {0: "RMP_OK", 1: "RMP_ERR_INVALID_ARG", 2: "RMP_ERR_NO_MEMORY", 3: "RMP_ERR_CUDA",
@@ -181,7 +184,9 @@ def lib_path() -> str:
 
 def lib() -> C.CDLL:
     """Load librmp.so (building it if the sources are newer).  Raises if unavailable."""
-    global _lib
+    global _lib, _fast
+    if _lib is not None:
+        return _lib
     with _lock:
         if _lib is None:
             path = _build.LIB
@@ -202,8 +207,19 @@ def lib() -> C.CDLL:
             L.rmp_workspace_bytes.restype = C.c_size_t
             L.rmp_batch_workspace_bytes.argtypes = [C.c_uint32, C.c_uint32]
             L.rmp_batch_workspace_bytes.restype = C.c_size_t
+            if os.path.exists(_build.FAST) and _build.fast_up_to_date():
+                try:    # linked against the library just loaded (same file, one copy)
+                    _fast = importlib.import_module(__package__ + "._rmp_fast")
+                except ImportError:
+                    _fast = None
             _lib = L
     return _lib
+
+
+def fast_binding() -> bool:
+    """True when the synchronous calls go through the CPython extension."""
+    lib()
+    return _fast is not None
 
 
 def _check(status: int, what: str):
@@ -278,6 +294,13 @@ def result_from_bytes(b: bytes) -> dict:
     return result_dict(rmp_result_t.from_buffer_copy(b))
 
 
+def _result_from_raw(b: bytes) -> dict:
+    v = np.frombuffer(bytearray(b), np.float64, 15)   # f, sum A, sum A f, eig (writable)
+    n_rays, n_hits, n_active, rank, status, _ = struct.unpack_from("<IIIIiI", b, 120)
+    return dict(f=v[0:3], sumA=v[3:9], sumAf=v[9:12], eig=v[12:15], n_rays=n_rays,
+                n_hits=n_hits, n_active=n_active, rank=rank, status=status)
+
+
 # ----------------------------------------------------------------------------- C-named calls
 def rmp_status_string(status: int) -> str:
     return lib().rmp_status_string(int(status)).decode()
@@ -341,8 +364,14 @@ def rmp_workspace_init(workspace, stream=None):
 
 def rmp_raycast_eval(ctx: int, map_id: int, x, xdot, n_rays: int, params: rmp_params_t,
                      stream=None, hits=None, per_ray=None) -> dict:
+    L = _lib if _lib is not None else lib()
+    if _fast is not None:
+        st, raw = _fast.raycast_eval(ctx, int(map_id), x, xdot, int(n_rays), C.addressof(params),
+                                     _stream(stream), _dptr(hits), _dptr(per_ray))
+        _check(st, "rmp_raycast_eval")
+        return _result_from_raw(raw)
     out = rmp_result_t()
-    _check(lib().rmp_raycast_eval(ctx, int(map_id), _vec3(x), _vec3(xdot), int(n_rays),
+    _check(L.rmp_raycast_eval(ctx, int(map_id), _vec3(x), _vec3(xdot), int(n_rays),
                                   C.byref(params), _stream(stream), C.byref(out), _dptr(hits),
                                   _dptr(per_ray)), "rmp_raycast_eval")
     return result_dict(out)
@@ -359,8 +388,14 @@ def rmp_raycast_eval_async(ctx: int, map_id: int, state, n_rays: int, params: rm
 
 def rmp_scan_eval(ctx: int, points, x, xdot, params: rmp_params_t, stream=None,
                   per_ray=None) -> dict:
-    out = rmp_result_t()
+    lib()
     n = points.shape[0]
+    if _fast is not None:
+        st, raw = _fast.scan_eval(ctx, _dptr(points), int(n), x, xdot, C.addressof(params),
+                                  _stream(stream), _dptr(per_ray))
+        _check(st, "rmp_scan_eval")
+        return _result_from_raw(raw)
+    out = rmp_result_t()
     _check(lib().rmp_scan_eval(ctx, _dptr(points), int(n), _vec3(x), _vec3(xdot), C.byref(params),
                                _stream(stream), C.byref(out), _dptr(per_ray)), "rmp_scan_eval")
     return result_dict(out)

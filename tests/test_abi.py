@@ -214,3 +214,32 @@ def test_context_without_gpu_is_an_error(rmp):
         pytest.skip("a GPU is present")
     with pytest.raises(rmp.RmpError):
         rmp.Context(0)
+
+
+def test_fast_binding_marshalling():
+    """The CPython extension of the synchronous calls (argument marshalling only) reaches
+    the C ABI: a null context is refused with RMP_ERR_INVALID_ARG, malformed vectors raise,
+    and its result decoding equals the ctypes structure's."""
+    import numpy as np
+    from paper_2301_08068_gb300 import rmp
+    if not rmp.fast_binding():
+        pytest.skip("CPython extension not built here (no Python headers)")
+    bad = rmp.STATUS_CODES["RMP_ERR_INVALID_ARG"]
+    for x, v in (([1.0, 2.0, 3.0], (0.0, 0.0, 0.0)), (np.zeros(3), np.ones(3, np.float32))):
+        st, raw = rmp._fast.raycast_eval(None, 1, x, v, 64, 0, None, None, None)
+        assert st == bad and len(raw) == 144
+        st, raw = rmp._fast.scan_eval(None, None, 1, x, v, 0, None, None)
+        assert st == bad and len(raw) == 144
+    with pytest.raises(ValueError):
+        rmp._fast.raycast_eval(None, 1, [1.0, 2.0], [0.0, 0.0, 0.0], 64, 0, None, None, None)
+    r = rmp.rmp_result_t()
+    for i in range(3):
+        r.f[i], r.Af[i], r.eig[i] = 1.5 + i, -2.0 * i, 1e-3 * (i + 1)
+    for i in range(6):
+        r.A[i] = 0.25 * i
+    r.n_rays, r.n_hits, r.n_active, r.rank, r.status = 65536, 1234, 77, 3, 0
+    a, b = rmp.result_dict(r), rmp._result_from_raw(bytes(r))
+    for k in ("f", "sumA", "sumAf", "eig"):
+        assert np.array_equal(a[k], b[k])
+    for k in ("n_rays", "n_hits", "n_active", "rank", "status"):
+        assert a[k] == b[k]

@@ -528,3 +528,29 @@ def test_maximum_ray_count_sampled(ctx, dense):
     assert_per_ray_close(pv, por)
     with pytest.raises(R.RmpError):
         R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, n + 1, pg)
+
+
+def test_fast_binding_matches_ctypes(ctx, hashed):
+    """The synchronous calls through the CPython extension and through ctypes reach the
+    same C functions: results bitwise equal (raycast and scan)."""
+    if not R.fast_binding():
+        pytest.skip("CPython extension not built")
+    torch = torch_cuda()
+    wl, mid, om = hashed
+    p = R.make_params(wl.params, wl.max_range)
+    s = wl.states[2]
+    pts = torch.tensor(np.random.default_rng(4).uniform(-6, 6, (5000, 3)).astype(np.float32),
+                       device="cuda")
+    got = (R.rmp_raycast_eval(ctx.handle, mid, s.x, s.xdot, 65536, p),
+           R.rmp_scan_eval(ctx.handle, pts, s.x, s.xdot, p))
+    fast, R._fast = R._fast, None
+    try:
+        ref = (R.rmp_raycast_eval(ctx.handle, mid, list(s.x), list(s.xdot), 65536, p),
+               R.rmp_scan_eval(ctx.handle, pts, s.x, s.xdot, p))
+    finally:
+        R._fast = fast
+    for g, o in zip(got, ref):
+        for k in ("f", "sumA", "sumAf", "eig"):
+            assert g[k].tobytes() == o[k].tobytes(), k
+        for k in ("n_rays", "n_hits", "n_active", "rank", "status"):
+            assert g[k] == o[k], k
