@@ -1868,6 +1868,73 @@ __global__ void rollout_step_kernel(DevMap m, RolloutConsts rc, const rmp_result
   else if (running) atomicAdd(running, 1u);
 }
 
+// The last chunk of a group sums the group's chunk partials into a group partial; the last
+// group of a state sums the state's groups, adds the attractor (combined evaluations) and
+// resolves.  Called by all 32 lanes of the warp whose chunk completed the group.  Kept
+// out of line: it runs once per 32 chunks, and inlined it would sit between the march
+// loops in the instruction stream.
+__device__ __noinline__ void batch_group_finish(const EvalConsts& k, CtaPartial* cparts,
+                                                CtaPartial* gparts, uint32_t* sticket,
+                                                uint32_t chunk0, uint32_t gi, uint32_t gsz,
+                                                uint32_t n_chunks, uint32_t group0, uint32_t b,
+                                                uint32_t n_b, const double* states,
+                                                const double* goals, rmp_result_t* out) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t stage = 0;
+  // last chunk of its group: sum the group's chunk partials (lane i: chunk i)
+  __threadfence();
+  double gv[9] = {0., 0., 0., 0., 0., 0., 0., 0., 0.};
+  unsigned gh = 0, ga = 0;
+  if (lane < gsz) load_partial(cparts + chunk0 + gi * kBatchGroup + lane, gv, gh, ga);
+  warp_sum_partial(gv, gh, ga);
+  const uint32_t n_groups = (n_chunks + kBatchGroup - 1) / kBatchGroup;
+  if (lane == 0) {
+    CtaPartial p;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) p.v[i] = gv[i];
+    p.n_hits = gh;
+    p.n_active = ga;
+    gparts[group0 + gi] = p;
+    __threadfence();
+    stage = atomicAdd(&sticket[b], 1u) == n_groups - 1 ? 2u : 0u;
+  }
+  stage = __shfl_sync(0xffffffffu, stage, 0);
+  if (stage == 2) {
+    // last group of the state: lane i sums groups i, i + 32, ... in order, then the tree
+    __threadfence();
+    double tv[9] = {0., 0., 0., 0., 0., 0., 0., 0., 0.};
+    unsigned th = 0, ta = 0;
+    for (uint32_t j = lane; j < n_groups; j += 32) {
+      double pv2[9];
+      unsigned h2, a2;
+      load_partial(gparts + group0 + j, pv2, h2, a2);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) tv[i] += pv2[i];
+      th += h2;
+      ta += a2;
+    }
+    warp_sum_partial(tv, th, ta);
+    if (goals && lane == 0)
+      add_attractor(k, states + 6 * (size_t)b, goals + 3 * (size_t)b, n_b, tv);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) tv[i] = __shfl_sync(0xffffffffu, tv[i], 0);
+    rmp_result_t r;
+    resolve_pinv(tv, tv + 6, r);
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) r.A[i] = tv[i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) r.Af[i] = tv[6 + i];
+      r.n_rays = n_b;
+      r.n_hits = th;
+      r.n_active = ta;
+      r.status = RMP_OK;
+      r.reserved = 0;
+      out[b] = r;
+    }
+  }
+}
+
 // Persistent batched evaluation: every warp takes chunks (its own index first, then from
 // the work counter) until none is left; a chunk is 32 / S rays of one state (coherent ray order of that state), marched
 // and evaluated as in the single-state kernel.  The chunk's 9 terms are summed over the
@@ -1992,60 +2059,9 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
       stage = atomicAdd(&gticket[group0 + gi], 1u) == gsz - 1 ? 1u : 0u;
     }
     stage = __shfl_sync(0xffffffffu, stage, 0);
-    if (stage) {
-      // last chunk of its group: sum the group's chunk partials (lane i: chunk i)
-      __threadfence();
-      double gv[9] = {0., 0., 0., 0., 0., 0., 0., 0., 0.};
-      unsigned gh = 0, ga = 0;
-      if (lane < gsz) load_partial(cparts + chunk0 + gi * kBatchGroup + lane, gv, gh, ga);
-      warp_sum_partial(gv, gh, ga);
-      const uint32_t n_groups = (n_chunks + kBatchGroup - 1) / kBatchGroup;
-      if (lane == 0) {
-        CtaPartial p;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) p.v[i] = gv[i];
-        p.n_hits = gh;
-        p.n_active = ga;
-        gparts[group0 + gi] = p;
-        __threadfence();
-        stage = atomicAdd(&sticket[b], 1u) == n_groups - 1 ? 2u : 0u;
-      }
-      stage = __shfl_sync(0xffffffffu, stage, 0);
-      if (stage == 2) {
-        // last group of the state: lane i sums groups i, i + 32, ... in order, then the tree
-        __threadfence();
-        double tv[9] = {0., 0., 0., 0., 0., 0., 0., 0., 0.};
-        unsigned th = 0, ta = 0;
-        for (uint32_t j = lane; j < n_groups; j += 32) {
-          double pv2[9];
-          unsigned h2, a2;
-          load_partial(gparts + group0 + j, pv2, h2, a2);
-#pragma unroll
-          for (int i = 0; i < 9; ++i) tv[i] += pv2[i];
-          th += h2;
-          ta += a2;
-        }
-        warp_sum_partial(tv, th, ta);
-        if (goals && lane == 0)
-          add_attractor(k, states + 6 * (size_t)b, goals + 3 * (size_t)b, n_b, tv);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) tv[i] = __shfl_sync(0xffffffffu, tv[i], 0);
-        rmp_result_t r;
-        resolve_pinv(tv, tv + 6, r);
-        if (lane == 0) {
-#pragma unroll
-          for (int i = 0; i < 6; ++i) r.A[i] = tv[i];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) r.Af[i] = tv[6 + i];
-          r.n_rays = n_b;
-          r.n_hits = th;
-          r.n_active = ta;
-          r.status = RMP_OK;
-          r.reserved = 0;
-          out[b] = r;
-        }
-      }
-    }
+    if (stage)
+      batch_group_finish(k, cparts, gparts, sticket, chunk0, gi, gsz, n_chunks, group0, b, n_b,
+                         states, goals, out);
     c = __shfl_sync(0xffffffffu, cn, 0);
   }
   if (staged && bm_timeout && threadIdx.x == 0) bulk_load_wait(&bm_bar);   // let a late copy land
