@@ -228,18 +228,25 @@ def _check(status: int, what: str):
 
 
 _torch = None
+_raw_stream = None      # torch's C accessors of the current stream and device, once found
 
 
 def _current_stream() -> Optional[int]:
     """Handle of torch's current CUDA stream (None without a usable torch CUDA)."""
-    global _torch
+    global _torch, _raw_stream
     try:
+        if _raw_stream is not None:         # the C accessors directly (no Python-level init check)
+            return _raw_stream[0](_raw_stream[1]())
         if _torch is None:
             import torch
             _torch = torch
         raw = getattr(_torch._C, "_cuda_getCurrentRawStream", None)
+        dev = getattr(_torch._C, "_cuda_getDevice", None)
         if raw is not None:                 # one call instead of building a Stream object
-            return raw(_torch.cuda.current_device())
+            h = raw(_torch.cuda.current_device())     # initialises CUDA in torch if needed
+            if dev is not None:
+                _raw_stream = (raw, dev)
+            return h
         return _torch.cuda.current_stream().cuda_stream
     except Exception:
         return None
