@@ -965,9 +965,9 @@ def main():
                    "Grays_per_s": N_RAYS / float(np.mean(t_on)) / 1e6, "steps": 2000}
 
     # end to end through the public synchronous call with host buffers (after as many
-    # untimed calls as there are warm-up steps, at least 20, so the host path is warm too)
+    # untimed calls as there are warm-up steps, at least 200, so the host path is warm too)
     n_e2e = max(1, min(args.steps, 2000))
-    for i in range(max(args.warmup, 20)):
+    for i in range(max(args.warmup, 200)):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         s = wl.states[order[i % N_STATES]]
