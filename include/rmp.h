@@ -39,7 +39,7 @@ extern "C" {
 #define RMP_ERR_INVALID_ARG 1   /* a pointer, size, parameter or map is invalid        */
 #define RMP_ERR_NO_MEMORY 2     /* device or pinned host allocation failed             */
 #define RMP_ERR_CUDA 3          /* a CUDA runtime call or kernel launch failed         */
-#define RMP_ERR_TIMEOUT 4       /* a bounded wait expired (serving)                    */
+#define RMP_ERR_TIMEOUT 4       /* a bounded wait expired (serving, device waits)      */
 #define RMP_ERR_BUSY 5          /* no free slot / over the memory budget (serving)     */
 #define RMP_ERR_UNKNOWN_MAP 6   /* map id not registered in this context               */
 #define RMP_ERR_NOT_READY 7     /* polled work has not completed yet (serving)         */
@@ -203,14 +203,18 @@ int rmp_raycast_eval(rmp_ctx* ctx, uint32_t map_id, const double x[3], const dou
  * ray count). */
 size_t rmp_workspace_bytes(void);
 
-/* Zero a workspace before its first use (enqueued on `stream`).  Each evaluation
- * leaves its workspace ready for the next one, so this is needed once. */
+/* Initialise a workspace before its first use (enqueued on `stream`): a zero header and
+ * every per-CTA partial slot empty (all bytes 0xFF).  Each evaluation leaves its
+ * workspace ready for the next one, so this is needed once -- and again after an
+ * evaluation on it returned status RMP_ERR_TIMEOUT (a bounded device wait expired; the
+ * workspace then stays marked and every evaluation on it reports RMP_ERR_TIMEOUT until
+ * it is initialised again).  The synchronous calls re-initialise their own workspace. */
 int rmp_workspace_init(void* workspace_dev, size_t bytes, rmp_stream_t stream);
 
 /* Asynchronous form of rmp_raycast_eval for device-resident inputs and outputs:
  * state_dev holds x[3] then xdot[3] (doubles), the result is written to *out_dev.
  * Only enqueues one kernel; no host synchronisation, no allocation, so it may be
- * captured in a CUDA graph.  workspace_dev (>= rmp_workspace_bytes(), zeroed once by
+ * captured in a CUDA graph.  workspace_dev (>= rmp_workspace_bytes(), set up once by
  * rmp_workspace_init) must not be shared by evaluations that may run concurrently. */
 int rmp_raycast_eval_async(rmp_ctx* ctx, uint32_t map_id, const double* state_dev,
                            uint32_t n_rays, const rmp_params_t* params, void* workspace_dev,

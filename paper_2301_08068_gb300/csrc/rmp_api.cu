@@ -225,6 +225,13 @@ int build_radius(MapRec& r, cudaStream_t s) {
   return e == cudaSuccess ? RMP_OK : cuda_status(e);
 }
 
+// After a finish that timed out the context's workspace is poisoned (see grid_finish):
+// reset it before the next synchronous call.  Caller holds c->mu.
+cudaError_t refresh_ws(rmp_ctx* c, cudaStream_t s) {
+  cudaError_t e = workspace_reset(c->ws, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
 
 }  // namespace
 
@@ -277,7 +284,7 @@ int rmp_ctx_create(rmp_ctx** out, int device) {
   c->device = device;
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaMalloc(&c->ws, workspace_bytes());
-  if (e == cudaSuccess) e = cudaMemset(c->ws, 0, workspace_bytes());
+  if (e == cudaSuccess) e = workspace_reset(c->ws, 0);
   if (e == cudaSuccess)
     e = cudaHostAlloc((void**)&c->result_host, sizeof(rmp_result_t), cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->result_map, c->result_host, 0);
@@ -590,7 +597,7 @@ int rmp_tune_get(rmp_ctx* c, int knob, int* value) {
 
 int rmp_workspace_init(void* ws, size_t bytes, rmp_stream_t stream) {
   if (!ws || bytes < workspace_bytes()) return RMP_ERR_INVALID_ARG;
-  RMP_CUDA(cudaMemsetAsync(ws, 0, workspace_bytes(), (cudaStream_t)stream));
+  RMP_CUDA(workspace_reset(ws, (cudaStream_t)stream));
   return RMP_OK;
 }
 
@@ -641,6 +648,7 @@ int rmp_raycast_eval(rmp_ctx* c, uint32_t map_id, const double x[3], const doubl
                          s));
   RMP_CUDA(cudaStreamSynchronize(s));
   *out = *c->result_host;
+  if (out->status == RMP_ERR_TIMEOUT) RMP_CUDA(refresh_ws(c, s));
   return RMP_OK;
 }
 
@@ -687,6 +695,7 @@ int rmp_scan_eval(rmp_ctx* c, const float* points_dev, uint32_t n, const double 
                        s));
   RMP_CUDA(cudaStreamSynchronize(s));
   *out = *c->result_host;
+  if (out->status == RMP_ERR_TIMEOUT) RMP_CUDA(refresh_ws(c, s));
   return RMP_OK;
 }
 

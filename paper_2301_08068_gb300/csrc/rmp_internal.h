@@ -27,8 +27,6 @@ constexpr unsigned long long kEmptyKey = ~0ull;
 constexpr int kKeyBias = 1 << 20;
 constexpr int kMaxGrid = 4096;          // CTAs of one evaluation (grid-stride beyond)
 constexpr int kWsHeaderBytes = 1024;
-constexpr int kGroup = 32;                  // CTAs per reduction group (see grid_finish)
-constexpr int kMaxGroups = 4096 / kGroup;
 constexpr int kMaxRangeVoxels = 16384;  // keeps every DDA crossing numerator below 2^31
 // Block visits before a warp's unfinished pieces are split over its idle lanes; by default
 // never (measured: with coherent ray order the split does not shorten the slowest warps)
@@ -99,22 +97,29 @@ struct RolloutConsts {
   uint32_t max_steps, seg_steps, n_rays, pad;
 };
 
-// Workspace of one evaluation: tickets, one partial per CTA, one partial per group of
-// kGroup CTAs.  Every ticket is reset to 0 by the CTA that completes it.
+// Workspace of one single-state evaluation: a header, then one partial slot per CTA.  A
+// slot is empty when every byte is 0xFF; CTA i > 0 fills slot i, CTA 0 waits for the
+// slots, reads them and empties them again (see grid_finish).
 struct WsHeader {
-  unsigned int ticket;                     // groups completed
-  unsigned int pad0[31];
-  unsigned int group_ticket[kMaxGroups];   // CTAs completed, per group
-  unsigned int pad1[kWsHeaderBytes / 4 - 32 - kMaxGroups];
+  unsigned int poisoned;    // nonzero after a timed-out finish: re-initialise the workspace
+  unsigned int pad[kWsHeaderBytes / 4 - 1];
 };
 
-struct CtaPartial {         // 80 bytes per CTA (and per group)
+struct CtaPartial {         // 80 bytes per CTA
   double v[9];              // sum A (6), sum A f (3)
   unsigned int n_hits, n_active;
 };
 
 inline size_t workspace_bytes() {
-  return kWsHeaderBytes + sizeof(CtaPartial) * (size_t)(kMaxGrid + kMaxGroups);
+  return kWsHeaderBytes + sizeof(CtaPartial) * (size_t)kMaxGrid;
+}
+
+// Header zero, partial slots empty: the state every evaluation leaves a workspace in.
+inline cudaError_t workspace_reset(void* ws, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ws, 0, kWsHeaderBytes, s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync((char*)ws + kWsHeaderBytes, 0xFF, workspace_bytes() - kWsHeaderBytes, s);
+  return e;
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -1093,47 +1093,90 @@ __device__ void resolve_pinv_cta(const double* S, const double* b, rmp_result_t&
   resolve_finish(S, b, W, fa_sh[0], fa_sh[1], fa_sh[2], ok_sh, r);
 }
 
-// A partial in the workspace (80 bytes, one per CTA and one per group): the compensated
-// reduction stores each term as its FP32 pair (s, c), the FP64 reduction as a double
-// (CtaPartial).  Both are read back as five 16-byte words.
+// A partial in the workspace (80 bytes, one per CTA): the compensated reduction stores each
+// term as its FP32 pair (s, c), the FP64 reduction as a double (CtaPartial); both end with
+// the hit and active counts.  Bit 31 of the hit count flags a CTA whose map staging timed
+// out (counts stay below 2^25).  An empty slot holds 0xFF in every byte, a pattern no
+// stored field takes: FP32 and FP64 arithmetic on this GPU returns its canonical NaNs
+// (sign bit clear), never the all-ones word, and the counts stay far below 2^31.
 struct CtaPartial32 {
   float s[9], c[9];
   unsigned n_hits, n_active;
 };
 static_assert(sizeof(CtaPartial32) == sizeof(CtaPartial) && sizeof(CtaPartial) == 80,
               "partials are five 16-byte words");
+constexpr uint32_t kSlotTimeoutFlag = 0x80000000u;
+constexpr uint64_t kFinishWaitNs = 10000000000ull;   // CTA 0 waits at most 10 s for a slot
 
-__device__ __forceinline__ void load_partial_words(const CtaPartial* p, uint32_t w[20]) {
-  const uint4* q = reinterpret_cast<const uint4*>(p);
-  uint4 v[5];
+// Slots are written with relaxed stores at GPU scope (each field one single-copy-atomic
+// access) and read back with relaxed 64-bit loads, so a reader sees every field either
+// empty or complete.
+__device__ __forceinline__ void st_relaxed32(void* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed64(void* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void load_slot(const CtaPartial* p, uint32_t w[20]) {
+  const unsigned long long* q = reinterpret_cast<const unsigned long long*>(p);
+  unsigned long long v[10];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) v[i] = __ldcg(q + i);
+  for (int i = 0; i < 5; ++i)
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];"
+                 : "=l"(v[2 * i]), "=l"(v[2 * i + 1])
+                 : "l"(q + 2 * i)
+                 : "memory");
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    w[4 * i] = v[i].x;
-    w[4 * i + 1] = v[i].y;
-    w[4 * i + 2] = v[i].z;
-    w[4 * i + 3] = v[i].w;
+  for (int i = 0; i < 10; ++i) {
+    w[2 * i] = (uint32_t)v[i];
+    w[2 * i + 1] = (uint32_t)(v[i] >> 32);
   }
 }
+__device__ __forceinline__ void empty_slot(CtaPartial* p) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+  const uint4 e = make_uint4(~0u, ~0u, ~0u, ~0u);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) q[i] = e;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
-// Storing a CTA's (or a group's) sums as a partial, lanes 0-10 of warp 0 one field each,
-// and starting a thread's accumulator from the words of a partial / merging one into it.
+// Storing a CTA's sums in its slot, lanes 0-10 of warp 0 one field each; the words of a
+// CTA's own sums as its slot would hold them; whether a slot's words are all written; and
+// starting a thread's accumulator from the words of a partial / merging one into it.
 template <int RED>
 struct PartialIO;
 
 template <>
 struct PartialIO<RMP_REDUCE_KAHAN32> {
-  __device__ static void store(CtaPartial* slot, const CtaSums& cs, int t) {
+  __device__ static void store(CtaPartial* slot, const CtaSums& cs, int t, uint32_t flag) {
     CtaPartial32* p = reinterpret_cast<CtaPartial32*>(slot);
     if (t < 9) {
-      p->s[t] = cs.s[t];
-      p->c[t] = cs.c[t];
+      st_relaxed32(&p->s[t], __float_as_uint(cs.s[t]));
+      st_relaxed32(&p->c[t], __float_as_uint(cs.c[t]));
     } else if (t == 9) {
-      p->n_hits = cs.u[0];
+      st_relaxed32(&p->n_hits, cs.u[0] | flag);
     } else if (t == 10) {
-      p->n_active = cs.u[1];
+      st_relaxed32(&p->n_active, cs.u[1]);
     }
+  }
+  __device__ static void words(const CtaSums& cs, uint32_t w[20]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      w[q] = __float_as_uint(cs.s[q]);
+      w[9 + q] = __float_as_uint(cs.c[q]);
+    }
+    w[18] = cs.u[0];
+    w[19] = cs.u[1];
+  }
+  __device__ static bool ready(const uint32_t w[20]) {
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 20; ++i) ok = ok && w[i] != ~0u;
+    return ok;
   }
   __device__ static void set(Acc32& a, const uint32_t w[20]) {
 #pragma unroll
@@ -1150,10 +1193,26 @@ struct PartialIO<RMP_REDUCE_KAHAN32> {
 
 template <>
 struct PartialIO<RMP_REDUCE_FP64> {
-  __device__ static void store(CtaPartial* slot, const CtaSums& cs, int t) {
-    if (t < 9) slot->v[t] = cs.v[t];
-    else if (t == 9) slot->n_hits = cs.u[0];
-    else if (t == 10) slot->n_active = cs.u[1];
+  __device__ static void store(CtaPartial* slot, const CtaSums& cs, int t, uint32_t flag) {
+    if (t < 9) st_relaxed64(&slot->v[t], (unsigned long long)__double_as_longlong(cs.v[t]));
+    else if (t == 9) st_relaxed32(&slot->n_hits, cs.u[0] | flag);
+    else if (t == 10) st_relaxed32(&slot->n_active, cs.u[1]);
+  }
+  __device__ static void words(const CtaSums& cs, uint32_t w[20]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(cs.v[q]);
+      w[2 * q] = (uint32_t)b;
+      w[2 * q + 1] = (uint32_t)(b >> 32);
+    }
+    w[18] = cs.u[0];
+    w[19] = cs.u[1];
+  }
+  __device__ static bool ready(const uint32_t w[20]) {
+    bool ok = w[18] != ~0u && w[19] != ~0u;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) ok = ok && (w[2 * q] & w[2 * q + 1]) != ~0u;
+    return ok;
   }
   __device__ static double word_pair(const uint32_t w[20], int q) {
     return __hiloint2double((int)w[2 * q + 1], (int)w[2 * q]);
@@ -1168,88 +1227,86 @@ struct PartialIO<RMP_REDUCE_FP64> {
   }
 };
 
-// Grid ticket: add one, acquire-release at GPU scope (the partials this CTA's warp stored
-// before are visible to whichever CTA draws the last ticket, and that CTA sees all of
-// them), returning the previous count.
-__device__ __forceinline__ unsigned ticket_add(unsigned* p) {
-  unsigned t;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(t) : "l"(p) : "memory");
-  return t;
-}
-
-// Sum `count` <= 2 blockDim partials in a fixed order: thread t loads partials t and
-// t + blockDim (all loads in flight at once: one L2 round trip instead of one per
-// partial), then the block reduction combines the threads.  Result in out (as
-// BlockReduce::reduce leaves it).  Called by every thread.
+// CTA 0's wait, one warp at a time: every lane with a pending slot (`ok` false) loads it
+// until all of its fields are written (then its words are in w).  The warp polls as a
+// whole -- it leaves the loop when every lane is done, lanes never spin on their own --
+// because lanes that finished while others of their warp still spin stall for microseconds
+// (measured).  Returns false when the wait passed `deadline` (global timer, ns).  Called by
+// all lanes of the warp.
 template <int RED>
-__device__ void sum_partials(const CtaPartial* p, int count, CtaSums& out) {
-  const int t = threadIdx.x, B = blockDim.x;
-  uint32_t w0[20], w1[20];
-  const bool h0 = t < count, h1 = t + B < count;
-  if (h0) load_partial_words(p + t, w0);
-  if (h1) load_partial_words(p + t + B, w1);
-  typename BlockReduce<RED>::Acc acc;
-  BlockReduce<RED>::init(acc);
-  unsigned nh = 0, na = 0;
-  if (h0) {
-    PartialIO<RED>::set(acc, w0);
-    nh = w0[18];
-    na = w0[19];
+__device__ __forceinline__ bool wait_slots(const CtaPartial* p, bool ok, uint32_t w[20],
+                                           unsigned long long deadline) {
+  while (!__all_sync(0xffffffffu, ok)) {
+    if (!ok) {
+      load_slot(p, w);
+      ok = PartialIO<RED>::ready(w);
+    }
+    if (__any_sync(0xffffffffu, global_ns() > deadline)) return false;
   }
-  if (h1) {
-    PartialIO<RED>::merge(acc, w1);
-    nh += w1[18];
-    na += w1[19];
-  }
-  BlockReduce<RED>::reduce(acc, nh, na, out);
-  __syncthreads();
+  return true;
 }
 
-// Grid completion, deterministic and without one thread walking every CTA: lanes 0-10 of
-// warp 0 store the CTA's sums as its partial and lane 0 draws a ticket.  Up to blockDim
-// CTAs, the last CTA to finish sums every partial (sum_partials) and resolves; larger
-// grids add a level: the last CTA of each group of kGroup CTAs (group ticket) sums the
-// group's partials into a group partial, and the last group sums those.  (Each level costs
-// a ticket and an L2 round trip of partials, about 1.5 us on this GPU.)  A grid of one CTA
-// resolves its own sums.  Tickets are reset by the CTA that completes them.  Called by all
-// threads of every CTA after BlockReduce::reduce.
+// Grid completion, deterministic, with the partial sums streamed to CTA 0: lanes 0-10 of
+// warp 0 of every other CTA store its sums in its slot and the CTA exits (no atomics, no
+// fence); CTA 0, once its own rays are done, takes the slots as they fill -- thread t slot
+// t, then t + blockDim, ... in order, merging each into its accumulator and emptying the
+// slot -- then reduces the threads (BlockReduce) and resolves.  The summation order is
+// fixed by slot index, whatever the order of arrival, and the partials of CTAs that
+// finished early are read while the slowest still march: after the last partial only its
+// load, the block reduction and the resolve remain.  CTA 0 never waits on a CTA that
+// waits on it, so the wait ends once every CTA has run; it is bounded all the same
+// (kFinishWaitNs), and a wait that expires reports RMP_ERR_TIMEOUT and marks the workspace
+// poisoned (every later evaluation on it reports RMP_ERR_TIMEOUT until it is
+// re-initialised).  A grid of one CTA resolves its own sums.  Called by all threads of
+// every CTA after BlockReduce::reduce.
 template <int RED>
 __device__ void grid_finish(const CtaSums& cta, WsHeader* ws, CtaPartial* parts,
                             rmp_result_t* out, uint32_t n_rays, int status) {
-  __shared__ int stage;
   __shared__ CtaSums gsum;
-  CtaPartial* groups = parts + kMaxGrid;
+  __shared__ int poison_sh;
   const int G = gridDim.x;
-  const bool one_level = G <= (int)blockDim.x;
-  const int gi = one_level ? 0 : blockIdx.x / kGroup;
-  const int n_groups = one_level ? 1 : (G + kGroup - 1) / kGroup;
-  const int g0 = gi * kGroup;
-  const int gsz = one_level ? G : min(kGroup, G - g0);
   const CtaSums* tot = &cta;
+  int st = status;
   if (G > 1) {
-    if (threadIdx.x < 32) {
-      PartialIO<RED>::store(parts + blockIdx.x, cta, threadIdx.x);
-      __syncwarp();
-      if (threadIdx.x == 0) stage = ticket_add(&ws->group_ticket[gi]) == (unsigned)gsz - 1 ? 1 : 0;
+    if (blockIdx.x != 0) {
+      if (threadIdx.x < 32)
+        PartialIO<RED>::store(parts + blockIdx.x, cta, threadIdx.x,
+                              status == RMP_ERR_TIMEOUT ? kSlotTimeoutFlag : 0u);
+      return;
     }
+    if (threadIdx.x == 0) poison_sh = ws->poisoned ? 1 : 0;
     __syncthreads();
-    if (stage == 0) return;
-    sum_partials<RED>(parts + (one_level ? 0 : g0), gsz, gsum);
-    if (n_groups > 1) {
-      if (threadIdx.x < 32) {
-        PartialIO<RED>::store(groups + gi, gsum, threadIdx.x);
-        __syncwarp();
-        if (threadIdx.x == 0) {
-          ws->group_ticket[gi] = 0;
-          stage = ticket_add(&ws->ticket) == (unsigned)n_groups - 1 ? 2 : 0;
-        }
+    const bool poisoned = poison_sh != 0;
+    typename BlockReduce<RED>::Acc acc;
+    BlockReduce<RED>::init(acc);
+    unsigned nh = 0, na = 0, flags = 0;
+    bool expired = false;
+    const unsigned long long deadline = global_ns() + kFinishWaitNs;
+    // warp-uniform trip count: lane l of the warp takes slot base + l
+    for (int base = threadIdx.x & ~31; base < G && !poisoned; base += blockDim.x) {
+      const int i = base + (int)(threadIdx.x & 31);
+      uint32_t w[20];
+      if (i == 0) PartialIO<RED>::words(cta, w);
+      if (!wait_slots<RED>(parts + i, i == 0 || i >= G, w, deadline)) {
+        expired = true;
+        break;
       }
-      __syncthreads();
-      if (stage != 2) return;
-      sum_partials<RED>(groups, n_groups, gsum);
-    } else if (threadIdx.x == 0) {
-      // a single group: its sum is the total (the same value the second level would give)
-      ws->group_ticket[gi] = 0;
+      if (i >= G) continue;
+      if (i > 0) empty_slot(parts + i);
+      if (i == (int)threadIdx.x) PartialIO<RED>::set(acc, w);
+      else PartialIO<RED>::merge(acc, w);
+      flags |= w[18] & kSlotTimeoutFlag;
+      nh += w[18] & ~kSlotTimeoutFlag;
+      na += w[19];
+    }
+    BlockReduce<RED>::reduce(acc, nh, na, gsum);
+    const int any_expired = __syncthreads_or(expired);
+    const int any_flag = __syncthreads_or(flags != 0);
+    if (poisoned || any_expired) {
+      if (threadIdx.x == 0) ws->poisoned = 1;
+      st = RMP_ERR_TIMEOUT;
+    } else if (any_flag) {
+      st = RMP_ERR_TIMEOUT;
     }
     tot = &gsum;
   }
@@ -1261,15 +1318,12 @@ __device__ void grid_finish(const CtaSums& cta, WsHeader* ws, CtaPartial* parts,
     r.n_rays = n_rays;
     r.n_hits = tot->u[0];
     r.n_active = tot->u[1];
-    r.status = status;
+    r.status = st;
     r.reserved = 0;
   }
   __syncthreads();
   if (threadIdx.x < 64) resolve_pinv_cta(r.A, r.Af, r);
-  if (threadIdx.x == 0) {
-    *out = r;
-    if (G > 1) ws->ticket = 0;        // ready for the next evaluation
-  }
+  if (threadIdx.x == 0) *out = r;
 }
 
 // Per-CTA state: quantised position (FP64, threads 0-2 one axis each) and the velocity

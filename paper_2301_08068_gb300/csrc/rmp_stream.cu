@@ -68,7 +68,7 @@ int rmp_scan_pipeline_create(rmp_ctx* ctx, uint32_t max_points, uint32_t slots,
         cudaMallocHost((void**)&s.res_host, sizeof(rmp_result_t)) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMemset(s.ws, 0, wsb) != cudaSuccess)
+        rmp::workspace_reset(s.ws, p->compute) != cudaSuccess)
       st = RMP_ERR_NO_MEMORY;
   }
   if (st != RMP_OK) {

@@ -135,7 +135,8 @@ def test_status_strings(rmp):
 
 
 def test_workspace_size_is_fixed(rmp):
-    assert rmp.rmp_workspace_bytes() == 1024 + 80 * (4096 + 128)
+    """A 1024-byte header and one 80-byte partial slot per CTA of the largest grid."""
+    assert rmp.rmp_workspace_bytes() == 1024 + 80 * 4096
 
 
 def test_batch_workspace_size(rmp):

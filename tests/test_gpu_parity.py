@@ -219,6 +219,38 @@ def test_async_matches_sync_bitwise(ctx, hashed):
                                                             r_sync["rank"])
 
 
+def test_workspace_left_ready_and_poisoned_state(ctx, hashed):
+    """Each evaluation leaves its workspace as rmp_workspace_init does (header zero, every
+    partial slot back to all-ones); a workspace whose header is marked poisoned (the state
+    a finish whose bounded wait expired leaves) makes a multi-CTA evaluation report
+    RMP_ERR_TIMEOUT until it is initialised again, after which results are bit-identical
+    to the synchronous call."""
+    torch = torch_cuda()
+    wl, mid, om = hashed
+    s = wl.states[1]
+    pg = R.make_params(wl.params, wl.max_range)
+    r_sync, _, _ = gpu_raycast(ctx, mid, s.x, s.xdot, 30000, pg, want=False)
+    ws = torch.empty(R.rmp_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    R.rmp_workspace_init(ws)
+    fresh = ws.cpu().numpy().copy()
+    assert np.all(fresh[:1024] == 0) and np.all(fresh[1024:] == 0xFF)
+    state = torch.tensor(np.concatenate([s.x, s.xdot]), dtype=torch.float64, device="cuda")
+    out = torch.empty(R.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    R.rmp_raycast_eval_async(ctx.handle, mid, state, 30000, pg, ws, out)
+    assert R.result_from_bytes(out.cpu().numpy().tobytes())["status"] == 0
+    assert np.array_equal(ws.cpu().numpy(), fresh)
+    ws[0] = 1                                          # header: poisoned
+    for _ in range(2):
+        R.rmp_raycast_eval_async(ctx.handle, mid, state, 30000, pg, ws, out)
+        assert R.result_from_bytes(out.cpu().numpy().tobytes())["status"] == 4
+    R.rmp_workspace_init(ws)
+    R.rmp_raycast_eval_async(ctx.handle, mid, state, 30000, pg, ws, out)
+    r = R.result_from_bytes(out.cpu().numpy().tobytes())
+    assert r["status"] == 0
+    for k in ("f", "sumA", "sumAf", "eig"):
+        assert np.array_equal(r[k], r_sync[k]), k
+
+
 def test_async_bad_state_reports_invalid(ctx, hashed):
     torch = torch_cuda()
     wl, mid, om = hashed

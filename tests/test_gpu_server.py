@@ -74,16 +74,23 @@ def test_server_results_match_oracle(env):
 def test_server_same_result_alone_and_in_mix(env):
     ctx, maps = env
     ro, por = oracle_result(maps["hashed"], 7, 5000)
-    with R.Server(ctx, slots=3) as srv:
+    # one batch in flight at a time and every submission's arguments built beforehand, so
+    # requests queue behind the running batch and share the next one
+    with R.Server(ctx, slots=1) as srv:
         alone, _ = srv.wait(submit(srv, maps["hashed"], 7, 5000))
         rng = np.random.default_rng(2)
-        tickets = []
+        params = {k: R.make_params(v[0].params, v[0].max_range) for k, v in maps.items()}
+        plan = []
         for j in range(80):
             if j == 40:
-                tickets.append(("probe", submit(srv, maps["hashed"], 7, 5000)))
+                plan.append(("probe", "hashed", 7, 5000))
             name = ("hashed", "dense")[int(rng.integers(0, 2))]
-            tickets.append((name, submit(srv, maps[name], int(rng.integers(0, 40)),
-                                         int(rng.integers(1000, 60000)))))
+            plan.append((name, name, int(rng.integers(0, 40)), int(rng.integers(1000, 60000))))
+        tickets = []
+        for tag, name, i, n in plan:
+            wl, mid, _ = maps[name]
+            tickets.append((tag, srv.submit(mid, wl.states[i].x, wl.states[i].xdot, n,
+                                            params[name])))
         mixed = None
         for name, t in tickets:
             res, _ = srv.wait(t)
