@@ -290,21 +290,28 @@ __device__ __forceinline__ bool skip_box(const DevMap& m, int k[3], const int s[
     }
     return true;
   }
-  const float te = __uint2float_rn(Fe) * sel3f(rA, e);   // exit time, relative error < 2^-21
+  const float rAe = sel3f(rA, e) * (1.0f / 65536.0f);   // RN(1 / |D_e|) / 2^16
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
     if (b == e || A[b] == 0) continue;
     const bool le = b < e;
-    // est = (t_e |D_b| - N_b) / 2^16 is within 0.01 of its exact value: the count is
-    // floor(est) + 1 unless est lies within 1/64 of an integer, where exact comparisons
-    // decide (about 3% of the cases)
-    const float est = (te * __uint2float_rn(A[b]) - __uint2float_rn(N[b])) * (1.0f / 65536.0f);
+    // est = (F_e |D_b| - N_b |D_e|) / (|D_e| 2^16): the numerator formed exactly in 64 bits
+    // (-1 <= est <= 8 (2R + 1) < 2^8 and |D_e| <= 2^24, so |num| < 2^48) and converted from
+    // two exact 24-bit halves with one rounding; est then carries a relative error below
+    // 2^-22, an absolute one below 2^-14, and the count is floor(est) + 1 unless est lies
+    // within 2^-12 of an integer, where exact comparisons decide (an FP32 estimate of
+    // t_e |D_b| - N_b from the absolute numerators needed a band of 1/64, and then most
+    // warps took the exact path for some lane)
+    const long long num = (long long)((unsigned long long)Fe * A[b]) -
+                          (long long)((unsigned long long)N[b] * Ae);
+    const float est = __fmaf_rn(__int2float_rn((int)(num >> 24)), 16777216.0f,
+                                __int2float_rn((int)(num & 0xFFFFFF))) * rAe;
     const float fl = floorf(est);
     const float fr = est - fl;
     int cnt;
-    if (est < -0.015625f) {
+    if (est < -0.000244140625f) {
       cnt = 0;
-    } else if (fr > 0.015625f && fr < 0.984375f) {
+    } else if (fr > 0.000244140625f && fr < 0.999755859375f) {
       cnt = (int)fl + 1;
     } else {
       const unsigned long long X = (unsigned long long)Fe * A[b];
