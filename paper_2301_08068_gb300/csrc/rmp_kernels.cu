@@ -1356,6 +1356,12 @@ __device__ __forceinline__ double state_at(const double* state, const EvalConsts
   return v;
 }
 
+// Which state component (0-2 x, 3-5 xdot) thread t sets up, or -1: x on threads 0-2 and
+// xdot on threads 32-34, two warps, so that the FP64 work of each runs in parallel.
+__device__ __forceinline__ int state_component(unsigned t) {
+  return t < 3 ? (int)t : ((t >= 32 && t < 35) ? (int)t - 29 : -1);
+}
+
 __device__ __forceinline__ void split_velocity(double x, CtaState& cs, int a) {
   cs.v[a] = __double2float_rn(x);
   cs.vl[a] = __double2float_rn(__dsub_rn(x, (double)cs.v[a]));
@@ -1544,18 +1550,11 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
     bm_timeout = 0;
     if (staged) bulk_load_begin(&bm_bar, smem_radius, m.radius, bm_bytes);
   }
-  if (threadIdx.x < 3) {
-    const int a = threadIdx.x;
-    const double o = KIND != RMP_MAP_DENSE_U8 ? 0.0
-                     : (a == 0 ? m.origin[0] : (a == 1 ? m.origin[1] : m.origin[2]));
-    const double q = __dmul_rn(__ddiv_rn(__dsub_rn(state_at(state, k, a), o), m.vs), 65536.0);
-    // |voxel| < 2^22 keeps block keys and fixed-point products in range; NaN fails too
-    const int bad = !(fabs(q) < 274877906944.0);
-    cs.bad[a] = bad;
-    cs.P[a] = bad ? 0 : __double2ll_rn(q);
-  } else if (threadIdx.x < 6) {
-    split_velocity(state_at(state, k, threadIdx.x), cs, threadIdx.x - 3);
-  }
+  // state component of this thread: x on threads 0-2, xdot on threads 32-34 (another warp,
+  // so the two FP64 chains below run side by side instead of one after the other), loaded
+  // before the first ray is generated so that the ray's arithmetic covers the load
+  const int comp = state_component(threadIdx.x);
+  const double sv = comp >= 0 ? state_at(state, k, comp) : 0.0;
   typename BlockReduce<RED>::Acc acc;
   BlockReduce<RED>::init(acc);
   unsigned n_hit = 0, n_act = 0;
@@ -1564,9 +1563,20 @@ __global__ void __launch_bounds__(256) raycast_rmp_kernel(DevMap m, EvalConsts k
   const uint32_t total = k.n_rays << lgS;
   const uint32_t stride = gridDim.x * blockDim.x;
   uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-  // the first ray is generated while the radius copy and the state set-up are in flight
+  // the first ray is generated while the radius copy and the state loads are in flight
   uint32_t ray_idx = ray_of_slot(base + lane < total ? (base + lane) >> lgS : 0, k);
   Ray ray = make_ray(ray_idx + k.halton_offset);
+  if (comp >= 0 && comp < 3) {
+    const double o = KIND != RMP_MAP_DENSE_U8 ? 0.0
+                     : (comp == 0 ? m.origin[0] : (comp == 1 ? m.origin[1] : m.origin[2]));
+    const double q = __dmul_rn(__ddiv_rn(__dsub_rn(sv, o), m.vs), 65536.0);
+    // |voxel| < 2^22 keeps block keys and fixed-point products in range; NaN fails too
+    const int bad = !(fabs(q) < 274877906944.0);
+    cs.bad[comp] = bad;
+    cs.P[comp] = bad ? 0 : __double2ll_rn(q);
+  } else if (comp >= 3) {
+    split_velocity(sv, cs, comp - 3);
+  }
   __syncthreads();                                  // state ready, barrier initialised
   if (staged && !bulk_load_wait(&bm_bar)) bm_timeout = 1;
   __syncthreads();
@@ -2336,11 +2346,9 @@ __global__ void __launch_bounds__(256) scan_rmp_kernel(const float* __restrict__
                                                        WsHeader* ws, CtaPartial* parts,
                                                        rmp_result_t* out, float* per_ray) {
   __shared__ CtaState cs;
-  if (threadIdx.x < 3) {
-    cs.xf[threadIdx.x] = __double2float_rn(state_at(state, k, threadIdx.x));
-  } else if (threadIdx.x < 6) {
-    split_velocity(state_at(state, k, threadIdx.x), cs, threadIdx.x - 3);
-  }
+  const int comp = state_component(threadIdx.x);
+  if (comp >= 0 && comp < 3) cs.xf[comp] = __double2float_rn(state_at(state, k, comp));
+  else if (comp >= 3) split_velocity(state_at(state, k, comp), cs, comp - 3);
   __syncthreads();
   typename BlockReduce<RED>::Acc acc;
   BlockReduce<RED>::init(acc);
