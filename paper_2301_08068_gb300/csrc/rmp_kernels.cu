@@ -918,24 +918,64 @@ struct BlockReduce<RMP_REDUCE_FP64> {
 
 // ------------------------------------------------------------------ FP64 resolve (Eq. 1)
 // f = (sum A)^+ (sum A f) with eigenvalues <= 1e-12 lambda_max treated as zero.  FP64
-// division and square root cost hundreds of cycles each on this GPU and FP64 issues at a
-// low rate, so the work is split:
-//   eigenvectors by cyclic Jacobi rotations in FP32 (matrix scaled by a power of two), and,
-//   in another warp (or another lane of the same warp), the FP64 adjugate solve
-//   adj(S) b / det(S);
+// division and square root cost hundreds of cycles each on this GPU and every FP64
+// instruction of a warp occupies the FP64 pipe for tens of cycles whatever the number of
+// active lanes (measured: the resolve's stages take about 64 cycles per FP64 instruction),
+// so the FP64 arithmetic is kept to what the result needs and the work is split:
+//   eigenvectors by cyclic Jacobi rotations in FP32 (the matrix scaled by a power of two
+//   and narrowed to FP32 by integer operations on its bit patterns), and, in another warp
+//   (or another lane of the same warp), the FP64 adjugate solve adj(S) b / det(S);
 //   lanes 0-2: each eigenvalue as the FP64 Rayleigh quotient v^T S v / v^T v of its FP32
 //   eigenvector (second-order accurate, ~1e-14 lambda_max), with 1 / v^T v = 2 - v^T v to
-//   first order (v^T v = 1 + O(1e-7));
-//   lane 0: rank from the eigenvalues; full rank uses the adjugate solution, a deficient
-//   rank projects b on the kept eigenvectors, and writes f, eig, rank into r.
+//   first order (v^T v = 1 + O(1e-7)); the eigenvector components widened to FP64 by bit
+//   packing (exact);
+//   lane 0: the eigenvalues sorted and the rank decided by comparing order-preserving
+//   integer keys of the FP64 values; full rank uses the adjugate solution, a deficient
+//   rank projects b on the kept eigenvectors; writes f, eig, rank into r.
+
+// S / 2^(E - 1023) narrowed to FP32 by truncation, E the largest biased exponent of the six
+// entries (so the largest lies in [1, 2)); entries with a zero or subnormal exponent, or
+// below 2^-126 of the largest, become 0.  Integer operations only.
+__device__ __forceinline__ void narrow_scaled(const double* S, float a[6]) {
+  int hi[6];
+  unsigned lo[6];
+  int emax = 0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    hi[q] = __double2hiint(S[q]);
+    lo[q] = (unsigned)__double2loint(S[q]);
+    emax = max(emax, (hi[q] >> 20) & 0x7FF);
+  }
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const int e = (hi[q] >> 20) & 0x7FF;
+    const int fe = e - emax + 127;
+    const unsigned mant = ((unsigned)(hi[q] & 0xFFFFF) << 3) | (lo[q] >> 29);
+    const unsigned bits = ((unsigned)hi[q] & 0x80000000u) | ((unsigned)fe << 23) | mant;
+    a[q] = (e != 0 && fe > 0) ? __uint_as_float(bits) : 0.0f;
+  }
+}
+
+// An FP32 value widened to FP64 exactly by packing its bits (zero and subnormal inputs give
+// zero; the eigenvector components this serves are normal or zero).
+__device__ __forceinline__ double widen(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  return e == 0 ? 0.0 : __hiloint2double((int)hi, (int)((b & 7u) << 29));
+}
+
+// Integer key with the order of the (non-NaN) double x.
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+}
 
 // Eigenvectors (columns of W) of the symmetric S by FP32 Jacobi sweeps.  One thread.
 __device__ __forceinline__ void jacobi_f32(const double* S, float W[3][3]) {
-  const double smax = fmax(fmax(fabs(S[0]), fabs(S[1])), fmax(fmax(fabs(S[2]), fabs(S[3])),
-                                                           fmax(fabs(S[4]), fabs(S[5]))));
-  const double scale = smax > 1e-300 ? ldexp(1.0, -ilogb(smax)) : 1.0;   // power of two
-  float a00 = (float)(S[0] * scale), a01 = (float)(S[1] * scale), a02 = (float)(S[2] * scale),
-        a11 = (float)(S[3] * scale), a12 = (float)(S[4] * scale), a22 = (float)(S[5] * scale);
+  float sa[6];
+  narrow_scaled(S, sa);
+  float a00 = sa[0], a01 = sa[1], a02 = sa[2], a11 = sa[3], a12 = sa[4], a22 = sa[5];
   for (int sweep = 0; sweep < 6; ++sweep) {
     const float off = fabsf(a01) + fabsf(a02) + fabsf(a12);
     const float dia = fabsf(a00) + fabsf(a11) + fabsf(a22);
@@ -984,11 +1024,18 @@ __device__ __forceinline__ void adjugate_solve(const double* S, const double* b,
   }
 }
 
-// Rayleigh quotients, rank and f from the FP32 eigenvectors W (valid in lane 0) and the
-// adjugate solution (valid in every lane).  Called by all 32 lanes of one warp.
-__device__ __forceinline__ void resolve_finish(const double* S, const double* b,
-                                               const float (&W)[3][3], double fa0, double fa1,
-                                               double fa2, int ok, rmp_result_t& r) {
+// Sorted eigenpairs and rank from the FP32 eigenvectors W (valid in lane 0): lanes 0-2 take
+// the FP64 Rayleigh quotients; lane 0 sorts, decides the rank, writes eig and rank into r and
+// keeps in es what a rank-deficient projection needs.  Called by all 32 lanes of one warp;
+// only lane 0's r and es are set.
+struct EigenSet {
+  float c[3][3];   // eigenvector i (ascending eigenvalues) in c[i]
+  double d[3];     // its v^T v
+  bool keep[3];    // eigenvalue above the rank threshold
+};
+
+__device__ __forceinline__ void resolve_eigen(const double* S, const float (&W)[3][3],
+                                              rmp_result_t& r, EigenSet& es) {
   const int t = threadIdx.x & 31;
   float V[3][3];
 #pragma unroll
@@ -997,9 +1044,9 @@ __device__ __forceinline__ void resolve_finish(const double* S, const double* b,
     for (int j = 0; j < 3; ++j) V[i][j] = __shfl_sync(0xffffffffu, W[i][j], 0);
   double lam_t = 0.0, den_t = 0.0;
   if (t < 3) {
-    const double v0 = t == 0 ? V[0][0] : (t == 1 ? V[0][1] : V[0][2]);
-    const double v1 = t == 0 ? V[1][0] : (t == 1 ? V[1][1] : V[1][2]);
-    const double v2 = t == 0 ? V[2][0] : (t == 1 ? V[2][1] : V[2][2]);
+    const double v0 = widen(t == 0 ? V[0][0] : (t == 1 ? V[0][1] : V[0][2]));
+    const double v1 = widen(t == 0 ? V[1][0] : (t == 1 ? V[1][1] : V[1][2]));
+    const double v2 = widen(t == 0 ? V[2][0] : (t == 1 ? V[2][1] : V[2][2]));
     const double u0 = S[0] * v0 + S[1] * v1 + S[2] * v2;
     const double u1 = S[1] * v0 + S[3] * v1 + S[4] * v2;
     const double u2 = S[2] * v0 + S[4] * v1 + S[5] * v2;
@@ -1013,32 +1060,54 @@ __device__ __forceinline__ void resolve_finish(const double* S, const double* b,
     den[i] = __shfl_sync(0xffffffffu, den_t, i);
   }
   if (t != 0) return;
-  // ascending eigenpairs by a 3-element sorting network on registers (no indexed arrays)
+  // ascending eigenpairs by a 3-element sorting network on the values' integer keys
   double e0 = lam[0], e1 = lam[1], e2 = lam[2];
   double d0 = den[0], d1 = den[1], d2 = den[2];
+  long long q0 = order_key(e0), q1 = order_key(e1), q2 = order_key(e2);
   float c0[3] = {V[0][0], V[1][0], V[2][0]}, c1[3] = {V[0][1], V[1][1], V[2][1]},
         c2[3] = {V[0][2], V[1][2], V[2][2]};
   auto swap01 = [&]() {
     const double te = e0, td = d0;
-    e0 = e1; d0 = d1; e1 = te; d1 = td;
+    const long long tq = q0;
+    e0 = e1; d0 = d1; q0 = q1; e1 = te; d1 = td; q1 = tq;
 #pragma unroll
     for (int i = 0; i < 3; ++i) { const float tc = c0[i]; c0[i] = c1[i]; c1[i] = tc; }
   };
-  if (e1 < e0) swap01();
-  if (e2 < e1) {
+  if (q1 < q0) swap01();
+  if (q2 < q1) {
     const double te = e1, td = d1;
-    e1 = e2; d1 = d2; e2 = te; d2 = td;
+    const long long tq = q1;
+    e1 = e2; d1 = d2; q1 = q2; e2 = te; d2 = td; q2 = tq;
 #pragma unroll
     for (int i = 0; i < 3; ++i) { const float tc = c1[i]; c1[i] = c2[i]; c2[i] = tc; }
   }
-  if (e1 < e0) swap01();
-  const double lmax = e2;
-  const bool k0 = lmax > 1e-300 && e0 > 1e-12 * lmax, k1 = lmax > 1e-300 && e1 > 1e-12 * lmax,
-             k2 = lmax > 1e-300 && e2 > 1e-12 * lmax;
+  if (q1 < q0) swap01();
+  // kept: lambda_max > 1e-300 and lambda > 1e-12 lambda_max
+  const long long thr = order_key(1e-12 * e2);
+  const bool live = q2 > order_key(1e-300);
+  es.keep[0] = live && q0 > thr;
+  es.keep[1] = live && q1 > thr;
+  es.keep[2] = live && q2 > thr;
   r.eig[0] = e0;
   r.eig[1] = e1;
   r.eig[2] = e2;
-  r.rank = (k0 ? 1u : 0u) + (k1 ? 1u : 0u) + (k2 ? 1u : 0u);
+  r.rank = (es.keep[0] ? 1u : 0u) + (es.keep[1] ? 1u : 0u) + (es.keep[2] ? 1u : 0u);
+  es.d[0] = d0;
+  es.d[1] = d1;
+  es.d[2] = d2;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    es.c[0][i] = c0[i];
+    es.c[1][i] = c1[i];
+    es.c[2][i] = c2[i];
+  }
+}
+
+// f into r from the rank (resolve_eigen) and the adjugate solution: full rank takes the
+// adjugate, a deficient rank projects b on the kept eigenvectors.  Lane 0 of the warp that
+// ran resolve_eigen.
+__device__ __forceinline__ void resolve_f(const double* b, const EigenSet& es, double fa0,
+                                          double fa1, double fa2, int ok, rmp_result_t& r) {
   r.f[0] = r.f[1] = r.f[2] = 0.0;
   if (r.rank == 3 && ok) {
     r.f[0] = fa0;
@@ -1046,21 +1115,16 @@ __device__ __forceinline__ void resolve_finish(const double* S, const double* b,
     r.f[2] = fa2;
     return;
   }
-  // a deficient rank projects b on the kept eigenvectors
-  if (k0) {
-    const double proj = (c0[0] * b[0] + c0[1] * b[1] + c0[2] * b[2]) / (e0 * d0);
-    r.f[0] += proj * c0[0]; r.f[1] += proj * c0[1]; r.f[2] += proj * c0[2];
-  }
-  if (k1) {
-    const double proj = (c1[0] * b[0] + c1[1] * b[1] + c1[2] * b[2]) / (e1 * d1);
-    r.f[0] += proj * c1[0]; r.f[1] += proj * c1[1]; r.f[2] += proj * c1[2];
-  }
-  if (k2) {
-    const double proj = (c2[0] * b[0] + c2[1] * b[1] + c2[2] * b[2]) / (e2 * d2);
-    r.f[0] += proj * c2[0]; r.f[1] += proj * c2[1]; r.f[2] += proj * c2[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (!es.keep[i]) continue;
+    const float* c = es.c[i];
+    const double proj = (c[0] * b[0] + c[1] * b[1] + c[2] * b[2]) / (r.eig[i] * es.d[i]);
+    r.f[0] += proj * c[0];
+    r.f[1] += proj * c[1];
+    r.f[2] += proj * c[2];
   }
 }
-
 
 // One warp: lane 0 runs the Jacobi sweeps, lane 1 the adjugate solve (the two branches
 // of one warp run one after the other).  Called by all 32 lanes of one warp.
@@ -1075,32 +1139,40 @@ __device__ void resolve_pinv(const double* S, const double* b, rmp_result_t& r) 
   fa1 = __shfl_sync(0xffffffffu, fa1, 1);
   fa2 = __shfl_sync(0xffffffffu, fa2, 1);
   ok = __shfl_sync(0xffffffffu, ok, 1);
-  resolve_finish(S, b, W, fa0, fa1, fa2, ok, r);
+  EigenSet es;
+  resolve_eigen(S, W, r, es);
+  if (t == 0) resolve_f(b, es, fa0, fa1, fa2, ok, r);
 }
 
-// Two warps of a CTA (threads 0-63): warp 0 runs the Jacobi sweeps while warp 1 runs the
-// adjugate solve, so the two overlap; they meet at named barrier 1.  Called by threads
-// 0-63 of a CTA of at least 64 threads; S, b and r in shared memory.
+// Two warps of a CTA (threads 0-63): warp 0 runs the Jacobi sweeps and the Rayleigh
+// quotients while warp 1 runs the adjugate solve; they meet at named barrier 1 only for
+// the choice of f.  Called by threads 0-63 of a CTA of at least 64 threads; S, b and r in
+// shared memory.
 __device__ void resolve_pinv_cta(const double* S, const double* b, rmp_result_t& r) {
   __shared__ double fa_sh[3];
   __shared__ int ok_sh;
   const int t = threadIdx.x;
-  float W[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
-  if (t == 0) {
-    jacobi_f32(S, W);
-  } else if (t == 32) {
-    double fa0 = 0.0, fa1 = 0.0, fa2 = 0.0;
-    int ok = 0;
-    adjugate_solve(S, b, fa0, fa1, fa2, ok);
-    fa_sh[0] = fa0;
-    fa_sh[1] = fa1;
-    fa_sh[2] = fa2;
-    ok_sh = ok;
+  if (t >= 32) {
+    if (t == 32) {
+      double fa0 = 0.0, fa1 = 0.0, fa2 = 0.0;
+      int ok = 0;
+      adjugate_solve(S, b, fa0, fa1, fa2, ok);
+      fa_sh[0] = fa0;
+      fa_sh[1] = fa1;
+      fa_sh[2] = fa2;
+      ok_sh = ok;
+    }
+    __syncwarp();
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    return;
   }
+  float W[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+  if (t == 0) jacobi_f32(S, W);
+  EigenSet es;
+  resolve_eigen(S, W, r, es);
   __syncwarp();
   asm volatile("bar.sync 1, 64;" ::: "memory");
-  if (t >= 32) return;
-  resolve_finish(S, b, W, fa_sh[0], fa_sh[1], fa_sh[2], ok_sh, r);
+  if (t == 0) resolve_f(b, es, fa_sh[0], fa_sh[1], fa_sh[2], ok_sh, r);
 }
 
 // A partial in the workspace (80 bytes, one per CTA): the compensated reduction stores each
