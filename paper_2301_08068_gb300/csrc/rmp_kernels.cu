@@ -1030,9 +1030,21 @@ __device__ __forceinline__ void adjugate_solve(const double* S, const double* b,
 // only lane 0's r and es are set.
 struct EigenSet {
   float c[3][3];   // eigenvector i (ascending eigenvalues) in c[i]
-  double d[3];     // its v^T v
+  float dv[3];     // its v^T v - 1
   bool keep[3];    // eigenvalue above the rank threshold
 };
+
+// v^T v - 1 for an FP32 vector with v^T v = 1 + O(1e-7), in FP32 error-free arithmetic:
+// the squares split exactly into product and FMA error, the three products summed by TwoSum,
+// the sum minus 1 exact (Sterbenz), the small terms added last (error ~1e-15).
+__device__ __forceinline__ float norm2_minus_one(float v0, float v1, float v2) {
+  const float p0 = __fmul_rn(v0, v0), p1 = __fmul_rn(v1, v1), p2 = __fmul_rn(v2, v2);
+  const float e0 = __fmaf_rn(v0, v0, -p0), e1 = __fmaf_rn(v1, v1, -p1), e2 = __fmaf_rn(v2, v2, -p2);
+  float s1, r1, s2, r2;
+  two_sum(p0, p1, s1, r1);
+  two_sum(s1, p2, s2, r2);
+  return __fadd_rn(__fsub_rn(s2, 1.0f), __fadd_rn(__fadd_rn(r1, r2), __fadd_rn(__fadd_rn(e0, e1), e2)));
+}
 
 __device__ __forceinline__ void resolve_eigen(const double* S, const float (&W)[3][3],
                                               rmp_result_t& r, EigenSet& es) {
@@ -1042,32 +1054,44 @@ __device__ __forceinline__ void resolve_eigen(const double* S, const float (&W)[
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) V[i][j] = __shfl_sync(0xffffffffu, W[i][j], 0);
-  double lam_t = 0.0, den_t = 0.0;
-  if (t < 3) {
-    const double v0 = widen(t == 0 ? V[0][0] : (t == 1 ? V[0][1] : V[0][2]));
-    const double v1 = widen(t == 0 ? V[1][0] : (t == 1 ? V[1][1] : V[1][2]));
-    const double v2 = widen(t == 0 ? V[2][0] : (t == 1 ? V[2][1] : V[2][2]));
-    const double u0 = S[0] * v0 + S[1] * v1 + S[2] * v2;
-    const double u1 = S[1] * v0 + S[3] * v1 + S[4] * v2;
-    const double u2 = S[2] * v0 + S[4] * v1 + S[5] * v2;
-    den_t = v0 * v0 + v1 * v1 + v2 * v2;
-    lam_t = (v0 * u0 + v1 * u1 + v2 * u2) * (2.0 - den_t);
+  // lanes 0-8: lane 3 i + c takes component c of eigenvector i (column i of V): its term
+  // v_c (S v)_c in FP64; lane 3 i adds the three terms and applies 1 / v^T v = 1 - (v^T v - 1)
+  // to first order.  Seven FP64 instructions per warp (every FP64 instruction holds the
+  // pipe about 64 cycles whatever the active lanes).
+  const int iv = t < 9 ? t / 3 : 0, c = t < 9 ? t - 3 * iv : 0;
+  const float w0 = iv == 0 ? V[0][0] : (iv == 1 ? V[0][1] : V[0][2]);
+  const float w1 = iv == 0 ? V[1][0] : (iv == 1 ? V[1][1] : V[1][2]);
+  const float w2 = iv == 0 ? V[2][0] : (iv == 1 ? V[2][1] : V[2][2]);
+  double term = 0.0;
+  if (t < 9) {
+    const double sc0 = c == 0 ? S[0] : (c == 1 ? S[1] : S[2]);
+    const double sc1 = c == 0 ? S[1] : (c == 1 ? S[3] : S[4]);
+    const double sc2 = c == 0 ? S[2] : (c == 1 ? S[4] : S[5]);
+    const double u = sc0 * widen(w0) + sc1 * widen(w1) + sc2 * widen(w2);
+    term = widen(c == 0 ? w0 : (c == 1 ? w1 : w2)) * u;
   }
-  double lam[3], den[3];
+  const double t1 = __shfl_down_sync(0xffffffffu, term, 1);
+  const double t2 = __shfl_down_sync(0xffffffffu, term, 2);
+  const float dv_t = norm2_minus_one(w0, w1, w2);
+  double lam_t = (term + t1) + t2;
+  lam_t = fma(-lam_t, widen(dv_t), lam_t);
+  double lam[3];
+  float dv[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    lam[i] = __shfl_sync(0xffffffffu, lam_t, i);
-    den[i] = __shfl_sync(0xffffffffu, den_t, i);
+    lam[i] = __shfl_sync(0xffffffffu, lam_t, 3 * i);
+    dv[i] = __shfl_sync(0xffffffffu, dv_t, 3 * i);
   }
   if (t != 0) return;
   // ascending eigenpairs by a 3-element sorting network on the values' integer keys
   double e0 = lam[0], e1 = lam[1], e2 = lam[2];
-  double d0 = den[0], d1 = den[1], d2 = den[2];
+  float d0 = dv[0], d1 = dv[1], d2 = dv[2];
   long long q0 = order_key(e0), q1 = order_key(e1), q2 = order_key(e2);
   float c0[3] = {V[0][0], V[1][0], V[2][0]}, c1[3] = {V[0][1], V[1][1], V[2][1]},
         c2[3] = {V[0][2], V[1][2], V[2][2]};
   auto swap01 = [&]() {
-    const double te = e0, td = d0;
+    const double te = e0;
+    const float td = d0;
     const long long tq = q0;
     e0 = e1; d0 = d1; q0 = q1; e1 = te; d1 = td; q1 = tq;
 #pragma unroll
@@ -1075,7 +1099,8 @@ __device__ __forceinline__ void resolve_eigen(const double* S, const float (&W)[
   };
   if (q1 < q0) swap01();
   if (q2 < q1) {
-    const double te = e1, td = d1;
+    const double te = e1;
+    const float td = d1;
     const long long tq = q1;
     e1 = e2; d1 = d2; q1 = q2; e2 = te; d2 = td; q2 = tq;
 #pragma unroll
@@ -1092,9 +1117,9 @@ __device__ __forceinline__ void resolve_eigen(const double* S, const float (&W)[
   r.eig[1] = e1;
   r.eig[2] = e2;
   r.rank = (es.keep[0] ? 1u : 0u) + (es.keep[1] ? 1u : 0u) + (es.keep[2] ? 1u : 0u);
-  es.d[0] = d0;
-  es.d[1] = d1;
-  es.d[2] = d2;
+  es.dv[0] = d0;
+  es.dv[1] = d1;
+  es.dv[2] = d2;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     es.c[0][i] = c0[i];
@@ -1119,7 +1144,7 @@ __device__ __forceinline__ void resolve_f(const double* b, const EigenSet& es, d
   for (int i = 0; i < 3; ++i) {
     if (!es.keep[i]) continue;
     const float* c = es.c[i];
-    const double proj = (c[0] * b[0] + c[1] * b[1] + c[2] * b[2]) / (r.eig[i] * es.d[i]);
+    const double proj = (c[0] * b[0] + c[1] * b[1] + c[2] * b[2]) / (r.eig[i] * (1.0 + widen(es.dv[i])));
     r.f[0] += proj * c[0];
     r.f[1] += proj * c[1];
     r.f[2] += proj * c[2];
