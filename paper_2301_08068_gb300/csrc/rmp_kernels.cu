@@ -1008,6 +1008,28 @@ __device__ __forceinline__ void jacobi_f32(const double* S, float W[3][3]) {
   }
 }
 
+// 1 / x in FP64 for a positive x, by Newton's iteration for the reciprocal, r <- r + r (1 - m r),
+// on the mantissa m in [1, 2): two steps from the FP32 reciprocal of m truncated to FP32
+// (relative error 2^-22.4 -> 2^-44.8 -> below the FP64 rounding of the steps, about one ulp),
+// the exponent applied by integer operations.  Four FP64 instructions instead of a division's
+// sequence; subnormal, infinite or NaN x, and results outside the normal range, take the
+// division.
+__device__ __forceinline__ double recip_pos(double x) {
+  const long long bx = __double_as_longlong(x);
+  const int ex = (int)((bx >> 52) & 0x7FF);
+  const double m = __longlong_as_double((bx & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+  const float mf = __uint_as_float(0x3F800000u | (unsigned)((bx >> 29) & 0x7FFFFF));
+  double r = widen(__frcp_rn(mf));                        // in [0.5, 1]
+  double e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  const long long br = __double_as_longlong(r);
+  const int er = (int)((br >> 52) & 0x7FF) - (ex - 1023);
+  if (ex == 0 || ex == 2047 || er <= 0 || er >= 2047) return 1.0 / x;
+  return __longlong_as_double((br & 0x000FFFFFFFFFFFFFll) | ((long long)er << 52));
+}
+
 // FP64 solve adj(S) b / det(S); ok = det > 0.  One thread.
 __device__ __forceinline__ void adjugate_solve(const double* S, const double* b, double& fa0,
                                                double& fa1, double& fa2, int& ok) {
@@ -1017,7 +1039,7 @@ __device__ __forceinline__ void adjugate_solve(const double* S, const double* b,
   const double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
   ok = det > 0.0;
   if (det > 0.0) {
-    const double inv = 1.0 / det;
+    const double inv = recip_pos(det);
     fa0 = (c00 * b[0] + c01 * b[1] + c02 * b[2]) * inv;
     fa1 = (c01 * b[0] + c11 * b[1] + c12 * b[2]) * inv;
     fa2 = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * inv;
