@@ -447,7 +447,8 @@ __device__ __forceinline__ uint32_t crossings_within(const uint32_t N[3], const 
 // the step count and the entry crossing of the current voxel are brought up to date when
 // the walk leaves the block.  WALK_UNROLL: unroll factor of the voxel walk (its 24
 // iterations fully unrolled measured 57.4 -> 55.1 us for 65536 rays on the hashed map;
-// the batch kernel, held to 64 registers, spills then and keeps a factor of 4).
+// the batch kernel, held to 64 registers, spills then and uses a factor of 2: 1.297 ->
+// 1.290 ms against the compiler's 4, 1.43 ms with 6).
 template <int KIND, int LAYOUT, bool CELLS, int WALK_UNROLL>
 __device__ __forceinline__ int march_run(const DevMap& m, const uint32_t* bm, MarchState& st,
                                          const RayFx& r, const uint32_t L[3], int at_limit,
@@ -2200,7 +2201,7 @@ __global__ void __launch_bounds__(256, 4) raycast_batch_kernel(
     const uint32_t ray_idx = ray_of_slot_p(active ? slot : 0, pM, pQ, n_b - pQ * pM);
     const Ray ray = make_ray(ray_idx + k.halton_offset);
     MarchState mo;
-    const int mstat = march_ray<KIND, LAYOUT, true, true, 4>(m, bm, k, P, ray, seg, lgS, active, mo,
+    const int mstat = march_ray<KIND, LAYOUT, true, true, 2>(m, bm, k, P, ray, seg, lgS, active, mo,
                                                           sbr);
     // read after the march, so that they are not held in registers across it
     const float v[3] = {__ldg(&sp->v[0]), __ldg(&sp->v[1]), __ldg(&sp->v[2])};
