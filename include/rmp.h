@@ -515,9 +515,10 @@ int rmp_probe_l2_read(rmp_ctx* ctx, const void* buf_dev, size_t bytes, uint32_t 
  *                        one state, 256 when the launch fits in one wave of 256-thread CTAs,
  *                        else 128; scans 256; batches 128
  *  RMP_TUNE_LG_SEGMENTS  log2 of the segments each ray is split into and marched by that
- *                        many threads (0..2), or -1 (default) to choose: one state, the
- *                        most (up to 4) that keep the launch within one wave of 256-thread
- *                        CTAs; batches, per state the most (up to 4) whose threads the
+ *                        many threads (0..4; batches use at most 2, a larger value counts
+ *                        as 2 there), or -1 (default) to choose: one state, the most (up
+ *                        to 16) that keep the launch within one wave of 256-thread CTAs;
+ *                        batches, per state the most (up to 4) whose threads the
  *                        persistent launch holds at once
  *  RMP_TUNE_RAY_ORDER    0 (default): rays of one direction cell share warps (coherent
  *                        march); 1: Halton index order
@@ -527,8 +528,8 @@ int rmp_probe_l2_read(rmp_ctx* ctx, const void* buf_dev, size_t bytes, uint32_t 
  *                        choice (currently never); batches never split
  *  RMP_TUNE_CELL_SKIP    free boxes of voxels inside occupied blocks crossed in one step
  *                        (grid layout maps): 1 always, 0 never, -1 (default) in batched
- *                        evaluations and in single-state ones marched as 4 segments per
- *                        ray (measured faster there, slower for one segment per ray) */
+ *                        evaluations and in single-state ones marched as 4 or more segments
+ *                        per ray (measured faster there, slower for one segment per ray) */
 #define RMP_TUNE_BLOCK 1
 #define RMP_TUNE_LG_SEGMENTS 2
 #define RMP_TUNE_RAY_ORDER 3

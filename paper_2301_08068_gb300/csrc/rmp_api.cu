@@ -538,7 +538,7 @@ int rmp_tune_set(rmp_ctx* c, int knob, int value) {
     if (value != 0 && value != 64 && value != 128 && value != 256) return RMP_ERR_INVALID_ARG;
     c->tune_block = value;
   } else if (knob == RMP_TUNE_LG_SEGMENTS) {
-    if (value < -1 || value > 2) return RMP_ERR_INVALID_ARG;
+    if (value < -1 || value > (int)kMaxSingleLgSegs) return RMP_ERR_INVALID_ARG;
     c->tune_lg_segs = value;
   } else if (knob == RMP_TUNE_RAY_ORDER) {
     if (value < 0 || value > 1) return RMP_ERR_INVALID_ARG;
@@ -729,9 +729,11 @@ int batch_setup(rmp_ctx* c, uint32_t map_id, uint32_t n_states, uint32_t max_ray
   }
   int st = make_consts(params, dm->vs, max_rays, false, k, t);
   if (st != RMP_OK) return st;
-  // segments per ray: a fixed tuned value for every state, or (default) the single-state
-  // rule applied per state by the prep kernel
+  // segments per ray: a fixed tuned value for every state (at most kMaxBatchSegs, which the
+  // batch workspace is sized for), or (default) the batch rule applied per state by the
+  // prep kernel
   if (t.lg_segs < 0) k->lg_segs = 0xffffffffu;
+  else if ((1u << k->lg_segs) > kMaxBatchSegs) k->lg_segs = 2;
   const int occ = batch_occupancy(*dm, k->reduce_mode, *block);
   if (occ <= 0) return RMP_ERR_CUDA;
   *grid = c->sm_count * occ;

@@ -93,8 +93,12 @@ def test_batch_log_uniform_counts_fp64(ctx, hashed):
     check_batch(ctx, mid, om, wu.states, wu.n_rays, p, wl.max_range)
 
 
-@pytest.mark.parametrize("lgs,split,cells", [(2, 0, -1), (1, 3, 0), (0, 1, -1), (0, 0, 0)])
+@pytest.mark.parametrize("lgs,split,cells", [(2, 0, -1), (1, 3, 0), (0, 1, -1), (0, 0, 0),
+                                             (4, 0, -1)])
 def test_batch_segments_and_split_dense(ctx, dense, lgs, split, cells):
+    """Batches under fixed segment counts, split budgets and voxel-box settings (a segment
+    setting above 4 segments per ray counts as 4 for batches, whose workspace is sized for
+    4) keep hit records and results."""
     wl, mid, om = dense
     R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, lgs)
     R.rmp_tune_set(ctx.handle, R.RMP_TUNE_SPLIT_BUDGET, split)
