@@ -515,9 +515,9 @@ int rmp_probe_l2_read(rmp_ctx* ctx, const void* buf_dev, size_t bytes, uint32_t 
  *                        one state, 256 when the launch fits in one wave of 256-thread CTAs,
  *                        else 128; scans 256; batches 128
  *  RMP_TUNE_LG_SEGMENTS  log2 of the segments each ray is split into and marched by that
- *                        many threads (0..4; batches use at most 2, a larger value counts
+ *                        many threads (0..5; batches use at most 2, a larger value counts
  *                        as 2 there), or -1 (default) to choose: one state, the most (up
- *                        to 16) that keep the launch within one wave of 256-thread CTAs;
+ *                        to 32) that keep the launch within one wave of 256-thread CTAs;
  *                        batches, per state the most (up to 4) whose threads the
  *                        persistent launch holds at once
  *  RMP_TUNE_RAY_ORDER    0 (default): rays of one direction cell share warps (coherent

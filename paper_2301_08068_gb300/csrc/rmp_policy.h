@@ -43,15 +43,15 @@ inline void pick_ray_cells(uint32_t n, EvalConsts* k) {
   k->perm_R = n % k->perm_M;
 }
 
-// Segments per ray of a single-state evaluation left to the library: as many (up to 16,
+// Segments per ray of a single-state evaluation left to the library: as many (up to 32,
 // kMaxSingleLgSegs) as keep the launch within one wave of 256-thread CTAs (`wave256`
 // threads), since the evaluation lasts as long as its longest ray's serial march and
 // segments shorten it while the extra threads still find free SMs (measured, L2 flushed:
-// hashed map 1024 rays 33.0 / 26.6 / 22.0 us with 4 / 8 / 16 segments, 4096 rays 33.5 /
-// 26.7 / 23.7; dense 1024 rays 26.4 / 21.8 / 19.3; 16384 rays 54.3 us with 2 segments,
+// hashed map 1024 rays 33.0 / 26.6 / 22.0 / 19.9 us with 4 / 8 / 16 / 32 segments, 4096
+// rays 33.5 / 26.7 / 23.7; dense 1024 rays 26.4 / 21.8 / 19.3 / 18.3; 16384 rays 54.3 us with 2 segments,
 // 47.1 with 4; 32768 rays 65.5 with 1, 57.2 with 2; 65536 rays best with 1).  Without a
 // wave size (0) the ray-count rule of make_consts stays.
-constexpr uint32_t kMaxSingleLgSegs = 4;
+constexpr uint32_t kMaxSingleLgSegs = 5;
 inline void auto_segments(const Tuning& t, uint32_t n, uint64_t wave256, EvalConsts* k) {
   if (t.lg_segs >= 0 || wave256 == 0) return;
   uint32_t lg = kMaxSingleLgSegs;

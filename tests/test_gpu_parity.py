@@ -372,7 +372,7 @@ def test_layouts_grid_and_hash_fallback(ctx, hashed):
     assert a[1].tobytes() == b[1].tobytes()
 
 
-@pytest.mark.parametrize("cells,lgs", [(1, 0), (1, 2), (0, 0), (1, 4), (0, 3)])
+@pytest.mark.parametrize("cells,lgs", [(1, 0), (1, 2), (0, 0), (1, 4), (0, 3), (1, 5), (0, 5)])
 def test_cell_skip_keeps_results(ctx, hashed, dense, cells, lgs):
     """Voxel-box skipping inside occupied blocks on or off changes nothing: hit records
     bit-identical to the oracle's, values within tolerance (single-state kernel)."""
@@ -423,7 +423,7 @@ def test_split_and_ray_order_keep_results(ctx, hashed, dense, order, budget, lgs
 
 
 @pytest.mark.parametrize("block,lgs", [(64, 0), (128, 1), (256, 2), (128, -1), (0, -1),
-                                       (256, 3), (128, 4), (64, 4)])
+                                       (256, 3), (128, 4), (64, 4), (256, 5), (64, 5)])
 def test_tuning_knobs_keep_results(ctx, hashed, block, lgs):
     """Block size and ray segmentation change the launch shape only: hit records stay
     bit-identical to the oracle's, values within tolerance."""
@@ -440,11 +440,11 @@ def test_tuning_knobs_keep_results(ctx, hashed, block, lgs):
     with pytest.raises(R.RmpError):
         R.rmp_tune_set(ctx.handle, R.RMP_TUNE_BLOCK, 100)
     with pytest.raises(R.RmpError):
-        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, 5)
+        R.rmp_tune_set(ctx.handle, R.RMP_TUNE_LG_SEGMENTS, 6)
 
 
 def test_automatic_block_size(ctx, hashed):
-    """Launch shape by default: as many segments per ray (up to 16) as keep the launch within
+    """Launch shape by default: as many segments per ray (up to 32) as keep the launch within
     one wave of 256-thread CTAs (occupancy x SMs), 256 threads per CTA while it fits, 128
     beyond it; an explicit setting wins."""
     wl, mid, om = hashed
@@ -457,8 +457,8 @@ def test_automatic_block_size(ctx, hashed):
     assert wave >= 65536                       # the headline evaluation fits in one wave
     for n in (1, 1024, 4096, 16384, 19456, 19457, 32768, 38912, 38913, 65536, 262144, 1 << 20):
         li = R.rmp_eval_launch_info(ctx.handle, mid, n, p)
-        # segments per ray: the most (up to 16) that keep the launch within one wave
-        lg = 4
+        # segments per ray: the most (up to 32) that keep the launch within one wave
+        lg = 5
         while lg > 0 and (n << lg) > wave:
             lg -= 1
         assert li["lg_segments"] == lg, (n, li)

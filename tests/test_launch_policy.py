@@ -64,7 +64,8 @@ def test_direction_cells(policy):
 
 def test_segments_per_ray(policy):
     cases = []
-    for n in (1, 4096, 19456, 19457, 38912, 38913, 65536, 1 << 20, 4864, 4865, 9728, 9729):
+    for n in (1, 4096, 19456, 19457, 38912, 38913, 65536, 1 << 20, 4864, 4865, 9728, 9729,
+              2432, 2433):
         cases.append((-1, n, WAVE))
     cases += [(-1, 4096, 0), (0, 4096, WAVE), (1, 65536, WAVE), (2, 65536, WAVE)]
     got = policy(["segs %d %d %d" % c for c in cases])
@@ -72,13 +73,13 @@ def test_segments_per_ray(policy):
         if tune >= 0 or wave == 0:
             assert lg == 7                            # left to the tuned value / count rule
             continue
-        expect = 4
+        expect = 5
         while expect > 0 and (n << expect) > wave:
             expect -= 1
         assert lg == expect, (n, lg)
-    # the thresholds on this part: 16 segments up to 4864 rays, 8 up to 9728, 4 up to 19456,
-    # 2 up to 38912, else 1
-    assert [g[0] for g in got[:12]] == [4, 4, 2, 1, 1, 0, 0, 0, 4, 3, 3, 2]
+    # the thresholds on this part: 32 segments up to 2432 rays, 16 up to 4864, 8 up to 9728,
+    # 4 up to 19456, 2 up to 38912, else 1
+    assert [g[0] for g in got[:14]] == [5, 4, 2, 1, 1, 0, 0, 0, 4, 3, 3, 2, 5, 4]
 
 
 def test_single_state_shape(policy):
